@@ -1,0 +1,42 @@
+/* Plain FP64 CPU oracle of the cut-cell step (test infrastructure only).
+ * Used by tests/, the smoke check and the benchmark's CPU-baseline leg. */
+#ifndef CUTCELL_ORACLE_H
+#define CUTCELL_ORACLE_H
+#include <stdint.h>
+
+enum { OC_OK = 0, OC_EINVAL = 1, OC_EGEOM = 3 };
+enum { OC_F_RHOP = 0, OC_F_PP = 1, OC_F_MX = 2, OC_F_MY = 3, OC_F_MZ = 4, OC_F_UB = 5 };
+
+typedef struct {
+  int nx, ny, nz;
+  double dx, dy, dz;
+  double dt;
+  double U, N, theta0, p_surf, p0, g, R, cp;
+  double ra_nu, c4, sponge_frac, tau_max;
+  int bc_slip;
+} oc_params;
+
+typedef struct oc_model oc_model;
+
+oc_model *oc_create(const oc_params *P, const double *h, int *status);
+void oc_destroy(oc_model *m);
+void oc_init_state(oc_model *m);
+void oc_step(oc_model *m, int nsteps);
+int oc_dims(const oc_model *m, long *ncell, long *ncorner, long *ncol, int *gz);
+int oc_get_state(oc_model *m, int field, int level, double *out);
+int oc_set_state(oc_model *m, int field, int level, const double *in);
+int oc_get_geometry(const oc_model *m, double *vf, double *ax, double *ay, double *az, int8_t *cls,
+                    int32_t *root, double *vg, double *hc, double *gx, double *gy);
+int oc_get_points(const oc_model *m, int8_t *vcls, int32_t *bK, int32_t *bI, int32_t *bJ, double *ba,
+                  double *bb, double *bn, int32_t *mK, double *mg);
+int oc_get_base(const oc_model *m, double *rhob, double *pb, int *koff, int *nb);
+double oc_mass(const oc_model *m, int level);
+int oc_nsteps(const oc_model *m);
+
+double oc_line_int(double z, double ha, double hb, double len);
+double oc_line_frac(double z, double ha, double hb);
+double oc_col_int(double z, double h00, double h10, double h01, double h11, double dx, double dy,
+                  int kind);
+double oc_gauss_legendre8(double (*f)(double, void *), void *ctx, double a, double b);
+
+#endif
