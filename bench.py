@@ -1,0 +1,356 @@
+"""Benchmark of the cut-cell step on GB300 (one JSON line on rank 0).
+
+Workloads (synthetic, seeded; the paper's hills sampled at grid corners):
+  ensemble   64 independent single-level domains of uneven sizes (64^3 ..
+             192x192x96), seed 1509, bell or half-ellipsoid hills; all
+             instances advance together in one launch per stage in the FP32
+             perturbation form; the plain FP64 form loops over the instances.
+  hemisphere the 128x128x64 grid of 50 m cells over the 1 km hemisphere.
+
+A step is one leapfrog step of every domain of the workload (all stages:
+full-cell stencil, cut-cell groups, velocity diagnosis, ghost fill).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1509_02572_gb300 import workloads as W  # noqa: E402
+
+METRIC = "cell-updates/s"
+BYTES_PER_CELL = {"f32": 80, "f64": 160}  # 5 fields x (read n-1, read n, write n+1, write filtered n)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "hemisphere"])
+    ap.add_argument("--instances", type=int, default=64)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    return ap.parse_args()
+
+
+def workload_configs(args):
+    if args.workload == "ensemble":
+        cfgs = W.ensemble_configs(args.instances, 1509)
+        name = f"ensemble-{len(cfgs)}x(64^3..192x192x96)-seed1509"
+    else:
+        cfgs = [W.C2_HEMI]
+        name = W.C2_HEMI.name
+    return name, cfgs
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.dev = dev
+        self.p = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.NamedTemporaryFile("w+", delete=False, suffix=".csv")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        with open(self.f.name) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for n, v in zip(names, r[5:9]):
+                if "Active" in v and "Not" not in v:
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def fluid_cells(model, cfgs):
+    n = 0
+    for d in range(len(cfgs)):
+        g = model.geometry(d)
+        n += int((g["cls"] != 0).sum())
+    return n
+
+
+def make_model(cc, cfgs, prec):
+    m = cc.Model(cfgs, prec)
+    for d, c in enumerate(cfgs):
+        m.set_terrain(d, c.heights())
+    m.build_geometry()
+    m.init_state()
+    return m
+
+
+def time_steps(torch, model, steps, warmup):
+    """W untimed steps, then K steps between events on the model's stream."""
+    for _ in range(warmup):
+        model.step(1)
+    model.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches = 0
+    e0.record(st)
+    for _ in range(steps):
+        model.step(1)
+        launches += model.last_launch_count
+    e1.record(st)
+    e1.synchronize()
+    return e0.elapsed_time(e1), launches
+
+
+def cpu_baseline(cfgs, seconds):
+    """The FP64 oracle as it stands on the host cores, on a bounded sample of
+    the workload: whole instances, stepped until about `seconds` of CPU work."""
+    import oracle
+    t_used, cells_done, steps_done, inst = 0.0, 0, 0, []
+    for c in cfgs:
+        m = oracle.Model(c)
+        nf = int((m.geometry()["cls"] != 0).sum())
+        m.init_state()
+        m.step(1)  # forward-Euler start, not timed
+        s = 0
+        t0 = time.perf_counter()
+        while True:
+            m.step(1)
+            s += 1
+            if time.perf_counter() - t0 >= seconds / 2 or s >= 50:
+                break
+        dt = time.perf_counter() - t0
+        t_used += dt
+        cells_done += nf * s
+        steps_done += s
+        inst.append(f"{c.name} x {s} steps")
+        del m
+        if t_used >= seconds:
+            break
+    return {"value": cells_done / t_used, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": "; ".join(inst) + f" ({t_used:.1f} s, single-threaded FP64 oracle)"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    name, cfgs = workload_configs(args)
+    import oracle
+    oracle.build()
+    # each step: a bounded sample of the workload on the oracle
+    per = max(2.0, 60.0 / max(1, args.steps + args.warmup))
+    vals = []
+    for s in range(args.warmup + args.steps):
+        r = cpu_baseline(cfgs[s % len(cfgs):] + cfgs[:s % len(cfgs)], per)
+        if s >= args.warmup:
+            vals.append(r)
+    v = statistics.median(x["value"] for x in vals)
+    line = {"metric": METRIC, "value": v, "unit": METRIC, "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": name, "instances": len(cfgs)},
+            "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
+                             "sample": vals[-1]["sample"]},
+            "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_1509_02572_gb300 import build as B
+    B.build()
+    from paper_1509_02572_gb300 import cutcell as cc
+
+    name, cfgs = workload_configs(args)
+    prec_main = cc.CC_FP32 if args.workload == "ensemble" else cc.CC_FP64
+    dtype = "f32" if prec_main == cc.CC_FP32 else "f64"
+    model = make_model(cc, cfgs, prec_main)
+    nfluid = fluid_cells(model, cfgs)
+    ninterior = sum(c.cells for c in cfgs)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region (device time, CUDA events on the model's stream)
+    clocks = Clocks(local)
+    barrier()
+    model.profile(True)
+    model.profile_reset()
+    clocks.start()
+    ms, launches = time_steps(torch, model, args.steps, args.warmup)
+    clk = clocks.stop()
+    barrier()
+    kfull_ms, kfull_n = model.profile_read(cc.CC_K_FULL)
+    stage = {cc.KERNEL_NAMES[k]: model.profile_read(k) for k in range(4)}
+    model.profile(False)
+    t = torch.tensor([ms], device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms = float(t.item())
+    value = nfluid * args.steps * world / (ms / 1e3)
+
+    hbm, peak_kind = peaks()
+    kavg = kfull_ms / max(1, kfull_n)
+    achieved = BYTES_PER_CELL[dtype] * ninterior / (kavg / 1e3) / 1e9
+    roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+            "traffic": None, "kernel": "k_full", "kernel_ms": kavg, "peak_kind": f"{peak_kind} hbm_gbs",
+            "bytes_per_cell": BYTES_PER_CELL[dtype], "cells_per_launch": ninterior}
+    stages = {k: {"ms_total": v[0], "launches": v[1]} for k, v in stage.items()}
+    line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
+            "config": {"workload": name, "instances": len(cfgs), "interior_cells": ninterior,
+                       "fluid_cells": nfluid, "precision": ("fp32 perturbations, fp64 geometry and base state"
+                                                            if dtype == "f32" else "fp64"),
+                       "l2": "inputs larger than L2 (state of all domains)" if ninterior * 80 > 129e6 else
+                       "working set may fit in L2"},
+            "gpu_launches": launches, "roofline": roof, "stages": stages, "clocks": clk}
+
+    # ---- plain FP64 form on the same workload, one domain at a time
+    if not args.no_fp64 and args.workload == "ensemble":
+        singles = [make_model(cc, [c], cc.CC_FP64) for c in cfgs]
+        ksteps = max(2, min(args.steps, 5))
+        for s in singles:
+            s.step(args.warmup)
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        for _ in range(ksteps):
+            for s in singles:
+                s.step(1)
+        e1.record(st)
+        e1.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        v64 = nfluid * ksteps / (ms64 / 1e3)
+        # error of the FP32 batched state against the FP64 runs after the same
+        # number of steps (both started from the same initial state)
+        n32 = args.warmup + args.steps
+        n64 = args.warmup + ksteps
+        for s in singles:
+            s.step(n32 - n64)
+        errs = {}
+        for fname, f in (("rho'", cc.CC_RHOP), ("p'", cc.CC_PP), ("rho u", cc.CC_MX), ("rho v", cc.CC_MY),
+                         ("rho w", cc.CC_MZ)):
+            num = den = 0.0
+            linf = scale = 0.0
+            for d, s in enumerate(singles):
+                a = model.download(d, f)
+                b = s.download(0, f)
+                num += float(((a - b) ** 2).sum())
+                den += float((b ** 2).sum())
+                linf = max(linf, float(np.abs(a - b).max()))
+                scale = max(scale, float(np.abs(b).max()))
+            errs[fname] = {"rel_l2": (num / den) ** 0.5 if den > 0 else 0.0,
+                           "rel_linf": linf / scale if scale > 0 else 0.0}
+        line["fp64_plain"] = {"value": v64, "unit": METRIC, "dtype": "f64", "ms_per_step": ms64 / ksteps,
+                              "steps": ksteps, "how": "each domain stepped alone in FP64, looped over domains"}
+        line["l2_error"] = {"vs": "plain FP64 GPU form", "after_steps": n32, "fields": errs}
+        for s in singles:
+            s.close()
+
+    # ---- end to end through the C ABI with host buffers
+    if not args.no_e2e:
+        fields = (cc.CC_RHOP, cc.CC_PP, cc.CC_MX, cc.CC_MY, cc.CC_MZ)
+        host = {}
+        for d in range(len(cfgs)):
+            for f in fields:
+                for lev in (0, 1):
+                    a = torch.from_numpy(model.download(d, f, lev)).pin_memory()
+                    host[(d, f, lev)] = a
+        outs = [torch.empty(tuple(model._shape(d, cc.CC_PP)), dtype=torch.float64).pin_memory()
+                for d in range(len(cfgs))]
+        h2d = sum(a.numel() * 8 for a in host.values())
+        d2h = sum(o.numel() * 8 for o in outs)
+        ke = max(2, min(args.steps, 5))
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ke):
+            for (d, f, lev), a in host.items():
+                model.upload_ptr(d, f, lev, a.data_ptr())
+            model.step(1)
+            for d in range(len(cfgs)):
+                model.download_ptr(d, cc.CC_PP, 1, outs[d].data_ptr())
+        barrier()
+        te = time.perf_counter() - t0
+        line["e2e"] = {"value": nfluid * ke * world / te, "unit": METRIC, "h2d_bytes_per_step": h2d,
+                       "d2h_bytes_per_step": d2h, "steps": ke,
+                       "how": "per step: upload both time levels of every prognostic field from pinned host "
+                              "FP64 arrays, one step, download p' of every domain"}
+
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(cfgs, args.cpu_seconds)
+    model.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

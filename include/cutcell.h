@@ -1,0 +1,175 @@
+/*
+ * cutcell.h -- C ABI of the GB300 cut-cell step library (libcutcell.so).
+ *
+ * The library advances the fully compressible, quasi-flux-form equations of
+ * Yamazaki, Satomura & Nikiforakis, "3D cut-cell modelling for
+ * high-resolution atmospheric simulations" (arXiv 1509.02572), Sec 2.1
+ * (Eqs. momentum_u .. continuity), on Cartesian grids cut by bilinear terrain
+ * (Sec 2.3), with the finite-volume discretisation and three-step velocity of
+ * Sec 2.4 and leapfrog + Robert-Asselin time stepping (Sec 2.2).
+ *
+ * Conventions shared by every entry point
+ *   - A model holds one or more independent domains ("ensemble"); each domain
+ *     is one uniform block, periodic in x and y (cyclic lateral boundaries,
+ *     Sec 3), with a free-slip (or no-slip) terrain surface and a rigid lid.
+ *   - The library owns all device memory it allocates; the caller owns every
+ *     host buffer it passes.  Host buffers are FP64 for every precision mode.
+ *   - Every call returns a cc_status; CC_OK is 0.  On error the message of
+ *     cc_last_error() describes the failure.  A model is bound to the CUDA
+ *     stream given at creation; calls on one model are not thread-safe.
+ *   - Cell (i,j,k), 0 <= i < nx, 0 <= j < ny, 0 <= k < nz, has its centre at
+ *     ((i+1/2)dx, (j+1/2)dy, (k+1/2)dz).  Corner (I,J,K) sits at
+ *     (I dx, J dy, K dz) and carries the co-located velocity components of the
+ *     semi-staggered arrangement (Sec 2.3, Fig. 7).
+ *   - Host cell arrays: nz*ny*nx doubles, x fastest.  Host corner arrays:
+ *     (nz+5)*ny*nx doubles for levels K = -2 .. nz+2, x fastest (the levels
+ *     below the floor and above the lid carry boundary values).
+ */
+#ifndef CUTCELL_H
+#define CUTCELL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CC_OK = 0,
+  CC_EINVAL = 1,    /* invalid argument (null pointer, bad size, bad index) */
+  CC_ECUDA = 2,     /* a CUDA runtime call failed                           */
+  CC_EGEOM = 3,     /* merge or boundary stencil cannot be formed           */
+  CC_ENUMERIC = 4,  /* NaN or Inf found by cc_diagnostics                   */
+  CC_ENOMEM = 5,    /* device allocation failed                             */
+  CC_ESTATE = 6     /* call out of order (e.g. step before geometry)        */
+} cc_status;
+
+enum { CC_FP64 = 0, CC_FP32 = 1 };
+/* prognostic fields; CC_UB = boundary-point velocity (3 per column corner) */
+enum { CC_RHOP = 0, CC_PP = 1, CC_MX = 2, CC_MY = 3, CC_MZ = 4, CC_UB = 5 };
+
+/* One domain.  Reading of the paper's constants: g, R, cp, p0 physical
+ * constants (p0 = 1e5 Pa, Sec 2.1); base state of constant Brunt-Vaisala
+ * frequency N with surface potential temperature theta0 at pressure p_surf;
+ * ra_nu Robert-Asselin coefficient (Sec 2.2); c4 strength of the fourth-order
+ * artificial diffusion (Sec 2.1), applied as -(c4/(16 dt)) sum delta^4 on
+ * momentum and (rho theta)'; sponge: Rayleigh damping of momentum toward
+ * (rho_bar U, 0, 0) above (1 - sponge_frac) of the domain height with peak
+ * rate tau_max (Sec 3, Klemp-Lilly layer); bc_slip 1 = free slip (Sec 3),
+ * 0 = no slip (Sec 2.4). */
+typedef struct {
+  int nx, ny, nz;
+  double dx, dy, dz;
+  double dt;
+  double U, N, theta0, p_surf, p0, g, R, cp;
+  double ra_nu, c4, sponge_frac, tau_max;
+  int bc_slip;
+} cc_config;
+
+/* Conservation and sanity diagnostics of one domain, level "current". */
+typedef struct {
+  double mass;        /* sum over merged cells of V_G rho'_G (kg)           */
+  double mass_comp;   /* compensation term of the Neumaier sum              */
+  double max_u;       /* max |u| over corners above the terrain (m/s)       */
+  double max_w;       /* max |w| over corners above the terrain (m/s)       */
+  long long nonfinite;/* number of non-finite prognostic values             */
+  long long steps;    /* steps taken since cc_init_state                    */
+} cc_diag;
+
+typedef struct cc_model cc_model;
+
+/* Create a model of n independent domains (cfgs[0..n-1]) computing in
+ * precision CC_FP64 or CC_FP32 (FP32 perturbations about an FP64-evaluated
+ * hydrostatic base state; geometry always FP64).  stream: a cudaStream_t or
+ * NULL for the default stream.  Allocates all device memory.  *out receives
+ * the model; on failure *out is NULL and the status says why. */
+cc_status cc_create(const cc_config *cfgs, int n, int precision, void *stream, cc_model **out);
+
+/* Release every device and host resource of the model.  Null is accepted. */
+cc_status cc_destroy(cc_model *m);
+
+/* Last error message of the model (static storage owned by the model), or of
+ * the last failed cc_create when m is NULL. */
+const char *cc_last_error(const cc_model *m);
+
+/* Terrain of domain d: corner heights h(I dx, J dy) for I < nx, J < ny
+ * (periodic), ny*nx doubles x fastest, every value >= 0 and below the lid.
+ * Copied to the device; Sec 2.3, Eq. bilin and its coefficients. */
+cc_status cc_set_terrain(cc_model *m, int d, const double *corner_h);
+
+/* Build the cut-cell geometry of every domain on the GPU in FP64 (Sec 2.3 and
+ * 2.4): column gradients (Eqs. xgrad, ygrad), volumes and apertures by exact
+ * integration of the bilinear surface, cell classes, merge targets of the
+ * Fig. 6 pseudocode, merge groups, velocity-point classes, boundary-point
+ * normals and nearest-plane stencils, merged-face interpolation weights,
+ * and the compacted group lists.  CC_EGEOM when a merge chain ends below the
+ * terrain or loops, or a stencil cannot be formed. */
+cc_status cc_build_geometry(cc_model *m);
+
+/* Copy domain d's geometry to host buffers (any pointer may be NULL):
+ *   vf, ax, ay: nz*ny*nx (volume fraction; apertures of the faces x = I dx and
+ *   y = J dy of cell (I,J,k)); az: (nz+1)*ny*nx (face z = K dz of column
+ *   (i,j)); cls: nz*ny*nx (0 below terrain, 1 full, 2 cut, 3 absorbed);
+ *   root: nz*ny*nx (cell id (k*ny+j)*nx+i of the group's host, -1 below
+ *   terrain); vcls: (nz+5)*ny*nx corner classes for K = -2..nz+2 (0 at or
+ *   below terrain, 1 predicted, 2 merged face, 3 lid). */
+cc_status cc_get_geometry(const cc_model *m, int d, double *vf, double *ax, double *ay, double *az,
+                          int8_t *cls, int32_t *root, int8_t *vcls);
+
+/* Boundary-point and merged-face stencils of domain d (any pointer may be
+ * NULL): per column corner (ny*nx): bK level of the nearest plane, bI, bJ its
+ * low corner, ba, bb the weights alpha and beta, bn the unit normal (3 each);
+ * per corner ((nz+5)*ny*nx): mK the level of the predicted point above a
+ * merged-face point, mg its weight gamma. */
+cc_status cc_get_stencils(const cc_model *m, int d, int32_t *bK, int32_t *bI, int32_t *bJ, double *ba,
+                          double *bb, double *bn, int32_t *mK, double *mg);
+
+/* Compacted merge-group list of domain d, ascending by host cell id.
+ * *ngroups and *nmembers receive the sizes; if host and start/members are
+ * non-NULL they receive: host[g], start[g] (ngroups+1 entries), members
+ * (ascending cell ids of each group, host included).  Call once with NULLs to
+ * get the sizes. */
+cc_status cc_get_groups(const cc_model *m, int d, int *ngroups, int *nmembers, int32_t *host,
+                        int32_t *start, int32_t *members);
+
+/* Initial state of every domain: zero perturbations, uniform wind U on the
+ * predicted velocity points, diagnosed boundary / merged-face / lid values. */
+cc_status cc_init_state(cc_model *m);
+
+/* Replace one field of domain d at level 0 (filtered previous) or 1 (current)
+ * with a host array in the layout above (cells, corners or 3*ny*nx for
+ * CC_UB).  The next step uses the uploaded values.  Copies through pinned
+ * staging; synchronous with respect to the model's stream. */
+cc_status cc_upload_state(cc_model *m, int d, int field, int level, const double *host);
+
+/* Copy one field of domain d at level 0 or 1 to a host array (same layout). */
+cc_status cc_download_state(const cc_model *m, int d, int field, int level, double *host);
+
+/* Advance every domain by n steps (leapfrog; the first step after
+ * cc_init_state is forward Euler).  Asynchronous on the model's stream. */
+cc_status cc_step(cc_model *m, int n);
+
+/* Diagnostics of domain d at the current level; synchronises the stream.
+ * Returns CC_ENUMERIC when non-finite values are present. */
+cc_status cc_diagnostics(cc_model *m, int d, cc_diag *out);
+
+/* Wait for all work queued on the model's stream. */
+cc_status cc_synchronize(cc_model *m);
+
+/* Number of kernels the last cc_step launched (for launch accounting). */
+long long cc_last_launch_count(const cc_model *m);
+
+/* Kernel timing for measurement (no counterpart in the paper).  When enabled,
+ * cc_step brackets each stage with CUDA events on the model's stream;
+ * cc_profile_read synchronises and returns the summed device time (ms) and the
+ * number of timed launches of one stage since the last cc_profile_reset. */
+enum { CC_K_FULL = 0, CC_K_GROUPS = 1, CC_K_DIAGNOSE = 2, CC_K_GHOST = 3 };
+cc_status cc_profile_enable(cc_model *m, int on);
+cc_status cc_profile_read(cc_model *m, int kernel, double *total_ms, long long *launches);
+cc_status cc_profile_reset(cc_model *m);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CUTCELL_H */

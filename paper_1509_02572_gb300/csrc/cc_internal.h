@@ -1,0 +1,118 @@
+// Internal definitions shared by the CUDA translation units of libcutcell.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/cutcell.h"
+
+namespace cc {
+
+constexpr int GH = 4;          // ghost width of every padded array (x, y and z)
+constexpr int HOST_GZ = 2;     // corner levels below floor / above lid in host arrays
+constexpr int NFIELD = 5;      // rho', p', rho u, rho v, rho w
+constexpr int NBUF = 4;        // rotating time levels
+constexpr int TILE_X = 32, TILE_Y = 8;  // full-cell stencil tile (x, y)
+
+// cell classes and corner classes
+enum : int8_t { C_UG = 0, C_FULL = 1, C_CUT = 2, C_ABS = 3 };
+enum : int8_t { V_UG = 0, V_PRED = 1, V_MF = 2, V_LID = 3 };
+
+// Device-side description of one domain.  Pointers are device pointers;
+// field arrays are of the model's precision (double or float).
+struct DomDev {
+  int nx, ny, nz;
+  int px, py, pz;            // padded extents (n + 2*GH)
+  long long plane;           // px*py
+  long long ncellp;          // px*py*pz
+  double dx, dy, dz, dt;
+  double U, g, p0, R, cp;
+  double kap;                // R/cp
+  double cvcp;               // cv/cp
+  double Cp;                 // cp R / cv
+  double kdif;               // c4 / (16 dt)
+  double ra_nu;              // Robert-Asselin coefficient
+  int bc_slip;
+  void *f[NBUF][NFIELD];     // prognostic fields, padded layout
+  void *ub[NBUF];            // boundary-point velocity per level, 3*ny*nx
+  // base state per padded level, precision of the model
+  const void *rhob, *pb, *thb, *pik, *rhobc, *tau;
+  // geometry (FP64 / int), padded cell layout unless noted
+  const double *h;           // corner heights, ny*nx (periodic)
+  const double *vf;          // nz*ny*nx interior layout (cell id)
+  const double *ax, *ay;     // nz*ny*nx
+  const double *az;          // (nz+1)*ny*nx
+  const int8_t *cls;         // nz*ny*nx
+  const int32_t *root;       // nz*ny*nx, cell id of host or -1
+  const int32_t *kug;        // ny*nx: cells k < kug are below the terrain
+  const int8_t *vcls;        // corner classes, padded layout
+  const int32_t *bK, *bI, *bJ;
+  const double *ba, *bb, *bn;
+  const int32_t *mK;         // padded corner layout
+  const double *mg;          // padded corner layout
+  const int32_t *ktop;       // ny*nx: highest non-predicted corner level below nz
+};
+
+// (block, tile) work item of the full-cell stencil
+struct WorkItem {
+  int dom, i0, j0, k0, k1, pad0, pad1, pad2;
+};
+
+// column work item of the velocity diagnosis
+struct ColItem {
+  int dom, I, J, pad;
+};
+
+// merge group record
+struct GroupRec {
+  int dom;
+  int host;      // cell id (interior layout) of the host
+  int start;     // index into the member array
+  int count;
+  double vg;     // group volume
+};
+
+__host__ __device__ inline long long pidx(const DomDev &D, int i, int j, int k) {
+  return ((long long)(k + GH) * D.py + (j + GH)) * D.px + (i + GH);
+}
+__host__ __device__ inline int wrapi(int i, int n) {
+  int r = i % n;
+  return r < 0 ? r + n : r;
+}
+__host__ __device__ inline long long cid(const DomDev &D, int i, int j, int k) {
+  return ((long long)k * D.ny + j) * D.nx + i;
+}
+
+// geometry of one domain (geometry.cu); returns the group list of the domain
+// as device allocations owned by the caller
+cudaError_t geom_build_one(DomDev &D, cudaStream_t st, int dom, int *d_err, int32_t **members_out,
+                           GroupRec **recs_out, int *ng_out, int *nm_out);
+
+// step kernels (step.cu)
+struct StepLaunch {
+  const DomDev *d_doms;
+  const WorkItem *items;
+  int nitems;
+  const GroupRec *groups;
+  int ngroups;
+  const int32_t *members;
+  const ColItem *cols;
+  int ncols;
+  int ndom;
+  long long ghost_points;  // lateral ghost points over all domains (per level and field)
+  const long long *ghost_off;  // per-domain prefix of ghost points (device)
+};
+cudaError_t launch_base(const DomDev &D, int prec, double theta0, double N, double p_surf,
+                        double sponge_frac, double tau_max, cudaStream_t st);
+cudaError_t launch_full(const StepLaunch &L, int prec, int rO, int rC, int rN, int rF, int first,
+                        cudaStream_t st);
+cudaError_t launch_groups(const StepLaunch &L, int prec, int rO, int rC, int rN, int rF, int first,
+                          cudaStream_t st);
+cudaError_t launch_diagnose(const StepLaunch &L, int prec, int rV, int rC, int rO, int rF, int first,
+                            int filter, cudaStream_t st);
+cudaError_t launch_ghost(const StepLaunch &L, int prec, int r1, int r2, cudaStream_t st);
+cudaError_t launch_init_momentum(const DomDev &D, const DomDev *d_dom, int prec, int r, double U,
+                                 cudaStream_t st);
+cudaError_t launch_diag_reduce(const DomDev &D, const DomDev *d_dom, int prec, int r, double *d_out,
+                               cudaStream_t st);
+
+}  // namespace cc

@@ -1,0 +1,838 @@
+// One leapfrog step of the cut-cell model on the GPU (paper Sec 2.2 and 2.4).
+//
+//   k_full   every interior cell and corner of every (domain, tile) work item:
+//            scalar fluxes and divergence with full apertures (Eq. fvm_d), the
+//            p' and rho' tendencies, momentum on regular velocity cells
+//            (Eqs. momentum_u_d .. w_d), fourth-order diffusion, sponge,
+//            leapfrog and Robert-Asselin filter.  A 2.5D march in z keeps a
+//            ring of halo planes in shared memory, so each field plane is read
+//            from HBM once per tile.  Branch-free: cut cells and diagnosed
+//            corners are recomputed afterwards by the list kernels.
+//   k_groups one thread per merge group / cut cell: face fluxes weighted by
+//            the apertures, divergence over the merged volume, host update
+//            and scatter to the absorbed cells (Sec 2.3, 2.4).
+//   k_diag   one thread per column: boundary velocity by the nearest-plane
+//            interpolation and free-slip projection (Eq. 33), merged-face
+//            interpolation, lid values, the values below the terrain.
+//   k_ghost  periodic copy of the lateral ghost frames.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "cc_internal.h"
+
+namespace cc {
+
+// ------------------------------------------------------------------ arithmetic
+template <typename T>
+struct Ar;
+template <>
+struct Ar<double> {
+  static __device__ __forceinline__ double add(double a, double b) { return __dadd_rn(a, b); }
+  static __device__ __forceinline__ double sub(double a, double b) { return __dsub_rn(a, b); }
+  static __device__ __forceinline__ double mul(double a, double b) { return __dmul_rn(a, b); }
+};
+template <>
+struct Ar<float> {
+  static __device__ __forceinline__ float add(float a, float b) { return __fadd_rn(a, b); }
+  static __device__ __forceinline__ float sub(float a, float b) { return __fsub_rn(a, b); }
+  static __device__ __forceinline__ float mul(float a, float b) { return __fmul_rn(a, b); }
+};
+
+// Face flux phi_f * u_n * S with phi_f the mean of the two cells (lower index
+// first) and u_n the mean of the four corner values in a fixed order.  Every
+// operation is rounded as written, so a face evaluated from either side, or
+// by either kernel, gives the same bits and cancels exactly in the sum.
+template <typename T>
+__device__ __forceinline__ T face_flux(T pa, T pb, T u1, T u2, T u3, T u4, T S) {
+  using A = Ar<T>;
+  T un = A::mul(A::add(A::add(A::add(u1, u2), u3), u4), T(0.25));
+  return A::mul(A::mul(A::mul(A::add(pa, pb), T(0.5)), un), S);
+}
+
+// Corner density: mean of the eight surrounding cell totals, fixed order
+// (dk outer, then dj, then di; -1 before 0).
+template <typename T>
+__device__ __forceinline__ T rho8(T a, T b, T c, T d, T e, T f, T g, T h) {
+  using A = Ar<T>;
+  return A::mul(A::add(A::add(A::add(A::add(A::add(A::add(A::add(a, b), c), d), e), f), g), h), T(0.125));
+}
+
+// rho*theta as a function of pressure, total and perturbation (equation of
+// state, Sec 2.1: rho theta = (p0/R)(p/p0)^(cv/cp)).
+__device__ __forceinline__ double theta_tot(const DomDev &D, const double *thb, const double *pb, int kp,
+                                            double pp) {
+  return D.p0 / D.R * pow((pb[kp] + pp) / D.p0, D.cvcp);
+}
+__device__ __forceinline__ double theta_pert(const DomDev &D, const double *thb, const double *pb, int kp,
+                                             double pp) {
+  return theta_tot(D, thb, pb, kp, pp) - thb[kp];
+}
+__device__ __forceinline__ double exner_fac(const DomDev &D, const double *pik, const double *pb, int kp,
+                                            double pp) {
+  return pow((pb[kp] + pp) / D.p0, D.kap);
+}
+// FP32 perturbation form: the ratio p'/p_bar enters through log1p / expm1 so
+// that a perturbation of a few pascals keeps full relative precision.
+__device__ __forceinline__ float theta_pert(const DomDev &D, const float *thb, const float *pb, int kp,
+                                            float pp) {
+  return thb[kp] * expm1f((float)D.cvcp * log1pf(pp / pb[kp]));
+}
+__device__ __forceinline__ float theta_tot(const DomDev &D, const float *thb, const float *pb, int kp,
+                                           float pp) {
+  return thb[kp] + theta_pert(D, thb, pb, kp, pp);
+}
+__device__ __forceinline__ float exner_fac(const DomDev &D, const float *pik, const float *pb, int kp,
+                                           float pp) {
+  return pik[kp] * expf((float)D.kap * log1pf(pp / pb[kp]));
+}
+
+__device__ __forceinline__ double d4(double a, double b, double c, double d, double e) {
+  return a - 4.0 * b + 6.0 * c - 4.0 * d + e;
+}
+__device__ __forceinline__ float d4(float a, float b, float c, float d, float e) {
+  return a - 4.0f * b + 6.0f * c - 4.0f * d + e;
+}
+
+// ------------------------------------------------------------------ base state
+// Hydrostatic base state of constant N on every padded level, evaluated in
+// FP64 and stored in the model precision.
+template <typename T>
+__global__ void k_base(DomDev D, double theta0, double N, double p_surf, double sponge_frac,
+                       double tau_max, T *rhob, T *pb, T *thb, T *pik, T *rhobc, T *tau) {
+  int kp = blockIdx.x * blockDim.x + threadIdx.x;
+  if (kp >= D.pz) return;
+  auto base = [&](double z, double &rho, double &p) {
+    double pis = pow(p_surf / D.p0, D.kap);
+    double th, pi;
+    if (N > 0.0) {
+      double n2g = N * N / D.g;
+      th = theta0 * exp(n2g * z);
+      pi = pis + D.g * D.g / (D.cp * theta0 * N * N) * (exp(-n2g * z) - 1.0);
+    } else {
+      th = theta0;
+      pi = pis - D.g * z / (D.cp * theta0);
+    }
+    p = D.p0 * pow(pi, D.cp / D.R);
+    rho = p / (D.R * th * pi);
+  };
+  int k = kp - GH;
+  double r, p, rm, pm;
+  base((k + 0.5) * D.dz, r, p);
+  base((k - 0.5) * D.dz, rm, pm);
+  rhob[kp] = (T)r;
+  pb[kp] = (T)p;
+  thb[kp] = (T)(D.p0 / D.R * pow(p / D.p0, D.cvcp));
+  pik[kp] = (T)pow(p / D.p0, D.kap);
+  // corner level K = k: mean of the two adjacent cell levels
+  rhobc[kp] = (T)(0.5 * (rm + r));
+  double ztop = D.nz * D.dz, zs = ztop * (1.0 - sponge_frac), z = k * D.dz, t = 0.0;
+  if (sponge_frac > 0.0 && z > zs && z <= ztop) {
+    double s = sin(0.5 * M_PI * (z - zs) / (ztop - zs));
+    t = tau_max * s * s;
+  }
+  tau[kp] = (T)t;
+}
+
+// ------------------------------------------------------------------ full-cell stencil
+constexpr int TX = TILE_X, TY = TILE_Y, HX = TX + 4, HY = TY + 4, PL = HX * HY;
+
+template <typename T>
+struct FullSmem {
+  T rho[3][PL], rp[3][PL], th[3][PL], pp[3][PL];
+  T tho[5][PL];
+  T u[3][3][PL];
+  T mo[5][3][PL];
+  T mt[3][PL];
+};
+
+__device__ __forceinline__ int s3(int k) { return (k + 9) % 3; }
+__device__ __forceinline__ int s5(int k) { return (k + 10) % 5; }
+
+template <typename T>
+__global__ void __launch_bounds__(TX * TY) k_full(const DomDev *__restrict__ doms,
+                                                   const WorkItem *__restrict__ items, int rO, int rC,
+                                                   int rN, int rF, int first) {
+  using A = Ar<T>;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  FullSmem<T> &S = *reinterpret_cast<FullSmem<T> *>(smraw);
+  const WorkItem W = items[blockIdx.x];
+  const DomDev &D = doms[W.dom];
+  const T dt2 = (T)(first ? D.dt : 2.0 * D.dt);
+  const T nu = (T)(first ? 0.0 : D.ra_nu);
+  const int tid = threadIdx.x;
+  const int nx = D.nx, ny = D.ny, nz = D.nz, px = D.px, py = D.py;
+  const T *__restrict__ rpC = (const T *)D.f[rC][0];
+  const T *__restrict__ ppC = (const T *)D.f[rC][1];
+  const T *__restrict__ mC[3] = {(const T *)D.f[rC][2], (const T *)D.f[rC][3], (const T *)D.f[rC][4]};
+  const T *__restrict__ rpO = (const T *)D.f[rO][0];
+  const T *__restrict__ ppO = (const T *)D.f[rO][1];
+  const T *__restrict__ mO[3] = {(const T *)D.f[rO][2], (const T *)D.f[rO][3], (const T *)D.f[rO][4]};
+  const T *__restrict__ rhob = (const T *)D.rhob;
+  const T *__restrict__ pb = (const T *)D.pb;
+  const T *__restrict__ thb = (const T *)D.thb;
+  const T *__restrict__ pik = (const T *)D.pik;
+  const T *__restrict__ rhobc = (const T *)D.rhobc;
+  const T *__restrict__ tau = (const T *)D.tau;
+  const int i0 = W.i0, j0 = W.j0, k0 = W.k0, k1 = W.k1;
+
+  auto gidx = [&](int hx, int hy, int kk, bool &ok) -> long long {
+    int gi = i0 - 2 + hx, gj = j0 - 2 + hy;
+    ok = gi < nx + GH && gj < ny + GH;
+    return ((long long)(kk + GH) * py + (gj + GH)) * px + (gi + GH);
+  };
+  auto load_cells = [&](int kk) {
+    int s = s3(kk);
+    int kp = kk + GH;
+    T rb = rhob[kp];
+    for (int p = tid; p < PL; p += TX * TY) {
+      bool ok;
+      long long g = gidx(p % HX, p / HX, kk, ok);
+      T r = 0, q = 0;
+      if (ok) {
+        r = rpC[g];
+        q = ppC[g];
+      }
+      S.rp[s][p] = r;
+      S.pp[s][p] = q;
+      S.rho[s][p] = A::add(rb, r);
+      S.th[s][p] = theta_tot(D, thb, pb, kp, q);
+    }
+  };
+  auto load_old = [&](int kk) {
+    int s = s5(kk);
+    int kp = kk + GH;
+    for (int p = tid; p < PL; p += TX * TY) {
+      bool ok;
+      long long g = gidx(p % HX, p / HX, kk, ok);
+      T q = 0, a = 0, b = 0, c = 0;
+      if (ok) {
+        q = ppO[g];
+        a = mO[0][g];
+        b = mO[1][g];
+        c = mO[2][g];
+      }
+      S.tho[s][p] = theta_pert(D, thb, pb, kp, q);
+      S.mo[s][0][p] = a;
+      S.mo[s][1][p] = b;
+      S.mo[s][2][p] = c;
+    }
+  };
+  auto load_mt = [&](int kk) {
+    for (int p = tid; p < PL; p += TX * TY) {
+      bool ok;
+      long long g = gidx(p % HX, p / HX, kk, ok);
+      T a = 0, b = 0, c = 0;
+      if (ok) {
+        a = mC[0][g];
+        b = mC[1][g];
+        c = mC[2][g];
+      }
+      S.mt[0][p] = a;
+      S.mt[1][p] = b;
+      S.mt[2][p] = c;
+    }
+  };
+  // corner velocity = momentum / mean density of the 8 surrounding cells
+  auto compute_u = [&](int K) {
+    int sl = s3(K - 1), sh = s3(K), su = s3(K);
+    for (int p = tid; p < PL; p += TX * TY) {
+      int hx = p % HX, hy = p / HX;
+      if (hx == 0 || hy == 0) continue;
+      const T *lo = S.rho[sl], *hi = S.rho[sh];
+      int q00 = p - HX - 1, q01 = p - HX, q10 = p - 1, q11 = p;
+      T rc = rho8(lo[q00], lo[q01], lo[q10], lo[q11], hi[q00], hi[q01], hi[q10], hi[q11]);
+      S.u[su][0][p] = S.mt[0][p] / rc;
+      S.u[su][1][p] = S.mt[1][p] / rc;
+      S.u[su][2][p] = S.mt[2][p] / rc;
+    }
+  };
+
+  // prologue
+  load_cells(k0 - 2);
+  load_cells(k0 - 1);
+  for (int kk = k0 - 2; kk <= k0 + 1; kk++) load_old(kk);
+  load_mt(k0 - 1);
+  __syncthreads();
+  compute_u(k0 - 1);
+  __syncthreads();
+  load_cells(k0);
+  load_mt(k0);
+  __syncthreads();
+  compute_u(k0);
+  __syncthreads();
+
+  const int tx = tid % TX, ty = tid / TX;
+  const int i = i0 + tx, j = j0 + ty;
+  const bool active = i < nx && j < ny;
+  const int hx = tx + 2, hy = ty + 2, c = hy * HX + hx;
+  const T dx = (T)D.dx, dy = (T)D.dy, dz = (T)D.dz;
+  const T Sx = (T)(D.dy * D.dz), Sy = (T)(D.dx * D.dz), Sz = (T)(D.dx * D.dy);
+  const T v0inv = (T)(1.0 / (D.dx * D.dy * D.dz));
+  const T kdif = (T)D.kdif, Cp = (T)D.Cp, g = (T)D.g, U = (T)D.U;
+  const int kug = active ? D.kug[(long long)j * nx + i] : 0;
+
+  for (int k = k0; k < k1; k++) {
+    load_cells(k + 1);
+    load_old(k + 2);
+    load_mt(k + 1);
+    __syncthreads();
+    compute_u(k + 1);
+    __syncthreads();
+    if (active) {
+      const int sk = s3(k), skm = s3(k - 1), skp = s3(k + 1);
+      const T *R0 = S.rho[sk], *Rm = S.rho[skm], *Rp = S.rho[skp];
+      const T *H0 = S.th[sk], *Hm = S.th[skm], *Hp = S.th[skp];
+      const T *ux0 = S.u[sk][0], *uy0 = S.u[sk][1], *uz0 = S.u[sk][2];
+      const T *uxp = S.u[skp][0], *uyp = S.u[skp][1], *uzp = S.u[skp][2];
+      // ---- scalar cell (i,j,k): face fluxes, lower-index cell first
+      T fxm = face_flux(R0[c - 1], R0[c], ux0[c], ux0[c + HX], uxp[c], uxp[c + HX], Sx);
+      T fxp = face_flux(R0[c], R0[c + 1], ux0[c + 1], ux0[c + 1 + HX], uxp[c + 1], uxp[c + 1 + HX], Sx);
+      T fym = face_flux(R0[c - HX], R0[c], uy0[c], uy0[c + 1], uyp[c], uyp[c + 1], Sy);
+      T fyp = face_flux(R0[c], R0[c + HX], uy0[c + HX], uy0[c + HX + 1], uyp[c + HX], uyp[c + HX + 1], Sy);
+      T fzm = face_flux(Rm[c], R0[c], uz0[c], uz0[c + 1], uz0[c + HX], uz0[c + HX + 1], Sz);
+      T fzp = face_flux(R0[c], Rp[c], uzp[c], uzp[c + 1], uzp[c + HX], uzp[c + HX + 1], Sz);
+      T hxm = face_flux(H0[c - 1], H0[c], ux0[c], ux0[c + HX], uxp[c], uxp[c + HX], Sx);
+      T hxp = face_flux(H0[c], H0[c + 1], ux0[c + 1], ux0[c + 1 + HX], uxp[c + 1], uxp[c + 1 + HX], Sx);
+      T hym = face_flux(H0[c - HX], H0[c], uy0[c], uy0[c + 1], uyp[c], uyp[c + 1], Sy);
+      T hyp = face_flux(H0[c], H0[c + HX], uy0[c + HX], uy0[c + HX + 1], uyp[c + HX], uyp[c + HX + 1], Sy);
+      T hzm = face_flux(Hm[c], H0[c], uz0[c], uz0[c + 1], uz0[c + HX], uz0[c + HX + 1], Sz);
+      T hzp = face_flux(H0[c], Hp[c], uzp[c], uzp[c + 1], uzp[c + HX], uzp[c + HX + 1], Sz);
+      if (k == 0) { fzm = 0; hzm = 0; }          // floor
+      if (k == nz - 1) { fzp = 0; hzp = 0; }     // rigid lid
+      T RM = A::add(A::add(A::sub(fxp, fxm), A::sub(fyp, fym)), A::sub(fzp, fzm));
+      T RH = A::add(A::add(A::sub(hxp, hxm), A::sub(hyp, hym)), A::sub(hzp, hzm));
+      // fourth-order diffusion of (rho theta)' at n-1
+      const T *Tk = S.tho[s5(k)];
+      T dd = d4(Tk[c - 2], Tk[c - 1], Tk[c], Tk[c + 1], Tk[c + 2]) +
+             d4(Tk[c - 2 * HX], Tk[c - HX], Tk[c], Tk[c + HX], Tk[c + 2 * HX]) +
+             d4(S.tho[s5(k - 2)][c], S.tho[s5(k - 1)][c], Tk[c], S.tho[s5(k + 1)][c], S.tho[s5(k + 2)][c]);
+      T Dth = -kdif * dd;
+      const long long o = ((long long)(k + GH) * py + (j + GH)) * px + (i + GH);
+      const int kp = k + GH;
+      T rC_ = S.rp[sk][c], pC_ = S.pp[sk][c];
+      T rO_ = rpO[o], pO_ = ppO[o];
+      T rN_ = rO_ - dt2 * (RM * v0inv);
+      T pN_ = pO_ - dt2 * Cp * exner_fac(D, pik, pb, kp, pC_) * (RH * v0inv - Dth);
+      if (k < kug) { rN_ = 0; pN_ = 0; }
+      T rF_ = rC_ + nu * (rN_ - T(2) * rC_ + rO_);
+      T pF_ = pC_ + nu * (pN_ - T(2) * pC_ + pO_);
+      if (k < kug) { rF_ = 0; pF_ = 0; }
+      ((T *)D.f[rN][0])[o] = rN_;
+      ((T *)D.f[rN][1])[o] = pN_;
+      ((T *)D.f[rF][0])[o] = rF_;
+      ((T *)D.f[rF][1])[o] = pF_;
+
+      // ---- velocity cell centred on corner (i,j,K=k): Eqs. momentum_u_d .. w_d
+      T rE = (Rm[c - HX] + Rm[c] + R0[c - HX] + R0[c]) * T(0.25);
+      T rW = (Rm[c - HX - 1] + Rm[c - 1] + R0[c - HX - 1] + R0[c - 1]) * T(0.25);
+      T rNn = (Rm[c - 1] + Rm[c] + R0[c - 1] + R0[c]) * T(0.25);
+      T rS = (Rm[c - HX - 1] + Rm[c - HX] + R0[c - HX - 1] + R0[c - HX]) * T(0.25);
+      T rT = (R0[c - HX - 1] + R0[c - HX] + R0[c - 1] + R0[c]) * T(0.25);
+      T rB = (Rm[c - HX - 1] + Rm[c - HX] + Rm[c - 1] + Rm[c]) * T(0.25);
+      const T *uxm = S.u[skm][0], *uym = S.u[skm][1], *uzm = S.u[skm][2];
+      T u0[3] = {ux0[c], uy0[c], uz0[c]};
+      T uE[3] = {ux0[c + 1], uy0[c + 1], uz0[c + 1]};
+      T uW[3] = {ux0[c - 1], uy0[c - 1], uz0[c - 1]};
+      T uN[3] = {ux0[c + HX], uy0[c + HX], uz0[c + HX]};
+      T uS[3] = {ux0[c - HX], uy0[c - HX], uz0[c - HX]};
+      T uT[3] = {uxp[c], uyp[c], uzp[c]};
+      T uB[3] = {uxm[c], uym[c], uzm[c]};
+      T fE = rE * T(0.5) * (u0[0] + uE[0]) * Sx, fW = rW * T(0.5) * (uW[0] + u0[0]) * Sx;
+      T fN = rNn * T(0.5) * (u0[1] + uN[1]) * Sy, fS = rS * T(0.5) * (uS[1] + u0[1]) * Sy;
+      T fT = rT * T(0.5) * (u0[2] + uT[2]) * Sz, fB = rB * T(0.5) * (uB[2] + u0[2]) * Sz;
+      const T *P0 = S.pp[sk], *Pm = S.pp[skm];
+      T pE = Pm[c - HX] + Pm[c] + P0[c - HX] + P0[c];
+      T pW = Pm[c - HX - 1] + Pm[c - 1] + P0[c - HX - 1] + P0[c - 1];
+      T pNn = Pm[c - 1] + Pm[c] + P0[c - 1] + P0[c];
+      T pS = Pm[c - HX - 1] + Pm[c - HX] + P0[c - HX - 1] + P0[c - HX];
+      T pT = P0[c - HX - 1] + P0[c - HX] + P0[c - 1] + P0[c];
+      T pB = Pm[c - HX - 1] + Pm[c - HX] + Pm[c - 1] + Pm[c];
+      const T *Q0 = S.rp[sk], *Qm = S.rp[skm];
+      T r8 = (Q0[c - HX - 1] + Q0[c - HX] + Q0[c - 1] + Q0[c]) + (Qm[c - HX - 1] + Qm[c - HX] + Qm[c - 1] + Qm[c]);
+      T pg[3] = {T(0.25) * (pE - pW) / dx, T(0.25) * (pNn - pS) / dy, T(0.25) * (pT - pB) / dz};
+      const T mref = rhobc[kp] * U;
+      const T tk = tau[kp];
+#pragma unroll
+      for (int d = 0; d < 3; d++) {
+        T adv = fE * T(0.5) * (u0[d] + uE[d]) - fW * T(0.5) * (uW[d] + u0[d]) + fN * T(0.5) * (u0[d] + uN[d]) -
+                fS * T(0.5) * (uS[d] + u0[d]) + fT * T(0.5) * (u0[d] + uT[d]) - fB * T(0.5) * (uB[d] + u0[d]);
+        T tend = -adv * v0inv - pg[d];
+        if (d == 2) tend -= g * r8 * T(0.125);
+        const T *Mk = S.mo[s5(k)][d];
+        T ref0 = d == 0 ? mref : T(0);
+        // diffusion of the departure from the reference momentum (rho_bar U, 0, 0)
+        T dm = d4(Mk[c - 2] - ref0, Mk[c - 1] - ref0, Mk[c] - ref0, Mk[c + 1] - ref0, Mk[c + 2] - ref0) +
+               d4(Mk[c - 2 * HX] - ref0, Mk[c - HX] - ref0, Mk[c] - ref0, Mk[c + HX] - ref0,
+                  Mk[c + 2 * HX] - ref0);
+        T zr[5];
+#pragma unroll
+        for (int a = -2; a <= 2; a++) zr[a + 2] = d == 0 ? rhobc[kp + a] * U : T(0);
+        dm += d4(S.mo[s5(k - 2)][d][c] - zr[0], S.mo[s5(k - 1)][d][c] - zr[1], Mk[c] - zr[2],
+                 S.mo[s5(k + 1)][d][c] - zr[3], S.mo[s5(k + 2)][d][c] - zr[4]);
+        T mold = Mk[c];
+        tend += -kdif * dm - tk * (mold - ref0);
+        T mnew = mold + dt2 * tend;
+        T mcur = mC[d][o];
+        T mf = mcur + nu * (mnew - T(2) * mcur + mold);
+        ((T *)D.f[rN][2 + d])[o] = mnew;
+        ((T *)D.f[rF][2 + d])[o] = mf;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ cut cells and merge groups
+template <typename T>
+__device__ __forceinline__ T cell_rho(const DomDev &D, const T *rp, const T *rhob, int i, int j, int k) {
+  long long o = ((long long)(k + GH) * D.py + (j + GH)) * D.px + (i + GH);
+  return Ar<T>::add(rhob[k + GH], rp[o]);
+}
+
+// corner velocity component at corner (I,J,K) (padded reads: the ghost frames
+// of the level are valid)
+template <typename T>
+__device__ __forceinline__ void corner_u(const DomDev &D, const T *rp, const T *const *M, const T *rhob, int I,
+                                         int J, int K, T u[3]) {
+  T rc = rho8(cell_rho(D, rp, rhob, I - 1, J - 1, K - 1), cell_rho(D, rp, rhob, I, J - 1, K - 1),
+              cell_rho(D, rp, rhob, I - 1, J, K - 1), cell_rho(D, rp, rhob, I, J, K - 1),
+              cell_rho(D, rp, rhob, I - 1, J - 1, K), cell_rho(D, rp, rhob, I, J - 1, K),
+              cell_rho(D, rp, rhob, I - 1, J, K), cell_rho(D, rp, rhob, I, J, K));
+  long long o = ((long long)(K + GH) * D.py + (J + GH)) * D.px + (I + GH);
+  u[0] = M[0][o] / rc;
+  u[1] = M[1][o] / rc;
+  u[2] = M[2][o] / rc;
+}
+
+template <typename T>
+__global__ void k_groups(const DomDev *__restrict__ doms, const GroupRec *__restrict__ recs, int ng,
+                         const int32_t *__restrict__ members, int rO, int rC, int rN, int rF, int first) {
+  using A = Ar<T>;
+  int gi = blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= ng) return;
+  const GroupRec R = recs[gi];
+  const DomDev &D = doms[R.dom];
+  const T dt2 = (T)(first ? D.dt : 2.0 * D.dt);
+  const T nu = (T)(first ? 0.0 : D.ra_nu);
+  const int nx = D.nx, ny = D.ny, nz = D.nz;
+  const T *rpC = (const T *)D.f[rC][0];
+  const T *ppC = (const T *)D.f[rC][1];
+  const T *MC[3] = {(const T *)D.f[rC][2], (const T *)D.f[rC][3], (const T *)D.f[rC][4]};
+  const T *rpO = (const T *)D.f[rO][0];
+  const T *ppO = (const T *)D.f[rO][1];
+  const T *rhob = (const T *)D.rhob, *pb = (const T *)D.pb, *thb = (const T *)D.thb, *pik = (const T *)D.pik;
+  const T Sfull[3] = {(T)(D.dy * D.dz), (T)(D.dx * D.dz), (T)(D.dx * D.dy)};
+  T rm = 0, rh = 0;
+  for (int a = 0; a < R.count; a++) {
+    int m = members[R.start + a];
+    int i = m % nx, j = (m / nx) % ny, k = m / (nx * ny);
+    for (int ax = 0; ax < 3; ax++)
+      for (int sd = 0; sd <= 1; sd++) {
+        int ni = i, nj = j, nk = k;
+        double Ap;
+        int cI[4], cJ[4], cK[4];
+        if (ax == 0) {
+          int I = i + sd;
+          ni = i + (sd ? 1 : -1);
+          Ap = D.ax[cid(D, wrapi(I, nx), j, k)];
+          cI[0] = I; cJ[0] = j; cK[0] = k;
+          cI[1] = I; cJ[1] = j + 1; cK[1] = k;
+          cI[2] = I; cJ[2] = j; cK[2] = k + 1;
+          cI[3] = I; cJ[3] = j + 1; cK[3] = k + 1;
+        } else if (ax == 1) {
+          int J = j + sd;
+          nj = j + (sd ? 1 : -1);
+          Ap = D.ay[cid(D, i, wrapi(J, ny), k)];
+          cI[0] = i; cJ[0] = J; cK[0] = k;
+          cI[1] = i + 1; cJ[1] = J; cK[1] = k;
+          cI[2] = i; cJ[2] = J; cK[2] = k + 1;
+          cI[3] = i + 1; cJ[3] = J; cK[3] = k + 1;
+        } else {
+          int K = k + sd;
+          nk = k + (sd ? 1 : -1);
+          Ap = D.az[((long long)K * ny + j) * nx + i];
+          cI[0] = i; cJ[0] = j; cK[0] = K;
+          cI[1] = i + 1; cJ[1] = j; cK[1] = K;
+          cI[2] = i; cJ[2] = j + 1; cK[2] = K;
+          cI[3] = i + 1; cJ[3] = j + 1; cK[3] = K;
+        }
+        if (Ap == 0.0) continue;
+        if (nk < 0 || nk >= nz) continue;
+        int wni = wrapi(ni, nx), wnj = wrapi(nj, ny);
+        long long nb = cid(D, wni, wnj, nk);
+        if (D.cls[nb] != C_UG && D.root[nb] == R.host) continue;  // face inside the group
+        T uc[4][3];
+        for (int s = 0; s < 4; s++) corner_u(D, rpC, MC, rhob, cI[s], cJ[s], cK[s], uc[s]);
+        // neighbour read through its padded position (ghost frames valid)
+        T phm = cell_rho(D, rpC, rhob, i, j, k), phn = cell_rho(D, rpC, rhob, ni, nj, nk);
+        long long om = ((long long)(k + GH) * D.py + (j + GH)) * D.px + (i + GH);
+        long long on = ((long long)(nk + GH) * D.py + (nj + GH)) * D.px + (ni + GH);
+        T thm = theta_tot(D, thb, pb, k + GH, ppC[om]), thn = theta_tot(D, thb, pb, nk + GH, ppC[on]);
+        T S = (Ap == 1.0) ? Sfull[ax] : (T)(Ap * (double)Sfull[ax]);
+        T fm, fh;
+        if (sd) {
+          fm = face_flux(phm, phn, uc[0][ax], uc[1][ax], uc[2][ax], uc[3][ax], S);
+          fh = face_flux(thm, thn, uc[0][ax], uc[1][ax], uc[2][ax], uc[3][ax], S);
+          rm = A::add(rm, fm);
+          rh = A::add(rh, fh);
+        } else {
+          fm = face_flux(phn, phm, uc[0][ax], uc[1][ax], uc[2][ax], uc[3][ax], S);
+          fh = face_flux(thn, thm, uc[0][ax], uc[1][ax], uc[2][ax], uc[3][ax], S);
+          rm = A::sub(rm, fm);
+          rh = A::sub(rh, fh);
+        }
+      }
+  }
+  // host update
+  int h = R.host;
+  int ih = h % nx, jh = (h / nx) % ny, kh = h / (nx * ny);
+  auto po = [&](int ii, int jj, int kk) { return ((long long)(kk + GH) * D.py + (jj + GH)) * D.px + (ii + GH); };
+  auto tho = [&](int ii, int jj, int kk) { return theta_pert(D, thb, pb, kk + GH, ppO[po(ii, jj, kk)]); };
+  T dd = d4(tho(ih - 2, jh, kh), tho(ih - 1, jh, kh), tho(ih, jh, kh), tho(ih + 1, jh, kh), tho(ih + 2, jh, kh)) +
+         d4(tho(ih, jh - 2, kh), tho(ih, jh - 1, kh), tho(ih, jh, kh), tho(ih, jh + 1, kh), tho(ih, jh + 2, kh)) +
+         d4(tho(ih, jh, kh - 2), tho(ih, jh, kh - 1), tho(ih, jh, kh), tho(ih, jh, kh + 1), tho(ih, jh, kh + 2));
+  T Dth = -(T)D.kdif * dd;
+  long long oh = po(ih, jh, kh);
+  T rC_ = rpC[oh], pC_ = ppC[oh], rO_ = rpO[oh], pO_ = ppO[oh];
+  T VG = (T)R.vg;
+  T rN_ = rO_ - dt2 * (rm / VG);
+  T pN_ = pO_ - dt2 * (T)D.Cp * exner_fac(D, pik, pb, kh + GH, pC_) * (rh / VG - Dth);
+  T rF_ = rC_ + nu * (rN_ - T(2) * rC_ + rO_);
+  T pF_ = pC_ + nu * (pN_ - T(2) * pC_ + pO_);
+  for (int a = 0; a < R.count; a++) {
+    int m = members[R.start + a];
+    int i = m % nx, j = (m / nx) % ny, k = m / (nx * ny);
+    long long o = po(i, j, k);
+    ((T *)D.f[rN][0])[o] = rN_;
+    ((T *)D.f[rN][1])[o] = pN_;
+    ((T *)D.f[rF][0])[o] = rF_;
+    ((T *)D.f[rF][1])[o] = pF_;
+  }
+}
+
+// ------------------------------------------------------------------ velocity diagnosis
+// Corner velocity of the new level from wrapped interior positions (the new
+// level's ghost frames are not filled yet).
+template <typename T>
+__device__ __forceinline__ T rho_new_corner(const DomDev &D, const T *rp, const T *rhob, int I, int J, int K) {
+  int Im = wrapi(I - 1, D.nx), I0 = wrapi(I, D.nx), Jm = wrapi(J - 1, D.ny), J0 = wrapi(J, D.ny);
+  return rho8(cell_rho(D, rp, rhob, Im, Jm, K - 1), cell_rho(D, rp, rhob, I0, Jm, K - 1),
+              cell_rho(D, rp, rhob, Im, J0, K - 1), cell_rho(D, rp, rhob, I0, J0, K - 1),
+              cell_rho(D, rp, rhob, Im, Jm, K), cell_rho(D, rp, rhob, I0, Jm, K),
+              cell_rho(D, rp, rhob, Im, J0, K), cell_rho(D, rp, rhob, I0, J0, K));
+}
+
+template <typename T>
+__global__ void k_diag(const DomDev *__restrict__ doms, const ColItem *__restrict__ cols, int ncols, int rV,
+                       int rC, int rO, int rF, int first, int filter) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= ncols) return;
+  const ColItem CI = cols[t];
+  const DomDev &D = doms[CI.dom];
+  const T nu = (T)(first ? 0.0 : D.ra_nu);
+  const int I = CI.I, J = CI.J;
+  const T *rp = (const T *)D.f[rV][0];
+  T *M[3] = {(T *)D.f[rV][2], (T *)D.f[rV][3], (T *)D.f[rV][4]};
+  const T *rhob = (const T *)D.rhob;
+  const long long q = (long long)J * D.nx + I;
+  auto vel = [&](int i, int j, int K, T u[3]) {
+    int wi = wrapi(i, D.nx), wj = wrapi(j, D.ny);
+    T rc = rho_new_corner(D, rp, rhob, wi, wj, K);
+    long long o = pidx(D, wi, wj, K);
+    u[0] = M[0][o] / rc;
+    u[1] = M[1][o] / rc;
+    u[2] = M[2][o] / rc;
+  };
+  // boundary point: bilinear in the nearest plane, then free-slip projection
+  int K = D.bK[q], i0 = D.bI[q], j0 = D.bJ[q];
+  T a = (T)D.ba[q], b = (T)D.bb[q];
+  T w[4] = {(T(1) - a) * (T(1) - b), a * (T(1) - b), (T(1) - a) * b, a * b};
+  int ci[4] = {i0, i0 + 1, i0, i0 + 1}, cj[4] = {j0, j0, j0 + 1, j0 + 1};
+  T uN[3] = {0, 0, 0};
+  for (int s = 0; s < 4; s++) {
+    if (w[s] == T(0)) continue;
+    T u[3];
+    vel(ci[s], cj[s], K, u);
+    for (int d = 0; d < 3; d++) uN[d] += w[s] * u[d];
+  }
+  T n[3] = {(T)D.bn[3 * q], (T)D.bn[3 * q + 1], (T)D.bn[3 * q + 2]};
+  T ub[3];
+  if (D.bc_slip) {
+    T un = uN[0] * n[0] + uN[1] * n[1] + uN[2] * n[2];
+    for (int d = 0; d < 3; d++) ub[d] = uN[d] - un * n[d];
+  } else {
+    ub[0] = ub[1] = ub[2] = 0;
+  }
+  T *ubv = (T *)D.ub[rV];
+  for (int d = 0; d < 3; d++) ubv[3 * q + d] = ub[d];
+  T *mcur[3] = {(T *)D.f[rC][2], (T *)D.f[rC][3], (T *)D.f[rC][4]};
+  T *mold[3] = {(T *)D.f[rO][2], (T *)D.f[rO][3], (T *)D.f[rO][4]};
+  T *mflt[3] = {(T *)D.f[rF][2], (T *)D.f[rF][3], (T *)D.f[rF][4]};
+  auto store = [&](int KK, const T u[3]) {
+    long long o = pidx(D, I, J, KK);
+    T rc = rho_new_corner(D, rp, rhob, I, J, KK);
+    for (int d = 0; d < 3; d++) {
+      T mv = rc * u[d];
+      M[d][o] = mv;
+      if (filter) {
+        T mc = mcur[d][o];
+        mflt[d][o] = mc + nu * (mv - T(2) * mc + mold[d][o]);
+      }
+    }
+  };
+  // corner levels from -GH+1: the density of corner K averages cell levels
+  // K-1 and K, and the lowest padded cell level is -GH
+  const int kt = D.ktop[q];
+  for (int KK = -GH + 1; KK <= kt; KK++) {
+    long long p = pidx(D, I, J, KK);
+    int8_t v = D.vcls[p];
+    if (v == V_PRED) continue;
+    T u[3];
+    if (v == V_UG) {
+      u[0] = ub[0]; u[1] = ub[1]; u[2] = ub[2];
+    } else {
+      int ka = D.mK[p];
+      T gm = (T)D.mg[p];
+      T ua[3];
+      vel(I, J, ka, ua);
+      for (int d = 0; d < 3; d++) u[d] = gm * ua[d] + (T(1) - gm) * ub[d];
+    }
+    store(KK, u);
+  }
+  T ul[3];
+  vel(I, J, D.nz - 1, ul);
+  ul[2] = 0;
+  for (int KK = D.nz; KK < D.nz + GH; KK++) store(KK, ul);
+}
+
+// ------------------------------------------------------------------ ghost frames
+// Periodic copy of the lateral ghost frame (cyclic lateral boundaries, Sec 3)
+// for 5 fields of two levels; blockIdx.y = level*5 + field, blockIdx.z = domain.
+template <typename T>
+__global__ void k_ghost(const DomDev *__restrict__ doms, int r1, int r2) {
+  const DomDev &D = doms[blockIdx.z];
+  const long long frame = (long long)D.px * D.py - (long long)D.nx * D.ny;
+  const long long n = frame * D.pz;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int lev = blockIdx.y / NFIELD, fld = blockIdx.y % NFIELD;
+  T *a = (T *)D.f[lev == 0 ? r1 : r2][fld];
+  long long q = t % frame;
+  int kz = (int)(t / frame);
+  int gi, gj;
+  long long band = (long long)GH * D.px;
+  if (q < band) {
+    gj = (int)(q / D.px) - GH;
+    gi = (int)(q % D.px) - GH;
+  } else if (q < 2 * band) {
+    q -= band;
+    gj = D.ny + (int)(q / D.px);
+    gi = (int)(q % D.px) - GH;
+  } else {
+    q -= 2 * band;
+    gj = (int)(q / (2 * GH));
+    int r = (int)(q % (2 * GH));
+    gi = r < GH ? r - GH : D.nx + (r - GH);
+  }
+  long long dst = ((long long)kz * D.py + (gj + GH)) * D.px + (gi + GH);
+  long long src = ((long long)kz * D.py + (wrapi(gj, D.ny) + GH)) * D.px + (wrapi(gi, D.nx) + GH);
+  a[dst] = a[src];
+}
+
+// initial momentum rho_corner * U on the predicted points of level r
+template <typename T>
+__global__ void k_init_momentum(const DomDev *__restrict__ dom, int r, double U) {
+  const DomDev &D = *dom;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long n = (long long)D.nx * D.ny * D.nz;
+  if (t >= n) return;
+  int I = (int)(t % D.nx), J = (int)((t / D.nx) % D.ny), K = (int)(t / ((long long)D.nx * D.ny));
+  long long o = pidx(D, I, J, K);
+  if (D.vcls[o] != V_PRED) return;
+  const T *rp = (const T *)D.f[r][0];
+  T rc = rho_new_corner(D, rp, (const T *)D.rhob, I, J, K);
+  ((T *)D.f[r][2])[o] = rc * (T)U;
+}
+
+// ------------------------------------------------------------------ diagnostics
+// Neumaier-compensated mass sum and maxima; fixed block count and fixed
+// reduction order, so the result does not depend on scheduling.
+template <typename T>
+struct NSum {
+  T s, c;
+  __device__ void add(T x) {
+    T t = s + x;
+    if (fabs((double)s) >= fabs((double)x)) c += (s - t) + x;
+    else c += (x - t) + s;
+    s = t;
+  }
+};
+
+constexpr int DIAG_BLOCKS = 256, DIAG_TPB = 256;
+
+template <typename T>
+__global__ void k_diag_partial(const DomDev *__restrict__ dom, int r, double *part) {
+  const DomDev &D = *dom;
+  const T *rp = (const T *)D.f[r][0];
+  const T *pp = (const T *)D.f[r][1];
+  const T *M[3] = {(const T *)D.f[r][2], (const T *)D.f[r][3], (const T *)D.f[r][4]};
+  const T *rhob = (const T *)D.rhob;
+  const double V0 = D.dx * D.dy * D.dz;
+  long long n = (long long)D.nx * D.ny * D.nz;
+  NSum<T> acc{0, 0};
+  double mu = 0, mw = 0, bad = 0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t % D.nx), j = (int)((t / D.nx) % D.ny), k = (int)(t / ((long long)D.nx * D.ny));
+    long long o = pidx(D, i, j, k);
+    T rv = rp[o];
+    acc.add((T)(D.vf[t] * V0) * rv);
+    T vals[5] = {rv, pp[o], M[0][o], M[1][o], M[2][o]};
+    for (int a = 0; a < 5; a++)
+      if (!isfinite((double)vals[a])) bad += 1;
+    if (D.vcls[o] == V_PRED) {
+      T rc = rho_new_corner(D, rp, rhob, i, j, k);
+      double uu = fabs((double)(M[0][o] / rc)), ww = fabs((double)(M[2][o] / rc));
+      mu = fmax(mu, uu);
+      mw = fmax(mw, ww);
+    }
+  }
+  __shared__ double sh[5][DIAG_TPB];
+  sh[0][threadIdx.x] = (double)acc.s;
+  sh[1][threadIdx.x] = (double)acc.c;
+  sh[2][threadIdx.x] = mu;
+  sh[3][threadIdx.x] = mw;
+  sh[4][threadIdx.x] = bad;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    NSum<double> S{0, 0};
+    double cc = 0, a2 = 0, a3 = 0, a4 = 0;
+    for (int a = 0; a < DIAG_TPB; a++) {
+      S.add(sh[0][a]);
+      cc += sh[1][a];
+      a2 = fmax(a2, sh[2][a]);
+      a3 = fmax(a3, sh[3][a]);
+      a4 += sh[4][a];
+    }
+    part[5 * blockIdx.x + 0] = S.s;
+    part[5 * blockIdx.x + 1] = S.c + cc;
+    part[5 * blockIdx.x + 2] = a2;
+    part[5 * blockIdx.x + 3] = a3;
+    part[5 * blockIdx.x + 4] = a4;
+  }
+}
+
+__global__ void k_diag_final(const double *part, int nb, double *out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  NSum<double> S{0, 0};
+  double cc = 0, a2 = 0, a3 = 0, a4 = 0;
+  for (int b = 0; b < nb; b++) {
+    S.add(part[5 * b]);
+    cc += part[5 * b + 1];
+    a2 = fmax(a2, part[5 * b + 2]);
+    a3 = fmax(a3, part[5 * b + 3]);
+    a4 += part[5 * b + 4];
+  }
+  out[0] = S.s + (S.c + cc);
+  out[1] = S.c + cc;
+  out[2] = a2;
+  out[3] = a3;
+  out[4] = a4;
+}
+
+// ------------------------------------------------------------------ launchers
+namespace {
+template <typename T>
+cudaError_t ensure_full_attr() {
+  static bool done = false;
+  if (!done) {
+    cudaError_t e = cudaFuncSetAttribute(k_full<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)sizeof(FullSmem<T>));
+    if (e != cudaSuccess) return e;
+    done = true;
+  }
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t full_t(const StepLaunch &L, int rO, int rC, int rN, int rF, int first, cudaStream_t st) {
+  cudaError_t e = ensure_full_attr<T>();
+  if (e != cudaSuccess) return e;
+  if (L.nitems > 0)
+    k_full<T><<<L.nitems, TX * TY, sizeof(FullSmem<T>), st>>>(L.d_doms, L.items, rO, rC, rN, rF, first);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t groups_t(const StepLaunch &L, int rO, int rC, int rN, int rF, int first, cudaStream_t st) {
+  if (L.ngroups > 0)
+    k_groups<T><<<(L.ngroups + 127) / 128, 128, 0, st>>>(L.d_doms, L.groups, L.ngroups, L.members, rO, rC, rN,
+                                                          rF, first);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t ghost_t(const StepLaunch &L, int r1, int r2, cudaStream_t st) {
+  if (L.ndom <= 0 || L.ghost_points <= 0) return cudaSuccess;
+  dim3 grid((unsigned)((L.ghost_points + 255) / 256), 2 * NFIELD, L.ndom);
+  k_ghost<T><<<grid, 256, 0, st>>>(L.d_doms, r1, r2);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_base(const DomDev &D, int prec, double theta0, double N, double p_surf, double sponge_frac,
+                        double tau_max, cudaStream_t st) {
+  unsigned nb = (unsigned)((D.pz + 127) / 128);
+  if (prec == CC_FP64)
+    k_base<double><<<nb, 128, 0, st>>>(D, theta0, N, p_surf, sponge_frac, tau_max, (double *)D.rhob,
+                                       (double *)D.pb, (double *)D.thb, (double *)D.pik, (double *)D.rhobc,
+                                       (double *)D.tau);
+  else
+    k_base<float><<<nb, 128, 0, st>>>(D, theta0, N, p_surf, sponge_frac, tau_max, (float *)D.rhob,
+                                      (float *)D.pb, (float *)D.thb, (float *)D.pik, (float *)D.rhobc,
+                                      (float *)D.tau);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_full(const StepLaunch &L, int prec, int rO, int rC, int rN, int rF, int first,
+                        cudaStream_t st) {
+  return prec == CC_FP64 ? full_t<double>(L, rO, rC, rN, rF, first, st) : full_t<float>(L, rO, rC, rN, rF, first, st);
+}
+
+cudaError_t launch_groups(const StepLaunch &L, int prec, int rO, int rC, int rN, int rF, int first,
+                          cudaStream_t st) {
+  return prec == CC_FP64 ? groups_t<double>(L, rO, rC, rN, rF, first, st)
+                         : groups_t<float>(L, rO, rC, rN, rF, first, st);
+}
+
+cudaError_t launch_diagnose(const StepLaunch &L, int prec, int rV, int rC, int rO, int rF, int first, int filter,
+                            cudaStream_t st) {
+  if (L.ncols <= 0) return cudaSuccess;
+  if (prec == CC_FP64)
+    k_diag<double><<<(L.ncols + 127) / 128, 128, 0, st>>>(L.d_doms, L.cols, L.ncols, rV, rC, rO, rF, first, filter);
+  else
+    k_diag<float><<<(L.ncols + 127) / 128, 128, 0, st>>>(L.d_doms, L.cols, L.ncols, rV, rC, rO, rF, first, filter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ghost(const StepLaunch &L, int prec, int r1, int r2, cudaStream_t st) {
+  return prec == CC_FP64 ? ghost_t<double>(L, r1, r2, st) : ghost_t<float>(L, r1, r2, st);
+}
+
+cudaError_t launch_init_momentum(const DomDev &D, const DomDev *d_dom, int prec, int r, double U, cudaStream_t st) {
+  long long n = (long long)D.nx * D.ny * D.nz;
+  unsigned nb = (unsigned)((n + 255) / 256);
+  if (prec == CC_FP64) k_init_momentum<double><<<nb, 256, 0, st>>>(d_dom, r, U);
+  else k_init_momentum<float><<<nb, 256, 0, st>>>(d_dom, r, U);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_diag_reduce(const DomDev &D, const DomDev *d_dom, int prec, int r, double *d_out,
+                               cudaStream_t st) {
+  double *part = d_out + 8;
+  if (prec == CC_FP64) k_diag_partial<double><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(d_dom, r, part);
+  else k_diag_partial<float><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(d_dom, r, part);
+  k_diag_final<<<1, 32, 0, st>>>(part, DIAG_BLOCKS, d_out);
+  return cudaGetLastError();
+}
+
+}  // namespace cc

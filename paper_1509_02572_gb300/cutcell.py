@@ -1,0 +1,246 @@
+"""ctypes binding of libcutcell.so (include/cutcell.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Importing works without a GPU; creating a model needs the built
+library and a CUDA device, and fails loudly otherwise (there is no CPU path).
+"""
+from __future__ import annotations
+
+import ctypes as ct
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcutcell.so")
+
+CC_OK, CC_EINVAL, CC_ECUDA, CC_EGEOM, CC_ENUMERIC, CC_ENOMEM, CC_ESTATE = range(7)
+CC_FP64, CC_FP32 = 0, 1
+CC_RHOP, CC_PP, CC_MX, CC_MY, CC_MZ, CC_UB = range(6)
+STATUS = {0: "CC_OK", 1: "CC_EINVAL", 2: "CC_ECUDA", 3: "CC_EGEOM", 4: "CC_ENUMERIC", 5: "CC_ENOMEM",
+          6: "CC_ESTATE"}
+HOST_GZ = 2
+
+# every entry point of include/cutcell.h
+EXPORTS = ("cc_create", "cc_destroy", "cc_last_error", "cc_set_terrain", "cc_build_geometry",
+           "cc_get_geometry", "cc_get_stencils", "cc_get_groups", "cc_init_state", "cc_upload_state",
+           "cc_download_state", "cc_step", "cc_diagnostics", "cc_synchronize", "cc_last_launch_count",
+           "cc_profile_enable", "cc_profile_read", "cc_profile_reset")
+CC_K_FULL, CC_K_GROUPS, CC_K_DIAGNOSE, CC_K_GHOST = range(4)
+KERNEL_NAMES = {CC_K_FULL: "k_full", CC_K_GROUPS: "k_groups", CC_K_DIAGNOSE: "k_diag", CC_K_GHOST: "k_ghost"}
+
+
+class CCConfig(ct.Structure):
+    _fields_ = [("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int),
+                ("dx", ct.c_double), ("dy", ct.c_double), ("dz", ct.c_double),
+                ("dt", ct.c_double),
+                ("U", ct.c_double), ("N", ct.c_double), ("theta0", ct.c_double),
+                ("p_surf", ct.c_double), ("p0", ct.c_double), ("g", ct.c_double),
+                ("R", ct.c_double), ("cp", ct.c_double),
+                ("ra_nu", ct.c_double), ("c4", ct.c_double), ("sponge_frac", ct.c_double),
+                ("tau_max", ct.c_double), ("bc_slip", ct.c_int)]
+
+
+class CCDiag(ct.Structure):
+    _fields_ = [("mass", ct.c_double), ("mass_comp", ct.c_double), ("max_u", ct.c_double),
+                ("max_w", ct.c_double), ("nonfinite", ct.c_longlong), ("steps", ct.c_longlong)]
+
+
+class CutcellError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libcutcell.so; raise if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    L = ct.CDLL(path)
+    vp, i, d = ct.c_void_p, ct.c_int, ct.c_double
+    L.cc_create.argtypes = [ct.POINTER(CCConfig), i, i, vp, ct.POINTER(vp)]
+    L.cc_destroy.argtypes = [vp]
+    L.cc_last_error.restype = ct.c_char_p
+    L.cc_last_error.argtypes = [vp]
+    L.cc_set_terrain.argtypes = [vp, i, vp]
+    L.cc_build_geometry.argtypes = [vp]
+    L.cc_get_geometry.argtypes = [vp, i] + [vp] * 7
+    L.cc_get_stencils.argtypes = [vp, i] + [vp] * 8
+    L.cc_get_groups.argtypes = [vp, i, ct.POINTER(i), ct.POINTER(i), vp, vp, vp]
+    L.cc_init_state.argtypes = [vp]
+    L.cc_upload_state.argtypes = [vp, i, i, i, vp]
+    L.cc_download_state.argtypes = [vp, i, i, i, vp]
+    L.cc_step.argtypes = [vp, i]
+    L.cc_diagnostics.argtypes = [vp, i, ct.POINTER(CCDiag)]
+    L.cc_synchronize.argtypes = [vp]
+    L.cc_last_launch_count.restype = ct.c_longlong
+    L.cc_last_launch_count.argtypes = [vp]
+    L.cc_profile_enable.argtypes = [vp, i]
+    L.cc_profile_read.argtypes = [vp, i, ct.POINTER(d), ct.POINTER(ct.c_longlong)]
+    L.cc_profile_reset.argtypes = [vp]
+    _lib = L
+    return L
+
+
+def _p(a: np.ndarray | None):
+    return None if a is None else a.ctypes.data_as(ct.c_void_p)
+
+
+def config_from(cfg) -> CCConfig:
+    c = CCConfig()
+    for name, _ in CCConfig._fields_:
+        setattr(c, name, getattr(cfg, name))
+    return c
+
+
+def _current_stream():
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return ct.c_void_p(torch.cuda.current_stream().cuda_stream)
+    except Exception:
+        pass
+    return None
+
+
+class Model:
+    """Ensemble of periodic domains advanced on the GPU through the C ABI."""
+
+    def __init__(self, cfgs, precision: int = CC_FP64, stream=None):
+        self.L = load()
+        if not isinstance(cfgs, (list, tuple)):
+            cfgs = [cfgs]
+        self.cfgs = list(cfgs)
+        arr = (CCConfig * len(cfgs))(*[config_from(c) for c in cfgs])
+        self._arr = arr
+        if stream is None:
+            stream = _current_stream()
+        self.stream = stream
+        h = ct.c_void_p()
+        st = self.L.cc_create(arr, len(cfgs), precision, stream, ct.byref(h))
+        if st != CC_OK:
+            raise CutcellError(st, self.L.cc_last_error(None).decode())
+        self.h = h
+        self.precision = precision
+
+    def _check(self, st):
+        if st != CC_OK:
+            raise CutcellError(st, self.L.cc_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None) and self.h.value:
+            self.L.cc_destroy(self.h)
+            self.h = ct.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---------------------------------------------------------------- set-up
+    def set_terrain(self, d: int, h: np.ndarray):
+        h = np.ascontiguousarray(h, dtype=np.float64)
+        c = self.cfgs[d]
+        assert h.shape == (c.ny, c.nx)
+        self._check(self.L.cc_set_terrain(self.h, d, _p(h)))
+
+    def build_geometry(self):
+        self._check(self.L.cc_build_geometry(self.h))
+
+    def geometry(self, d: int = 0) -> dict:
+        c = self.cfgs[d]
+        cs = (c.nz, c.ny, c.nx)
+        out = dict(vf=np.zeros(cs), ax=np.zeros(cs), ay=np.zeros(cs), az=np.zeros((c.nz + 1, c.ny, c.nx)),
+                   cls=np.zeros(cs, np.int8), root=np.zeros(cs, np.int32),
+                   vcls=np.zeros((c.nz + 1 + 2 * HOST_GZ, c.ny, c.nx), np.int8))
+        self._check(self.L.cc_get_geometry(self.h, d, *[_p(out[k]) for k in
+                                                         ("vf", "ax", "ay", "az", "cls", "root", "vcls")]))
+        return out
+
+    def stencils(self, d: int = 0) -> dict:
+        c = self.cfgs[d]
+        q = (c.ny, c.nx)
+        ps = (c.nz + 1 + 2 * HOST_GZ, c.ny, c.nx)
+        out = dict(bK=np.zeros(q, np.int32), bI=np.zeros(q, np.int32), bJ=np.zeros(q, np.int32),
+                   ba=np.zeros(q), bb=np.zeros(q), bn=np.zeros(q + (3,)), mK=np.zeros(ps, np.int32),
+                   mg=np.zeros(ps))
+        self._check(self.L.cc_get_stencils(self.h, d, *[_p(out[k]) for k in
+                                                         ("bK", "bI", "bJ", "ba", "bb", "bn", "mK", "mg")]))
+        return out
+
+    def groups(self, d: int = 0):
+        ng, nm = ct.c_int(), ct.c_int()
+        self._check(self.L.cc_get_groups(self.h, d, ct.byref(ng), ct.byref(nm), None, None, None))
+        host = np.zeros(ng.value, np.int32)
+        start = np.zeros(ng.value + 1, np.int32)
+        mem = np.zeros(nm.value, np.int32)
+        self._check(self.L.cc_get_groups(self.h, d, ct.byref(ng), ct.byref(nm), _p(host), _p(start), _p(mem)))
+        return host, start, mem
+
+    # ---------------------------------------------------------------- state
+    def init_state(self):
+        self._check(self.L.cc_init_state(self.h))
+
+    def _shape(self, d, field):
+        c = self.cfgs[d]
+        if field in (CC_RHOP, CC_PP):
+            return (c.nz, c.ny, c.nx)
+        if field == CC_UB:
+            return (c.ny, c.nx, 3)
+        return (c.nz + 1 + 2 * HOST_GZ, c.ny, c.nx)
+
+    def download(self, d: int, field: int, level: int = 1, out: np.ndarray | None = None) -> np.ndarray:
+        shape = self._shape(d, field)
+        if out is None:
+            out = np.zeros(shape, np.float64)
+        assert out.shape == shape and out.dtype == np.float64 and out.flags.c_contiguous
+        self._check(self.L.cc_download_state(self.h, d, field, level, _p(out)))
+        return out
+
+    def download_ptr(self, d: int, field: int, level: int, ptr: int):
+        self._check(self.L.cc_download_state(self.h, d, field, level, ct.c_void_p(ptr)))
+
+    def upload(self, d: int, field: int, level: int, a: np.ndarray):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        assert a.shape == self._shape(d, field)
+        self._check(self.L.cc_upload_state(self.h, d, field, level, _p(a)))
+
+    def upload_ptr(self, d: int, field: int, level: int, ptr: int):
+        self._check(self.L.cc_upload_state(self.h, d, field, level, ct.c_void_p(ptr)))
+
+    def step(self, n: int = 1):
+        self._check(self.L.cc_step(self.h, int(n)))
+
+    def synchronize(self):
+        self._check(self.L.cc_synchronize(self.h))
+
+    def diagnostics(self, d: int = 0, check: bool = True) -> dict:
+        g = CCDiag()
+        st = self.L.cc_diagnostics(self.h, d, ct.byref(g))
+        if check:
+            self._check(st)
+        return dict(mass=g.mass, mass_comp=g.mass_comp, max_u=g.max_u, max_w=g.max_w,
+                    nonfinite=g.nonfinite, steps=g.steps, status=st)
+
+    @property
+    def last_launch_count(self) -> int:
+        return int(self.L.cc_last_launch_count(self.h))
+
+    def profile(self, on: bool = True):
+        self._check(self.L.cc_profile_enable(self.h, 1 if on else 0))
+
+    def profile_reset(self):
+        self._check(self.L.cc_profile_reset(self.h))
+
+    def profile_read(self, kernel: int):
+        ms, n = ct.c_double(), ct.c_longlong()
+        self._check(self.L.cc_profile_read(self.h, kernel, ct.byref(ms), ct.byref(n)))
+        return ms.value, n.value

@@ -143,7 +143,7 @@ def ensemble_configs(n: int = 64, seed: int = 1509) -> list[RunConfig]:
         top = nz * d
         if h0 > 0.5 * top:
             h0 = 0.5 * top
-        dt = 0.15 * d / 200.0 * (20.0 / max(U, 10.0)) ** 0.0
+        dt = 0.15 * d / 200.0
         out.append(RunConfig(f"ens{e}-{kind}-{nx}x{nx}x{nz}", nx, nx, nz, d, d, d, dt, 500,
                              kind, h0, a, U=U, N=N))
     return out

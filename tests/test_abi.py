@@ -1,0 +1,65 @@
+"""The C ABI library builds for sm_103a, loads without a GPU and exports every
+entry point that include/cutcell.h declares (no compute call here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", f)).read()
+            txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+            names |= set(re.findall(r"\b(cc_[a-z_0-9]+)\s*\(", txt))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1509_02572_gb300 import build
+    path = build.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    assert "cc_create" in names and "cc_step" in names and len(names) >= 14
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in _declared():
+        assert hasattr(lib, name), name
+
+
+def test_binding_lists_every_export():
+    from paper_1509_02572_gb300 import cutcell
+    assert set(_declared()) <= set(cutcell.EXPORTS)
+
+
+def test_create_rejects_bad_config_without_touching_the_gpu(lib):
+    # argument validation happens before any CUDA call
+    from paper_1509_02572_gb300 import cutcell, workloads as W
+    L = cutcell.load()
+    bad = cutcell.config_from(W.C1_BELL.replace(nx=2))
+    h = ctypes.c_void_p()
+    st = L.cc_create(ctypes.byref(bad), 1, cutcell.CC_FP64, None, ctypes.byref(h))
+    assert st == cutcell.CC_EINVAL and not h.value
+    assert b"nx" in L.cc_last_error(None)
+    st = L.cc_create(ctypes.byref(cutcell.config_from(W.C1_BELL)), 1, 7, None, ctypes.byref(h))
+    assert st == cutcell.CC_EINVAL
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    from paper_1509_02572_gb300 import cutcell
+    saved = cutcell._lib
+    cutcell._lib = None
+    try:
+        with pytest.raises(RuntimeError):
+            cutcell.load(str(tmp_path / "missing.so"))
+    finally:
+        cutcell._lib = saved

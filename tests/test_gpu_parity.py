@@ -1,0 +1,243 @@
+"""CUDA path against the FP64 oracle, through the C ABI (needs a GB300)."""
+import numpy as np
+import pytest
+
+from paper_1509_02572_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GZ_HOST = 2
+
+
+@pytest.fixture(scope="module")
+def cc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1509_02572_gb300 import build, cutcell
+    build.build()
+    cutcell.load()
+    return cutcell
+
+
+def gpu_model(cc, cfgs, prec=None, heights=None):
+    prec = cc.CC_FP64 if prec is None else prec
+    cfgs = cfgs if isinstance(cfgs, list) else [cfgs]
+    m = cc.Model(cfgs, prec)
+    for d, c in enumerate(cfgs):
+        m.set_terrain(d, c.heights() if heights is None else heights[d])
+    m.build_geometry()
+    return m
+
+
+def expected_groups(og):
+    cls, root = og["cls"].ravel(), og["root"].ravel()
+    sel = (cls == 2) | (cls == 3)
+    hosts = np.unique(root[sel])
+    start = [0]
+    mem = []
+    for h in hosts:
+        mm = np.flatnonzero(root == h)
+        mem.extend(mm.tolist())
+        start.append(len(mem))
+    return hosts.astype(np.int32), np.array(start, np.int32), np.array(mem, np.int32)
+
+
+GEOM_CASES = [W.C1_BELL, W.SMALL_HEMI, W.C2_HEMI]
+
+
+@pytest.mark.parametrize("cfg", GEOM_CASES, ids=lambda c: c.name)
+def test_geometry_bit_exact(cc, oracle_mod, cfg):
+    om = oracle_mod.Model(cfg)
+    og, op = om.geometry(), om.points()
+    m = gpu_model(cc, cfg)
+    g, s = m.geometry(), m.stencils()
+    # integer maps: bit-exact
+    assert np.array_equal(g["cls"], og["cls"])
+    assert np.array_equal(g["root"], og["root"])
+    assert np.array_equal(g["vcls"], op["vcls"])
+    for k in ("bK", "bI", "bJ"):
+        assert np.array_equal(s[k], op[k]), k
+    mf = op["vcls"] == 2
+    assert np.array_equal(s["mK"][mf], op["mK"][mf])
+    # compacted merge-group lists: bit-exact
+    host, start, mem = m.groups()
+    eh, es, em = expected_groups(og)
+    assert np.array_equal(host, eh) and np.array_equal(start, es) and np.array_equal(mem, em)
+    # volumes, apertures and stencil weights: same operations in the same order
+    for k in ("vf", "ax", "ay", "az"):
+        assert np.max(np.abs(g[k] - og[k])) <= 1e-14, k
+    assert np.max(np.abs(s["ba"] - op["ba"])) <= 1e-14
+    assert np.max(np.abs(s["bb"] - op["bb"])) <= 1e-14
+    assert np.max(np.abs(s["bn"] - op["bn"])) <= 1e-15
+    assert np.max(np.abs(s["mg"][mf] - op["mg"][mf])) <= 1e-14
+    m.close()
+
+
+FIELDS = None
+
+
+def _compare(cc, oracle_mod, m, om, d=0, rel_l2=1e-10, rel_inf=1e-8, report=None):
+    pairs = [(cc.CC_RHOP, oracle_mod.F_RHOP), (cc.CC_PP, oracle_mod.F_PP), (cc.CC_MX, oracle_mod.F_MX),
+             (cc.CC_MY, oracle_mod.F_MY), (cc.CC_MZ, oracle_mod.F_MZ), (cc.CC_UB, oracle_mod.F_UB)]
+    errs = {}
+    for fg, fo in pairs:
+        for level in ((1,) if fg == cc.CC_UB else (0, 1)):
+            a = m.download(d, fg, level)
+            b = om.field(fo, level)
+            scale = np.abs(b).max()
+            if scale == 0.0:
+                assert np.abs(a).max() == 0.0, (fg, level)
+                continue
+            l2 = np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2))
+            li = np.abs(a - b).max() / scale
+            errs[(fg, level)] = (l2, li)
+            if report is None:
+                assert l2 <= rel_l2 and li <= rel_inf, (fg, level, l2, li)
+    return errs
+
+
+@pytest.mark.parametrize("cfg,steps", [(W.C1_BELL, 100), (W.SMALL_HEMI, 40),
+                                       (W.SMALL_HEMI.replace(bc_slip=0, name="hemi-noslip"), 10)],
+                         ids=["bell-100", "hemisphere-40", "hemisphere-noslip-10"])
+def test_fp64_step_parity(cc, oracle_mod, cfg, steps):
+    om = oracle_mod.Model(cfg)
+    om.init_state()
+    m = gpu_model(cc, cfg)
+    m.init_state()
+    _compare(cc, oracle_mod, m, om, rel_l2=1e-13, rel_inf=1e-11)  # initial diagnosis
+    om.step(1)
+    m.step(1)
+    _compare(cc, oracle_mod, m, om, rel_l2=1e-12, rel_inf=1e-10)  # forward-Euler start
+    om.step(steps - 1)
+    m.step(steps - 1)
+    _compare(cc, oracle_mod, m, om)
+    m.close()
+
+
+def test_fp64_parity_full_size_hemisphere(cc, oracle_mod):
+    """The 128x128x64 hemisphere at full size (the benchmark's domain), as the
+    benchmark launches it, a few steps against the oracle element by element."""
+    cfg = W.C2_HEMI
+    om = oracle_mod.Model(cfg)
+    om.init_state()
+    m = gpu_model(cc, cfg)
+    m.init_state()
+    om.step(4)
+    m.step(4)
+    _compare(cc, oracle_mod, m, om)
+    m.close()
+
+
+def test_upload_download_roundtrip_and_resume(cc, oracle_mod):
+    """A state uploaded from the oracle continues exactly like the oracle."""
+    cfg = W.SMALL_HEMI
+    om = oracle_mod.Model(cfg)
+    om.init_state()
+    om.step(7)
+    m = gpu_model(cc, cfg)
+    m.init_state()
+    m.step(1)  # leave the forward-Euler start behind
+    for fg, fo in [(cc.CC_RHOP, oracle_mod.F_RHOP), (cc.CC_PP, oracle_mod.F_PP), (cc.CC_MX, oracle_mod.F_MX),
+                   (cc.CC_MY, oracle_mod.F_MY), (cc.CC_MZ, oracle_mod.F_MZ)]:
+        for level in (0, 1):
+            a = om.field(fo, level)
+            m.upload(0, fg, level, a)
+            assert np.array_equal(m.download(0, fg, level), a)
+    m.upload(0, cc.CC_UB, 1, om.field(oracle_mod.F_UB, 1))
+    om.step(5)
+    m.step(5)
+    _compare(cc, oracle_mod, m, om)
+    m.close()
+
+
+def test_rest_state_exact_on_gpu(cc):
+    cfg = W.SMALL_HEMI.replace(U=0.0)
+    for prec in (cc.CC_FP64, cc.CC_FP32):
+        m = gpu_model(cc, cfg, prec)
+        m.init_state()
+        m.step(20)
+        for f in (cc.CC_RHOP, cc.CC_PP, cc.CC_MX, cc.CC_MY, cc.CC_MZ, cc.CC_UB):
+            assert np.abs(m.download(0, f)).max() == 0.0, (prec, f)
+        m.close()
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+def test_mass_conservation_on_gpu(cc, prec, tol):
+    cfg = W.SMALL_HEMI
+    m = gpu_model(cc, cfg, cc.CC_FP64 if prec == "fp64" else cc.CC_FP32)
+    m.init_state()
+    d0 = m.diagnostics()
+    m.step(60)
+    d1 = m.diagnostics()
+    rp = m.download(0, cc.CC_RHOP)
+    scale = np.abs(rp).max() * cfg.dx * cfg.dy * cfg.dz * cfg.cells
+    assert abs(d1["mass"] - d0["mass"]) <= tol * scale, (d0, d1, scale)
+    assert d1["nonfinite"] == 0 and d1["max_u"] > 5.0
+    m.close()
+
+
+def test_fp32_error_against_oracle(cc, oracle_mod):
+    """FP32 perturbation form: per-field relative L2 / Linf against the oracle."""
+    cfg = W.C1_BELL
+    om = oracle_mod.Model(cfg)
+    om.init_state()
+    om.step(100)
+    m = gpu_model(cc, cfg, cc.CC_FP32)
+    m.init_state()
+    m.step(100)
+    errs = _compare(cc, oracle_mod, m, om, report=True)
+    for key, (l2, li) in errs.items():
+        assert l2 <= 1e-3 and li <= 1e-2, (key, l2, li)
+    m.close()
+
+
+def test_ensemble_equals_single_domain_runs(cc):
+    """Domains of uneven sizes advanced in one launch give the same bits as
+    each domain advanced alone."""
+    a = W.SMALL_HEMI
+    b = W.C1_BELL.replace(nx=48, ny=40, nz=20, U=7.0, N=0.012, dt=0.12)
+    both = gpu_model(cc, [a, b])
+    both.init_state()
+    both.step(12)
+    for d, c in enumerate((a, b)):
+        one = gpu_model(cc, c)
+        one.init_state()
+        one.step(12)
+        for f in (cc.CC_RHOP, cc.CC_PP, cc.CC_MX, cc.CC_MY, cc.CC_MZ):
+            assert np.array_equal(both.download(d, f), one.download(0, f)), (d, f)
+        one.close()
+    both.close()
+
+
+def test_error_paths(cc):
+    m = cc.Model(W.C1_BELL)
+    with pytest.raises(cc.CutcellError) as e:
+        m.step(1)
+    assert e.value.status == cc.CC_ESTATE
+    with pytest.raises(cc.CutcellError) as e:
+        m.build_geometry()
+    assert e.value.status == cc.CC_ESTATE
+    bad = np.full((W.C1_BELL.ny, W.C1_BELL.nx), -1.0)
+    with pytest.raises(cc.CutcellError) as e:
+        m.set_terrain(0, bad)
+    assert e.value.status == cc.CC_EINVAL
+    m.close()
+
+
+def test_v_shaped_valley_is_a_geometry_error(cc, oracle_mod):
+    """Two steep slopes facing each other make two cells merge into each other
+    (the excluded 'v-shaped valley' of Sec 2.3): both sides report it."""
+    cfg = W.RunConfig("valley", 16, 8, 8, 50.0, 50.0, 50.0, 0.05, 1, "flat", 0.0, 1.0)
+    h = np.zeros((8, 16))
+    h[:, 7] = 120.0
+    h[:, 8] = 20.0
+    h[:, 9] = 120.0
+    with pytest.raises(oracle_mod.OracleError):
+        oracle_mod.Model(cfg, h)
+    m = cc.Model(cfg)
+    m.set_terrain(0, h)
+    with pytest.raises(cc.CutcellError) as e:
+        m.build_geometry()
+    assert e.value.status == cc.CC_EGEOM
+    m.close()
