@@ -43,7 +43,7 @@ def build(force: bool = False) -> str:
         return LIB
     tmp = LIB + f".{os.getpid()}.tmp"
     cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-ffp-contract=off", "-fPIC", "-shared",
-           "-fopenmp", "-o", tmp, SRC, "-lm"]
+           "-o", tmp, SRC, "-lm"]
     subprocess.run(cmd, check=True, cwd=HERE)
     os.replace(tmp, LIB)
     return LIB
