@@ -59,13 +59,15 @@ __device__ __forceinline__ T rho8(T a, T b, T c, T d, T e, T f, T g, T h) {
 
 // rho*theta as a function of pressure, total and perturbation (equation of
 // state, Sec 2.1: rho theta = (p0/R)(p/p0)^(cv/cp)).
+// The product is rounded before the subtraction of the base value (no fused
+// multiply-add), so the perturbation of a resting state is exactly zero.
 __device__ __forceinline__ double theta_tot(const DomDev &D, const double *thb, const double *pb, int kp,
                                             double pp) {
-  return D.p0 / D.R * pow((pb[kp] + pp) / D.p0, D.cvcp);
+  return __dmul_rn(D.p0 / D.R, pow((pb[kp] + pp) / D.p0, D.cvcp));
 }
 __device__ __forceinline__ double theta_pert(const DomDev &D, const double *thb, const double *pb, int kp,
                                              double pp) {
-  return theta_tot(D, thb, pb, kp, pp) - thb[kp];
+  return __dsub_rn(theta_tot(D, thb, pb, kp, pp), thb[kp]);
 }
 __device__ __forceinline__ double exner_fac(const DomDev &D, const double *pik, const double *pb, int kp,
                                             double pp) {
@@ -121,7 +123,7 @@ __global__ void k_base(DomDev D, double theta0, double N, double p_surf, double 
   base((k - 0.5) * D.dz, rm, pm);
   rhob[kp] = (T)r;
   pb[kp] = (T)p;
-  thb[kp] = (T)(D.p0 / D.R * pow(p / D.p0, D.cvcp));
+  thb[kp] = (T)__dmul_rn(D.p0 / D.R, pow(p / D.p0, D.cvcp));
   pik[kp] = (T)pow(p / D.p0, D.kap);
   // corner level K = k: mean of the two adjacent cell levels
   rhobc[kp] = (T)(0.5 * (rm + r));
