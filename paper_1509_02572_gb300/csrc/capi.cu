@@ -210,10 +210,20 @@ cc_status cc_create(const cc_config *cfgs, int n, int precision, void *stream, c
         if ((e = dalloc(H.allocs, &D.f[b][f], D.ncellp * m->esz, m->st)) != cudaSuccess) return bail(e, "field alloc");
       if ((e = dalloc(H.allocs, &D.ub[b], 3 * ncol * m->esz, m->st)) != cudaSuccess) return bail(e, "ub alloc");
     }
-    void *bt[6];
-    for (int a = 0; a < 6; a++)
+    void *bt[7];
+    for (int a = 0; a < 7; a++)
       if ((e = dalloc(H.allocs, &bt[a], (size_t)D.pz * m->esz, m->st)) != cudaSuccess) return bail(e, "base alloc");
-    D.rhob = bt[0]; D.pb = bt[1]; D.thb = bt[2]; D.pik = bt[3]; D.rhobc = bt[4]; D.tau = bt[5];
+    D.rhob = bt[0]; D.pb = bt[1]; D.thb = bt[2]; D.pik = bt[3]; D.rhobc = bt[4]; D.tau = bt[5]; D.ipb = bt[6];
+    // binomial coefficients C(a, n), n = 1..7, of (1 + x)^a - 1
+    for (int w = 0; w < 2; w++) {
+      double a = w == 0 ? D.cvcp : D.kap, cn = 1.0;
+      float *out = w == 0 ? D.sth : D.sex;
+      for (int nn = 1; nn <= 7; nn++) {
+        cn = cn * (a - (nn - 1)) / nn;
+        out[nn - 1] = (float)cn;
+      }
+      out[7] = (float)a;
+    }
     double *h, *vf, *ax, *ay, *az, *ba, *bb, *bn, *mg;
     int8_t *cls, *vcls;
     int32_t *root, *kug, *bK, *bI, *bJ, *mK, *ktop;
@@ -251,10 +261,11 @@ cc_status cc_create(const cc_config *cfgs, int n, int precision, void *stream, c
   // (domain, tile, z-chunk) work list of the full-cell stencil: z is split so
   // that every SM gets several work items
   {
+    const int TILE_Y = full_tile_y(precision);
     long long tiles = 0;
     for (auto &H : m->dom)
       tiles += (long long)((H.D.nx + TILE_X - 1) / TILE_X) * ((H.D.ny + TILE_Y - 1) / TILE_Y);
-    const long long want = 4 * 152;
+    const long long want = 2 * 152;
     long long splits = std::max(1LL, (want + tiles - 1) / tiles);
     std::vector<WorkItem> items;
     for (int d = 0; d < n; d++) {
@@ -487,7 +498,6 @@ cc_status cc_init_state(cc_model *m) {
     CK(m, launch_init_momentum(m->dom[d].D, m->d_doms + d, m->prec, m->r[1], m->dom[d].cfg.U, m->st), "init momentum");
   StepLaunch L = make_launch(m);
   CK(m, launch_diagnose(L, m->prec, m->r[1], m->r[1], m->r[1], m->r[1], 1, 0, m->st), "init diagnose");
-  CK(m, launch_ghost(L, m->prec, m->r[1], m->r[1], m->st), "init ghost");
   CK(m, cudaStreamSynchronize(m->st), "init sync");
   m->nsteps = 0;
   m->state = true;
@@ -530,8 +540,6 @@ cc_status cc_upload_state(cc_model *m, int d, int field, int level, const double
     else k_scatter<float><<<nb256(n), 256, 0, m->st>>>(m->d_stage, (float *)dst, D, nlev, kfirst);
   }
   CK(m, cudaGetLastError(), "upload scatter");
-  StepLaunch L = make_launch(m);
-  CK(m, launch_ghost(L, m->prec, buf, buf, m->st), "upload ghost");
   CK(m, cudaStreamSynchronize(m->st), "upload sync");
   return CC_OK;
 }
@@ -614,10 +622,6 @@ cc_status cc_step(cc_model *m, int n) {
     if (L.ncols > 0) {
       CK(m, timed(m, CC_K_DIAGNOSE, [&] { return launch_diagnose(L, pr, rN, rC, rO, rF, first, 1, st); }),
          "velocity diagnosis");
-      nl++;
-    }
-    if (L.ghost_points > 0) {
-      CK(m, timed(m, CC_K_GHOST, [&] { return launch_ghost(L, pr, rN, rF, st); }), "ghost fill");
       nl++;
     }
     int o = m->r[0], c = m->r[1];

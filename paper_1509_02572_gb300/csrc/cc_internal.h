@@ -11,7 +11,8 @@ constexpr int GH = 4;          // ghost width of every padded array (x, y and z)
 constexpr int HOST_GZ = 2;     // corner levels below floor / above lid in host arrays
 constexpr int NFIELD = 5;      // rho', p', rho u, rho v, rho w
 constexpr int NBUF = 4;        // rotating time levels
-constexpr int TILE_X = 32, TILE_Y = 8;  // full-cell stencil tile (x, y)
+constexpr int TILE_X = 32;                          // full-cell stencil tile width (x)
+constexpr int TILE_Y_F32 = 16, TILE_Y_F64 = 8;     // tile height (y) per precision
 
 // cell classes and corner classes
 enum : int8_t { C_UG = 0, C_FULL = 1, C_CUT = 2, C_ABS = 3 };
@@ -35,7 +36,10 @@ struct DomDev {
   void *f[NBUF][NFIELD];     // prognostic fields, padded layout
   void *ub[NBUF];            // boundary-point velocity per level, 3*ny*nx
   // base state per padded level, precision of the model
-  const void *rhob, *pb, *thb, *pik, *rhobc, *tau;
+  const void *rhob, *pb, *thb, *pik, *rhobc, *tau, *ipb;
+  // binomial-series coefficients C(a, 1..7) and the exponent a, for
+  // (1 + x)^a - 1 with a = cv/cp (rho theta) and a = R/cp (Exner factor)
+  float sth[8], sex[8];
   // geometry (FP64 / int), padded cell layout unless noted
   const double *h;           // corner heights, ny*nx (periodic)
   const double *vf;          // nz*ny*nx interior layout (cell id)
@@ -109,7 +113,7 @@ cudaError_t launch_groups(const StepLaunch &L, int prec, int rO, int rC, int rN,
                           cudaStream_t st);
 cudaError_t launch_diagnose(const StepLaunch &L, int prec, int rV, int rC, int rO, int rF, int first,
                             int filter, cudaStream_t st);
-cudaError_t launch_ghost(const StepLaunch &L, int prec, int r1, int r2, cudaStream_t st);
+int full_tile_y(int prec);
 cudaError_t launch_init_momentum(const DomDev &D, const DomDev *d_dom, int prec, int r, double U,
                                  cudaStream_t st);
 cudaError_t launch_diag_reduce(const DomDev &D, const DomDev *d_dom, int prec, int r, double *d_out,

@@ -5,16 +5,17 @@
 //            p' and rho' tendencies, momentum on regular velocity cells
 //            (Eqs. momentum_u_d .. w_d), fourth-order diffusion, sponge,
 //            leapfrog and Robert-Asselin filter.  A 2.5D march in z keeps a
-//            ring of halo planes in shared memory, so each field plane is read
-//            from HBM once per tile.  Branch-free: cut cells and diagnosed
-//            corners are recomputed afterwards by the list kernels.
+//            ring of haloed planes in shared memory; the loads of plane k+2 are
+//            issued before the work on plane k, two barriers per plane.  The
+//            periodic lateral boundary (Sec 3) is folded into the per-thread
+//            load offsets, so no ghost exchange is needed.  Branch-free: cut
+//            cells and diagnosed corners are recomputed by the list kernels.
 //   k_groups one thread per merge group / cut cell: face fluxes weighted by
 //            the apertures, divergence over the merged volume, host update
 //            and scatter to the absorbed cells (Sec 2.3, 2.4).
 //   k_diag   one thread per column: boundary velocity by the nearest-plane
 //            interpolation and free-slip projection (Eq. 33), merged-face
 //            interpolation, lid values, the values below the terrain.
-//   k_ghost  periodic copy of the lateral ghost frames.
 #include <cuda_runtime.h>
 #include <math.h>
 
@@ -57,35 +58,56 @@ __device__ __forceinline__ T rho8(T a, T b, T c, T d, T e, T f, T g, T h) {
   return A::mul(A::add(A::add(A::add(A::add(A::add(A::add(A::add(a, b), c), d), e), f), g), h), T(0.125));
 }
 
-// rho*theta as a function of pressure, total and perturbation (equation of
-// state, Sec 2.1: rho theta = (p0/R)(p/p0)^(cv/cp)).
-// The product is rounded before the subtraction of the base value (no fused
-// multiply-add), so the perturbation of a resting state is exactly zero.
-__device__ __forceinline__ double theta_tot(const DomDev &D, const double *thb, const double *pb, int kp,
-                                            double pp) {
+// reciprocal of the corner density; the velocity is momentum times it
+template <typename T>
+__device__ __forceinline__ T rinv(T rc) {
+  return T(1) / rc;
+}
+
+// rho*theta as a function of pressure (equation of state, Sec 2.1:
+// rho theta = (p0/R)(p/p0)^(cv/cp)) and the Exner-type factor (p/p0)^(R/cp).
+// FP64: direct powers; the product is rounded before the subtraction of the
+// base value (no fused multiply-add), so a resting state gives exactly zero.
+__device__ __forceinline__ double theta_tot(const DomDev &D, const double *thb, const double *pb,
+                                            const double *ipb, int kp, double pp) {
   return __dmul_rn(D.p0 / D.R, pow((pb[kp] + pp) / D.p0, D.cvcp));
 }
-__device__ __forceinline__ double theta_pert(const DomDev &D, const double *thb, const double *pb, int kp,
-                                             double pp) {
-  return __dsub_rn(theta_tot(D, thb, pb, kp, pp), thb[kp]);
+__device__ __forceinline__ double theta_pert(const DomDev &D, const double *thb, const double *pb,
+                                             const double *ipb, int kp, double pp) {
+  return __dsub_rn(theta_tot(D, thb, pb, ipb, kp, pp), thb[kp]);
 }
-__device__ __forceinline__ double exner_fac(const DomDev &D, const double *pik, const double *pb, int kp,
-                                            double pp) {
+__device__ __forceinline__ double exner_fac(const DomDev &D, const double *pik, const double *pb,
+                                            const double *ipb, int kp, double pp) {
   return pow((pb[kp] + pp) / D.p0, D.kap);
 }
-// FP32 perturbation form: the ratio p'/p_bar enters through log1p / expm1 so
-// that a perturbation of a few pascals keeps full relative precision.
-__device__ __forceinline__ float theta_pert(const DomDev &D, const float *thb, const float *pb, int kp,
-                                            float pp) {
-  return thb[kp] * expm1f((float)D.cvcp * log1pf(pp / pb[kp]));
+// FP32 perturbation form: with x = p'/p_bar, (1 + x)^a - 1 is summed as the
+// binomial series sum_{n=1..7} C(a, n) x^n for |x| < 1/16 (truncation below
+// 1e-10 relative), else through log1p / expm1.  Every step uses an explicit
+// fused multiply-add or a rounded operation, so all kernels agree bitwise.
+__device__ __forceinline__ float pow1pm1(float x, const float *c) {
+  if (fabsf(x) < 0.0625f) {
+    float s = c[6];
+    s = fmaf(s, x, c[5]);
+    s = fmaf(s, x, c[4]);
+    s = fmaf(s, x, c[3]);
+    s = fmaf(s, x, c[2]);
+    s = fmaf(s, x, c[1]);
+    s = fmaf(s, x, c[0]);
+    return __fmul_rn(s, x);
+  }
+  return expm1f(__fmul_rn(c[7], log1pf(x)));
 }
-__device__ __forceinline__ float theta_tot(const DomDev &D, const float *thb, const float *pb, int kp,
-                                           float pp) {
-  return thb[kp] + theta_pert(D, thb, pb, kp, pp);
+__device__ __forceinline__ float theta_pert(const DomDev &D, const float *thb, const float *pb,
+                                            const float *ipb, int kp, float pp) {
+  return __fmul_rn(thb[kp], pow1pm1(__fmul_rn(pp, ipb[kp]), D.sth));
 }
-__device__ __forceinline__ float exner_fac(const DomDev &D, const float *pik, const float *pb, int kp,
-                                           float pp) {
-  return pik[kp] * expf((float)D.kap * log1pf(pp / pb[kp]));
+__device__ __forceinline__ float theta_tot(const DomDev &D, const float *thb, const float *pb,
+                                           const float *ipb, int kp, float pp) {
+  return __fadd_rn(thb[kp], theta_pert(D, thb, pb, ipb, kp, pp));
+}
+__device__ __forceinline__ float exner_fac(const DomDev &D, const float *pik, const float *pb,
+                                           const float *ipb, int kp, float pp) {
+  return fmaf(pik[kp], pow1pm1(__fmul_rn(pp, ipb[kp]), D.sex), pik[kp]);
 }
 
 __device__ __forceinline__ double d4(double a, double b, double c, double d, double e) {
@@ -95,12 +117,18 @@ __device__ __forceinline__ float d4(float a, float b, float c, float d, float e)
   return a - 4.0f * b + 6.0f * c - 4.0f * d + e;
 }
 
+// padded index of a cell / corner with the lateral coordinates wrapped
+// (periodic domains)
+__device__ __forceinline__ long long widx(const DomDev &D, int i, int j, int k) {
+  return pidx(D, wrapi(i, D.nx), wrapi(j, D.ny), k);
+}
+
 // ------------------------------------------------------------------ base state
 // Hydrostatic base state of constant N on every padded level, evaluated in
 // FP64 and stored in the model precision.
 template <typename T>
 __global__ void k_base(DomDev D, double theta0, double N, double p_surf, double sponge_frac,
-                       double tau_max, T *rhob, T *pb, T *thb, T *pik, T *rhobc, T *tau) {
+                       double tau_max, T *rhob, T *pb, T *thb, T *pik, T *rhobc, T *tau, T *ipb) {
   int kp = blockIdx.x * blockDim.x + threadIdx.x;
   if (kp >= D.pz) return;
   auto base = [&](double z, double &rho, double &p) {
@@ -123,6 +151,7 @@ __global__ void k_base(DomDev D, double theta0, double N, double p_surf, double 
   base((k - 0.5) * D.dz, rm, pm);
   rhob[kp] = (T)r;
   pb[kp] = (T)p;
+  ipb[kp] = (T)(1.0 / p);
   thb[kp] = (T)__dmul_rn(D.p0 / D.R, pow(p / D.p0, D.cvcp));
   pik[kp] = (T)pow(p / D.p0, D.kap);
   // corner level K = k: mean of the two adjacent cell levels
@@ -136,156 +165,195 @@ __global__ void k_base(DomDev D, double theta0, double N, double p_surf, double 
 }
 
 // ------------------------------------------------------------------ full-cell stencil
-constexpr int TX = TILE_X, TY = TILE_Y, HX = TX + 4, HY = TY + 4, PL = HX * HY;
-
-template <typename T>
-struct FullSmem {
-  T rho[3][PL], rp[3][PL], th[3][PL], pp[3][PL];
-  T tho[5][PL];
-  T u[3][3][PL];
-  T mo[5][3][PL];
-  T mt[3][PL];
+template <typename T, int TYv>
+struct FullCfg {
+  static constexpr int TX = TILE_X, TY = TYv, NT = TX * TY, HX = TX + 4, HY = TY + 4, PL = HX * HY,
+                       NLP = (PL + NT - 1) / NT;
 };
 
-__device__ __forceinline__ int s3(int k) { return (k + 9) % 3; }
-__device__ __forceinline__ int s5(int k) { return (k + 10) % 5; }
+template <typename T, int PLn>
+struct FullSmem {
+  T rho[4][PLn], rp[4][PLn], th[4][PLn], pp[4][PLn];  // cell planes k-1 .. k+2
+  T u[3][3][PLn];                                     // corner velocity planes k-1 .. k+1
+  T mt[2][3][PLn];                                    // raw momentum planes awaiting conversion
+  T mo[3][PLn];                                       // momentum at n-1, plane k
+  T tho[PLn];                                         // (rho theta)' at n-1, plane k
+};
 
-template <typename T>
-__global__ void __launch_bounds__(TX * TY) k_full(const DomDev *__restrict__ doms,
-                                                   const WorkItem *__restrict__ items, int rO, int rC,
-                                                   int rN, int rF, int first) {
+__device__ __forceinline__ int s4(int k) { return (k + 8) & 3; }
+__device__ __forceinline__ int s2(int k) { return (k + 8) & 1; }
+__device__ __forceinline__ int s3(int k) { return (k + 9) % 3; }
+
+template <typename T, int TYv>
+__global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict__ doms,
+                                                        const WorkItem *__restrict__ items, int rO, int rC,
+                                                        int rN, int rF, int first) {
   using A = Ar<T>;
+  using C = FullCfg<T, TYv>;
+  constexpr int TX = C::TX, NT = C::NT, HX = C::HX, PL = C::PL, NLP = C::NLP;
   extern __shared__ __align__(16) unsigned char smraw[];
-  FullSmem<T> &S = *reinterpret_cast<FullSmem<T> *>(smraw);
+  FullSmem<T, PL> &S = *reinterpret_cast<FullSmem<T, PL> *>(smraw);
   const WorkItem W = items[blockIdx.x];
   const DomDev &D = doms[W.dom];
   const T dt2 = (T)(first ? D.dt : 2.0 * D.dt);
   const T nu = (T)(first ? 0.0 : D.ra_nu);
   const int tid = threadIdx.x;
-  const int nx = D.nx, ny = D.ny, nz = D.nz, px = D.px, py = D.py;
+  const int nx = D.nx, ny = D.ny, nz = D.nz, px = D.px;
+  const long long plane = D.plane;
   const T *__restrict__ rpC = (const T *)D.f[rC][0];
   const T *__restrict__ ppC = (const T *)D.f[rC][1];
-  const T *__restrict__ mC[3] = {(const T *)D.f[rC][2], (const T *)D.f[rC][3], (const T *)D.f[rC][4]};
+  const T *__restrict__ mC0 = (const T *)D.f[rC][2];
+  const T *__restrict__ mC1 = (const T *)D.f[rC][3];
+  const T *__restrict__ mC2 = (const T *)D.f[rC][4];
   const T *__restrict__ rpO = (const T *)D.f[rO][0];
   const T *__restrict__ ppO = (const T *)D.f[rO][1];
-  const T *__restrict__ mO[3] = {(const T *)D.f[rO][2], (const T *)D.f[rO][3], (const T *)D.f[rO][4]};
+  const T *__restrict__ mO0 = (const T *)D.f[rO][2];
+  const T *__restrict__ mO1 = (const T *)D.f[rO][3];
+  const T *__restrict__ mO2 = (const T *)D.f[rO][4];
   const T *__restrict__ rhob = (const T *)D.rhob;
   const T *__restrict__ pb = (const T *)D.pb;
+  const T *__restrict__ ipb = (const T *)D.ipb;
   const T *__restrict__ thb = (const T *)D.thb;
   const T *__restrict__ pik = (const T *)D.pik;
   const T *__restrict__ rhobc = (const T *)D.rhobc;
   const T *__restrict__ tau = (const T *)D.tau;
   const int i0 = W.i0, j0 = W.j0, k0 = W.k0, k1 = W.k1;
 
-  auto gidx = [&](int hx, int hy, int kk, bool &ok) -> long long {
-    int gi = i0 - 2 + hx, gj = j0 - 2 + hy;
-    ok = gi < nx + GH && gj < ny + GH;
-    return ((long long)(kk + GH) * py + (gj + GH)) * px + (gi + GH);
-  };
+  // per-thread plane points of the haloed tile and their in-plane offsets
+  // (lateral coordinates wrapped: cyclic boundaries)
+  long long loff[NLP];
+  int lpt[NLP];
+#pragma unroll
+  for (int s = 0; s < NLP; s++) {
+    int p = tid + s * NT;
+    lpt[s] = p;
+    int hx = p % HX, hy = p / HX;
+    int gi = wrapi(i0 - 2 + hx, nx), gj = wrapi(j0 - 2 + hy, ny);
+    loff[s] = (long long)(gj + GH) * px + (gi + GH);
+  }
   auto load_cells = [&](int kk) {
-    int s = s3(kk);
-    int kp = kk + GH;
-    T rb = rhob[kp];
-    for (int p = tid; p < PL; p += TX * TY) {
-      bool ok;
-      long long g = gidx(p % HX, p / HX, kk, ok);
-      T r = 0, q = 0;
-      if (ok) {
-        r = rpC[g];
-        q = ppC[g];
+    const int sl = s4(kk), kp = kk + GH;
+    const T rb = rhob[kp];
+    const long long zo = (long long)kp * plane;
+#pragma unroll
+    for (int s = 0; s < NLP; s++) {
+      const int p = lpt[s];
+      if (p < PL) {
+        const long long gg = zo + loff[s];
+        T r = rpC[gg], q = ppC[gg];
+        S.rp[sl][p] = r;
+        S.pp[sl][p] = q;
+        S.rho[sl][p] = A::add(rb, r);
+        S.th[sl][p] = theta_tot(D, thb, pb, ipb, kp, q);
       }
-      S.rp[s][p] = r;
-      S.pp[s][p] = q;
-      S.rho[s][p] = A::add(rb, r);
-      S.th[s][p] = theta_tot(D, thb, pb, kp, q);
-    }
-  };
-  auto load_old = [&](int kk) {
-    int s = s5(kk);
-    int kp = kk + GH;
-    for (int p = tid; p < PL; p += TX * TY) {
-      bool ok;
-      long long g = gidx(p % HX, p / HX, kk, ok);
-      T q = 0, a = 0, b = 0, c = 0;
-      if (ok) {
-        q = ppO[g];
-        a = mO[0][g];
-        b = mO[1][g];
-        c = mO[2][g];
-      }
-      S.tho[s][p] = theta_pert(D, thb, pb, kp, q);
-      S.mo[s][0][p] = a;
-      S.mo[s][1][p] = b;
-      S.mo[s][2][p] = c;
     }
   };
   auto load_mt = [&](int kk) {
-    for (int p = tid; p < PL; p += TX * TY) {
-      bool ok;
-      long long g = gidx(p % HX, p / HX, kk, ok);
-      T a = 0, b = 0, c = 0;
-      if (ok) {
-        a = mC[0][g];
-        b = mC[1][g];
-        c = mC[2][g];
+    const int sl = s2(kk);
+    const long long zo = (long long)(kk + GH) * plane;
+#pragma unroll
+    for (int s = 0; s < NLP; s++) {
+      const int p = lpt[s];
+      if (p < PL) {
+        const long long gg = zo + loff[s];
+        S.mt[sl][0][p] = mC0[gg];
+        S.mt[sl][1][p] = mC1[gg];
+        S.mt[sl][2][p] = mC2[gg];
       }
-      S.mt[0][p] = a;
-      S.mt[1][p] = b;
-      S.mt[2][p] = c;
+    }
+  };
+  auto load_old_plane = [&](int kk) {
+    const int kp = kk + GH;
+    const long long zo = (long long)kp * plane;
+#pragma unroll
+    for (int s = 0; s < NLP; s++) {
+      const int p = lpt[s];
+      if (p < PL) {
+        const long long gg = zo + loff[s];
+        S.tho[p] = theta_pert(D, thb, pb, ipb, kp, ppO[gg]);
+        S.mo[0][p] = mO0[gg];
+        S.mo[1][p] = mO1[gg];
+        S.mo[2][p] = mO2[gg];
+      }
     }
   };
   // corner velocity = momentum / mean density of the 8 surrounding cells
   auto compute_u = [&](int K) {
-    int sl = s3(K - 1), sh = s3(K), su = s3(K);
-    for (int p = tid; p < PL; p += TX * TY) {
-      int hx = p % HX, hy = p / HX;
-      if (hx == 0 || hy == 0) continue;
-      const T *lo = S.rho[sl], *hi = S.rho[sh];
-      int q00 = p - HX - 1, q01 = p - HX, q10 = p - 1, q11 = p;
-      T rc = rho8(lo[q00], lo[q01], lo[q10], lo[q11], hi[q00], hi[q01], hi[q10], hi[q11]);
-      S.u[su][0][p] = S.mt[0][p] / rc;
-      S.u[su][1][p] = S.mt[1][p] / rc;
-      S.u[su][2][p] = S.mt[2][p] / rc;
+    const int sl = s4(K - 1), sh = s4(K), su = s3(K), sm = s2(K);
+#pragma unroll
+    for (int s = 0; s < NLP; s++) {
+      const int p = lpt[s];
+      const int hx = p % HX, hy = p / HX;
+      if (p < PL && hx != 0 && hy != 0) {
+        const T *lo = S.rho[sl], *hi = S.rho[sh];
+        const int q00 = p - HX - 1, q01 = p - HX, q10 = p - 1, q11 = p;
+        T iv = rinv(rho8(lo[q00], lo[q01], lo[q10], lo[q11], hi[q00], hi[q01], hi[q10], hi[q11]));
+        S.u[su][0][p] = S.mt[sm][0][p] * iv;
+        S.u[su][1][p] = S.mt[sm][1][p] * iv;
+        S.u[su][2][p] = S.mt[sm][2][p] * iv;
+      }
     }
   };
-
-  // prologue
-  load_cells(k0 - 2);
-  load_cells(k0 - 1);
-  for (int kk = k0 - 2; kk <= k0 + 1; kk++) load_old(kk);
-  load_mt(k0 - 1);
-  __syncthreads();
-  compute_u(k0 - 1);
-  __syncthreads();
-  load_cells(k0);
-  load_mt(k0);
-  __syncthreads();
-  compute_u(k0);
-  __syncthreads();
 
   const int tx = tid % TX, ty = tid / TX;
   const int i = i0 + tx, j = j0 + ty;
   const bool active = i < nx && j < ny;
-  const int hx = tx + 2, hy = ty + 2, c = hy * HX + hx;
+  const int c = (ty + 2) * HX + (tx + 2);
+  const long long own = active ? (long long)(j + GH) * px + (i + GH) : 0;
   const T dx = (T)D.dx, dy = (T)D.dy, dz = (T)D.dz;
   const T Sx = (T)(D.dy * D.dz), Sy = (T)(D.dx * D.dz), Sz = (T)(D.dx * D.dy);
   const T v0inv = (T)(1.0 / (D.dx * D.dy * D.dz));
   const T kdif = (T)D.kdif, Cp = (T)D.Cp, g = (T)D.g, U = (T)D.U;
   const int kug = active ? D.kug[(long long)j * nx + i] : 0;
 
+  // own column at n-1 for the vertical diffusion stencils, levels k-2 .. k+2
+  T treg[5], mreg[5][3];
+  auto load_own_old = [&](int a, int kk) {
+    if (active) {
+      const int kp = kk + GH;
+      const long long o = (long long)kp * plane + own;
+      treg[a] = theta_pert(D, thb, pb, ipb, kp, ppO[o]);
+      mreg[a][0] = mO0[o];
+      mreg[a][1] = mO1[o];
+      mreg[a][2] = mO2[o];
+    } else {
+      treg[a] = 0;
+      mreg[a][0] = mreg[a][1] = mreg[a][2] = 0;
+    }
+  };
+
+  // prologue
+  load_cells(k0 - 2);
+  load_cells(k0 - 1);
+  load_cells(k0);
+  load_cells(k0 + 1);
+  load_mt(k0 - 1);
+  load_mt(k0);
+#pragma unroll
+  for (int a = 0; a < 4; a++) load_own_old(a, k0 - 2 + a);
+  __syncthreads();
+  compute_u(k0 - 1);
+  compute_u(k0);
+  __syncthreads();
+  load_mt(k0 + 1);
+  __syncthreads();
+
   for (int k = k0; k < k1; k++) {
-    load_cells(k + 1);
-    load_old(k + 2);
-    load_mt(k + 1);
-    __syncthreads();
+    // phase 1: loads for plane k+2 (and the n-1 plane k), velocities of plane k+1
+    load_cells(k + 2);
+    load_mt(k + 2);
+    load_old_plane(k);
+    load_own_old(4, k + 2);
     compute_u(k + 1);
     __syncthreads();
+    // phase 2: the cell and corner of this thread on plane k
     if (active) {
-      const int sk = s3(k), skm = s3(k - 1), skp = s3(k + 1);
+      const int sk = s4(k), skm = s4(k - 1), skp = s4(k + 1);
       const T *R0 = S.rho[sk], *Rm = S.rho[skm], *Rp = S.rho[skp];
       const T *H0 = S.th[sk], *Hm = S.th[skm], *Hp = S.th[skp];
-      const T *ux0 = S.u[sk][0], *uy0 = S.u[sk][1], *uz0 = S.u[sk][2];
-      const T *uxp = S.u[skp][0], *uyp = S.u[skp][1], *uzp = S.u[skp][2];
+      const int uk = s3(k), ukp = s3(k + 1), ukm = s3(k - 1);
+      const T *ux0 = S.u[uk][0], *uy0 = S.u[uk][1], *uz0 = S.u[uk][2];
+      const T *uxp = S.u[ukp][0], *uyp = S.u[ukp][1], *uzp = S.u[ukp][2];
       // ---- scalar cell (i,j,k): face fluxes, lower-index cell first
       T fxm = face_flux(R0[c - 1], R0[c], ux0[c], ux0[c + HX], uxp[c], uxp[c + HX], Sx);
       T fxp = face_flux(R0[c], R0[c + 1], ux0[c + 1], ux0[c + 1 + HX], uxp[c + 1], uxp[c + 1 + HX], Sx);
@@ -304,17 +372,17 @@ __global__ void __launch_bounds__(TX * TY) k_full(const DomDev *__restrict__ dom
       T RM = A::add(A::add(A::sub(fxp, fxm), A::sub(fyp, fym)), A::sub(fzp, fzm));
       T RH = A::add(A::add(A::sub(hxp, hxm), A::sub(hyp, hym)), A::sub(hzp, hzm));
       // fourth-order diffusion of (rho theta)' at n-1
-      const T *Tk = S.tho[s5(k)];
+      const T *Tk = S.tho;
       T dd = d4(Tk[c - 2], Tk[c - 1], Tk[c], Tk[c + 1], Tk[c + 2]) +
              d4(Tk[c - 2 * HX], Tk[c - HX], Tk[c], Tk[c + HX], Tk[c + 2 * HX]) +
-             d4(S.tho[s5(k - 2)][c], S.tho[s5(k - 1)][c], Tk[c], S.tho[s5(k + 1)][c], S.tho[s5(k + 2)][c]);
+             d4(treg[0], treg[1], treg[2], treg[3], treg[4]);
       T Dth = -kdif * dd;
-      const long long o = ((long long)(k + GH) * py + (j + GH)) * px + (i + GH);
+      const long long o = (long long)(k + GH) * plane + own;
       const int kp = k + GH;
       T rC_ = S.rp[sk][c], pC_ = S.pp[sk][c];
       T rO_ = rpO[o], pO_ = ppO[o];
       T rN_ = rO_ - dt2 * (RM * v0inv);
-      T pN_ = pO_ - dt2 * Cp * exner_fac(D, pik, pb, kp, pC_) * (RH * v0inv - Dth);
+      T pN_ = pO_ - dt2 * Cp * exner_fac(D, pik, pb, ipb, kp, pC_) * (RH * v0inv - Dth);
       if (k < kug) { rN_ = 0; pN_ = 0; }
       T rF_ = rC_ + nu * (rN_ - T(2) * rC_ + rO_);
       T pF_ = pC_ + nu * (pN_ - T(2) * pC_ + pO_);
@@ -331,7 +399,7 @@ __global__ void __launch_bounds__(TX * TY) k_full(const DomDev *__restrict__ dom
       T rS = (Rm[c - HX - 1] + Rm[c - HX] + R0[c - HX - 1] + R0[c - HX]) * T(0.25);
       T rT = (R0[c - HX - 1] + R0[c - HX] + R0[c - 1] + R0[c]) * T(0.25);
       T rB = (Rm[c - HX - 1] + Rm[c - HX] + Rm[c - 1] + Rm[c]) * T(0.25);
-      const T *uxm = S.u[skm][0], *uym = S.u[skm][1], *uzm = S.u[skm][2];
+      const T *uxm = S.u[ukm][0], *uym = S.u[ukm][1], *uzm = S.u[ukm][2];
       T u0[3] = {ux0[c], uy0[c], uz0[c]};
       T uE[3] = {ux0[c + 1], uy0[c + 1], uz0[c + 1]};
       T uW[3] = {ux0[c - 1], uy0[c - 1], uz0[c - 1]};
@@ -352,58 +420,69 @@ __global__ void __launch_bounds__(TX * TY) k_full(const DomDev *__restrict__ dom
       const T *Q0 = S.rp[sk], *Qm = S.rp[skm];
       T r8 = (Q0[c - HX - 1] + Q0[c - HX] + Q0[c - 1] + Q0[c]) + (Qm[c - HX - 1] + Qm[c - HX] + Qm[c - 1] + Qm[c]);
       T pg[3] = {T(0.25) * (pE - pW) / dx, T(0.25) * (pNn - pS) / dy, T(0.25) * (pT - pB) / dz};
-      const T mref = rhobc[kp] * U;
       const T tk = tau[kp];
+      const T *mcur[3] = {mC0, mC1, mC2};
 #pragma unroll
       for (int d = 0; d < 3; d++) {
         T adv = fE * T(0.5) * (u0[d] + uE[d]) - fW * T(0.5) * (uW[d] + u0[d]) + fN * T(0.5) * (u0[d] + uN[d]) -
                 fS * T(0.5) * (uS[d] + u0[d]) + fT * T(0.5) * (u0[d] + uT[d]) - fB * T(0.5) * (uB[d] + u0[d]);
         T tend = -adv * v0inv - pg[d];
         if (d == 2) tend -= g * r8 * T(0.125);
-        const T *Mk = S.mo[s5(k)][d];
-        T ref0 = d == 0 ? mref : T(0);
+        const T *Mk = S.mo[d];
         // diffusion of the departure from the reference momentum (rho_bar U, 0, 0)
+        T ref0 = d == 0 ? rhobc[kp] * U : T(0);
         T dm = d4(Mk[c - 2] - ref0, Mk[c - 1] - ref0, Mk[c] - ref0, Mk[c + 1] - ref0, Mk[c + 2] - ref0) +
                d4(Mk[c - 2 * HX] - ref0, Mk[c - HX] - ref0, Mk[c] - ref0, Mk[c + HX] - ref0,
                   Mk[c + 2 * HX] - ref0);
-        T zr[5];
-#pragma unroll
-        for (int a = -2; a <= 2; a++) zr[a + 2] = d == 0 ? rhobc[kp + a] * U : T(0);
-        dm += d4(S.mo[s5(k - 2)][d][c] - zr[0], S.mo[s5(k - 1)][d][c] - zr[1], Mk[c] - zr[2],
-                 S.mo[s5(k + 1)][d][c] - zr[3], S.mo[s5(k + 2)][d][c] - zr[4]);
-        T mold = Mk[c];
+        if (d == 0)
+          dm += d4(mreg[0][0] - rhobc[kp - 2] * U, mreg[1][0] - rhobc[kp - 1] * U, mreg[2][0] - ref0,
+                   mreg[3][0] - rhobc[kp + 1] * U, mreg[4][0] - rhobc[kp + 2] * U);
+        else
+          dm += d4(mreg[0][d], mreg[1][d], mreg[2][d], mreg[3][d], mreg[4][d]);
+        T mold = mreg[2][d];
         tend += -kdif * dm - tk * (mold - ref0);
         T mnew = mold + dt2 * tend;
-        T mcur = mC[d][o];
-        T mf = mcur + nu * (mnew - T(2) * mcur + mold);
+        T mc = mcur[d][o];
+        T mf = mc + nu * (mnew - T(2) * mc + mold);
         ((T *)D.f[rN][2 + d])[o] = mnew;
         ((T *)D.f[rF][2 + d])[o] = mf;
       }
     }
     __syncthreads();
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+      treg[a] = treg[a + 1];
+      mreg[a][0] = mreg[a + 1][0];
+      mreg[a][1] = mreg[a + 1][1];
+      mreg[a][2] = mreg[a + 1][2];
+    }
   }
 }
 
 // ------------------------------------------------------------------ cut cells and merge groups
 template <typename T>
 __device__ __forceinline__ T cell_rho(const DomDev &D, const T *rp, const T *rhob, int i, int j, int k) {
-  long long o = ((long long)(k + GH) * D.py + (j + GH)) * D.px + (i + GH);
-  return Ar<T>::add(rhob[k + GH], rp[o]);
+  return Ar<T>::add(rhob[k + GH], rp[widx(D, i, j, k)]);
 }
 
-// corner velocity component at corner (I,J,K) (padded reads: the ghost frames
-// of the level are valid)
+// corner density (the same operations as the full-cell stencil)
 template <typename T>
-__device__ __forceinline__ void corner_u(const DomDev &D, const T *rp, const T *const *M, const T *rhob, int I,
-                                         int J, int K, T u[3]) {
-  T rc = rho8(cell_rho(D, rp, rhob, I - 1, J - 1, K - 1), cell_rho(D, rp, rhob, I, J - 1, K - 1),
+__device__ __forceinline__ T corner_rho(const DomDev &D, const T *rp, const T *rhob, int I, int J, int K) {
+  return rho8(cell_rho(D, rp, rhob, I - 1, J - 1, K - 1), cell_rho(D, rp, rhob, I, J - 1, K - 1),
               cell_rho(D, rp, rhob, I - 1, J, K - 1), cell_rho(D, rp, rhob, I, J, K - 1),
               cell_rho(D, rp, rhob, I - 1, J - 1, K), cell_rho(D, rp, rhob, I, J - 1, K),
               cell_rho(D, rp, rhob, I - 1, J, K), cell_rho(D, rp, rhob, I, J, K));
-  long long o = ((long long)(K + GH) * D.py + (J + GH)) * D.px + (I + GH);
-  u[0] = M[0][o] / rc;
-  u[1] = M[1][o] / rc;
-  u[2] = M[2][o] / rc;
+}
+
+// corner velocity (the same operations as the full-cell stencil)
+template <typename T>
+__device__ __forceinline__ void corner_u(const DomDev &D, const T *rp, const T *const *M, const T *rhob, int I,
+                                         int J, int K, T u[3]) {
+  T iv = rinv(corner_rho(D, rp, rhob, I, J, K));
+  long long o = widx(D, I, J, K);
+  u[0] = M[0][o] * iv;
+  u[1] = M[1][o] * iv;
+  u[2] = M[2][o] * iv;
 }
 
 template <typename T>
@@ -423,6 +502,7 @@ __global__ void k_groups(const DomDev *__restrict__ doms, const GroupRec *__rest
   const T *rpO = (const T *)D.f[rO][0];
   const T *ppO = (const T *)D.f[rO][1];
   const T *rhob = (const T *)D.rhob, *pb = (const T *)D.pb, *thb = (const T *)D.thb, *pik = (const T *)D.pik;
+  const T *ipb = (const T *)D.ipb;
   const T Sfull[3] = {(T)(D.dy * D.dz), (T)(D.dx * D.dz), (T)(D.dx * D.dy)};
   T rm = 0, rh = 0;
   for (int a = 0; a < R.count; a++) {
@@ -460,16 +540,13 @@ __global__ void k_groups(const DomDev *__restrict__ doms, const GroupRec *__rest
         }
         if (Ap == 0.0) continue;
         if (nk < 0 || nk >= nz) continue;
-        int wni = wrapi(ni, nx), wnj = wrapi(nj, ny);
-        long long nb = cid(D, wni, wnj, nk);
+        long long nb = cid(D, wrapi(ni, nx), wrapi(nj, ny), nk);
         if (D.cls[nb] != C_UG && D.root[nb] == R.host) continue;  // face inside the group
         T uc[4][3];
         for (int s = 0; s < 4; s++) corner_u(D, rpC, MC, rhob, cI[s], cJ[s], cK[s], uc[s]);
-        // neighbour read through its padded position (ghost frames valid)
         T phm = cell_rho(D, rpC, rhob, i, j, k), phn = cell_rho(D, rpC, rhob, ni, nj, nk);
-        long long om = ((long long)(k + GH) * D.py + (j + GH)) * D.px + (i + GH);
-        long long on = ((long long)(nk + GH) * D.py + (nj + GH)) * D.px + (ni + GH);
-        T thm = theta_tot(D, thb, pb, k + GH, ppC[om]), thn = theta_tot(D, thb, pb, nk + GH, ppC[on]);
+        T thm = theta_tot(D, thb, pb, ipb, k + GH, ppC[widx(D, i, j, k)]);
+        T thn = theta_tot(D, thb, pb, ipb, nk + GH, ppC[widx(D, ni, nj, nk)]);
         T S = (Ap == 1.0) ? Sfull[ax] : (T)(Ap * (double)Sfull[ax]);
         T fm, fh;
         if (sd) {
@@ -488,23 +565,22 @@ __global__ void k_groups(const DomDev *__restrict__ doms, const GroupRec *__rest
   // host update
   int h = R.host;
   int ih = h % nx, jh = (h / nx) % ny, kh = h / (nx * ny);
-  auto po = [&](int ii, int jj, int kk) { return ((long long)(kk + GH) * D.py + (jj + GH)) * D.px + (ii + GH); };
-  auto tho = [&](int ii, int jj, int kk) { return theta_pert(D, thb, pb, kk + GH, ppO[po(ii, jj, kk)]); };
+  auto tho = [&](int ii, int jj, int kk) { return theta_pert(D, thb, pb, ipb, kk + GH, ppO[widx(D, ii, jj, kk)]); };
   T dd = d4(tho(ih - 2, jh, kh), tho(ih - 1, jh, kh), tho(ih, jh, kh), tho(ih + 1, jh, kh), tho(ih + 2, jh, kh)) +
          d4(tho(ih, jh - 2, kh), tho(ih, jh - 1, kh), tho(ih, jh, kh), tho(ih, jh + 1, kh), tho(ih, jh + 2, kh)) +
          d4(tho(ih, jh, kh - 2), tho(ih, jh, kh - 1), tho(ih, jh, kh), tho(ih, jh, kh + 1), tho(ih, jh, kh + 2));
   T Dth = -(T)D.kdif * dd;
-  long long oh = po(ih, jh, kh);
+  long long oh = pidx(D, ih, jh, kh);
   T rC_ = rpC[oh], pC_ = ppC[oh], rO_ = rpO[oh], pO_ = ppO[oh];
   T VG = (T)R.vg;
   T rN_ = rO_ - dt2 * (rm / VG);
-  T pN_ = pO_ - dt2 * (T)D.Cp * exner_fac(D, pik, pb, kh + GH, pC_) * (rh / VG - Dth);
+  T pN_ = pO_ - dt2 * (T)D.Cp * exner_fac(D, pik, pb, ipb, kh + GH, pC_) * (rh / VG - Dth);
   T rF_ = rC_ + nu * (rN_ - T(2) * rC_ + rO_);
   T pF_ = pC_ + nu * (pN_ - T(2) * pC_ + pO_);
   for (int a = 0; a < R.count; a++) {
     int m = members[R.start + a];
     int i = m % nx, j = (m / nx) % ny, k = m / (nx * ny);
-    long long o = po(i, j, k);
+    long long o = pidx(D, i, j, k);
     ((T *)D.f[rN][0])[o] = rN_;
     ((T *)D.f[rN][1])[o] = pN_;
     ((T *)D.f[rF][0])[o] = rF_;
@@ -513,17 +589,6 @@ __global__ void k_groups(const DomDev *__restrict__ doms, const GroupRec *__rest
 }
 
 // ------------------------------------------------------------------ velocity diagnosis
-// Corner velocity of the new level from wrapped interior positions (the new
-// level's ghost frames are not filled yet).
-template <typename T>
-__device__ __forceinline__ T rho_new_corner(const DomDev &D, const T *rp, const T *rhob, int I, int J, int K) {
-  int Im = wrapi(I - 1, D.nx), I0 = wrapi(I, D.nx), Jm = wrapi(J - 1, D.ny), J0 = wrapi(J, D.ny);
-  return rho8(cell_rho(D, rp, rhob, Im, Jm, K - 1), cell_rho(D, rp, rhob, I0, Jm, K - 1),
-              cell_rho(D, rp, rhob, Im, J0, K - 1), cell_rho(D, rp, rhob, I0, J0, K - 1),
-              cell_rho(D, rp, rhob, Im, Jm, K), cell_rho(D, rp, rhob, I0, Jm, K),
-              cell_rho(D, rp, rhob, Im, J0, K), cell_rho(D, rp, rhob, I0, J0, K));
-}
-
 template <typename T>
 __global__ void k_diag(const DomDev *__restrict__ doms, const ColItem *__restrict__ cols, int ncols, int rV,
                        int rC, int rO, int rF, int first, int filter) {
@@ -535,16 +600,9 @@ __global__ void k_diag(const DomDev *__restrict__ doms, const ColItem *__restric
   const int I = CI.I, J = CI.J;
   const T *rp = (const T *)D.f[rV][0];
   T *M[3] = {(T *)D.f[rV][2], (T *)D.f[rV][3], (T *)D.f[rV][4]};
+  const T *const *Mc = (const T *const *)M;
   const T *rhob = (const T *)D.rhob;
   const long long q = (long long)J * D.nx + I;
-  auto vel = [&](int i, int j, int K, T u[3]) {
-    int wi = wrapi(i, D.nx), wj = wrapi(j, D.ny);
-    T rc = rho_new_corner(D, rp, rhob, wi, wj, K);
-    long long o = pidx(D, wi, wj, K);
-    u[0] = M[0][o] / rc;
-    u[1] = M[1][o] / rc;
-    u[2] = M[2][o] / rc;
-  };
   // boundary point: bilinear in the nearest plane, then free-slip projection
   int K = D.bK[q], i0 = D.bI[q], j0 = D.bJ[q];
   T a = (T)D.ba[q], b = (T)D.bb[q];
@@ -554,7 +612,7 @@ __global__ void k_diag(const DomDev *__restrict__ doms, const ColItem *__restric
   for (int s = 0; s < 4; s++) {
     if (w[s] == T(0)) continue;
     T u[3];
-    vel(ci[s], cj[s], K, u);
+    corner_u(D, rp, Mc, rhob, ci[s], cj[s], K, u);
     for (int d = 0; d < 3; d++) uN[d] += w[s] * u[d];
   }
   T n[3] = {(T)D.bn[3 * q], (T)D.bn[3 * q + 1], (T)D.bn[3 * q + 2]};
@@ -572,7 +630,7 @@ __global__ void k_diag(const DomDev *__restrict__ doms, const ColItem *__restric
   T *mflt[3] = {(T *)D.f[rF][2], (T *)D.f[rF][3], (T *)D.f[rF][4]};
   auto store = [&](int KK, const T u[3]) {
     long long o = pidx(D, I, J, KK);
-    T rc = rho_new_corner(D, rp, rhob, I, J, KK);
+    T rc = corner_rho(D, rp, rhob, I, J, KK);
     for (int d = 0; d < 3; d++) {
       T mv = rc * u[d];
       M[d][o] = mv;
@@ -596,49 +654,15 @@ __global__ void k_diag(const DomDev *__restrict__ doms, const ColItem *__restric
       int ka = D.mK[p];
       T gm = (T)D.mg[p];
       T ua[3];
-      vel(I, J, ka, ua);
+      corner_u(D, rp, Mc, rhob, I, J, ka, ua);
       for (int d = 0; d < 3; d++) u[d] = gm * ua[d] + (T(1) - gm) * ub[d];
     }
     store(KK, u);
   }
   T ul[3];
-  vel(I, J, D.nz - 1, ul);
+  corner_u(D, rp, Mc, rhob, I, J, D.nz - 1, ul);
   ul[2] = 0;
   for (int KK = D.nz; KK < D.nz + GH; KK++) store(KK, ul);
-}
-
-// ------------------------------------------------------------------ ghost frames
-// Periodic copy of the lateral ghost frame (cyclic lateral boundaries, Sec 3)
-// for 5 fields of two levels; blockIdx.y = level*5 + field, blockIdx.z = domain.
-template <typename T>
-__global__ void k_ghost(const DomDev *__restrict__ doms, int r1, int r2) {
-  const DomDev &D = doms[blockIdx.z];
-  const long long frame = (long long)D.px * D.py - (long long)D.nx * D.ny;
-  const long long n = frame * D.pz;
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= n) return;
-  int lev = blockIdx.y / NFIELD, fld = blockIdx.y % NFIELD;
-  T *a = (T *)D.f[lev == 0 ? r1 : r2][fld];
-  long long q = t % frame;
-  int kz = (int)(t / frame);
-  int gi, gj;
-  long long band = (long long)GH * D.px;
-  if (q < band) {
-    gj = (int)(q / D.px) - GH;
-    gi = (int)(q % D.px) - GH;
-  } else if (q < 2 * band) {
-    q -= band;
-    gj = D.ny + (int)(q / D.px);
-    gi = (int)(q % D.px) - GH;
-  } else {
-    q -= 2 * band;
-    gj = (int)(q / (2 * GH));
-    int r = (int)(q % (2 * GH));
-    gi = r < GH ? r - GH : D.nx + (r - GH);
-  }
-  long long dst = ((long long)kz * D.py + (gj + GH)) * D.px + (gi + GH);
-  long long src = ((long long)kz * D.py + (wrapi(gj, D.ny) + GH)) * D.px + (wrapi(gi, D.nx) + GH);
-  a[dst] = a[src];
 }
 
 // initial momentum rho_corner * U on the predicted points of level r
@@ -652,7 +676,7 @@ __global__ void k_init_momentum(const DomDev *__restrict__ dom, int r, double U)
   long long o = pidx(D, I, J, K);
   if (D.vcls[o] != V_PRED) return;
   const T *rp = (const T *)D.f[r][0];
-  T rc = rho_new_corner(D, rp, (const T *)D.rhob, I, J, K);
+  T rc = corner_rho(D, rp, (const T *)D.rhob, I, J, K);
   ((T *)D.f[r][2])[o] = rc * (T)U;
 }
 
@@ -692,7 +716,7 @@ __global__ void k_diag_partial(const DomDev *__restrict__ dom, int r, double *pa
     for (int a = 0; a < 5; a++)
       if (!isfinite((double)vals[a])) bad += 1;
     if (D.vcls[o] == V_PRED) {
-      T rc = rho_new_corner(D, rp, rhob, i, j, k);
+      T rc = corner_rho(D, rp, rhob, i, j, k);
       double uu = fabs((double)(M[0][o] / rc)), ww = fabs((double)(M[2][o] / rc));
       mu = fmax(mu, uu);
       mw = fmax(mw, ww);
@@ -743,24 +767,23 @@ __global__ void k_diag_final(const double *part, int nb, double *out) {
 
 // ------------------------------------------------------------------ launchers
 namespace {
-template <typename T>
-cudaError_t ensure_full_attr() {
-  static bool done = false;
-  if (!done) {
-    cudaError_t e = cudaFuncSetAttribute(k_full<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)sizeof(FullSmem<T>));
-    if (e != cudaSuccess) return e;
-    done = true;
-  }
-  return cudaSuccess;
+template <typename T, int TYv>
+size_t full_smem() {
+  return sizeof(FullSmem<T, FullCfg<T, TYv>::PL>);
 }
 
-template <typename T>
+template <typename T, int TYv>
 cudaError_t full_t(const StepLaunch &L, int rO, int rC, int rN, int rF, int first, cudaStream_t st) {
-  cudaError_t e = ensure_full_attr<T>();
-  if (e != cudaSuccess) return e;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_full<T, TYv>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)full_smem<T, TYv>());
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
   if (L.nitems > 0)
-    k_full<T><<<L.nitems, TX * TY, sizeof(FullSmem<T>), st>>>(L.d_doms, L.items, rO, rC, rN, rF, first);
+    k_full<T, TYv><<<L.nitems, TILE_X * TYv, full_smem<T, TYv>(), st>>>(L.d_doms, L.items, rO, rC, rN, rF,
+                                                                        first);
   return cudaGetLastError();
 }
 
@@ -771,15 +794,9 @@ cudaError_t groups_t(const StepLaunch &L, int rO, int rC, int rN, int rF, int fi
                                                           rF, first);
   return cudaGetLastError();
 }
-
-template <typename T>
-cudaError_t ghost_t(const StepLaunch &L, int r1, int r2, cudaStream_t st) {
-  if (L.ndom <= 0 || L.ghost_points <= 0) return cudaSuccess;
-  dim3 grid((unsigned)((L.ghost_points + 255) / 256), 2 * NFIELD, L.ndom);
-  k_ghost<T><<<grid, 256, 0, st>>>(L.d_doms, r1, r2);
-  return cudaGetLastError();
-}
 }  // namespace
+
+int full_tile_y(int prec) { return prec == CC_FP64 ? TILE_Y_F64 : TILE_Y_F32; }
 
 cudaError_t launch_base(const DomDev &D, int prec, double theta0, double N, double p_surf, double sponge_frac,
                         double tau_max, cudaStream_t st) {
@@ -787,17 +804,18 @@ cudaError_t launch_base(const DomDev &D, int prec, double theta0, double N, doub
   if (prec == CC_FP64)
     k_base<double><<<nb, 128, 0, st>>>(D, theta0, N, p_surf, sponge_frac, tau_max, (double *)D.rhob,
                                        (double *)D.pb, (double *)D.thb, (double *)D.pik, (double *)D.rhobc,
-                                       (double *)D.tau);
+                                       (double *)D.tau, (double *)D.ipb);
   else
     k_base<float><<<nb, 128, 0, st>>>(D, theta0, N, p_surf, sponge_frac, tau_max, (float *)D.rhob,
                                       (float *)D.pb, (float *)D.thb, (float *)D.pik, (float *)D.rhobc,
-                                      (float *)D.tau);
+                                      (float *)D.tau, (float *)D.ipb);
   return cudaGetLastError();
 }
 
 cudaError_t launch_full(const StepLaunch &L, int prec, int rO, int rC, int rN, int rF, int first,
                         cudaStream_t st) {
-  return prec == CC_FP64 ? full_t<double>(L, rO, rC, rN, rF, first, st) : full_t<float>(L, rO, rC, rN, rF, first, st);
+  return prec == CC_FP64 ? full_t<double, TILE_Y_F64>(L, rO, rC, rN, rF, first, st)
+                         : full_t<float, TILE_Y_F32>(L, rO, rC, rN, rF, first, st);
 }
 
 cudaError_t launch_groups(const StepLaunch &L, int prec, int rO, int rC, int rN, int rF, int first,
@@ -814,10 +832,6 @@ cudaError_t launch_diagnose(const StepLaunch &L, int prec, int rV, int rC, int r
   else
     k_diag<float><<<(L.ncols + 127) / 128, 128, 0, st>>>(L.d_doms, L.cols, L.ncols, rV, rC, rO, rF, first, filter);
   return cudaGetLastError();
-}
-
-cudaError_t launch_ghost(const StepLaunch &L, int prec, int r1, int r2, cudaStream_t st) {
-  return prec == CC_FP64 ? ghost_t<double>(L, r1, r2, st) : ghost_t<float>(L, r1, r2, st);
 }
 
 cudaError_t launch_init_momentum(const DomDev &D, const DomDev *d_dom, int prec, int r, double U, cudaStream_t st) {
