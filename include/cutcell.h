@@ -169,6 +169,30 @@ cc_status cc_profile_enable(cc_model *m, int on);
 cc_status cc_profile_read(cc_model *m, int kernel, double *total_ms, long long *launches);
 cc_status cc_profile_reset(cc_model *m);
 
+/* Allocation-free mass sum (the paper has no counterpart; it is an entry
+ * point for callers that cannot call cudaMalloc -- code running inside
+ * another framework's memory pool, or a host application that reserves all
+ * device memory up front and must not allocate afterwards).
+ * Computes, on `stream`, the Neumaier-compensated sum that cc_diagnostics
+ * reports as the mass: out[0] = sum_i volume[i] * rho_prime[i] and
+ * out[1] = its compensation term, from device buffers the caller owns:
+ *   rho_prime: n device values (double for CC_FP64, float for CC_FP32);
+ *   volume:    n device doubles (cell volumes in m^3);
+ *   out:       2 device doubles, overwritten.
+ * The scratch is a fixed array inside the library holding
+ * CC_NOALLOC_MAX_PARTS partial sums (16 KiB per GPU that loads the library,
+ * kept until the process exits); the call uses nparts of them and rejects
+ * nparts outside 1..CC_NOALLOC_MAX_PARTS with CC_EINVAL.  Nothing is
+ * allocated and nothing is freed.  The first call on a device looks up the
+ * array's device address with that device current, so make that first call
+ * before any stream capture.  Every call shares the array: calls that overlap
+ * on the GPU (for example on two streams) race, so serialise them.
+ * Errors (CC_EINVAL, CC_ECUDA) are described by cc_noalloc_last_error(). */
+#define CC_NOALLOC_MAX_PARTS 1024 /* the message of cc_noalloc_last_error() quotes this limit */
+cc_status cc_mass_sum_noalloc(const void *rho_prime, int precision, const double *volume, long long n,
+                              int nparts, double *out, void *stream);
+const char *cc_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

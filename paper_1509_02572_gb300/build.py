@@ -20,6 +20,7 @@ UNITS = {
     "geometry.cu": ["-fmad=false"],
     "step.cu": [],
     "capi.cu": [],
+    "noalloc.cu": [],
 }
 
 

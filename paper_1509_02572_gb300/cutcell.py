@@ -25,7 +25,9 @@ HOST_GZ = 2
 EXPORTS = ("cc_create", "cc_destroy", "cc_last_error", "cc_set_terrain", "cc_build_geometry",
            "cc_get_geometry", "cc_get_stencils", "cc_get_groups", "cc_init_state", "cc_upload_state",
            "cc_download_state", "cc_step", "cc_diagnostics", "cc_synchronize", "cc_last_launch_count",
-           "cc_profile_enable", "cc_profile_read", "cc_profile_reset")
+           "cc_profile_enable", "cc_profile_read", "cc_profile_reset", "cc_mass_sum_noalloc",
+           "cc_noalloc_last_error")
+CC_NOALLOC_MAX_PARTS = 1024
 CC_K_FULL, CC_K_GROUPS, CC_K_DIAGNOSE, CC_K_GHOST = range(4)
 KERNEL_NAMES = {CC_K_FULL: "k_full", CC_K_GROUPS: "k_groups", CC_K_DIAGNOSE: "k_diag", CC_K_GHOST: "k_ghost"}
 
@@ -85,6 +87,9 @@ def load(path: str = LIB_PATH):
     L.cc_profile_enable.argtypes = [vp, i]
     L.cc_profile_read.argtypes = [vp, i, ct.POINTER(d), ct.POINTER(ct.c_longlong)]
     L.cc_profile_reset.argtypes = [vp]
+    L.cc_mass_sum_noalloc.argtypes = [vp, i, vp, ct.c_longlong, i, vp, vp]
+    L.cc_noalloc_last_error.restype = ct.c_char_p
+    L.cc_noalloc_last_error.argtypes = []
     _lib = L
     return L
 
@@ -108,6 +113,22 @@ def _current_stream():
     except Exception:
         pass
     return None
+
+
+def mass_sum_noalloc(rho_ptr: int, precision: int, volume_ptr: int, n: int, nparts: int, out_ptr: int,
+                     stream=None) -> int:
+    """cc_mass_sum_noalloc on caller-owned device buffers (raw pointers).
+
+    For callers that cannot allocate device memory: the library allocates
+    nothing for this call.  Returns the status; raises on errors."""
+    L = load()
+    if stream is None:
+        stream = _current_stream()
+    st = L.cc_mass_sum_noalloc(ct.c_void_p(rho_ptr), precision, ct.c_void_p(volume_ptr), int(n), int(nparts),
+                               ct.c_void_p(out_ptr), stream)
+    if st != CC_OK:
+        raise CutcellError(st, L.cc_noalloc_last_error().decode())
+    return st
 
 
 class Model:
