@@ -12,7 +12,7 @@ constexpr int HOST_GZ = 2;     // corner levels below floor / above lid in host 
 constexpr int NFIELD = 5;      // rho', p', rho u, rho v, rho w
 constexpr int NBUF = 4;        // rotating time levels
 constexpr int TILE_X = 32;                          // full-cell stencil tile width (x)
-constexpr int TILE_Y_F32 = 16, TILE_Y_F64 = 8;     // tile height (y) per precision
+constexpr int TILE_Y_F32 = 8, TILE_Y_F64 = 8;      // tile height (y) per precision
 
 // cell classes and corner classes
 enum : int8_t { C_UG = 0, C_FULL = 1, C_CUT = 2, C_ABS = 3 };

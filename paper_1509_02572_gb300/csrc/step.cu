@@ -4,9 +4,10 @@
 //            scalar fluxes and divergence with full apertures (Eq. fvm_d), the
 //            p' and rho' tendencies, momentum on regular velocity cells
 //            (Eqs. momentum_u_d .. w_d), fourth-order diffusion, sponge,
-//            leapfrog and Robert-Asselin filter.  A 2.5D march in z keeps a
-//            ring of haloed planes in shared memory; the loads of plane k+2 are
-//            issued before the work on plane k, two barriers per plane.  The
+//            leapfrog and Robert-Asselin filter.  A 2.5D march in z keeps
+//            rings of haloed planes in shared memory, filled by asynchronous
+//            copies (cp.async) issued three planes ahead of the work; two
+//            barriers per plane.  The
 //            periodic lateral boundary (Sec 3) is folded into the per-thread
 //            load offsets, so no ghost exchange is needed.  Branch-free: cut
 //            cells and diagnosed corners are recomputed by the list kernels.
@@ -171,18 +172,40 @@ struct FullCfg {
                        NLP = (PL + NT - 1) / NT;
 };
 
+// Shared-memory rings of haloed planes.  Raw planes arrive by asynchronous
+// copies issued three planes ahead; derived planes (total density, total rho
+// theta, corner velocity) are formed one plane ahead of their use.
 template <typename T, int PLn>
 struct FullSmem {
-  T rho[4][PLn], rp[4][PLn], th[4][PLn], pp[4][PLn];  // cell planes k-1 .. k+2
-  T u[3][3][PLn];                                     // corner velocity planes k-1 .. k+1
-  T mt[2][3][PLn];                                    // raw momentum planes awaiting conversion
-  T mo[3][PLn];                                       // momentum at n-1, plane k
-  T tho[PLn];                                         // (rho theta)' at n-1, plane k
+  T cr[6][PLn], cp[6][PLn];  // raw rho', p' (current level), planes k-2 .. k+3
+  T cm[4][3][PLn];           // raw momentum (current level), planes k-1 .. k+2 (+ in flight)
+  T op[5][PLn];              // raw p' at n-1, planes k-1 .. k+3
+  T om[5][3][PLn];           // raw momentum at n-1, planes k-1 .. k+3
+  T rh[4][PLn], th[4][PLn];  // total density and total rho theta, planes k-1 .. k+2
+  T uu[3][3][PLn];           // corner velocity, planes k-1 .. k+1
+  T to[PLn];                 // (rho theta)' at n-1, plane k
 };
 
-__device__ __forceinline__ int s4(int k) { return (k + 8) & 3; }
 __device__ __forceinline__ int s2(int k) { return (k + 8) & 1; }
 __device__ __forceinline__ int s3(int k) { return (k + 9) % 3; }
+__device__ __forceinline__ int s4(int k) { return (k + 8) & 3; }
+__device__ __forceinline__ int s5(int k) { return (k + 10) % 5; }
+__device__ __forceinline__ int s6(int k) { return (k + 12) % 6; }
+
+// asynchronous global -> shared copy of one element (cp.async, L1-allocating)
+template <typename T>
+__device__ __forceinline__ void acopy(T *dst, const T *src) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  if (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
+}
+__device__ __forceinline__ void acommit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void await_groups() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 
 template <typename T, int TYv>
 __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict__ doms,
@@ -231,67 +254,67 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
     int gi = wrapi(i0 - 2 + hx, nx), gj = wrapi(j0 - 2 + hy, ny);
     loff[s] = (long long)(gj + GH) * px + (gi + GH);
   }
-  auto load_cells = [&](int kk) {
-    const int sl = s4(kk), kp = kk + GH;
-    const T rb = rhob[kp];
-    const long long zo = (long long)kp * plane;
-#pragma unroll
-    for (int s = 0; s < NLP; s++) {
-      const int p = lpt[s];
-      if (p < PL) {
-        const long long gg = zo + loff[s];
-        T r = rpC[gg], q = ppC[gg];
-        S.rp[sl][p] = r;
-        S.pp[sl][p] = q;
-        S.rho[sl][p] = A::add(rb, r);
-        S.th[sl][p] = theta_tot(D, thb, pb, ipb, kp, q);
-      }
-    }
-  };
-  auto load_mt = [&](int kk) {
-    const int sl = s2(kk);
+  // issue the asynchronous copies of every raw field of plane kk (the
+  // current-level momentum only when with_m: its ring has four slots)
+  auto issue = [&](int kk, bool with_m) {
     const long long zo = (long long)(kk + GH) * plane;
+    const int a6 = s6(kk), a4 = s4(kk), a5 = s5(kk);
 #pragma unroll
     for (int s = 0; s < NLP; s++) {
       const int p = lpt[s];
       if (p < PL) {
-        const long long gg = zo + loff[s];
-        S.mt[sl][0][p] = mC0[gg];
-        S.mt[sl][1][p] = mC1[gg];
-        S.mt[sl][2][p] = mC2[gg];
+        const long long g = zo + loff[s];
+        acopy(&S.cr[a6][p], rpC + g);
+        acopy(&S.cp[a6][p], ppC + g);
+        if (with_m) {
+          acopy(&S.cm[a4][0][p], mC0 + g);
+          acopy(&S.cm[a4][1][p], mC1 + g);
+          acopy(&S.cm[a4][2][p], mC2 + g);
+        }
+        acopy(&S.op[a5][p], ppO + g);
+        acopy(&S.om[a5][0][p], mO0 + g);
+        acopy(&S.om[a5][1][p], mO1 + g);
+        acopy(&S.om[a5][2][p], mO2 + g);
       }
     }
   };
-  auto load_old_plane = [&](int kk) {
-    const int kp = kk + GH;
-    const long long zo = (long long)kp * plane;
+  // totals of plane kk from its raw plane
+  auto derive = [&](int kk) {
+    const int a6 = s6(kk), a4 = s4(kk), kp = kk + GH;
+    const T rb = rhob[kp];
 #pragma unroll
     for (int s = 0; s < NLP; s++) {
       const int p = lpt[s];
       if (p < PL) {
-        const long long gg = zo + loff[s];
-        S.tho[p] = theta_pert(D, thb, pb, ipb, kp, ppO[gg]);
-        S.mo[0][p] = mO0[gg];
-        S.mo[1][p] = mO1[gg];
-        S.mo[2][p] = mO2[gg];
+        S.rh[a4][p] = A::add(rb, S.cr[a6][p]);
+        S.th[a4][p] = theta_tot(D, thb, pb, ipb, kp, S.cp[a6][p]);
       }
     }
   };
-  // corner velocity = momentum / mean density of the 8 surrounding cells
-  auto compute_u = [&](int K) {
-    const int sl = s4(K - 1), sh = s4(K), su = s3(K), sm = s2(K);
+  // corner velocity of plane K = momentum / mean density of the 8 cells around
+  auto velocity = [&](int K) {
+    const int sl = s4(K - 1), sh = s4(K), su = s3(K), sm = s4(K);
 #pragma unroll
     for (int s = 0; s < NLP; s++) {
       const int p = lpt[s];
       const int hx = p % HX, hy = p / HX;
       if (p < PL && hx != 0 && hy != 0) {
-        const T *lo = S.rho[sl], *hi = S.rho[sh];
+        const T *lo = S.rh[sl], *hi = S.rh[sh];
         const int q00 = p - HX - 1, q01 = p - HX, q10 = p - 1, q11 = p;
         T iv = rinv(rho8(lo[q00], lo[q01], lo[q10], lo[q11], hi[q00], hi[q01], hi[q10], hi[q11]));
-        S.u[su][0][p] = S.mt[sm][0][p] * iv;
-        S.u[su][1][p] = S.mt[sm][1][p] * iv;
-        S.u[su][2][p] = S.mt[sm][2][p] * iv;
+        S.uu[su][0][p] = S.cm[sm][0][p] * iv;
+        S.uu[su][1][p] = S.cm[sm][1][p] * iv;
+        S.uu[su][2][p] = S.cm[sm][2][p] * iv;
       }
+    }
+  };
+  // (rho theta)' at n-1 of plane kk (in-plane diffusion stencil)
+  auto derive_old = [&](int kk) {
+    const int a5 = s5(kk), kp = kk + GH;
+#pragma unroll
+    for (int s = 0; s < NLP; s++) {
+      const int p = lpt[s];
+      if (p < PL) S.to[p] = theta_pert(D, thb, pb, ipb, kp, S.op[a5][p]);
     }
   };
 
@@ -308,52 +331,56 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
 
   // own column at n-1 for the vertical diffusion stencils, levels k-2 .. k+2
   T treg[5], mreg[5][3];
-  auto load_own_old = [&](int a, int kk) {
-    if (active) {
-      const int kp = kk + GH;
-      const long long o = (long long)kp * plane + own;
-      treg[a] = theta_pert(D, thb, pb, ipb, kp, ppO[o]);
-      mreg[a][0] = mO0[o];
-      mreg[a][1] = mO1[o];
-      mreg[a][2] = mO2[o];
-    } else {
-      treg[a] = 0;
-      mreg[a][0] = mreg[a][1] = mreg[a][2] = 0;
-    }
+  auto own_old = [&](int a, int kk) {
+    const int a5 = s5(kk);
+    treg[a] = theta_pert(D, thb, pb, ipb, kk + GH, S.op[a5][c]);
+    mreg[a][0] = S.om[a5][0][c];
+    mreg[a][1] = S.om[a5][1][c];
+    mreg[a][2] = S.om[a5][2][c];
   };
 
-  // prologue
-  load_cells(k0 - 2);
-  load_cells(k0 - 1);
-  load_cells(k0);
-  load_cells(k0 + 1);
-  load_mt(k0 - 1);
-  load_mt(k0);
+  // prologue: raw planes k0-2 .. k0+2, totals k0-2 .. k0+1, velocities k0-1, k0
+  // (momentum of plane k0-2 is not needed and would share a ring slot with k0+2)
+  for (int kk = k0 - 2; kk <= k0 + 2; kk++) issue(kk, kk != k0 - 2);
+  acommit();
+  await_groups<0>();
+  __syncthreads();
+  for (int kk = k0 - 2; kk <= k0 + 1; kk++) derive(kk);
 #pragma unroll
-  for (int a = 0; a < 4; a++) load_own_old(a, k0 - 2 + a);
+  for (int a = 0; a < 4; a++) own_old(a, k0 - 2 + a);
   __syncthreads();
-  compute_u(k0 - 1);
-  compute_u(k0);
-  __syncthreads();
-  load_mt(k0 + 1);
-  __syncthreads();
+  velocity(k0 - 1);
+  velocity(k0);
 
   for (int k = k0; k < k1; k++) {
-    // phase 1: loads for plane k+2 (and the n-1 plane k), velocities of plane k+1
-    load_cells(k + 2);
-    load_mt(k + 2);
-    load_old_plane(k);
-    load_own_old(4, k + 2);
-    compute_u(k + 1);
+    // phase 1: copies for plane k+3 in flight; totals of plane k+2,
+    // velocities of plane k+1, the n-1 fields of plane k
+    issue(k + 3, true);
+    acommit();
+    T rO_ = 0, mcur[3] = {0, 0, 0};
+    const long long o = (long long)(k + GH) * plane + own;
+    if (active) {
+      rO_ = rpO[o];
+      mcur[0] = mC0[o];
+      mcur[1] = mC1[o];
+      mcur[2] = mC2[o];
+    }
+    await_groups<1>();
+    __syncthreads();
+    derive(k + 2);
+    velocity(k + 1);
+    derive_old(k);
+    own_old(4, k + 2);
     __syncthreads();
     // phase 2: the cell and corner of this thread on plane k
     if (active) {
       const int sk = s4(k), skm = s4(k - 1), skp = s4(k + 1);
-      const T *R0 = S.rho[sk], *Rm = S.rho[skm], *Rp = S.rho[skp];
+      const int ck = s6(k), ckm = s6(k - 1);
+      const T *R0 = S.rh[sk], *Rm = S.rh[skm], *Rp = S.rh[skp];
       const T *H0 = S.th[sk], *Hm = S.th[skm], *Hp = S.th[skp];
       const int uk = s3(k), ukp = s3(k + 1), ukm = s3(k - 1);
-      const T *ux0 = S.u[uk][0], *uy0 = S.u[uk][1], *uz0 = S.u[uk][2];
-      const T *uxp = S.u[ukp][0], *uyp = S.u[ukp][1], *uzp = S.u[ukp][2];
+      const T *ux0 = S.uu[uk][0], *uy0 = S.uu[uk][1], *uz0 = S.uu[uk][2];
+      const T *uxp = S.uu[ukp][0], *uyp = S.uu[ukp][1], *uzp = S.uu[ukp][2];
       // ---- scalar cell (i,j,k): face fluxes, lower-index cell first
       T fxm = face_flux(R0[c - 1], R0[c], ux0[c], ux0[c + HX], uxp[c], uxp[c + HX], Sx);
       T fxp = face_flux(R0[c], R0[c + 1], ux0[c + 1], ux0[c + 1 + HX], uxp[c + 1], uxp[c + 1 + HX], Sx);
@@ -372,15 +399,14 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
       T RM = A::add(A::add(A::sub(fxp, fxm), A::sub(fyp, fym)), A::sub(fzp, fzm));
       T RH = A::add(A::add(A::sub(hxp, hxm), A::sub(hyp, hym)), A::sub(hzp, hzm));
       // fourth-order diffusion of (rho theta)' at n-1
-      const T *Tk = S.tho;
+      const T *Tk = S.to;
       T dd = d4(Tk[c - 2], Tk[c - 1], Tk[c], Tk[c + 1], Tk[c + 2]) +
              d4(Tk[c - 2 * HX], Tk[c - HX], Tk[c], Tk[c + HX], Tk[c + 2 * HX]) +
              d4(treg[0], treg[1], treg[2], treg[3], treg[4]);
       T Dth = -kdif * dd;
-      const long long o = (long long)(k + GH) * plane + own;
       const int kp = k + GH;
-      T rC_ = S.rp[sk][c], pC_ = S.pp[sk][c];
-      T rO_ = rpO[o], pO_ = ppO[o];
+      T rC_ = S.cr[ck][c], pC_ = S.cp[ck][c];
+      T pO_ = S.op[s5(k)][c];
       T rN_ = rO_ - dt2 * (RM * v0inv);
       T pN_ = pO_ - dt2 * Cp * exner_fac(D, pik, pb, ipb, kp, pC_) * (RH * v0inv - Dth);
       if (k < kug) { rN_ = 0; pN_ = 0; }
@@ -399,7 +425,7 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
       T rS = (Rm[c - HX - 1] + Rm[c - HX] + R0[c - HX - 1] + R0[c - HX]) * T(0.25);
       T rT = (R0[c - HX - 1] + R0[c - HX] + R0[c - 1] + R0[c]) * T(0.25);
       T rB = (Rm[c - HX - 1] + Rm[c - HX] + Rm[c - 1] + Rm[c]) * T(0.25);
-      const T *uxm = S.u[ukm][0], *uym = S.u[ukm][1], *uzm = S.u[ukm][2];
+      const T *uxm = S.uu[ukm][0], *uym = S.uu[ukm][1], *uzm = S.uu[ukm][2];
       T u0[3] = {ux0[c], uy0[c], uz0[c]};
       T uE[3] = {ux0[c + 1], uy0[c + 1], uz0[c + 1]};
       T uW[3] = {ux0[c - 1], uy0[c - 1], uz0[c - 1]};
@@ -410,25 +436,25 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
       T fE = rE * T(0.5) * (u0[0] + uE[0]) * Sx, fW = rW * T(0.5) * (uW[0] + u0[0]) * Sx;
       T fN = rNn * T(0.5) * (u0[1] + uN[1]) * Sy, fS = rS * T(0.5) * (uS[1] + u0[1]) * Sy;
       T fT = rT * T(0.5) * (u0[2] + uT[2]) * Sz, fB = rB * T(0.5) * (uB[2] + u0[2]) * Sz;
-      const T *P0 = S.pp[sk], *Pm = S.pp[skm];
+      const T *P0 = S.cp[ck], *Pm = S.cp[ckm];
       T pE = Pm[c - HX] + Pm[c] + P0[c - HX] + P0[c];
       T pW = Pm[c - HX - 1] + Pm[c - 1] + P0[c - HX - 1] + P0[c - 1];
       T pNn = Pm[c - 1] + Pm[c] + P0[c - 1] + P0[c];
       T pS = Pm[c - HX - 1] + Pm[c - HX] + P0[c - HX - 1] + P0[c - HX];
       T pT = P0[c - HX - 1] + P0[c - HX] + P0[c - 1] + P0[c];
       T pB = Pm[c - HX - 1] + Pm[c - HX] + Pm[c - 1] + Pm[c];
-      const T *Q0 = S.rp[sk], *Qm = S.rp[skm];
+      const T *Q0 = S.cr[ck], *Qm = S.cr[ckm];
       T r8 = (Q0[c - HX - 1] + Q0[c - HX] + Q0[c - 1] + Q0[c]) + (Qm[c - HX - 1] + Qm[c - HX] + Qm[c - 1] + Qm[c]);
       T pg[3] = {T(0.25) * (pE - pW) / dx, T(0.25) * (pNn - pS) / dy, T(0.25) * (pT - pB) / dz};
       const T tk = tau[kp];
-      const T *mcur[3] = {mC0, mC1, mC2};
+      const int ok5 = s5(k);
 #pragma unroll
       for (int d = 0; d < 3; d++) {
         T adv = fE * T(0.5) * (u0[d] + uE[d]) - fW * T(0.5) * (uW[d] + u0[d]) + fN * T(0.5) * (u0[d] + uN[d]) -
                 fS * T(0.5) * (uS[d] + u0[d]) + fT * T(0.5) * (u0[d] + uT[d]) - fB * T(0.5) * (uB[d] + u0[d]);
         T tend = -adv * v0inv - pg[d];
         if (d == 2) tend -= g * r8 * T(0.125);
-        const T *Mk = S.mo[d];
+        const T *Mk = S.om[ok5][d];
         // diffusion of the departure from the reference momentum (rho_bar U, 0, 0)
         T ref0 = d == 0 ? rhobc[kp] * U : T(0);
         T dm = d4(Mk[c - 2] - ref0, Mk[c - 1] - ref0, Mk[c] - ref0, Mk[c + 1] - ref0, Mk[c + 2] - ref0) +
@@ -442,13 +468,11 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
         T mold = mreg[2][d];
         tend += -kdif * dm - tk * (mold - ref0);
         T mnew = mold + dt2 * tend;
-        T mc = mcur[d][o];
-        T mf = mc + nu * (mnew - T(2) * mc + mold);
+        T mf = mcur[d] + nu * (mnew - T(2) * mcur[d] + mold);
         ((T *)D.f[rN][2 + d])[o] = mnew;
         ((T *)D.f[rF][2 + d])[o] = mf;
       }
     }
-    __syncthreads();
 #pragma unroll
     for (int a = 0; a < 4; a++) {
       treg[a] = treg[a + 1];
@@ -457,6 +481,7 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
       mreg[a][2] = mreg[a + 1][2];
     }
   }
+  await_groups<0>();
 }
 
 // ------------------------------------------------------------------ cut cells and merge groups
