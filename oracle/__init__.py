@@ -34,7 +34,7 @@ class Params(ct.Structure):
                 ("p_surf", ct.c_double), ("p0", ct.c_double), ("g", ct.c_double),
                 ("R", ct.c_double), ("cp", ct.c_double),
                 ("ra_nu", ct.c_double), ("c4", ct.c_double), ("sponge_frac", ct.c_double),
-                ("tau_max", ct.c_double), ("bc_slip", ct.c_int)]
+                ("tau_max", ct.c_double), ("bc_slip", ct.c_int), ("ztop", ct.c_double)]
 
 
 def build(force: bool = False) -> str:
@@ -87,7 +87,7 @@ def lib():
 def params_from(cfg) -> Params:
     p = Params()
     for name, _ in Params._fields_:
-        setattr(p, name, getattr(cfg, name))
+        setattr(p, name, getattr(cfg, name, 0.0 if name == "ztop" else None))
     return p
 
 

@@ -14,7 +14,12 @@ typedef struct {
   double U, N, theta0, p_surf, p0, g, R, cp;
   double ra_nu, c4, sponge_frac, tau_max;
   int bc_slip;
+  double ztop;  /* height of the domain top for the sponge; 0: nz*dz */
 } oc_params;
+
+/* refined level l >= 1: nx, ny, nz cells of spacing 2^-l H starting at the
+ * floor; its cell i covers the cell (i + ox)/2 of level l-1 */
+typedef struct { int nx, ny, nz, ox, oy; } oc_box;
 
 typedef struct oc_model oc_model;
 
@@ -38,5 +43,14 @@ double oc_line_frac(double z, double ha, double hb);
 double oc_col_int(double z, double h00, double h10, double h01, double h11, double dx, double dy,
                   int kind);
 double oc_gauss_legendre8(double (*f)(double, void *), void *ctx, double a, double b);
+
+typedef struct oc_refine oc_refine;
+oc_refine *oc_refine_create(const oc_params *P0, int nlev, const oc_box *boxes, const double *h_finest,
+                            int *status);
+void oc_refine_destroy(oc_refine *R);
+void oc_refine_init(oc_refine *R);
+void oc_refine_step(oc_refine *R, int n);
+oc_model *oc_refine_level(oc_refine *R, int l);
+double oc_refine_mass(oc_refine *R, int both);
 
 #endif
