@@ -67,6 +67,7 @@ def lib():
             L.oc_get_points.argtypes = [ct.c_void_p] + [ct.c_void_p] * 9
             L.oc_get_base.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_void_p,
                                       ct.POINTER(ct.c_int), ct.POINTER(ct.c_int)]
+            L.oc_base_len.argtypes = [ct.c_void_p]
             L.oc_mass.restype = ct.c_double
             L.oc_mass.argtypes = [ct.c_void_p, ct.c_int]
             L.oc_nsteps.argtypes = [ct.c_void_p]
@@ -76,6 +77,16 @@ def lib():
             L.oc_line_frac.argtypes = [ct.c_double] * 3
             L.oc_col_int.restype = ct.c_double
             L.oc_col_int.argtypes = [ct.c_double] * 7 + [ct.c_int]
+            L.oc_refine_create.restype = ct.c_void_p
+            L.oc_refine_create.argtypes = [ct.POINTER(Params), ct.c_int, ct.c_void_p, ct.c_void_p,
+                                           ct.POINTER(ct.c_int)]
+            L.oc_refine_destroy.argtypes = [ct.c_void_p]
+            L.oc_refine_init.argtypes = [ct.c_void_p]
+            L.oc_refine_step.argtypes = [ct.c_void_p, ct.c_int]
+            L.oc_refine_level.restype = ct.c_void_p
+            L.oc_refine_level.argtypes = [ct.c_void_p, ct.c_int]
+            L.oc_refine_mass.restype = ct.c_double
+            L.oc_refine_mass.argtypes = [ct.c_void_p, ct.c_int]
             FN = ct.CFUNCTYPE(ct.c_double, ct.c_double, ct.c_void_p)
             L.oc_gauss_legendre8.restype = ct.c_double
             L.oc_gauss_legendre8.argtypes = [FN, ct.c_void_p, ct.c_double, ct.c_double]
@@ -166,7 +177,7 @@ class Model:
         return out
 
     def base(self):
-        nb = self.cfg.nz + 2 * (self.gz + 2)
+        nb = lib().oc_base_len(self._m)
         rhob, pb = np.zeros(nb), np.zeros(nb)
         koff, n = ct.c_int(), ct.c_int()
         lib().oc_get_base(self._m, _ptr(rhob), _ptr(pb), ct.byref(koff), ct.byref(n))
@@ -223,3 +234,72 @@ def gauss_legendre8(f, a, b):
     L = lib()
     cb = L._FN(lambda s, _ctx: f(s))
     return L.oc_gauss_legendre8(cb, None, a, b)
+
+
+class Box(ct.Structure):
+    _fields_ = [("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int), ("ox", ct.c_int), ("oy", ct.c_int)]
+
+
+class _LevelView(Model):
+    """A level owned by a Refine driver (not destroyed by itself)."""
+
+    def __init__(self, owner, ptr, cfg):
+        self._owner = owner
+        self.cfg = cfg
+        self._m = ptr
+        nc, np_, nq, gz = ct.c_long(), ct.c_long(), ct.c_long(), ct.c_int()
+        lib().oc_dims(self._m, ct.byref(nc), ct.byref(np_), ct.byref(nq), ct.byref(gz))
+        self.ncell, self.ncorner, self.ncol, self.gz = nc.value, np_.value, nq.value, gz.value
+
+    def __del__(self):
+        pass
+
+
+class Refine:
+    """Block-structured refinement: level 0 = cfg (periodic, lid), levels
+    1.. = boxes (nx, ny, nz, ox, oy) in cells of that level; h_finest = corner
+    heights of the finest level over I, J = -4 .. n+4 ((ny+9) x (nx+9))."""
+
+    def __init__(self, cfg, boxes, h_finest=None):
+        L = lib()
+        self.cfg = cfg
+        self.boxes = [tuple(b) for b in boxes]
+        self._p = params_from(cfg)
+        nlev = 1 + len(boxes)
+        arr = (Box * max(1, len(boxes)))(*[Box(*b) for b in boxes])
+        self._arr = arr
+        hp = None
+        if h_finest is not None:
+            h_finest = np.ascontiguousarray(h_finest, dtype=np.float64)
+            hp = _ptr(h_finest)
+        st = ct.c_int(0)
+        self._r = L.oc_refine_create(ct.byref(self._p), nlev, ct.cast(arr, ct.c_void_p), hp, ct.byref(st))
+        if not self._r:
+            raise OracleError(f"refine create failed with status {st.value}")
+        self.nlev = nlev
+        self.levels = []
+        for l in range(nlev):
+            import dataclasses
+            f = 2.0 ** -l
+            if l == 0:
+                c = cfg
+            else:
+                nx, ny, nz, ox, oy = self.boxes[l - 1]
+                c = dataclasses.replace(cfg, nx=nx, ny=ny, nz=nz, dx=cfg.dx * f, dy=cfg.dy * f, dz=cfg.dz * f,
+                                        dt=cfg.dt * f)
+            self.levels.append(_LevelView(self, L.oc_refine_level(self._r, l), c))
+
+    def __del__(self):
+        r = getattr(self, "_r", None)
+        if r:
+            lib().oc_refine_destroy(r)
+            self._r = None
+
+    def init_state(self):
+        lib().oc_refine_init(self._r)
+
+    def step(self, n: int = 1):
+        lib().oc_refine_step(self._r, int(n))
+
+    def mass(self, both: bool = True) -> float:
+        return lib().oc_refine_mass(self._r, 1 if both else 0)

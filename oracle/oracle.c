@@ -62,8 +62,10 @@ struct oc_model {
   int nxp, nyp, nzp;  /* padded extents                                     */
   long np;            /* nxp*nyp*nzp: cells and corners share the index   */
   long nq;            /* nxp*nyp: columns                                  */
-  /* computed region: cells (i,j,k) with ci0<=i<ci1, cj0<=j<cj1, 0<=k<ck1 */
-  int ci0, ci1, cj0, cj1, ck1;
+  /* computed region: cells (i,j,k) with ci0<=i<ci1, cj0<=j<cj1, 0<=k<ck1;
+   * corner columns (I,J) with qi0<=I<ci1, qj0<=J<cj1 (a box level integrates
+   * the corners -1 .. n+1, symmetric about its centre) */
+  int ci0, ci1, cj0, cj1, ck1, qi0, qj0;
   /* geometry region (cells whose geometry is evaluated) */
   int gi0, gi1, gj0, gj1, gk1;
   /* terrain */
@@ -115,7 +117,7 @@ static inline long cell_id(const oc_model *m, long p) {
   return (k * m->ny + j) * m->nx + i;
 }
 static inline int in_comp_col(const oc_model *m, int I, int J) {
-  return I >= m->ci0 && I < m->ci1 && J >= m->cj0 && J < m->cj1;
+  return I >= m->qi0 && I < m->ci1 && J >= m->qj0 && J < m->cj1;
 }
 /* highest corner level written by the velocity diagnosis */
 static inline int diag_top(const oc_model *m) { return m->lid ? m->nz + G - 1 : m->ck1 - 1; }
@@ -270,6 +272,8 @@ static oc_model *level_create(const oc_params *P, int periodic, int lid, const d
     m->ci0 = -2; m->ci1 = m->nx + 2; m->cj0 = -2; m->cj1 = m->ny + 2;
     m->gi0 = -G; m->gi1 = m->nx + G; m->gj0 = -G; m->gj1 = m->ny + G;
   }
+  m->qi0 = periodic ? 0 : -1;
+  m->qj0 = periodic ? 0 : -1;
   m->ck1 = lid ? m->nz : m->nz + 2;
   m->gk1 = lid ? m->nz : m->nz + G;
   long nh = periodic ? (long)m->nx * m->ny : (long)(m->nxp + 1) * (m->nyp + 1);
@@ -491,16 +495,16 @@ static int build_geometry(oc_model *m) {
       }
   /* the lid rule needs a predicted point just below the lid in every column */
   if (m->lid)
-    for (int J = m->cj0; J < m->cj1; J++)
-      for (int I = m->ci0; I < m->ci1; I++)
+    for (int J = m->qj0; J < m->cj1; J++)
+      for (int I = m->qi0; I < m->ci1; I++)
         if (m->vcls[CI(m, I, J, nz - 1)] != V_PRED) return OC_EGEOM;
 
   /* boundary-point stencils: unit normal from the corner gradients of the
    * column-centre heights, then the nearest plane of predicted points crossed
    * by the normal line (Sec 2.4, nearest-plane construction) */
   int ktopsearch = m->lid ? nz - 1 : m->ck1 - 1;
-  for (int J = m->cj0; J < m->cj1; J++)
-    for (int I = m->ci0; I < m->ci1; I++) {
+  for (int J = m->qj0; J < m->cj1; J++)
+    for (int I = m->qi0; I < m->ci1; I++) {
       long q = QI(m, I, J);
       double hm = m->hc[QI(m, I - 1, J - 1)], h0m = m->hc[QI(m, I, J - 1)];
       double hm0 = m->hc[QI(m, I - 1, J)], h00 = m->hc[QI(m, I, J)];
@@ -541,8 +545,8 @@ static int build_geometry(oc_model *m) {
   /* merged-face points: interpolate along the vertical line between the
    * boundary point and the nearest predicted point above */
   for (int K = -G; K < nz + G; K++)
-    for (int J = m->cj0; J < m->cj1; J++)
-      for (int I = m->ci0; I < m->ci1; I++) {
+    for (int J = m->qj0; J < m->cj1; J++)
+      for (int I = m->qi0; I < m->ci1; I++) {
         long p = CI(m, I, J, K);
         m->mK[p] = -1; m->mg[p] = 0.0;
         if (m->vcls[p] != V_MF || K >= m->ck1) continue;
@@ -603,8 +607,8 @@ static void corner_velocity(const oc_model *m, int L, int I, int J, int K, doubl
  *  the terrain hold the boundary velocity as momentum (rho_corner * u_B). */
 static void diagnose_velocity(oc_model *m, int L) {
   int nz = m->nz;
-  for (int J = m->cj0; J < m->cj1; J++)
-    for (int I = m->ci0; I < m->ci1; I++) {
+  for (int J = m->qj0; J < m->cj1; J++)
+    for (int I = m->qi0; I < m->ci1; I++) {
       long q = QI(m, I, J);
       double uN[3] = {0, 0, 0};
       int K = m->bK[q], i0 = m->bI[q], j0 = m->bJ[q];
@@ -630,8 +634,8 @@ static void diagnose_velocity(oc_model *m, int L) {
       for (int d = 0; d < 3; d++) m->ub[L][3 * q + d] = ubv[d];
     }
   int ktop = diag_top(m);
-  for (int J = m->cj0; J < m->cj1; J++)
-    for (int I = m->ci0; I < m->ci1; I++) {
+  for (int J = m->qj0; J < m->cj1; J++)
+    for (int I = m->qi0; I < m->ci1; I++) {
       long q = QI(m, I, J);
       for (int K = -G + 1; K <= ktop; K++) {
         long p = CI(m, I, J, K);
@@ -671,8 +675,8 @@ void oc_init_state(oc_model *m) {
   }
   /* uniform flow U on predicted points; zero perturbations */
   for (int K = -G; K < m->nz + G; K++)
-    for (int J = m->cj0; J < m->cj1; J++)
-      for (int I = m->ci0; I < m->ci1; I++) {
+    for (int J = m->qj0; J < m->cj1; J++)
+      for (int I = m->qi0; I < m->ci1; I++) {
         long p = CI(m, I, J, K);
         if (m->vcls[p] == V_PRED) m->mx[1][p] = rho_corner(m, 1, I, J, K) * P->U;
       }
@@ -782,7 +786,7 @@ void oc_step(oc_model *m, int nsteps) {
     /* momentum on predicted velocity cells, Eqs. momentum_u_d .. w_d */
     FOR_COMP(m, I, J, K) {
       long p = CI(m, I, J, K);
-      if (m->vcls[p] != V_PRED) continue;
+      if (m->vcls[p] != V_PRED || !in_comp_col(m, I, J)) continue;
       double rE = 0, rW = 0, rN = 0, rS = 0, rT = 0, rB = 0;
       double pE = 0, pW = 0, pN = 0, pS = 0, pT = 0, pB = 0, r8 = 0;
       for (int a = -1; a <= 0; a++)
@@ -845,8 +849,8 @@ void oc_step(oc_model *m, int nsteps) {
     /* Robert-Asselin filter on every corner value of the computed columns
      * (prognostic or diagnosed) */
     for (int K = -G + 1; K <= ktop; K++)
-      for (int J = m->cj0; J < m->cj1; J++)
-        for (int I = m->ci0; I < m->ci1; I++) {
+      for (int J = m->qj0; J < m->cj1; J++)
+        for (int I = m->qi0; I < m->ci1; I++) {
           long p = CI(m, I, J, K);
           m->mx[3][p] = m->mx[1][p] + nu * (m->mx[2][p] - 2.0 * m->mx[1][p] + m->mx[O][p]);
           m->my[3][p] = m->my[1][p] + nu * (m->my[2][p] - 2.0 * m->my[1][p] + m->my[O][p]);
@@ -1040,6 +1044,8 @@ int oc_get_points(const oc_model *m, int8_t *vcls, int32_t *bK, int32_t *bI, int
   return OC_OK;
 }
 
+int oc_base_len(const oc_model *m) { return m->nb; }
+
 int oc_get_base(const oc_model *m, double *rhob, double *pb, int *koff, int *nb) {
   memcpy(rhob, m->rhob, 8 * m->nb); memcpy(pb, m->pb, 8 * m->nb);
   *koff = m->boff; *nb = m->nb;
@@ -1091,9 +1097,10 @@ static inline void covered(const oc_box *b, int *x0, int *x1, int *y0, int *y1, 
 }
 
 /* Coarse -> fine (Sec 2.2): every fine ghost cell outside the region the fine
- * level integrates takes the value of the coarse cell that covers it
- * (injection); fine ghost corners take the coarse momentum interpolated
- * linearly along each axis (coincident points copy; reading C-14).  All four
+ * level integrates (cells -2 .. n+1) takes the value of the coarse cell that
+ * covers it (injection); fine ghost corners outside the integrated corners
+ * (-1 .. n+1) take the coarse momentum interpolated linearly along each axis
+ * (coincident points copy; reading C-14).  All four
  * time-level buffers of the fine level receive the current coarse values. */
 static void prolong(oc_model *c, oc_model *f, const oc_box *b) {
   for (int k = 0; k < f->nz + G; k++)
@@ -1111,7 +1118,7 @@ static void prolong(oc_model *c, oc_model *f, const oc_box *b) {
   for (int K = -G + 1; K < f->nz + G; K++)
     for (int J = -G; J < f->ny + G; J++)
       for (int I = -G; I < f->nx + G; I++) {
-        if (I >= -2 && I < f->nx + 2 && J >= -2 && J < f->ny + 2 && K < f->nz + 2) continue;
+        if (I >= -1 && I < f->nx + 2 && J >= -1 && J < f->ny + 2 && K < f->nz + 2) continue;
         int X = I + b->ox, Y = J + b->oy;
         int xs[2] = {X >> 1, (X + 1) >> 1}, ys[2] = {Y >> 1, (Y + 1) >> 1}, zs[2] = {K >> 1, (K + 1) >> 1};
         double s[3] = {0, 0, 0};

@@ -34,6 +34,7 @@ int oc_get_geometry(const oc_model *m, double *vf, double *ax, double *ay, doubl
                     int32_t *root, double *vg, double *hc, double *gx, double *gy);
 int oc_get_points(const oc_model *m, int8_t *vcls, int32_t *bK, int32_t *bI, int32_t *bJ, double *ba,
                   double *bb, double *bn, int32_t *mK, double *mg);
+int oc_base_len(const oc_model *m);
 int oc_get_base(const oc_model *m, double *rhob, double *pb, int *koff, int *nb);
 double oc_mass(const oc_model *m, int level);
 int oc_nsteps(const oc_model *m);

@@ -147,3 +147,76 @@ def ensemble_configs(n: int = 64, seed: int = 1509) -> list[RunConfig]:
         out.append(RunConfig(f"ens{e}-{kind}-{nx}x{nx}x{nz}", nx, nx, nz, d, d, d, dt, 500,
                              kind, h0, a, U=U, N=N))
     return out
+
+
+@dataclasses.dataclass
+class RefinedConfig:
+    """Block-structured refinement: level 0 is `base` (the periodic domain);
+    level l >= 1 is a box (nx, ny, nz, ox, oy) of cells of spacing 2^-l of the
+    base spacing starting at the floor, whose cell i covers cell (i + ox) // 2
+    of level l-1.  The hill (terrain, h0, a of `base`) lies in the finest
+    level, centred on the domain centre; coarser levels see a flat floor."""
+    name: str
+    base: RunConfig
+    boxes: list
+
+    @property
+    def nlev(self) -> int:
+        return 1 + len(self.boxes)
+
+    def level_origin(self, l: int) -> tuple:
+        """Absolute (x, y) of the low corner of level l's cell (0, 0)."""
+        x = y = 0.0
+        for m in range(1, l + 1):
+            nx, ny, nz, ox, oy = self.boxes[m - 1]
+            d = self.base.dx * 2.0 ** -m
+            x += ox * d
+            y += oy * d
+        return x, y
+
+    def finest_heights(self, pad: int = 0) -> np.ndarray:
+        """Corner heights of the finest level for I, J = -pad .. n+pad-1
+        (interior corners when pad = 0; the padded set has n + 2 pad + 1 per
+        row when pad > 0, i.e. I, J = -pad .. n+pad)."""
+        l = self.nlev - 1
+        b = self.base
+        f = 2.0 ** -l
+        dx, dy = b.dx * f, b.dy * f
+        if l == 0:
+            return corner_heights(b.terrain, b.nx, b.ny, dx, dy, b.h0, b.a)
+        nx, ny = self.boxes[l - 1][0], self.boxes[l - 1][1]
+        x0, y0 = self.level_origin(l)
+        xc, yc = 0.5 * b.nx * b.dx, 0.5 * b.ny * b.dy
+        n_x = nx + 2 * pad + (1 if pad else 0)
+        n_y = ny + 2 * pad + (1 if pad else 0)
+        return corner_heights(b.terrain, n_x, n_y, dx, dy, b.h0, b.a,
+                              xc=xc - (x0 - pad * dx), yc=yc - (y0 - pad * dy))
+
+    def cells(self) -> int:
+        n = self.base.cells
+        for bx in self.boxes:
+            n += bx[0] * bx[1] * bx[2]
+        return n
+
+    def active_cells(self) -> int:
+        n = self.cells()
+        for bx in self.boxes:
+            n -= (bx[0] // 2) * (bx[1] // 2) * (bx[2] // 2)
+        return n
+
+
+# Three levels around a hemisphere of radius 600 m: 400 m / 200 m / 100 m,
+# 32 x 32 x 16 cells per level (oracle-sized).
+SMALL_REFINED = RefinedConfig(
+    "refined-3x32x32x16-hemisphere",
+    RunConfig("refined-base", 32, 32, 16, 400.0, 400.0, 400.0, 0.3, 20, "hemisphere", 600.0, 600.0),
+    [(32, 32, 16, 16, 16), (32, 32, 16, 16, 16)])
+
+# Hemisphere of radius 1 km with three levels: 200 m over the 64 x 32 x 16 km
+# domain, 100 m over x in [6.4, 57.6] km, y in [1.6, 30.4] km, z < 8 km, and
+# 50 m over x in [12.8, 51.2] km, y in [4.8, 27.2] km, z < 4.8 km.
+C4_REFINED = RefinedConfig(
+    "refined-hemisphere-200-100-50m",
+    RunConfig("refined-base-320x160x80-200m", 320, 160, 80, 200.0, 200.0, 200.0, 0.15, 200,
+              "hemisphere", 1000.0, 1000.0),
+    [(512, 288, 80, 64, 16), (768, 448, 96, 128, 64)])

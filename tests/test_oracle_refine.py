@@ -1,0 +1,112 @@
+"""Pins of the oracle's block-structured refinement (paper Sec 2.2): rest
+state, mass conservation across the coarse-fine interfaces, mirror symmetry
+across the nested boxes, stability."""
+import numpy as np
+import pytest
+
+from paper_1509_02572_gb300 import workloads as W
+
+RC = W.SMALL_REFINED
+
+
+def _refine(oracle_mod, **kw):
+    base = RC.base.replace(**kw)
+    R = oracle_mod.Refine(base, RC.boxes, RC.finest_heights(pad=4))
+    R.init_state()
+    return R
+
+
+def test_finest_terrain_is_flat_near_box_edges():
+    h = RC.finest_heights(pad=4)
+    assert h.max() > 100.0
+    assert np.all(h[:11] == 0) and np.all(h[-11:] == 0) and np.all(h[:, :11] == 0) and np.all(h[:, -11:] == 0)
+
+
+def test_refined_rest_state_stays_at_rest(oracle_mod):
+    """No wind, no perturbation: the ghost fill, the restriction and the flux
+    register add nothing, on every level."""
+    R = _refine(oracle_mod, U=0.0)
+    R.step(3)
+    for lev in R.levels:
+        for f in (oracle_mod.F_RHOP, oracle_mod.F_PP, oracle_mod.F_MX, oracle_mod.F_MY, oracle_mod.F_MZ):
+            assert np.abs(lev.field(f)).max() == 0.0
+
+
+def test_refined_mass_conserved_with_filter_off(oracle_mod):
+    """With the Robert-Asselin filter off, the two-time-level perturbation mass
+    of the active cells of all levels is conserved to round-off once every
+    level has left its forward-Euler start: the coarse face flux at a
+    coarse-fine interface is the mean of the fine fluxes of the two substeps
+    (the cube-boundary flux of Sec 2.2)."""
+    R = _refine(oracle_mod, ra_nu=0.0)
+    R.step(1)
+    q0 = R.mass()
+    qs = []
+    for _ in range(5):
+        R.step(1)
+        qs.append(R.mass())
+    # scale: the mass the flow carries through the level-1 box boundary in one
+    # coarse step (rho U times the box's upstream face area times 2 dt)
+    nx, ny, nz, ox, oy = RC.boxes[0]
+    face = (ny * RC.base.dy / 2) * (nz * RC.base.dz / 2)
+    flux = 1.2 * RC.base.U * face * 2 * RC.base.dt
+    for q in qs:
+        assert abs(q - q0) <= 1e-13 * flux, (q, q0, flux)
+
+
+def test_refined_mass_drift_reported_with_filter(oracle_mod):
+    """With the filter on the invariant is not exact; its drift stays small
+    against the transport (recorded, not part of the method's guarantees)."""
+    R = _refine(oracle_mod)
+    R.step(1)
+    q0 = R.mass()
+    R.step(4)
+    nx, ny, nz, ox, oy = RC.boxes[0]
+    flux = 1.2 * RC.base.U * (ny * RC.base.dy / 2) * (nz * RC.base.dz / 2) * 2 * RC.base.dt
+    assert abs(R.mass() - q0) <= 1e-3 * flux
+
+
+def _mirror_checks(lev, oracle_mod, tol):
+    c = lev.cfg
+    p = lev.field(oracle_mod.F_PP)
+    mx, my, mz = lev.field(oracle_mod.F_MX), lev.field(oracle_mod.F_MY), lev.field(oracle_mod.F_MZ)
+    sp = max(np.abs(p).max(), 1e-300)
+    sm = max(np.abs(mx).max(), np.abs(mz).max(), 1e-300)
+    assert np.max(np.abs(p - p[:, :, ::-1])) <= tol * sp
+    assert np.max(np.abs(p - p[:, ::-1, :])) <= tol * sp
+    # corners: I -> nx - I; corner nx is not stored (interior corners only), so
+    # compare I = 1 .. nx-1 against nx-1 .. 1
+    assert np.max(np.abs(mx[:, :, 1:] + mx[:, :, :0:-1])) <= tol * sm
+    assert np.max(np.abs(mz[:, :, 1:] - mz[:, :, :0:-1])) <= tol * sm
+    assert np.max(np.abs(my[:, 1:, :] + my[:, :0:-1, :])) <= tol * sm
+    assert np.max(np.abs(mz[:, 1:, :] - mz[:, :0:-1, :])) <= tol * sm
+
+
+def test_refined_mirror_symmetry(oracle_mod):
+    """The nested boxes and the hemisphere are centred, so a pressure bubble
+    above the hill at rest evolves mirror-symmetrically in x and y on every
+    level: injection, restriction and the register treat both sides alike."""
+    R = _refine(oracle_mod, U=0.0)
+    lev0 = R.levels[0]
+    c = lev0.cfg
+    kk, jj, ii = np.meshgrid(np.arange(c.nz) + 0.5, np.arange(c.ny) + 0.5, np.arange(c.nx) + 0.5, indexing="ij")
+    x = ii * c.dx - 0.5 * c.nx * c.dx
+    y = jj * c.dy - 0.5 * c.ny * c.dy
+    z = kk * c.dz - 1400.0
+    bubble = 40.0 * np.exp(-(x * x + y * y + z * z) / (900.0 ** 2))
+    for L in (0, 1):
+        lev0.set_field(oracle_mod.F_PP, L, bubble)
+    R.step(3)
+    for lev in R.levels:
+        _mirror_checks(lev, oracle_mod, 1e-11)
+
+
+def test_refined_run_is_stable(oracle_mod):
+    R = _refine(oracle_mod)
+    R.step(12)
+    for lev in R.levels:
+        for f in (oracle_mod.F_RHOP, oracle_mod.F_PP, oracle_mod.F_MZ):
+            a = lev.field(f)
+            assert np.isfinite(a).all()
+    w = R.levels[-1].field(oracle_mod.F_MZ)
+    assert 0.5 < np.abs(w).max() < 50.0
