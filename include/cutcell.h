@@ -164,10 +164,68 @@ long long cc_last_launch_count(const cc_model *m);
  * cc_step brackets each stage with CUDA events on the model's stream;
  * cc_profile_read synchronises and returns the summed device time (ms) and the
  * number of timed launches of one stage since the last cc_profile_reset. */
-enum { CC_K_FULL = 0, CC_K_GROUPS = 1, CC_K_DIAGNOSE = 2, CC_K_GHOST = 3 };
+enum { CC_K_FULL = 0, CC_K_GROUPS = 1, CC_K_DIAGNOSE = 2, CC_K_GHOST = 3, CC_K_REFINE = 4 };
 cc_status cc_profile_enable(cc_model *m, int on);
 cc_status cc_profile_read(cc_model *m, int kernel, double *total_ms, long long *launches);
 cc_status cc_profile_reset(cc_model *m);
+
+/* ------------------------------------------------------------------------
+ * Block-structured refinement with subcycling (Sec 2.2).
+ *
+ * A refined model holds nlev levels as domains 0 .. nlev-1 of one model.
+ * Level 0 is `base` (periodic, rigid lid).  Level l >= 1 is the box
+ * boxes[l-1] = {nx, ny, nz, ox, oy}: nx x ny x nz cells of spacing 2^-l of
+ * the base spacing, resting on the floor, whose cell i covers cell
+ * (i + ox) / 2 of level l-1 (likewise j with oy; cell k covers k / 2).  Its
+ * time step is 2^-l dt: every step of level l-1 takes two steps of level l
+ * first (subcycling), then the coarse step, then the exchange:
+ *   - coarse -> fine: every ghost cell of level l outside the cells it
+ *     integrates (-2 .. n+1 laterally, k < nz+2) takes the value of the
+ *     coarse cell covering it; every ghost corner outside the corners it
+ *     integrates (-1 .. n+1, K < nz+2) the coarse momentum interpolated
+ *     linearly along each axis;
+ *   - fine -> coarse: coarse cells of the covered box within 4 cells of its
+ *     boundary take the mean of their 8 fine cells; coarse corners strictly
+ *     inside it (within 4) the coincident fine corner;
+ *   - flux register: a coarse face on the boundary of the covered box
+ *     carries, for the mass and rho-theta updates of the coarse cell outside
+ *     the box, the mean over the two fine substeps of the sum of its 2 x 2
+ *     fine face fluxes, so the fluxes leaving one level enter the other.
+ * With the Robert-Asselin filter off, the two-time-level perturbation mass
+ * over the active cells of all levels (cc_refine_mass) is then conserved to
+ * round-off.
+ * Constraints (CC_EINVAL otherwise): 2 <= nlev <= 8; nx, ny, nz, ox, oy even;
+ * the covered box (ox/2 .. (ox+nx)/2, oy/2 .. (oy+ny)/2, 0 .. nz/2) at least
+ * 8 cells inside the coarser level's edges and below its top.  Terrain: a
+ * box level takes corner heights for I < nx, J < ny (cc_set_terrain) that
+ * are zero within 8 corners of its edges; at cc_build_geometry every coarser
+ * level must be flat (zero heights) within 4 cells of each covered box
+ * (CC_EGEOM otherwise).  Host arrays of a box level cover its cells and
+ * corners 0 .. n-1 (the layouts above with its nx, ny, nz).
+ * cc_init_state, cc_step (n steps of level 0, each a full cycle),
+ * cc_upload_state / cc_download_state / cc_diagnostics (domain = level) work
+ * on refined models as on ensembles. */
+typedef struct {
+  int nx, ny, nz, ox, oy;
+} cc_box;
+
+/* Create a refined model of nlev levels: level 0 from *base, levels 1 ..
+ * nlev-1 from boxes[0 .. nlev-2] (spacings and time step halved per level,
+ * every other constant from *base; the sponge of every level is measured
+ * against the top of level 0).  Precision, stream and ownership as in
+ * cc_create. */
+cc_status cc_create_refined(const cc_config *base, int nlev, const cc_box *boxes, int precision,
+                            void *stream, cc_model **out);
+
+/* Two-time-level perturbation mass of a refined model (Sec 2.2, reading of
+ * the conservation check): sum over the levels of V rho' over the merged cells
+ * of each level outside the box covered by the next finer level, at the
+ * current level, plus the same sum at the previous level when both != 0.
+ * out[0] receives the sum (kg).  Synchronises the stream. */
+cc_status cc_refine_mass(cc_model *m, int both, double *out);
+
+/* Number of domains (ensemble members, or levels of a refined model). */
+int cc_domain_count(const cc_model *m);
 
 /* Allocation-free mass sum (the paper has no counterpart; it is an entry
  * point for callers that cannot call cudaMalloc -- code running inside

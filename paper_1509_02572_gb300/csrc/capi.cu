@@ -8,6 +8,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "cc_internal.h"
@@ -21,8 +22,21 @@ struct DomHost {
   DomDev D{};
   std::vector<void *> allocs;
   bool terrain = false;
+  std::vector<double> hh;  // host copy of the corner heights
   int ng = 0, nm = 0;
   std::vector<int32_t> ghost, gstart, gmem;
+  int r[4] = {0, 1, 2, 3};  // roles: old (filtered n-1), current, new, filtered n
+  long long nsteps = 0;
+  // this domain's ranges of the model-wide work, group and column lists
+  int item0 = 0, nitem = 0, group0 = 0, ngroup = 0, col0 = 0, ncol = 0;
+};
+
+// Coarse-fine link of refined level l >= 1 with level l-1 (host side; the
+// LevelLink holds the device lists)
+struct LinkHost {
+  cc_box box{};
+  int x0 = 0, x1 = 0, y0 = 0, y1 = 0, z1 = 0;  // covered box in coarse cells
+  LevelLink L{};
 };
 
 thread_local std::string g_create_error;
@@ -44,8 +58,8 @@ struct cc_model {
   ColItem *d_cols = nullptr;
   int ncols = 0;
   long long ghost_points = 0;
-  int r[4] = {0, 1, 2, 3};  // roles: old (filtered n-1), current, new, filtered n
-  long long nsteps = 0;
+  bool refined = false;
+  std::vector<LinkHost> link;  // link[l] for level l >= 1 of a refined model
   long long last_launches = 0;
   bool geom = false, state = false;
   // kernel timing with CUDA events on the model's stream (cc_profile_*)
@@ -124,16 +138,6 @@ __global__ void k_gather(const T *src, double *dst, DomDev D, int nlev, int k_fi
   int i = (int)(t % D.nx), j = (int)((t / D.nx) % D.ny), k = (int)(t / ((long long)D.nx * D.ny)) + k_first;
   dst[t] = (double)src[pidx(D, i, j, k)];
 }
-template <typename T>
-__global__ void k_cvt_to(const double *src, T *dst, long long n) {
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) dst[t] = (T)src[t];
-}
-template <typename T>
-__global__ void k_cvt_from(const T *src, double *dst, long long n) {
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < n) dst[t] = (double)src[t];
-}
 template <typename P>
 __global__ void k_gather_raw(const P *src, P *dst, DomDev D, int nlev, int k_first) {
   long long n = (long long)D.nx * D.ny * nlev;
@@ -145,7 +149,8 @@ __global__ void k_gather_raw(const P *src, P *dst, DomDev D, int nlev, int k_fir
 
 inline unsigned nb256(long long n) { return (unsigned)((n + 255) / 256); }
 
-StepLaunch make_launch(const cc_model *m) {
+// launch description of every domain (d < 0) or of domain d alone
+StepLaunch make_launch(const cc_model *m, int d = -1) {
   StepLaunch L{};
   L.d_doms = m->d_doms;
   L.items = m->d_items;
@@ -158,28 +163,78 @@ StepLaunch make_launch(const cc_model *m) {
   L.ndom = m->ndom;
   L.ghost_points = m->ghost_points;
   L.ghost_off = nullptr;
+  if (d >= 0) {
+    const DomHost &H = m->dom[d];
+    L.items = m->d_items + H.item0;
+    L.nitems = H.nitem;
+    L.groups = m->d_groups + H.group0;
+    L.ngroups = H.ngroup;
+    L.cols = m->d_cols + H.col0;
+    L.ncols = H.ncol;
+  }
   return L;
 }
 
+// padded columns <-> host columns (w values per column)
+template <typename P>
+__global__ void k_gather_cols(const P *src, P *dst, DomDev D, int w) {
+  long long n = (long long)D.nx * D.ny * w;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int c = (int)(t % w);
+  long long q = t / w;
+  int I = (int)(q % D.nx), J = (int)(q / D.nx);
+  dst[t] = src[qidx(D, I, J) * w + c];
+}
+template <typename T>
+__global__ void k_scatter_cols(const double *src, T *dst, DomDev D, int w) {
+  long long n = (long long)D.nx * D.ny * w;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int c = (int)(t % w);
+  long long q = t / w;
+  int I = (int)(q % D.nx), J = (int)(q / D.nx);
+  dst[qidx(D, I, J) * w + c] = (T)src[t];
+}
+template <typename T>
+__global__ void k_gather_cols_cvt(const T *src, double *dst, DomDev D, int w) {
+  long long n = (long long)D.nx * D.ny * w;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  int c = (int)(t % w);
+  long long q = t / w;
+  int I = (int)(q % D.nx), J = (int)(q / D.nx);
+  dst[t] = (double)src[qidx(D, I, J) * w + c];
+}
+
+// corner heights of a box level must vanish within this many corners of its
+// edges: the geometry of the cells near the edges is evaluated as over a flat
+// floor, which the padded frame continues
+constexpr int FLAT_MARGIN = 8;
+
+// domain kinds: a periodic block with the lid (ensemble member, level 0), or
+// a refined box resting on the floor
+struct DomKind {
+  int periodic, lid;
+  double ztop;
+};
+
 }  // namespace
 
-extern "C" {
+namespace {
 
-cc_status cc_create(const cc_config *cfgs, int n, int precision, void *stream, cc_model **out) {
-  if (!out) return fail(nullptr, CC_EINVAL, "out is NULL");
-  *out = nullptr;
-  if (!cfgs || n <= 0) return fail(nullptr, CC_EINVAL, "need at least one domain");
-  if (precision != CC_FP64 && precision != CC_FP32) return fail(nullptr, CC_EINVAL, "precision must be CC_FP64 or CC_FP32");
-  for (int d = 0; d < n; d++) {
-    std::string why;
-    if (!valid_cfg(cfgs[d], why)) return fail(nullptr, CC_EINVAL, "domain " + std::to_string(d) + ": " + why);
-  }
+// Creates the model of the given domains (shared by cc_create and
+// cc_create_refined); boxes non-empty makes it a refined model.
+cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomKind> &kinds,
+                      const std::vector<cc_box> &boxes, int precision, void *stream, cc_model **out) {
+  const int n = (int)cfgs.size();
   cc_model *m = new cc_model();
   m->ndom = n;
   m->prec = precision;
   m->esz = precision == CC_FP64 ? 8 : 4;
   m->st = (cudaStream_t)stream;
   m->dom.resize(n);
+  m->refined = !boxes.empty();
   cudaError_t e = cudaSuccess;
   auto bail = [&](cudaError_t ee, const char *where) {
     std::string msg = std::string(where) + ": " + cudaGetErrorString(ee);
@@ -204,11 +259,21 @@ cc_status cc_create(const cc_config *cfgs, int n, int precision, void *stream, c
     D.kdif = c.c4 / (16.0 * c.dt);
     D.ra_nu = c.ra_nu;
     D.bc_slip = c.bc_slip;
-    long long ncol = (long long)c.nx * c.ny, ncell = ncol * c.nz;
+    D.periodic = kinds[d].periodic;
+    D.lid = kinds[d].lid;
+    D.ztop = kinds[d].ztop;
+    if (D.periodic) {
+      // the whole block, corners 0 .. n-1
+      D.ci0 = 0; D.ci1 = c.nx; D.cj0 = 0; D.cj1 = c.ny; D.ck1 = c.nz; D.qi0 = 0; D.qj0 = 0;
+    } else {
+      // a box integrates its cells -2 .. n+1 (k < nz+2) and corners -1 .. n+1
+      D.ci0 = -2; D.ci1 = c.nx + 2; D.cj0 = -2; D.cj1 = c.ny + 2; D.ck1 = c.nz + 2; D.qi0 = -1; D.qj0 = -1;
+    }
+    long long ncol = (long long)c.nx * c.ny, ncell = ncol * c.nz, npc = D.plane;
     for (int b = 0; b < NBUF; b++) {
       for (int f = 0; f < NFIELD; f++)
         if ((e = dalloc(H.allocs, &D.f[b][f], D.ncellp * m->esz, m->st)) != cudaSuccess) return bail(e, "field alloc");
-      if ((e = dalloc(H.allocs, &D.ub[b], 3 * ncol * m->esz, m->st)) != cudaSuccess) return bail(e, "ub alloc");
+      if ((e = dalloc(H.allocs, &D.ub[b], 3 * npc * m->esz, m->st)) != cudaSuccess) return bail(e, "ub alloc");
     }
     void *bt[7];
     for (int a = 0; a < 7; a++)
@@ -217,12 +282,12 @@ cc_status cc_create(const cc_config *cfgs, int n, int precision, void *stream, c
     // binomial coefficients C(a, n), n = 1..7, of (1 + x)^a - 1
     for (int w = 0; w < 2; w++) {
       double a = w == 0 ? D.cvcp : D.kap, cn = 1.0;
-      float *out = w == 0 ? D.sth : D.sex;
+      float *o = w == 0 ? D.sth : D.sex;
       for (int nn = 1; nn <= 7; nn++) {
         cn = cn * (a - (nn - 1)) / nn;
-        out[nn - 1] = (float)cn;
+        o[nn - 1] = (float)cn;
       }
-      out[7] = (float)a;
+      o[7] = (float)a;
     }
     double *h, *vf, *ax, *ay, *az, *ba, *bb, *bn, *mg;
     int8_t *cls, *vcls;
@@ -232,12 +297,12 @@ cc_status cc_create(const cc_config *cfgs, int n, int precision, void *stream, c
         (e = dalloc(H.allocs, &ay, ncell * 8, m->st)) ||
         (e = dalloc(H.allocs, &az, ncol * (c.nz + 1) * 8, m->st)) ||
         (e = dalloc(H.allocs, &cls, ncell, m->st)) || (e = dalloc(H.allocs, &root, ncell * 4, m->st)) ||
-        (e = dalloc(H.allocs, &kug, ncol * 4, m->st)) || (e = dalloc(H.allocs, &vcls, D.ncellp, m->st)) ||
-        (e = dalloc(H.allocs, &bK, ncol * 4, m->st)) || (e = dalloc(H.allocs, &bI, ncol * 4, m->st)) ||
-        (e = dalloc(H.allocs, &bJ, ncol * 4, m->st)) || (e = dalloc(H.allocs, &ba, ncol * 8, m->st)) ||
-        (e = dalloc(H.allocs, &bb, ncol * 8, m->st)) || (e = dalloc(H.allocs, &bn, 3 * ncol * 8, m->st)) ||
+        (e = dalloc(H.allocs, &kug, npc * 4, m->st)) || (e = dalloc(H.allocs, &vcls, D.ncellp, m->st)) ||
+        (e = dalloc(H.allocs, &bK, npc * 4, m->st)) || (e = dalloc(H.allocs, &bI, npc * 4, m->st)) ||
+        (e = dalloc(H.allocs, &bJ, npc * 4, m->st)) || (e = dalloc(H.allocs, &ba, npc * 8, m->st)) ||
+        (e = dalloc(H.allocs, &bb, npc * 8, m->st)) || (e = dalloc(H.allocs, &bn, 3 * npc * 8, m->st)) ||
         (e = dalloc(H.allocs, &mK, D.ncellp * 4, m->st)) || (e = dalloc(H.allocs, &mg, D.ncellp * 8, m->st)) ||
-        (e = dalloc(H.allocs, &ktop, ncol * 4, m->st)))
+        (e = dalloc(H.allocs, &ktop, npc * 4, m->st)))
       return bail(e, "geometry alloc");
     D.h = h; D.vf = vf; D.ax = ax; D.ay = ay; D.az = az; D.cls = cls; D.root = root; D.kug = kug;
     D.vcls = vcls; D.bK = bK; D.bI = bI; D.bJ = bJ; D.ba = ba; D.bb = bb; D.bn = bn; D.mK = mK; D.mg = mg;
@@ -246,8 +311,7 @@ cc_status cc_create(const cc_config *cfgs, int n, int precision, void *stream, c
       return bail(e, "base state");
     max_stage = std::max(max_stage, (size_t)(ncol * (c.nz + 1 + 2 * HOST_GZ)));
     max_stage = std::max(max_stage, (size_t)(ncol * (c.nz + 1)));
-    long long frame = D.plane - ncol;
-    m->ghost_points = std::max(m->ghost_points, frame * D.pz);
+    max_stage = std::max(max_stage, (size_t)(3 * ncol));
   }
   // device domain table
   if ((e = dalloc(m->allocs, &m->d_doms, sizeof(DomDev) * n, m->st)) != cudaSuccess) return bail(e, "domain table");
@@ -258,26 +322,39 @@ cc_status cc_create(const cc_config *cfgs, int n, int precision, void *stream, c
       return bail(e, "domain table copy");
     if ((e = cudaStreamSynchronize(m->st)) != cudaSuccess) return bail(e, "sync");
   }
-  // (domain, tile, z-chunk) work list of the full-cell stencil: z is split so
-  // that every SM gets several work items
+  // (domain, tile, z-chunk) work list of the full-cell stencil over each
+  // domain's computed region; z is split so that every SM gets several work
+  // items per launch (all domains of an ensemble share one launch, each level
+  // of a refined model has its own)
   {
     const int TILE_Y = full_tile_y(precision);
-    long long tiles = 0;
-    for (auto &H : m->dom)
-      tiles += (long long)((H.D.nx + TILE_X - 1) / TILE_X) * ((H.D.ny + TILE_Y - 1) / TILE_Y);
+    auto tiles_of = [&](const DomDev &D) {
+      return (long long)((D.ci1 - D.ci0 + TILE_X - 1) / TILE_X) * ((D.cj1 - D.cj0 + TILE_Y - 1) / TILE_Y);
+    };
+    long long all_tiles = 0;
+    for (auto &H : m->dom) all_tiles += tiles_of(H.D);
     const long long want = 2 * 152;
-    long long splits = std::max(1LL, (want + tiles - 1) / tiles);
     std::vector<WorkItem> items;
+    std::vector<ColItem> cols;
     for (int d = 0; d < n; d++) {
-      const DomDev &D = m->dom[d].D;
-      int chunk = (int)std::max(8LL, (D.nz + splits - 1) / splits);
-      for (int k0 = 0; k0 < D.nz; k0 += chunk)
-        for (int j0 = 0; j0 < D.ny; j0 += TILE_Y)
-          for (int i0 = 0; i0 < D.nx; i0 += TILE_X) {
+      DomHost &H = m->dom[d];
+      const DomDev &D = H.D;
+      long long tiles = m->refined ? tiles_of(D) : all_tiles;
+      long long splits = std::max(1LL, (want + tiles - 1) / tiles);
+      int chunk = (int)std::max(8LL, (D.ck1 + splits - 1) / splits);
+      H.item0 = (int)items.size();
+      for (int k0 = 0; k0 < D.ck1; k0 += chunk)
+        for (int j0 = D.cj0; j0 < D.cj1; j0 += TILE_Y)
+          for (int i0 = D.ci0; i0 < D.ci1; i0 += TILE_X) {
             WorkItem w{};
-            w.dom = d; w.i0 = i0; w.j0 = j0; w.k0 = k0; w.k1 = std::min(D.nz, k0 + chunk);
+            w.dom = d; w.i0 = i0; w.j0 = j0; w.k0 = k0; w.k1 = std::min(D.ck1, k0 + chunk);
             items.push_back(w);
           }
+      H.nitem = (int)items.size() - H.item0;
+      H.col0 = (int)cols.size();
+      for (int J = D.qj0; J < D.cj1; J++)
+        for (int I = D.qi0; I < D.ci1; I++) cols.push_back(ColItem{d, I, J, 0});
+      H.ncol = (int)cols.size() - H.col0;
     }
     m->nitems = (int)items.size();
     if ((e = dalloc(m->allocs, &m->d_items, sizeof(WorkItem) * items.size(), m->st)) != cudaSuccess)
@@ -285,10 +362,6 @@ cc_status cc_create(const cc_config *cfgs, int n, int precision, void *stream, c
     if ((e = cudaMemcpyAsync(m->d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice,
                              m->st)) != cudaSuccess)
       return bail(e, "work list copy");
-    std::vector<ColItem> cols;
-    for (int d = 0; d < n; d++)
-      for (int J = 0; J < m->dom[d].D.ny; J++)
-        for (int I = 0; I < m->dom[d].D.nx; I++) cols.push_back(ColItem{d, I, J, 0});
     m->ncols = (int)cols.size();
     if ((e = dalloc(m->allocs, &m->d_cols, sizeof(ColItem) * cols.size(), m->st)) != cudaSuccess)
       return bail(e, "column list");
@@ -296,6 +369,94 @@ cc_status cc_create(const cc_config *cfgs, int n, int precision, void *stream, c
                              m->st)) != cudaSuccess)
       return bail(e, "column list copy");
     if ((e = cudaStreamSynchronize(m->st)) != cudaSuccess) return bail(e, "sync");
+  }
+  // coarse-fine links of a refined model
+  if (m->refined) {
+    m->link.resize(n);
+    for (int l = 1; l < n; l++) {
+      LinkHost &K = m->link[l];
+      K.box = boxes[l - 1];
+      const DomDev &C = m->dom[l - 1].D, &F = m->dom[l].D;
+      const cc_box &b = K.box;
+      K.x0 = b.ox / 2; K.x1 = (b.ox + b.nx) / 2;
+      K.y0 = b.oy / 2; K.y1 = (b.oy + b.ny) / 2;
+      K.z1 = b.nz / 2;
+      std::vector<long long> pcell, pcorn, rcell, rcorn;
+      for (int k = 0; k < F.nz + GH; k++)
+        for (int j = -GH; j < F.ny + GH; j++)
+          for (int i = -GH; i < F.nx + GH; i++)
+            if (!(i >= -2 && i < F.nx + 2 && j >= -2 && j < F.ny + 2 && k < F.nz + 2)) pcell.push_back(pidx(F, i, j, k));
+      for (int Kk = -GH + 1; Kk < F.nz + GH; Kk++)
+        for (int J = -GH; J < F.ny + GH; J++)
+          for (int I = -GH; I < F.nx + GH; I++)
+            if (!(I >= -1 && I < F.nx + 2 && J >= -1 && J < F.ny + 2 && Kk < F.nz + 2))
+              pcorn.push_back(pidx(F, I, J, Kk));
+      for (int kc = 0; kc < K.z1; kc++)
+        for (int jc = K.y0; jc < K.y1; jc++)
+          for (int ic = K.x0; ic < K.x1; ic++) {
+            int dd = std::min({ic - K.x0, K.x1 - 1 - ic, jc - K.y0, K.y1 - 1 - jc, K.z1 - 1 - kc});
+            if (dd < GH) rcell.push_back(pidx(C, ic, jc, kc));
+          }
+      for (int Kc = 1; Kc < K.z1; Kc++)
+        for (int Jc = K.y0 + 1; Jc < K.y1; Jc++)
+          for (int Ic = K.x0 + 1; Ic < K.x1; Ic++) {
+            int dd = std::min({Ic - K.x0, K.x1 - Ic, Jc - K.y0, K.y1 - Jc, K.z1 - Kc});
+            if (dd <= GH) rcorn.push_back(pidx(C, Ic, Jc, Kc));
+          }
+      // interface faces (x low, x high, y low, y high, top) and the coarse
+      // cell outside the box that each one bounds
+      std::vector<IfaceFace> faces;
+      std::vector<IfaceCell> icells;
+      auto add = [&](int ax, int fi, int fj, int fk, int ci, int cj, int ck, int side) {
+        IfaceCell ic{};
+        ic.i = ci; ic.j = cj; ic.k = ck;
+        for (int q = 0; q < 6; q++) ic.slot[q] = -1;
+        ic.slot[ax * 2 + side] = (int)faces.size();
+        faces.push_back(IfaceFace{ax, fi, fj, fk});
+        icells.push_back(ic);
+      };
+      for (int sd = 0; sd < 2; sd++)
+        for (int kc = 0; kc < K.z1; kc++)
+          for (int jc = K.y0; jc < K.y1; jc++)
+            add(0, sd ? b.nx : 0, 2 * jc - b.oy, 2 * kc, sd ? K.x1 : K.x0 - 1, jc, kc, sd ? 0 : 1);
+      for (int sd = 0; sd < 2; sd++)
+        for (int kc = 0; kc < K.z1; kc++)
+          for (int ic = K.x0; ic < K.x1; ic++)
+            add(1, 2 * ic - b.ox, sd ? b.ny : 0, 2 * kc, ic, sd ? K.y1 : K.y0 - 1, kc, sd ? 0 : 1);
+      for (int jc = K.y0; jc < K.y1; jc++)
+        for (int ic = K.x0; ic < K.x1; ic++) add(2, 2 * ic - b.ox, 2 * jc - b.oy, b.nz, ic, jc, K.z1, 0);
+      LevelLink &L = K.L;
+      L.dc = m->d_doms + (l - 1);
+      L.df = m->d_doms + l;
+      L.ox = b.ox;
+      L.oy = b.oy;
+      auto up = [&](auto &vec, auto **dst) -> cudaError_t {
+        using E = typename std::remove_reference<decltype(vec)>::type::value_type;
+        E *p = nullptr;
+        cudaError_t ee = dalloc(m->allocs, &p, sizeof(E) * vec.size(), m->st);
+        if (ee != cudaSuccess) return ee;
+        if (!vec.empty())
+          ee = cudaMemcpyAsync(p, vec.data(), sizeof(E) * vec.size(), cudaMemcpyHostToDevice, m->st);
+        *dst = p;
+        return ee;
+      };
+      const long long *pc = nullptr, *pq = nullptr, *rc = nullptr, *rq = nullptr;
+      const IfaceFace *fp = nullptr;
+      const IfaceCell *cp = nullptr;
+      if ((e = up(pcell, &pc)) || (e = up(pcorn, &pq)) || (e = up(rcell, &rc)) || (e = up(rcorn, &rq)) ||
+          (e = up(faces, &fp)) || (e = up(icells, &cp)))
+        return bail(e, "refinement lists");
+      L.pcell = pc; L.npcell = (long long)pcell.size();
+      L.pcorn = pq; L.npcorn = (long long)pcorn.size();
+      L.rcell = rc; L.nrcell = (long long)rcell.size();
+      L.rcorn = rq; L.nrcorn = (long long)rcorn.size();
+      L.faces = fp; L.nfaces = (int)faces.size();
+      L.icells = cp; L.nicells = (int)icells.size();
+      if ((e = dalloc(m->allocs, &L.regm, faces.size() * m->esz, m->st)) ||
+          (e = dalloc(m->allocs, &L.regh, faces.size() * m->esz, m->st)))
+        return bail(e, "flux register");
+      if ((e = cudaStreamSynchronize(m->st)) != cudaSuccess) return bail(e, "sync");
+    }
   }
   if ((e = dalloc(m->allocs, &m->d_diag, sizeof(double) * (8 + 5 * 256), m->st)) != cudaSuccess) return bail(e, "diag");
   if ((e = dalloc(m->allocs, &m->d_stage, sizeof(double) * max_stage, m->st)) != cudaSuccess) return bail(e, "stage");
@@ -305,6 +466,64 @@ cc_status cc_create(const cc_config *cfgs, int n, int precision, void *stream, c
   *out = m;
   return CC_OK;
 }
+
+}  // namespace
+
+extern "C" {
+
+cc_status cc_create(const cc_config *cfgs, int n, int precision, void *stream, cc_model **out) {
+  if (!out) return fail(nullptr, CC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfgs || n <= 0) return fail(nullptr, CC_EINVAL, "need at least one domain");
+  if (precision != CC_FP64 && precision != CC_FP32) return fail(nullptr, CC_EINVAL, "precision must be CC_FP64 or CC_FP32");
+  std::vector<cc_config> cv(cfgs, cfgs + n);
+  std::vector<DomKind> kinds(n);
+  for (int d = 0; d < n; d++) {
+    std::string why;
+    if (!valid_cfg(cfgs[d], why)) return fail(nullptr, CC_EINVAL, "domain " + std::to_string(d) + ": " + why);
+    kinds[d] = DomKind{1, 1, cfgs[d].nz * cfgs[d].dz};
+  }
+  return create_impl(cv, kinds, {}, precision, stream, out);
+}
+
+cc_status cc_create_refined(const cc_config *base, int nlev, const cc_box *boxes, int precision, void *stream,
+                            cc_model **out) {
+  if (!out) return fail(nullptr, CC_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!base || !boxes) return fail(nullptr, CC_EINVAL, "null argument");
+  if (nlev < 2 || nlev > 8) return fail(nullptr, CC_EINVAL, "nlev must be 2 .. 8");
+  if (precision != CC_FP64 && precision != CC_FP32) return fail(nullptr, CC_EINVAL, "precision must be CC_FP64 or CC_FP32");
+  std::string why;
+  if (!valid_cfg(*base, why)) return fail(nullptr, CC_EINVAL, "level 0: " + why);
+  std::vector<cc_config> cv(nlev);
+  std::vector<DomKind> kinds(nlev);
+  std::vector<cc_box> bx(boxes, boxes + nlev - 1);
+  const double ztop = base->nz * base->dz;
+  cv[0] = *base;
+  kinds[0] = DomKind{1, 1, ztop};
+  for (int l = 1; l < nlev; l++) {
+    const cc_box &b = bx[l - 1];
+    const cc_config &c = cv[l - 1];
+    int x0 = b.ox / 2, x1 = (b.ox + b.nx) / 2, y0 = b.oy / 2, y1 = (b.oy + b.ny) / 2, z1 = b.nz / 2;
+    if (((b.ox | b.oy | b.nx | b.ny | b.nz) & 1) || b.nx <= 0 || b.ny <= 0 || b.nz <= 0)
+      return fail(nullptr, CC_EINVAL, "box " + std::to_string(l) + ": extents and offsets must be even and positive");
+    if (x0 < 8 || y0 < 8 || x1 > c.nx - 8 || y1 > c.ny - 8 || z1 > c.nz - 8)
+      return fail(nullptr, CC_EINVAL,
+                  "box " + std::to_string(l) + ": covered box must lie 8 cells inside the coarser level");
+    if (b.nx <= 2 * FLAT_MARGIN || b.ny <= 2 * FLAT_MARGIN)
+      return fail(nullptr, CC_EINVAL, "box " + std::to_string(l) + ": nx and ny must exceed 16");
+    cc_config f = *base;
+    double s = std::ldexp(1.0, -l);
+    f.nx = b.nx; f.ny = b.ny; f.nz = b.nz;
+    f.dx = base->dx * s; f.dy = base->dy * s; f.dz = base->dz * s; f.dt = base->dt * s;
+    if (!valid_cfg(f, why)) return fail(nullptr, CC_EINVAL, "level " + std::to_string(l) + ": " + why);
+    cv[l] = f;
+    kinds[l] = DomKind{0, 0, ztop};
+  }
+  return create_impl(cv, kinds, bx, precision, stream, out);
+}
+
+int cc_domain_count(const cc_model *m) { return m ? m->ndom : 0; }
 
 cc_status cc_destroy(cc_model *m) {
   if (!m) return CC_OK;
@@ -332,15 +551,25 @@ cc_status cc_set_terrain(cc_model *m, int d, const double *corner_h) {
   if (!m || !corner_h) return fail(m, CC_EINVAL, "null argument");
   if (d < 0 || d >= m->ndom) return fail(m, CC_EINVAL, "domain index out of range");
   DomHost &H = m->dom[d];
-  long long ncol = (long long)H.cfg.nx * H.cfg.ny;
+  const int nx = H.cfg.nx, ny = H.cfg.ny;
+  long long ncol = (long long)nx * ny;
   double top = H.cfg.nz * H.cfg.dz;
   for (long long q = 0; q < ncol; q++) {
     double v = corner_h[q];
     if (!std::isfinite(v) || v < 0.0 || v >= top)
-      return fail(m, CC_EINVAL, "terrain heights must be finite, >= 0 and below the lid");
+      return fail(m, CC_EINVAL, "terrain heights must be finite, >= 0 and below the top");
+  }
+  if (!H.D.periodic) {
+    for (int J = 0; J < ny; J++)
+      for (int I = 0; I < nx; I++) {
+        bool edge = I <= FLAT_MARGIN || J <= FLAT_MARGIN || I >= nx - FLAT_MARGIN || J >= ny - FLAT_MARGIN;
+        if (edge && corner_h[(long long)J * nx + I] != 0.0)
+          return fail(m, CC_EINVAL, "terrain of a refined box must be zero within 8 corners of its edges");
+      }
   }
   CK(m, cudaMemcpyAsync((void *)H.D.h, corner_h, ncol * 8, cudaMemcpyHostToDevice, m->st), "terrain copy");
   CK(m, cudaStreamSynchronize(m->st), "terrain sync");
+  H.hh.assign(corner_h, corner_h + ncol);
   H.terrain = true;
   m->geom = false;
   m->state = false;
@@ -351,6 +580,17 @@ cc_status cc_build_geometry(cc_model *m) {
   if (!m) return fail(m, CC_EINVAL, "null model");
   for (auto &H : m->dom)
     if (!H.terrain) return fail(m, CC_ESTATE, "terrain not set for every domain");
+  // a coarser level is flat around every covered box: the coarse cells that
+  // exchange fluxes with the box are full cells
+  for (int l = 1; l < (int)m->link.size(); l++) {
+    const LinkHost &K = m->link[l];
+    const DomHost &C = m->dom[l - 1];
+    for (int J = K.y0 - 4; J <= K.y1 + 4; J++)
+      for (int I = K.x0 - 4; I <= K.x1 + 4; I++)
+        if (C.hh[(long long)wrapi(J, C.cfg.ny) * C.cfg.nx + wrapi(I, C.cfg.nx)] != 0.0)
+          return fail(m, CC_EGEOM, "level " + std::to_string(l - 1) +
+                                       ": terrain must be flat within 4 cells of the refined box");
+  }
   cudaFree(m->d_groups);
   cudaFree(m->d_members);
   m->d_groups = nullptr;
@@ -365,6 +605,7 @@ cc_status cc_build_geometry(cc_model *m) {
     int ng = 0, nm = 0;
     cudaError_t e = geom_build_one(H.D, m->st, d, m->d_err, &mem, &recs, &ng, &nm);
     if (e != cudaSuccess) return cuda_fail(m, e, "geometry");
+    if (!H.D.periodic) CK(m, launch_flat_columns(H.D, m->st), "frame columns");
     int herr = 0;
     CK(m, cudaMemcpy(&herr, m->d_err, sizeof(int), cudaMemcpyDeviceToHost), "err read");
     std::vector<GroupRec> r(ng);
@@ -384,6 +625,8 @@ cc_status cc_build_geometry(cc_model *m) {
     }
     H.ng = ng;
     H.nm = nm;
+    H.group0 = (int)all.size();
+    H.ngroup = ng;
     H.ghost.resize(ng);
     H.gstart.resize(ng + 1);
     H.gmem = mm;
@@ -444,12 +687,23 @@ cc_status cc_get_stencils(const cc_model *mc, int d, int32_t *bK, int32_t *bI, i
   if (!m->geom) return fail(m, CC_ESTATE, "geometry not built");
   const DomDev &D = m->dom[d].D;
   long long ncol = (long long)D.nx * D.ny;
-  if (bK) CK(m, cudaMemcpy(bK, D.bK, ncol * 4, cudaMemcpyDeviceToHost), "bK");
-  if (bI) CK(m, cudaMemcpy(bI, D.bI, ncol * 4, cudaMemcpyDeviceToHost), "bI");
-  if (bJ) CK(m, cudaMemcpy(bJ, D.bJ, ncol * 4, cudaMemcpyDeviceToHost), "bJ");
-  if (ba) CK(m, cudaMemcpy(ba, D.ba, ncol * 8, cudaMemcpyDeviceToHost), "ba");
-  if (bb) CK(m, cudaMemcpy(bb, D.bb, ncol * 8, cudaMemcpyDeviceToHost), "bb");
-  if (bn) CK(m, cudaMemcpy(bn, D.bn, 3 * ncol * 8, cudaMemcpyDeviceToHost), "bn");
+  // interior columns of the padded column arrays
+  auto cols = [&](const auto *src, auto *dst, int w, const char *what) -> cc_status {
+    using E = typename std::remove_const<typename std::remove_pointer<decltype(src)>::type>::type;
+    E *tmp = (E *)m->d_stage;
+    k_gather_cols<E><<<nb256(ncol * w), 256, 0, m->st>>>(src, tmp, D, w);
+    CK(m, cudaGetLastError(), what);
+    CK(m, cudaMemcpyAsync(dst, tmp, ncol * w * sizeof(E), cudaMemcpyDeviceToHost, m->st), what);
+    CK(m, cudaStreamSynchronize(m->st), what);
+    return CC_OK;
+  };
+  cc_status r = CC_OK;
+  if (bK && (r = cols(D.bK, bK, 1, "bK")) != CC_OK) return r;
+  if (bI && (r = cols(D.bI, bI, 1, "bI")) != CC_OK) return r;
+  if (bJ && (r = cols(D.bJ, bJ, 1, "bJ")) != CC_OK) return r;
+  if (ba && (r = cols(D.ba, ba, 1, "ba")) != CC_OK) return r;
+  if (bb && (r = cols(D.bb, bb, 1, "bb")) != CC_OK) return r;
+  if (bn && (r = cols(D.bn, bn, 3, "bn")) != CC_OK) return r;
   int nlev = D.nz + 1 + 2 * HOST_GZ;
   if (mK) {
     int32_t *tmp = (int32_t *)m->d_stage;
@@ -490,16 +744,25 @@ cc_status cc_init_state(cc_model *m) {
     for (int b = 0; b < NBUF; b++) {
       for (int f = 0; f < NFIELD; f++)
         CK(m, cudaMemsetAsync(H.D.f[b][f], 0, H.D.ncellp * m->esz, m->st), "state reset");
-      CK(m, cudaMemsetAsync(H.D.ub[b], 0, 3 * (size_t)H.D.nx * H.D.ny * m->esz, m->st), "ub reset");
+      CK(m, cudaMemsetAsync(H.D.ub[b], 0, 3 * (size_t)H.D.plane * m->esz, m->st), "ub reset");
     }
+    for (int a = 0; a < 4; a++) H.r[a] = a;
+    H.nsteps = 0;
   }
-  m->r[0] = 0; m->r[1] = 1; m->r[2] = 2; m->r[3] = 3;
   for (int d = 0; d < m->ndom; d++)
-    CK(m, launch_init_momentum(m->dom[d].D, m->d_doms + d, m->prec, m->r[1], m->dom[d].cfg.U, m->st), "init momentum");
+    CK(m, launch_init_momentum(m->dom[d].D, m->d_doms + d, m->prec, m->dom[d].r[1], m->dom[d].cfg.U, m->st),
+       "init momentum");
   StepLaunch L = make_launch(m);
-  CK(m, launch_diagnose(L, m->prec, m->r[1], m->r[1], m->r[1], m->r[1], 1, 0, m->st), "init diagnose");
+  CK(m, launch_diagnose(L, m->prec, 1, 1, 1, 1, 1, 0, m->st), "init diagnose");
+  // refined model: fine -> coarse, then coarse -> fine, down the hierarchy
+  for (int l = 1; l < (int)m->link.size(); l++) {
+    const LevelLink &K = m->link[l].L;
+    CK(m, cudaMemsetAsync(K.regm, 0, K.nfaces * m->esz, m->st), "register reset");
+    CK(m, cudaMemsetAsync(K.regh, 0, K.nfaces * m->esz, m->st), "register reset");
+    CK(m, launch_restrict(K, m->prec, m->dom[l].r[1], m->st), "init restrict");
+    CK(m, launch_prolong(K, m->prec, m->dom[l - 1].r[1], m->st), "init prolong");
+  }
   CK(m, cudaStreamSynchronize(m->st), "init sync");
-  m->nsteps = 0;
   m->state = true;
   return CC_OK;
 }
@@ -515,7 +778,7 @@ static long long field_elems(const DomDev &D, int field, int *nlev, int *kfirst)
     *nlev = 0;
     *kfirst = 0;
     return 3 * ncol;
-  }
+  }  // CC_UB: 3 values per column, through the padded column layout
   *nlev = D.nz + 1 + 2 * HOST_GZ;
   *kfirst = -HOST_GZ;
   return ncol * (*nlev);
@@ -527,13 +790,13 @@ cc_status cc_upload_state(cc_model *m, int d, int field, int level, const double
   if (field < 0 || field > CC_UB || level < 0 || level > 1) return fail(m, CC_EINVAL, "bad field or level");
   if (!m->state) return fail(m, CC_ESTATE, "state not initialised");
   const DomDev &D = m->dom[d].D;
-  int buf = level == 0 ? m->r[0] : m->r[1];
+  int buf = level == 0 ? m->dom[d].r[0] : m->dom[d].r[1];
   int nlev, kfirst;
   long long n = field_elems(D, field, &nlev, &kfirst);
   CK(m, cudaMemcpyAsync(m->d_stage, host, n * 8, cudaMemcpyHostToDevice, m->st), "upload");
   if (field == CC_UB) {
-    if (m->prec == CC_FP64) k_cvt_to<double><<<nb256(n), 256, 0, m->st>>>(m->d_stage, (double *)D.ub[buf], n);
-    else k_cvt_to<float><<<nb256(n), 256, 0, m->st>>>(m->d_stage, (float *)D.ub[buf], n);
+    if (m->prec == CC_FP64) k_scatter_cols<double><<<nb256(n), 256, 0, m->st>>>(m->d_stage, (double *)D.ub[buf], D, 3);
+    else k_scatter_cols<float><<<nb256(n), 256, 0, m->st>>>(m->d_stage, (float *)D.ub[buf], D, 3);
   } else {
     void *dst = D.f[buf][field];
     if (m->prec == CC_FP64) k_scatter<double><<<nb256(n), 256, 0, m->st>>>(m->d_stage, (double *)dst, D, nlev, kfirst);
@@ -551,12 +814,14 @@ cc_status cc_download_state(const cc_model *mc, int d, int field, int level, dou
   if (field < 0 || field > CC_UB || level < 0 || level > 1) return fail(m, CC_EINVAL, "bad field or level");
   if (!m->state) return fail(m, CC_ESTATE, "state not initialised");
   const DomDev &D = m->dom[d].D;
-  int buf = level == 0 ? m->r[0] : m->r[1];
+  int buf = level == 0 ? m->dom[d].r[0] : m->dom[d].r[1];
   int nlev, kfirst;
   long long n = field_elems(D, field, &nlev, &kfirst);
   if (field == CC_UB) {
-    if (m->prec == CC_FP64) k_cvt_from<double><<<nb256(n), 256, 0, m->st>>>((const double *)D.ub[buf], m->d_stage, n);
-    else k_cvt_from<float><<<nb256(n), 256, 0, m->st>>>((const float *)D.ub[buf], m->d_stage, n);
+    if (m->prec == CC_FP64)
+      k_gather_cols_cvt<double><<<nb256(n), 256, 0, m->st>>>((const double *)D.ub[buf], m->d_stage, D, 3);
+    else
+      k_gather_cols_cvt<float><<<nb256(n), 256, 0, m->st>>>((const float *)D.ub[buf], m->d_stage, D, 3);
   } else {
     const void *src = D.f[buf][field];
     if (m->prec == CC_FP64)
@@ -598,48 +863,97 @@ static cudaError_t timed(cc_model *m, int kid, F &&launch) {
   return e;
 }
 
+// One step of domain d (every domain of an ensemble when d < 0): the
+// full-cell stencil, the cut cells, the coarse cells next to a refined box
+// (flux register), then the velocity diagnosis; rotates the roles.
+static cc_status step_domains(cc_model *m, int d, long long &nl) {
+  DomHost &H0 = m->dom[d < 0 ? 0 : d];
+  const int first = H0.nsteps == 0;
+  const int rO = first ? H0.r[1] : H0.r[0];
+  const int rC = H0.r[1], rN = H0.r[2], rF = H0.r[3], pr = m->prec;
+  cudaStream_t st = m->st;
+  StepLaunch L = make_launch(m, d);
+  if (L.nitems > 0) {
+    CK(m, timed(m, CC_K_FULL, [&] { return launch_full(L, pr, rO, rC, rN, rF, first, st); }), "full-cell stencil");
+    nl++;
+  }
+  if (L.ngroups > 0) {
+    CK(m, timed(m, CC_K_GROUPS, [&] { return launch_groups(L, pr, rO, rC, rN, rF, first, st); }), "cut cells");
+    nl++;
+  }
+  if (d >= 0 && d + 1 < (int)m->link.size()) {
+    const LevelLink &K = m->link[d + 1].L;
+    CK(m, timed(m, CC_K_REFINE, [&] { return launch_iface(K, pr, rO, rC, rN, rF, first, st); }), "flux register");
+    nl++;
+  }
+  if (L.ncols > 0) {
+    CK(m, timed(m, CC_K_DIAGNOSE, [&] { return launch_diagnose(L, pr, rN, rC, rO, rF, first, 1, st); }),
+       "velocity diagnosis");
+    nl++;
+  }
+  int lo = d < 0 ? 0 : d, hi = d < 0 ? m->ndom : d + 1;
+  for (int q = lo; q < hi; q++) {
+    DomHost &H = m->dom[q];
+    int o = H.r[0], c = H.r[1];
+    H.r[0] = H.r[3];
+    H.r[1] = H.r[2];
+    H.r[2] = o;
+    H.r[3] = c;
+    H.nsteps++;
+  }
+  return CC_OK;
+}
+
+// cycle(l) of a refined model (Sec 2.2): two steps of level l+1 (each after
+// adding the fine fluxes of its current state, the state that step uses, to
+// the register), the step of level l with the register, then the register
+// is cleared, level l+1 restricted onto level l and level l prolonged into the
+// ghost frame of level l+1.
+static cc_status cycle(cc_model *m, int l, long long &nl) {
+  const int pr = m->prec;
+  cudaStream_t st = m->st;
+  const bool fine = l + 1 < m->ndom;
+  if (fine) {
+    const LevelLink &K = m->link[l + 1].L;
+    for (int s = 0; s < 2; s++) {
+      CK(m, timed(m, CC_K_REFINE, [&] { return launch_register_add(K, pr, m->dom[l + 1].r[1], st); }),
+         "register add");
+      nl++;
+      cc_status r = cycle(m, l + 1, nl);
+      if (r != CC_OK) return r;
+    }
+  }
+  cc_status r = step_domains(m, l, nl);
+  if (r != CC_OK) return r;
+  if (fine) {
+    const LevelLink &K = m->link[l + 1].L;
+    CK(m, timed(m, CC_K_REFINE, [&] { return launch_register_clear(K, pr, st); }), "register clear");
+    CK(m, timed(m, CC_K_REFINE, [&] { return launch_restrict(K, pr, m->dom[l + 1].r[1], st); }), "restrict");
+    CK(m, timed(m, CC_K_REFINE, [&] { return launch_prolong(K, pr, m->dom[l].r[1], st); }), "prolong");
+    nl += 3;
+  }
+  return CC_OK;
+}
+
 extern "C" {
 
 cc_status cc_step(cc_model *m, int n) {
   if (!m) return fail(m, CC_EINVAL, "null model");
   if (n < 0) return fail(m, CC_EINVAL, "negative step count");
   if (!m->state) return fail(m, CC_ESTATE, "state not initialised");
-  StepLaunch L = make_launch(m);
   long long nl = 0;
-  for (int s = 0; s < n; s++) {
-    int first = m->nsteps == 0;
-    int rO = first ? m->r[1] : m->r[0];
-    const int rC = m->r[1], rN = m->r[2], rF = m->r[3], pr = m->prec;
-    cudaStream_t st = m->st;
-    if (L.nitems > 0) {
-      CK(m, timed(m, CC_K_FULL, [&] { return launch_full(L, pr, rO, rC, rN, rF, first, st); }), "full-cell stencil");
-      nl++;
-    }
-    if (L.ngroups > 0) {
-      CK(m, timed(m, CC_K_GROUPS, [&] { return launch_groups(L, pr, rO, rC, rN, rF, first, st); }), "cut cells");
-      nl++;
-    }
-    if (L.ncols > 0) {
-      CK(m, timed(m, CC_K_DIAGNOSE, [&] { return launch_diagnose(L, pr, rN, rC, rO, rF, first, 1, st); }),
-         "velocity diagnosis");
-      nl++;
-    }
-    int o = m->r[0], c = m->r[1];
-    m->r[0] = m->r[3];
-    m->r[1] = m->r[2];
-    m->r[2] = o;
-    m->r[3] = c;
-    m->nsteps++;
-  }
+  cc_status r = CC_OK;
+  for (int s = 0; s < n && r == CC_OK; s++) r = m->refined ? cycle(m, 0, nl) : step_domains(m, -1, nl);
   m->last_launches = nl;
-  return CC_OK;
+  return r;
 }
 
 cc_status cc_diagnostics(cc_model *m, int d, cc_diag *out) {
   if (!m || !out) return fail(m, CC_EINVAL, "null argument");
   if (d < 0 || d >= m->ndom) return fail(m, CC_EINVAL, "domain index out of range");
   if (!m->state) return fail(m, CC_ESTATE, "state not initialised");
-  CK(m, launch_diag_reduce(m->dom[d].D, m->d_doms + d, m->prec, m->r[1], m->d_diag, m->st), "diagnostics");
+  const DomHost &H = m->dom[d];
+  CK(m, launch_diag_reduce(H.D, m->d_doms + d, m->prec, H.r[1], m->d_diag, m->st), "diagnostics");
   double h[8];
   CK(m, cudaMemcpyAsync(h, m->d_diag, sizeof(double) * 5, cudaMemcpyDeviceToHost, m->st), "diag copy");
   CK(m, cudaStreamSynchronize(m->st), "diag sync");
@@ -648,8 +962,32 @@ cc_status cc_diagnostics(cc_model *m, int d, cc_diag *out) {
   out->max_u = h[2];
   out->max_w = h[3];
   out->nonfinite = (long long)h[4];
-  out->steps = m->nsteps;
+  out->steps = H.nsteps;
   if (out->nonfinite > 0) return fail(m, CC_ENUMERIC, "non-finite values in the state");
+  return CC_OK;
+}
+
+cc_status cc_refine_mass(cc_model *m, int both, double *out) {
+  if (!m || !out) return fail(m, CC_EINVAL, "null argument");
+  if (!m->refined) return fail(m, CC_EINVAL, "not a refined model");
+  if (!m->state) return fail(m, CC_ESTATE, "state not initialised");
+  double tot = 0.0;
+  for (int l = 0; l < m->ndom; l++) {
+    const DomHost &H = m->dom[l];
+    int x0 = 0, x1 = 0, y0 = 0, y1 = 0, z1 = 0;
+    if (l + 1 < m->ndom) {
+      const LinkHost &K = m->link[l + 1];
+      x0 = K.x0; x1 = K.x1; y0 = K.y0; y1 = K.y1; z1 = K.z1;
+    }
+    CK(m, launch_mass_active(H.D, m->d_doms + l, m->prec, H.r[1], H.r[0], both, x0, x1, y0, y1, z1, m->d_diag,
+                             m->st),
+       "mass");
+    double h = 0.0;
+    CK(m, cudaMemcpyAsync(&h, m->d_diag, sizeof(double), cudaMemcpyDeviceToHost, m->st), "mass copy");
+    CK(m, cudaStreamSynchronize(m->st), "mass sync");
+    tot += h;
+  }
+  *out = tot;
   return CC_OK;
 }
 
@@ -669,7 +1007,7 @@ cc_status cc_profile_enable(cc_model *m, int on) {
 
 cc_status cc_profile_read(cc_model *m, int kernel, double *total_ms, long long *launches) {
   if (!m || !total_ms || !launches) return fail(m, CC_EINVAL, "null argument");
-  if (kernel < 0 || kernel > CC_K_GHOST) return fail(m, CC_EINVAL, "bad kernel id");
+  if (kernel < 0 || kernel > CC_K_REFINE) return fail(m, CC_EINVAL, "bad kernel id");
   CK(m, cudaStreamSynchronize(m->st), "profile sync");
   double t = 0;
   long long c = 0;

@@ -33,8 +33,14 @@ struct DomDev {
   double kdif;               // c4 / (16 dt)
   double ra_nu;              // Robert-Asselin coefficient
   int bc_slip;
+  int periodic;              // lateral indices wrap (cyclic boundaries)
+  int lid;                   // the top is the rigid lid (else a refinement face)
+  // computed region: cells ci0 <= i < ci1, cj0 <= j < cj1, 0 <= k < ck1;
+  // corner columns qi0 <= I < ci1, qj0 <= J < cj1
+  int ci0, ci1, cj0, cj1, ck1, qi0, qj0;
+  double ztop;               // height of the domain top (sponge)
   void *f[NBUF][NFIELD];     // prognostic fields, padded layout
-  void *ub[NBUF];            // boundary-point velocity per level, 3*ny*nx
+  void *ub[NBUF];            // boundary-point velocity per level, 3 per padded column
   // base state per padded level, precision of the model
   const void *rhob, *pb, *thb, *pik, *rhobc, *tau, *ipb;
   // binomial-series coefficients C(a, 1..7) and the exponent a, for
@@ -47,13 +53,13 @@ struct DomDev {
   const double *az;          // (nz+1)*ny*nx
   const int8_t *cls;         // nz*ny*nx
   const int32_t *root;       // nz*ny*nx, cell id of host or -1
-  const int32_t *kug;        // ny*nx: cells k < kug are below the terrain
+  const int32_t *kug;        // padded columns: cells k < kug are below the terrain
   const int8_t *vcls;        // corner classes, padded layout
-  const int32_t *bK, *bI, *bJ;
-  const double *ba, *bb, *bn;
+  const int32_t *bK, *bI, *bJ;  // padded columns
+  const double *ba, *bb, *bn;   // padded columns (bn: 3 per column)
   const int32_t *mK;         // padded corner layout
   const double *mg;          // padded corner layout
-  const int32_t *ktop;       // ny*nx: highest non-predicted corner level below nz
+  const int32_t *ktop;       // padded columns: highest non-predicted corner level below the top
 };
 
 // (block, tile) work item of the full-cell stencil
@@ -85,6 +91,51 @@ __host__ __device__ inline int wrapi(int i, int n) {
 __host__ __device__ inline long long cid(const DomDev &D, int i, int j, int k) {
   return ((long long)k * D.ny + j) * D.nx + i;
 }
+// padded column index
+__host__ __device__ inline long long qidx(const DomDev &D, int I, int J) {
+  return (long long)(J + GH) * D.px + (I + GH);
+}
+
+// ---- refinement (step.cu)
+// A coarse face on the boundary of a refined box: the coarse cell on the
+// active side, the face (axis, side) seen from that cell, and the first of
+// the 2x2 fine faces that cover it (padded coordinates of the fine cell on
+// the high side of the fine face).
+struct IfaceFace {
+  int ax;          // 0, 1, 2
+  int fi, fj, fk;  // fine face: the x-face of fine cell (fi, fj, fk) etc.
+};
+// coarse cell next to the box with up to three interface faces
+struct IfaceCell {
+  int i, j, k;     // coarse cell
+  int slot[6];     // register slot of face (ax*2 + side), -1 if not an interface face
+};
+struct LevelLink {
+  const DomDev *dc, *df;     // device pointers of the coarse and fine level
+  int ox, oy;                // fine cell i covers coarse cell (i + ox) / 2
+  const long long *pcell;    // fine padded offsets of prolonged ghost cells
+  long long npcell;
+  const long long *pcorn;    // fine padded offsets of prolonged ghost corners
+  long long npcorn;
+  const long long *rcell;    // coarse padded offsets of restricted cells
+  long long nrcell;
+  const long long *rcorn;    // coarse padded offsets of restricted corners
+  long long nrcorn;
+  const IfaceFace *faces;    // interface faces (register slots)
+  int nfaces;
+  const IfaceCell *icells;
+  int nicells;
+  void *regm, *regh;         // register sums per face (model precision)
+};
+cudaError_t launch_prolong(const LevelLink &L, int prec, int rC, cudaStream_t st);
+cudaError_t launch_restrict(const LevelLink &L, int prec, int rF, cudaStream_t st);
+cudaError_t launch_register_add(const LevelLink &L, int prec, int rF, cudaStream_t st);
+cudaError_t launch_register_clear(const LevelLink &L, int prec, cudaStream_t st);
+cudaError_t launch_iface(const LevelLink &L, int prec, int rO, int rC, int rN, int rF, int first,
+                         cudaStream_t st);
+cudaError_t launch_mass_active(const DomDev &D, const DomDev *d_dom, int prec, int rC, int rO, int both,
+                               int bx0, int bx1, int by0, int by1, int bz1, double *d_out, cudaStream_t st);
+cudaError_t launch_flat_columns(const DomDev &D, cudaStream_t st);
 
 // geometry of one domain (geometry.cu); returns the group list of the domain
 // as device allocations owned by the caller

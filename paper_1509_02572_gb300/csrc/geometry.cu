@@ -112,7 +112,7 @@ __global__ void k_columns(DomDev D, double *hc, double *gx, double *gy, int32_t 
   double hmin = fmin(fmin(h00, h10), fmin(h01, h11));
   int k = 0;
   while (k < D.nz && (k + 1) * D.dz <= hmin) k++;
-  kug[t] = k;
+  kug[qidx(D, i, j)] = k;
 }
 
 // ---------------------------------------------------------------- cells
@@ -173,7 +173,7 @@ __global__ void k_zfaces(DomDev D, double *az) {
   if (t >= n) return;
   int i = (int)(t % D.nx), j = (int)((t / D.nx) % D.ny), K = (int)(t / ((long long)D.nx * D.ny));
   double a = 0.0;
-  if (K > 0 && K < D.nz) {
+  if (K > 0 && (K < D.nz || !D.lid)) {
     double z = K * D.dz;
     double h00 = hcorner(D, i, j), h10 = hcorner(D, i + 1, j), h01 = hcorner(D, i, j + 1),
            h11 = hcorner(D, i + 1, j + 1);
@@ -378,15 +378,17 @@ __global__ void k_vcls(DomDev D, const int8_t *cls, const int32_t *root, int8_t 
   int8_t v;
   if (K * D.dz <= hcorner(D, I, J)) {
     v = V_UG;
-  } else if (K >= D.nz) {
+  } else if (D.lid && K >= D.nz) {
     v = V_LID;
   } else if (K < 1) {
     v = V_MF;
   } else {
+    // cells above the box top of a refined level lie over flat floor: owners
     bool own = true;
     for (int dk = -1; dk <= 0; dk++)
       for (int dj = -1; dj <= 0; dj++)
         for (int di = -1; di <= 0; di++) {
+          if (K + dk >= D.nz) continue;
           long long c = (((long long)(K + dk)) * D.ny + wrapi(J + dj, D.ny)) * D.nx + wrapi(I + di, D.nx);
           if (cls[c] == C_UG || root[c] != (int32_t)c) own = false;
         }
@@ -403,11 +405,13 @@ __device__ inline int8_t vcls_at(const DomDev &D, const int8_t *vcls, int I, int
 // heights; nearest plane of predicted points crossed by the normal line
 __global__ void k_bstencil(DomDev D, const double *hc, const int8_t *vcls, int32_t *bK, int32_t *bI,
                            int32_t *bJ, double *ba, double *bb, double *bn, int *err) {
-  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= (long long)D.nx * D.ny) return;
-  int I = (int)(t % D.nx), J = (int)(t / D.nx);
+  long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t0 >= (long long)D.nx * D.ny) return;
+  int I = (int)(t0 % D.nx), J = (int)(t0 / D.nx);
+  const long long t = qidx(D, I, J);
   auto HCc = [&](int i, int j) { return hc[(long long)wrapi(j, D.ny) * D.nx + wrapi(i, D.nx)]; };
-  if (vcls_at(D, vcls, I, J, D.nz - 1) != V_PRED) atomicOr(err, 4);
+  if (D.lid && vcls_at(D, vcls, I, J, D.nz - 1) != V_PRED) atomicOr(err, 4);
+  const int ktopsearch = D.lid ? D.nz - 1 : D.nz + 1;
   double hm = HCc(I - 1, J - 1), h0m = HCc(I, J - 1), hm0 = HCc(I - 1, J), h00 = HCc(I, J);
   double gxc = ((h0m + h00) - (hm + hm0)) / (2.0 * D.dx);
   double gyc = ((hm0 + h00) - (hm + h0m)) / (2.0 * D.dy);
@@ -419,7 +423,7 @@ __global__ void k_bstencil(DomDev D, const double *hc, const int8_t *vcls, int32
   double hh = hcorner(D, I, J);
   int K0 = 0;
   while (K0 * D.dz <= hh) K0++;
-  for (int K = K0; K < K0 + 8 && K <= D.nz - 1; K++) {
+  for (int K = K0; K < K0 + 8 && K <= ktopsearch; K++) {
     double tt = (K * D.dz - hh) / nzv;
     double xN = I * D.dx + tt * nxv, yN = J * D.dy + tt * nyv;
     double fi = floor(xN / D.dx), fj = floor(yN / D.dy);
@@ -431,8 +435,8 @@ __global__ void k_bstencil(DomDev D, const double *hc, const int8_t *vcls, int32
               (a == 0.0 || b == 0.0 || vcls_at(D, vcls, i0 + 1, j0 + 1, K) == V_PRED);
     if (ok) {
       bK[t] = K;
-      bI[t] = wrapi(i0, D.nx);
-      bJ[t] = wrapi(j0, D.ny);
+      bI[t] = D.periodic ? wrapi(i0, D.nx) : i0;
+      bJ[t] = D.periodic ? wrapi(j0, D.ny) : j0;
       ba[t] = a;
       bb[t] = b;
       return;
@@ -454,7 +458,8 @@ __global__ void k_mstencil(DomDev D, const int8_t *vcls, int32_t *mK, double *mg
   mg[p] = 0.0;
   if (vcls[p] != V_MF) return;
   int ka = -1;
-  for (int K2 = K + 1; K2 <= D.nz - 1; K2++)
+  const int ktopsearch = D.lid ? D.nz - 1 : D.nz + 1;
+  for (int K2 = K + 1; K2 <= ktopsearch; K2++)
     if (vcls[pidx(D, I, J, K2)] == V_PRED) {
       ka = K2;
       break;
@@ -474,12 +479,41 @@ __global__ void k_ktop(DomDev D, const int8_t *vcls, int32_t *ktop) {
   if (t >= (long long)D.nx * D.ny) return;
   int I = (int)(t % D.nx), J = (int)(t / D.nx);
   int kt = -GH;
-  for (int K = -GH; K < D.nz; K++)
+  const int kend = D.lid ? D.nz : D.ck1;
+  for (int K = -GH; K < kend; K++)
     if (vcls[pidx(D, I, J, K)] != V_PRED) kt = K;
-  ktop[t] = kt;
+  ktop[qidx(D, I, J)] = kt;
+}
+
+// Columns of a refined level's padded frame lie over flat floor (h = 0):
+// predicted above the floor, boundary point at the floor corner with the
+// vertical normal and the corner above as its nearest plane.
+__global__ void k_flat_columns(DomDev D) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)D.px * D.py) return;
+  int I = (int)(t % D.px) - GH, J = (int)(t / D.px) - GH;
+  if (I >= 0 && I < D.nx && J >= 0 && J < D.ny) return;
+  const_cast<int32_t *>(D.kug)[t] = 0;
+  const_cast<int32_t *>(D.bK)[t] = 1;
+  const_cast<int32_t *>(D.bI)[t] = I;
+  const_cast<int32_t *>(D.bJ)[t] = J;
+  const_cast<double *>(D.ba)[t] = 0.0;
+  const_cast<double *>(D.bb)[t] = 0.0;
+  double *bn = const_cast<double *>(D.bn);
+  bn[3 * t] = 0.0;
+  bn[3 * t + 1] = 0.0;
+  bn[3 * t + 2] = 1.0;
+  const_cast<int32_t *>(D.ktop)[t] = 0;
+  int8_t *vcls = const_cast<int8_t *>(D.vcls);
+  for (int K = -GH; K < D.nz + GH; K++) vcls[pidx(D, I, J, K)] = K <= 0 ? V_UG : V_PRED;
 }
 
 }  // namespace
+
+cudaError_t launch_flat_columns(const DomDev &D, cudaStream_t st) {
+  k_flat_columns<<<nblk((long long)D.px * D.py), TPB, 0, st>>>(D);
+  return cudaGetLastError();
+}
 
 // ---------------------------------------------------------------- driver
 struct GeomScratch {

@@ -118,10 +118,10 @@ __device__ __forceinline__ float d4(float a, float b, float c, float d, float e)
   return a - 4.0f * b + 6.0f * c - 4.0f * d + e;
 }
 
-// padded index of a cell / corner with the lateral coordinates wrapped
-// (periodic domains)
+// padded index of a cell / corner; periodic domains wrap the lateral
+// coordinates, refined boxes read their ghost frame
 __device__ __forceinline__ long long widx(const DomDev &D, int i, int j, int k) {
-  return pidx(D, wrapi(i, D.nx), wrapi(j, D.ny), k);
+  return D.periodic ? pidx(D, wrapi(i, D.nx), wrapi(j, D.ny), k) : pidx(D, i, j, k);
 }
 
 // ------------------------------------------------------------------ base state
@@ -157,7 +157,7 @@ __global__ void k_base(DomDev D, double theta0, double N, double p_surf, double 
   pik[kp] = (T)pow(p / D.p0, D.kap);
   // corner level K = k: mean of the two adjacent cell levels
   rhobc[kp] = (T)(0.5 * (rm + r));
-  double ztop = D.nz * D.dz, zs = ztop * (1.0 - sponge_frac), z = k * D.dz, t = 0.0;
+  double ztop = D.ztop, zs = ztop * (1.0 - sponge_frac), z = k * D.dz, t = 0.0;
   if (sponge_frac > 0.0 && z > zs && z <= ztop) {
     double s = sin(0.5 * M_PI * (z - zs) / (ztop - zs));
     t = tau_max * s * s;
@@ -243,21 +243,31 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
   const int i0 = W.i0, j0 = W.j0, k0 = W.k0, k1 = W.k1;
 
   // per-thread plane points of the haloed tile and their in-plane offsets
-  // (lateral coordinates wrapped: cyclic boundaries)
+  // (periodic domains wrap the lateral coordinates; a refined box reads its
+  // ghost frame, clamped to the padding where no computed point needs it)
   long long loff[NLP];
   int lpt[NLP];
+  const int py = D.py;
 #pragma unroll
   for (int s = 0; s < NLP; s++) {
     int p = tid + s * NT;
     lpt[s] = p;
     int hx = p % HX, hy = p / HX;
-    int gi = wrapi(i0 - 2 + hx, nx), gj = wrapi(j0 - 2 + hy, ny);
+    int gi = i0 - 2 + hx, gj = j0 - 2 + hy;
+    if (D.periodic) {
+      gi = wrapi(gi, nx);
+      gj = wrapi(gj, ny);
+    } else {
+      gi = min(max(gi, -GH), px - GH - 1);
+      gj = min(max(gj, -GH), py - GH - 1);
+    }
     loff[s] = (long long)(gj + GH) * px + (gi + GH);
   }
+  const int kmaxp = D.pz - GH - 1;  // highest plane inside the padding
   // issue the asynchronous copies of every raw field of plane kk (the
   // current-level momentum only when with_m: its ring has four slots)
   auto issue = [&](int kk, bool with_m) {
-    const long long zo = (long long)(kk + GH) * plane;
+    const long long zo = (long long)(min(kk, kmaxp) + GH) * plane;  // planes past the top are never used
     const int a6 = s6(kk), a4 = s4(kk), a5 = s5(kk);
 #pragma unroll
     for (int s = 0; s < NLP; s++) {
@@ -320,14 +330,16 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
 
   const int tx = tid % TX, ty = tid / TX;
   const int i = i0 + tx, j = j0 + ty;
-  const bool active = i < nx && j < ny;
+  const bool active = i < D.ci1 && j < D.cj1;
+  // corners of a refined box outside -1 .. n+1 are ghost values from the coarser level
+  const bool corner_active = active && i >= D.qi0 && j >= D.qj0;
   const int c = (ty + 2) * HX + (tx + 2);
   const long long own = active ? (long long)(j + GH) * px + (i + GH) : 0;
   const T dx = (T)D.dx, dy = (T)D.dy, dz = (T)D.dz;
   const T Sx = (T)(D.dy * D.dz), Sy = (T)(D.dx * D.dz), Sz = (T)(D.dx * D.dy);
   const T v0inv = (T)(1.0 / (D.dx * D.dy * D.dz));
   const T kdif = (T)D.kdif, Cp = (T)D.Cp, g = (T)D.g, U = (T)D.U;
-  const int kug = active ? D.kug[(long long)j * nx + i] : 0;
+  const int kug = active ? D.kug[qidx(D, i, j)] : 0;
 
   // own column at n-1 for the vertical diffusion stencils, levels k-2 .. k+2
   T treg[5], mreg[5][3];
@@ -394,8 +406,8 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
       T hyp = face_flux(H0[c], H0[c + HX], uy0[c + HX], uy0[c + HX + 1], uyp[c + HX], uyp[c + HX + 1], Sy);
       T hzm = face_flux(Hm[c], H0[c], uz0[c], uz0[c + 1], uz0[c + HX], uz0[c + HX + 1], Sz);
       T hzp = face_flux(H0[c], Hp[c], uzp[c], uzp[c + 1], uzp[c + HX], uzp[c + HX + 1], Sz);
-      if (k == 0) { fzm = 0; hzm = 0; }          // floor
-      if (k == nz - 1) { fzp = 0; hzp = 0; }     // rigid lid
+      if (k == 0) { fzm = 0; hzm = 0; }                  // floor
+      if (D.lid && k == nz - 1) { fzp = 0; hzp = 0; }    // rigid lid
       T RM = A::add(A::add(A::sub(fxp, fxm), A::sub(fyp, fym)), A::sub(fzp, fzm));
       T RH = A::add(A::add(A::sub(hxp, hxm), A::sub(hyp, hym)), A::sub(hzp, hzm));
       // fourth-order diffusion of (rho theta)' at n-1
@@ -469,8 +481,10 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
         tend += -kdif * dm - tk * (mold - ref0);
         T mnew = mold + dt2 * tend;
         T mf = mcur[d] + nu * (mnew - T(2) * mcur[d] + mold);
-        ((T *)D.f[rN][2 + d])[o] = mnew;
-        ((T *)D.f[rF][2 + d])[o] = mf;
+        if (corner_active) {
+          ((T *)D.f[rN][2 + d])[o] = mnew;
+          ((T *)D.f[rF][2 + d])[o] = mf;
+        }
       }
     }
 #pragma unroll
@@ -627,7 +641,7 @@ __global__ void k_diag(const DomDev *__restrict__ doms, const ColItem *__restric
   T *M[3] = {(T *)D.f[rV][2], (T *)D.f[rV][3], (T *)D.f[rV][4]};
   const T *const *Mc = (const T *const *)M;
   const T *rhob = (const T *)D.rhob;
-  const long long q = (long long)J * D.nx + I;
+  const long long q = qidx(D, I, J);
   // boundary point: bilinear in the nearest plane, then free-slip projection
   int K = D.bK[q], i0 = D.bI[q], j0 = D.bJ[q];
   T a = (T)D.ba[q], b = (T)D.bb[q];
@@ -684,10 +698,12 @@ __global__ void k_diag(const DomDev *__restrict__ doms, const ColItem *__restric
     }
     store(KK, u);
   }
-  T ul[3];
-  corner_u(D, rp, Mc, rhob, I, J, D.nz - 1, ul);
-  ul[2] = 0;
-  for (int KK = D.nz; KK < D.nz + GH; KK++) store(KK, ul);
+  if (D.lid) {
+    T ul[3];
+    corner_u(D, rp, Mc, rhob, I, J, D.nz - 1, ul);
+    ul[2] = 0;
+    for (int KK = D.nz; KK < D.nz + GH; KK++) store(KK, ul);
+  }
 }
 
 // initial momentum rho_corner * U on the predicted points of level r
@@ -695,9 +711,10 @@ template <typename T>
 __global__ void k_init_momentum(const DomDev *__restrict__ dom, int r, double U) {
   const DomDev &D = *dom;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  long long n = (long long)D.nx * D.ny * D.nz;
+  const int wx = D.ci1 - D.qi0, wy = D.cj1 - D.qj0;
+  long long n = (long long)wx * wy * D.ck1;
   if (t >= n) return;
-  int I = (int)(t % D.nx), J = (int)((t / D.nx) % D.ny), K = (int)(t / ((long long)D.nx * D.ny));
+  int I = (int)(t % wx) + D.qi0, J = (int)((t / wx) % wy) + D.qj0, K = (int)(t / ((long long)wx * wy));
   long long o = pidx(D, I, J, K);
   if (D.vcls[o] != V_PRED) return;
   const T *rp = (const T *)D.f[r][0];
@@ -790,6 +807,271 @@ __global__ void k_diag_final(const double *part, int nb, double *out) {
   out[4] = a4;
 }
 
+
+// ------------------------------------------------------------------ refinement (Sec 2.2)
+__device__ __forceinline__ void decode(const DomDev &D, long long off, int &i, int &j, int &k) {
+  i = (int)(off % D.px) - GH;
+  j = (int)((off / D.px) % D.py) - GH;
+  k = (int)(off / D.plane) - GH;
+}
+
+// Coarse -> fine: fine ghost cells take the covering coarse cell (injection);
+// fine ghost corners take the coarse momentum interpolated linearly along each
+// axis (coincident points copy).  All four time-level buffers of the fine
+// level receive the current coarse values.
+template <typename T>
+__global__ void k_prolong(LevelLink L, int rC) {
+  const DomDev &C = *L.dc, &F = *L.df;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < L.npcell) {
+    long long off = L.pcell[t];
+    int i, j, k;
+    decode(F, off, i, j, k);
+    long long pc = pidx(C, (i + L.ox) >> 1, (j + L.oy) >> 1, k >> 1);
+    T r = ((const T *)C.f[rC][0])[pc], q = ((const T *)C.f[rC][1])[pc];
+    for (int b = 0; b < NBUF; b++) {
+      ((T *)F.f[b][0])[off] = r;
+      ((T *)F.f[b][1])[off] = q;
+    }
+  } else if (t < L.npcell + L.npcorn) {
+    long long off = L.pcorn[t - L.npcell];
+    int I, J, K;
+    decode(F, off, I, J, K);
+    int X = I + L.ox, Y = J + L.oy;
+    int xs[2] = {X >> 1, (X + 1) >> 1}, ys[2] = {Y >> 1, (Y + 1) >> 1}, zs[2] = {K >> 1, (K + 1) >> 1};
+    T s0 = 0, s1 = 0, s2 = 0;
+    for (int a = 0; a < 2; a++)
+      for (int b = 0; b < 2; b++)
+        for (int c = 0; c < 2; c++) {
+          long long pc = pidx(C, xs[a], ys[b], zs[c]);
+          s0 += ((const T *)C.f[rC][2])[pc];
+          s1 += ((const T *)C.f[rC][3])[pc];
+          s2 += ((const T *)C.f[rC][4])[pc];
+        }
+    s0 *= T(0.125);
+    s1 *= T(0.125);
+    s2 *= T(0.125);
+    for (int b = 0; b < NBUF; b++) {
+      ((T *)F.f[b][2])[off] = s0;
+      ((T *)F.f[b][3])[off] = s1;
+      ((T *)F.f[b][4])[off] = s2;
+    }
+  }
+}
+
+// Fine -> coarse: coarse cells near the covered box boundary take the mean of
+// the 8 fine cells they contain; coarse corners inside it take the coincident
+// fine corner.  All four time-level buffers of the coarse level.
+template <typename T>
+__global__ void k_restrict(LevelLink L, int rF) {
+  const DomDev &C = *L.dc, &F = *L.df;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < L.nrcell) {
+    long long off = L.rcell[t];
+    int ic, jc, kc;
+    decode(C, off, ic, jc, kc);
+    T sr = 0, sp = 0;
+    for (int dk = 0; dk < 2; dk++)
+      for (int dj = 0; dj < 2; dj++)
+        for (int di = 0; di < 2; di++) {
+          long long pf = pidx(F, 2 * ic - L.ox + di, 2 * jc - L.oy + dj, 2 * kc + dk);
+          sr += ((const T *)F.f[rF][0])[pf];
+          sp += ((const T *)F.f[rF][1])[pf];
+        }
+    sr *= T(0.125);
+    sp *= T(0.125);
+    for (int b = 0; b < NBUF; b++) {
+      ((T *)C.f[b][0])[off] = sr;
+      ((T *)C.f[b][1])[off] = sp;
+    }
+  } else if (t < L.nrcell + L.nrcorn) {
+    long long off = L.rcorn[t - L.nrcell];
+    int Ic, Jc, Kc;
+    decode(C, off, Ic, Jc, Kc);
+    long long pf = pidx(F, 2 * Ic - L.ox, 2 * Jc - L.oy, 2 * Kc);
+    T a = ((const T *)F.f[rF][2])[pf], b_ = ((const T *)F.f[rF][3])[pf], c = ((const T *)F.f[rF][4])[pf];
+    for (int b = 0; b < NBUF; b++) {
+      ((T *)C.f[b][2])[off] = a;
+      ((T *)C.f[b][3])[off] = b_;
+      ((T *)C.f[b][4])[off] = c;
+    }
+  }
+}
+
+// Mass and heat flux through one face of the level's current state, with the
+// operations of the full-cell stencil (so the two agree bit for bit): the x-face
+// of cell (I,j,k) lies between cells I-1 and I, and so on.
+template <typename T>
+__device__ __forceinline__ void face_fluxes(const DomDev &D, int rC, int ax, int I, int J, int K, T &fm, T &fh) {
+  const T *rp = (const T *)D.f[rC][0];
+  const T *pp = (const T *)D.f[rC][1];
+  const T *M[3] = {(const T *)D.f[rC][2], (const T *)D.f[rC][3], (const T *)D.f[rC][4]};
+  const T *rhob = (const T *)D.rhob, *pb = (const T *)D.pb, *thb = (const T *)D.thb, *ipb = (const T *)D.ipb;
+  int li = I, lj = J, lk = K;
+  int cI[4], cJ[4], cK[4];
+  T S;
+  if (ax == 0) {
+    li = I - 1;
+    S = (T)(D.dy * D.dz);
+    cI[0] = I; cJ[0] = J; cK[0] = K;
+    cI[1] = I; cJ[1] = J + 1; cK[1] = K;
+    cI[2] = I; cJ[2] = J; cK[2] = K + 1;
+    cI[3] = I; cJ[3] = J + 1; cK[3] = K + 1;
+  } else if (ax == 1) {
+    lj = J - 1;
+    S = (T)(D.dx * D.dz);
+    cI[0] = I; cJ[0] = J; cK[0] = K;
+    cI[1] = I + 1; cJ[1] = J; cK[1] = K;
+    cI[2] = I; cJ[2] = J; cK[2] = K + 1;
+    cI[3] = I + 1; cJ[3] = J; cK[3] = K + 1;
+  } else {
+    lk = K - 1;
+    S = (T)(D.dx * D.dy);
+    cI[0] = I; cJ[0] = J; cK[0] = K;
+    cI[1] = I + 1; cJ[1] = J; cK[1] = K;
+    cI[2] = I; cJ[2] = J + 1; cK[2] = K;
+    cI[3] = I + 1; cJ[3] = J + 1; cK[3] = K;
+  }
+  T u[4];
+  for (int s = 0; s < 4; s++) {
+    T iv = rinv(corner_rho(D, rp, rhob, cI[s], cJ[s], cK[s]));
+    u[s] = M[ax][widx(D, cI[s], cJ[s], cK[s])] * iv;
+  }
+  T ra = cell_rho(D, rp, rhob, li, lj, lk), rb = cell_rho(D, rp, rhob, I, J, K);
+  T ta = theta_tot(D, thb, pb, ipb, lk + GH, pp[widx(D, li, lj, lk)]);
+  T tb = theta_tot(D, thb, pb, ipb, K + GH, pp[widx(D, I, J, K)]);
+  fm = face_flux(ra, rb, u[0], u[1], u[2], u[3], S);
+  fh = face_flux(ta, tb, u[0], u[1], u[2], u[3], S);
+}
+
+// Flux register: add the fine fluxes of the 2x2 fine faces of every coarse
+// interface face, from the fine level's current state (the state its next
+// step uses).
+template <typename T>
+__global__ void k_reg_add(LevelLink L, int rF) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= L.nfaces) return;
+  const IfaceFace f = L.faces[q];
+  const DomDev &F = *L.df;
+  T sm = 0, sh = 0;
+  for (int a = 0; a < 2; a++)
+    for (int b = 0; b < 2; b++) {
+      int I = f.fi, J = f.fj, K = f.fk;
+      if (f.ax == 0) { J += a; K += b; }
+      else if (f.ax == 1) { I += a; K += b; }
+      else { I += a; J += b; }
+      T fm, fh;
+      face_fluxes<T>(F, rF, f.ax, I, J, K, fm, fh);
+      sm = Ar<T>::add(sm, fm);
+      sh = Ar<T>::add(sh, fh);
+    }
+  T *rm = (T *)L.regm, *rh = (T *)L.regh;
+  rm[q] = Ar<T>::add(rm[q], sm);
+  rh[q] = Ar<T>::add(rh[q], sh);
+}
+
+template <typename T>
+__global__ void k_reg_clear(LevelLink L) {
+  int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= L.nfaces) return;
+  ((T *)L.regm)[q] = 0;
+  ((T *)L.regh)[q] = 0;
+}
+
+// Coarse cells next to a refined box: the scalar update of the full-cell
+// stencil with the interface faces' fluxes taken from the register (the mean
+// over the two fine substeps; cube-boundary flux of Sec 2.2).
+template <typename T>
+__global__ void k_iface(LevelLink L, int rO, int rC, int rN, int rF, int first) {
+  using A = Ar<T>;
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= L.nicells) return;
+  const IfaceCell ic = L.icells[t];
+  const DomDev &D = *L.dc;
+  const T dt2 = (T)(first ? D.dt : 2.0 * D.dt);
+  const T nu = (T)(first ? 0.0 : D.ra_nu);
+  const int i = ic.i, j = ic.j, k = ic.k;
+  const T *rm_ = (const T *)L.regm, *rh_ = (const T *)L.regh;
+  T fl[6], hl[6];
+  for (int ax = 0; ax < 3; ax++)
+    for (int sd = 0; sd < 2; sd++) {
+      int sl = ic.slot[ax * 2 + sd];
+      T fm, fh;
+      if (sl >= 0) {
+        fm = A::mul(T(0.5), rm_[sl]);
+        fh = A::mul(T(0.5), rh_[sl]);
+      } else {
+        int I = i + (ax == 0 ? sd : 0), J = j + (ax == 1 ? sd : 0), K = k + (ax == 2 ? sd : 0);
+        face_fluxes<T>(D, rC, ax, I, J, K, fm, fh);
+      }
+      fl[ax * 2 + sd] = fm;
+      hl[ax * 2 + sd] = fh;
+    }
+  if (k == 0) { fl[4] = 0; hl[4] = 0; }
+  if (D.lid && k == D.nz - 1) { fl[5] = 0; hl[5] = 0; }
+  T RM = A::add(A::add(A::sub(fl[1], fl[0]), A::sub(fl[3], fl[2])), A::sub(fl[5], fl[4]));
+  T RH = A::add(A::add(A::sub(hl[1], hl[0]), A::sub(hl[3], hl[2])), A::sub(hl[5], hl[4]));
+  const T *ppO = (const T *)D.f[rO][1];
+  const T *rhobp = (const T *)D.pb, *thb = (const T *)D.thb, *pik = (const T *)D.pik, *ipb = (const T *)D.ipb;
+  auto tho = [&](int ii, int jj, int kk) { return theta_pert(D, thb, rhobp, ipb, kk + GH, ppO[widx(D, ii, jj, kk)]); };
+  T dd = d4(tho(i - 2, j, k), tho(i - 1, j, k), tho(i, j, k), tho(i + 1, j, k), tho(i + 2, j, k)) +
+         d4(tho(i, j - 2, k), tho(i, j - 1, k), tho(i, j, k), tho(i, j + 1, k), tho(i, j + 2, k)) +
+         d4(tho(i, j, k - 2), tho(i, j, k - 1), tho(i, j, k), tho(i, j, k + 1), tho(i, j, k + 2));
+  T Dth = -(T)D.kdif * dd;
+  const T v0inv = (T)(1.0 / (D.dx * D.dy * D.dz));
+  long long o = pidx(D, i, j, k);
+  T rC_ = ((const T *)D.f[rC][0])[o], pC_ = ((const T *)D.f[rC][1])[o];
+  T rO_ = ((const T *)D.f[rO][0])[o], pO_ = ppO[o];
+  T rN_ = rO_ - dt2 * (RM * v0inv);
+  T pN_ = pO_ - dt2 * (T)D.Cp * exner_fac(D, pik, rhobp, ipb, k + GH, pC_) * (RH * v0inv - Dth);
+  if (k < D.kug[qidx(D, i, j)]) { rN_ = 0; pN_ = 0; }
+  T rF_ = rC_ + nu * (rN_ - T(2) * rC_ + rO_);
+  T pF_ = pC_ + nu * (pN_ - T(2) * pC_ + pO_);
+  if (k < D.kug[qidx(D, i, j)]) { rF_ = 0; pF_ = 0; }
+  ((T *)D.f[rN][0])[o] = rN_;
+  ((T *)D.f[rN][1])[o] = pN_;
+  ((T *)D.f[rF][0])[o] = rF_;
+  ((T *)D.f[rF][1])[o] = pF_;
+}
+
+// Two-level perturbation mass of the active cells of one level (a box of
+// covered cells excluded), Neumaier-compensated, fixed reduction order.
+template <typename T>
+__global__ void k_mass_active(const DomDev *__restrict__ dom, int rC, int rO, int both, int bx0, int bx1, int by0,
+                              int by1, int bz1, double *part) {
+  const DomDev &D = *dom;
+  const T *r1 = (const T *)D.f[rC][0], *r0 = (const T *)D.f[rO][0];
+  const double V0 = D.dx * D.dy * D.dz;
+  long long n = (long long)D.nx * D.ny * D.nz;
+  NSum<double> acc{0, 0};
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    int i = (int)(t % D.nx), j = (int)((t / D.nx) % D.ny), k = (int)(t / ((long long)D.nx * D.ny));
+    if (i >= bx0 && i < bx1 && j >= by0 && j < by1 && k < bz1) continue;
+    const long long o = pidx(D, i, j, k);
+    // every member of a merge group carries the group's perturbation, so the
+    // cell sum of vf V0 rho' is the group sum of V_G rho'
+    double m = (double)r1[o] + (both ? (double)r0[o] : 0.0);
+    acc.add(D.vf[t] * V0 * m);
+  }
+  __shared__ double sh[2][DIAG_TPB];
+  sh[0][threadIdx.x] = acc.s;
+  sh[1][threadIdx.x] = acc.c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    NSum<double> S{0, 0};
+    double cc = 0;
+    for (int a = 0; a < DIAG_TPB; a++) {
+      S.add(sh[0][a]);
+      cc += sh[1][a];
+    }
+    part[5 * blockIdx.x + 0] = S.s;
+    part[5 * blockIdx.x + 1] = S.c + cc;
+    part[5 * blockIdx.x + 2] = 0;
+    part[5 * blockIdx.x + 3] = 0;
+    part[5 * blockIdx.x + 4] = 0;
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 namespace {
 template <typename T, int TYv>
@@ -860,7 +1142,7 @@ cudaError_t launch_diagnose(const StepLaunch &L, int prec, int rV, int rC, int r
 }
 
 cudaError_t launch_init_momentum(const DomDev &D, const DomDev *d_dom, int prec, int r, double U, cudaStream_t st) {
-  long long n = (long long)D.nx * D.ny * D.nz;
+  long long n = (long long)(D.ci1 - D.qi0) * (D.cj1 - D.qj0) * D.ck1;
   unsigned nb = (unsigned)((n + 255) / 256);
   if (prec == CC_FP64) k_init_momentum<double><<<nb, 256, 0, st>>>(d_dom, r, U);
   else k_init_momentum<float><<<nb, 256, 0, st>>>(d_dom, r, U);
@@ -872,6 +1154,59 @@ cudaError_t launch_diag_reduce(const DomDev &D, const DomDev *d_dom, int prec, i
   double *part = d_out + 8;
   if (prec == CC_FP64) k_diag_partial<double><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(d_dom, r, part);
   else k_diag_partial<float><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(d_dom, r, part);
+  k_diag_final<<<1, 32, 0, st>>>(part, DIAG_BLOCKS, d_out);
+  return cudaGetLastError();
+}
+
+
+namespace {
+inline unsigned nb256(long long n) { return (unsigned)((n + 255) / 256); }
+}
+
+cudaError_t launch_prolong(const LevelLink &L, int prec, int rC, cudaStream_t st) {
+  long long n = L.npcell + L.npcorn;
+  if (n <= 0) return cudaSuccess;
+  if (prec == CC_FP64) k_prolong<double><<<nb256(n), 256, 0, st>>>(L, rC);
+  else k_prolong<float><<<nb256(n), 256, 0, st>>>(L, rC);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(const LevelLink &L, int prec, int rF, cudaStream_t st) {
+  long long n = L.nrcell + L.nrcorn;
+  if (n <= 0) return cudaSuccess;
+  if (prec == CC_FP64) k_restrict<double><<<nb256(n), 256, 0, st>>>(L, rF);
+  else k_restrict<float><<<nb256(n), 256, 0, st>>>(L, rF);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_register_add(const LevelLink &L, int prec, int rF, cudaStream_t st) {
+  if (L.nfaces <= 0) return cudaSuccess;
+  if (prec == CC_FP64) k_reg_add<double><<<nb256(L.nfaces), 256, 0, st>>>(L, rF);
+  else k_reg_add<float><<<nb256(L.nfaces), 256, 0, st>>>(L, rF);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_register_clear(const LevelLink &L, int prec, cudaStream_t st) {
+  if (L.nfaces <= 0) return cudaSuccess;
+  if (prec == CC_FP64) k_reg_clear<double><<<nb256(L.nfaces), 256, 0, st>>>(L);
+  else k_reg_clear<float><<<nb256(L.nfaces), 256, 0, st>>>(L);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_iface(const LevelLink &L, int prec, int rO, int rC, int rN, int rF, int first, cudaStream_t st) {
+  if (L.nicells <= 0) return cudaSuccess;
+  if (prec == CC_FP64) k_iface<double><<<nb256(L.nicells), 256, 0, st>>>(L, rO, rC, rN, rF, first);
+  else k_iface<float><<<nb256(L.nicells), 256, 0, st>>>(L, rO, rC, rN, rF, first);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mass_active(const DomDev &D, const DomDev *d_dom, int prec, int rC, int rO, int both, int bx0,
+                               int bx1, int by0, int by1, int bz1, double *d_out, cudaStream_t st) {
+  double *part = d_out + 8;
+  if (prec == CC_FP64)
+    k_mass_active<double><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(d_dom, rC, rO, both, bx0, bx1, by0, by1, bz1, part);
+  else
+    k_mass_active<float><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(d_dom, rC, rO, both, bx0, bx1, by0, by1, bz1, part);
   k_diag_final<<<1, 32, 0, st>>>(part, DIAG_BLOCKS, d_out);
   return cudaGetLastError();
 }

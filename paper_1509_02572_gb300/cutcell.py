@@ -25,11 +25,12 @@ HOST_GZ = 2
 EXPORTS = ("cc_create", "cc_destroy", "cc_last_error", "cc_set_terrain", "cc_build_geometry",
            "cc_get_geometry", "cc_get_stencils", "cc_get_groups", "cc_init_state", "cc_upload_state",
            "cc_download_state", "cc_step", "cc_diagnostics", "cc_synchronize", "cc_last_launch_count",
-           "cc_profile_enable", "cc_profile_read", "cc_profile_reset", "cc_mass_sum_noalloc",
-           "cc_noalloc_last_error")
+           "cc_profile_enable", "cc_profile_read", "cc_profile_reset", "cc_create_refined",
+           "cc_refine_mass", "cc_domain_count", "cc_mass_sum_noalloc", "cc_noalloc_last_error")
 CC_NOALLOC_MAX_PARTS = 1024
-CC_K_FULL, CC_K_GROUPS, CC_K_DIAGNOSE, CC_K_GHOST = range(4)
-KERNEL_NAMES = {CC_K_FULL: "k_full", CC_K_GROUPS: "k_groups", CC_K_DIAGNOSE: "k_diag", CC_K_GHOST: "k_ghost"}
+CC_K_FULL, CC_K_GROUPS, CC_K_DIAGNOSE, CC_K_GHOST, CC_K_REFINE = range(5)
+KERNEL_NAMES = {CC_K_FULL: "k_full", CC_K_GROUPS: "k_groups", CC_K_DIAGNOSE: "k_diag", CC_K_GHOST: "k_ghost",
+                CC_K_REFINE: "refinement"}
 
 
 class CCConfig(ct.Structure):
@@ -41,6 +42,10 @@ class CCConfig(ct.Structure):
                 ("R", ct.c_double), ("cp", ct.c_double),
                 ("ra_nu", ct.c_double), ("c4", ct.c_double), ("sponge_frac", ct.c_double),
                 ("tau_max", ct.c_double), ("bc_slip", ct.c_int)]
+
+
+class CCBox(ct.Structure):
+    _fields_ = [("nx", ct.c_int), ("ny", ct.c_int), ("nz", ct.c_int), ("ox", ct.c_int), ("oy", ct.c_int)]
 
 
 class CCDiag(ct.Structure):
@@ -87,6 +92,10 @@ def load(path: str = LIB_PATH):
     L.cc_profile_enable.argtypes = [vp, i]
     L.cc_profile_read.argtypes = [vp, i, ct.POINTER(d), ct.POINTER(ct.c_longlong)]
     L.cc_profile_reset.argtypes = [vp]
+    L.cc_create_refined.argtypes = [ct.POINTER(CCConfig), i, ct.POINTER(CCBox), i, vp, ct.POINTER(vp)]
+    L.cc_refine_mass.argtypes = [vp, i, ct.POINTER(d)]
+    L.cc_domain_count.restype = i
+    L.cc_domain_count.argtypes = [vp]
     L.cc_mass_sum_noalloc.argtypes = [vp, i, vp, ct.c_longlong, i, vp, vp]
     L.cc_noalloc_last_error.restype = ct.c_char_p
     L.cc_noalloc_last_error.argtypes = []
@@ -265,3 +274,45 @@ class Model:
         ms, n = ct.c_double(), ct.c_longlong()
         self._check(self.L.cc_profile_read(self.h, kernel, ct.byref(ms), ct.byref(n)))
         return ms.value, n.value
+
+
+class _Level:
+    """Sizes of one level of a refined model (what Model's accessors read)."""
+
+    def __init__(self, base, l: int, box=None):
+        f = 2.0 ** -l
+        self.nx, self.ny, self.nz = (base.nx, base.ny, base.nz) if box is None else tuple(box[:3])
+        self.dx, self.dy, self.dz, self.dt = base.dx * f, base.dy * f, base.dz * f, base.dt * f
+
+
+class RefinedModel(Model):
+    """Block-structured refinement (levels as domains 0 .. nlev-1) advanced on
+    the GPU through the C ABI: cc_create_refined, cc_step (one cycle of level
+    0 per step), cc_refine_mass."""
+
+    def __init__(self, base, boxes, precision: int = CC_FP64, stream=None):
+        self.L = load()
+        self.base = base
+        self.boxes = [tuple(b) for b in boxes]
+        self.cfgs = [_Level(base, 0)] + [_Level(base, l + 1, b) for l, b in enumerate(self.boxes)]
+        cb = config_from(base)
+        arr = (CCBox * max(1, len(self.boxes)))(*[CCBox(*b) for b in self.boxes])
+        self._arr = (cb, arr)
+        if stream is None:
+            stream = _current_stream()
+        self.stream = stream
+        h = ct.c_void_p()
+        st = self.L.cc_create_refined(ct.byref(cb), len(self.boxes) + 1, arr, precision, stream, ct.byref(h))
+        if st != CC_OK:
+            raise CutcellError(st, self.L.cc_last_error(None).decode())
+        self.h = h
+        self.precision = precision
+
+    @property
+    def nlev(self) -> int:
+        return len(self.cfgs)
+
+    def mass(self, both: bool = True) -> float:
+        out = ct.c_double()
+        self._check(self.L.cc_refine_mass(self.h, 1 if both else 0, ct.byref(out)))
+        return out.value

@@ -1,0 +1,192 @@
+"""Block-structured refinement on the GPU (Sec 2.2) against the FP64 oracle,
+through the C ABI: per-level geometry, subcycled steps with the coarse-fine
+ghost fill, restriction and flux register, rest state and conservation
+(needs a GB300)."""
+import numpy as np
+import pytest
+
+from paper_1509_02572_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+RC = W.SMALL_REFINED
+
+
+@pytest.fixture(scope="module")
+def cc():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1509_02572_gb300 import build, cutcell
+    build.build()
+    cutcell.load()
+    return cutcell
+
+
+def gpu_refined(cc, rc, prec=None, **kw):
+    base = rc.base.replace(**kw) if kw else rc.base
+    m = cc.RefinedModel(base, rc.boxes, cc.CC_FP64 if prec is None else prec)
+    for l, c in enumerate(m.cfgs):
+        h = rc.finest_heights() if l == m.nlev - 1 else np.zeros((c.ny, c.nx))
+        m.set_terrain(l, h)
+    m.build_geometry()
+    return m
+
+
+def oracle_refined(oracle_mod, rc, **kw):
+    base = rc.base.replace(**kw) if kw else rc.base
+    return oracle_mod.Refine(base, rc.boxes, rc.finest_heights(pad=4))
+
+
+def _pairs(cc, oracle_mod):
+    return [(cc.CC_RHOP, oracle_mod.F_RHOP), (cc.CC_PP, oracle_mod.F_PP), (cc.CC_MX, oracle_mod.F_MX),
+            (cc.CC_MY, oracle_mod.F_MY), (cc.CC_MZ, oracle_mod.F_MZ), (cc.CC_UB, oracle_mod.F_UB)]
+
+
+def _compare(cc, oracle_mod, m, R, rel_l2, rel_inf, report=False):
+    errs = {}
+    for l, lev in enumerate(R.levels):
+        for fg, fo in _pairs(cc, oracle_mod):
+            for tl in ((1,) if fg == cc.CC_UB else (0, 1)):
+                a = m.download(l, fg, tl)
+                b = lev.field(fo, tl)
+                scale = np.abs(b).max()
+                if scale == 0.0:
+                    assert np.abs(a).max() == 0.0, (l, fg, tl)
+                    continue
+                l2 = np.sqrt(np.sum((a - b) ** 2) / np.sum(b ** 2))
+                li = np.abs(a - b).max() / scale
+                errs[(l, fg, tl)] = (l2, li)
+                if not report:
+                    assert l2 <= rel_l2 and li <= rel_inf, (l, fg, tl, l2, li)
+    return errs
+
+
+def test_level_geometry_bit_exact(cc, oracle_mod):
+    """Every level's cell classes, merge roots, velocity-point classes and
+    boundary stencils equal the oracle's, which evaluates the box levels over
+    their padded terrain."""
+    R = oracle_refined(oracle_mod, RC)
+    m = gpu_refined(cc, RC)
+    for l, lev in enumerate(R.levels):
+        og, op = lev.geometry(), lev.points()
+        g, s = m.geometry(l), m.stencils(l)
+        assert np.array_equal(g["cls"], og["cls"]), l
+        assert np.array_equal(g["root"], og["root"]), l
+        assert np.array_equal(g["vcls"], op["vcls"]), l
+        for k in ("bK", "bI", "bJ"):
+            assert np.array_equal(s[k], op[k]), (l, k)
+        for k in ("vf", "ax", "ay", "az"):
+            assert np.max(np.abs(g[k] - og[k])) <= 1e-14, (l, k)
+    assert (m.geometry(m.nlev - 1)["cls"] == 2).any()  # the hill is cut on the finest level
+    m.close()
+
+
+def test_fp64_refined_parity(cc, oracle_mod):
+    """Three levels, each subcycled step against the oracle element by element
+    on every level and both time levels."""
+    R = oracle_refined(oracle_mod, RC)
+    R.init_state()
+    m = gpu_refined(cc, RC)
+    m.init_state()
+    _compare(cc, oracle_mod, m, R, 1e-13, 1e-11)
+    R.step(1)
+    m.step(1)
+    _compare(cc, oracle_mod, m, R, 1e-12, 1e-10)
+    R.step(4)
+    m.step(4)
+    _compare(cc, oracle_mod, m, R, 1e-10, 1e-8)
+    m.close()
+
+
+def test_refined_rest_state_exact(cc):
+    for prec in (cc.CC_FP64, cc.CC_FP32):
+        m = gpu_refined(cc, RC, prec, U=0.0)
+        m.init_state()
+        m.step(3)
+        for l in range(m.nlev):
+            for f in (cc.CC_RHOP, cc.CC_PP, cc.CC_MX, cc.CC_MY, cc.CC_MZ, cc.CC_UB):
+                assert np.abs(m.download(l, f)).max() == 0.0, (prec, l, f)
+        m.close()
+
+
+def _flux_scale(rc):
+    nx, ny, nz, ox, oy = rc.boxes[0]
+    b = rc.base
+    return 1.2 * b.U * (ny * b.dy / 2) * (nz * b.dz / 2) * 2 * b.dt
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-13), ("fp32", 2e-6)])
+def test_refined_mass_conserved_filter_off(cc, oracle_mod, prec, tol):
+    """With the filter off, the two-time-level mass over the active cells of
+    all levels is conserved to round-off on the GPU (the register makes the
+    coarse flux through the box boundary the mean of the fine substeps), and
+    its value follows the oracle's."""
+    m = gpu_refined(cc, RC, cc.CC_FP64 if prec == "fp64" else cc.CC_FP32, ra_nu=0.0)
+    m.init_state()
+    m.step(1)
+    q0 = m.mass()
+    for _ in range(4):
+        m.step(1)
+        assert abs(m.mass() - q0) <= tol * _flux_scale(RC), (m.mass(), q0)
+    if prec == "fp64":
+        R = oracle_refined(oracle_mod, RC, ra_nu=0.0)
+        R.init_state()
+        R.step(5)
+        assert abs(m.mass() - R.mass()) <= 1e-10 * _flux_scale(RC)
+    m.close()
+
+
+def test_fp32_refined_error_against_oracle(cc, oracle_mod):
+    R = oracle_refined(oracle_mod, RC)
+    R.init_state()
+    R.step(6)
+    m = gpu_refined(cc, RC, cc.CC_FP32)
+    m.init_state()
+    m.step(6)
+    errs = _compare(cc, oracle_mod, m, R, 0, 0, report=True)
+    for key, (l2, li) in errs.items():
+        assert l2 <= 1e-3 and li <= 1e-2, (key, l2, li)
+    m.close()
+
+
+def test_full_size_refined_properties(cc):
+    """The three-level 200/100/50 m hemisphere as the benchmark runs it (FP32):
+    rest state exact, mass over the active cells conserved with the filter
+    off, finite state with the filter on."""
+    rc = W.C4_REFINED
+    m = gpu_refined(cc, rc, cc.CC_FP32, ra_nu=0.0)
+    m.init_state()
+    m.step(1)
+    q0 = m.mass()
+    m.step(2)
+    assert abs(m.mass() - q0) <= 2e-6 * _flux_scale(rc) * 4
+    for l in range(m.nlev):
+        d = m.diagnostics(l)
+        assert d["nonfinite"] == 0
+    m.close()
+
+
+def test_refined_error_paths(cc):
+    b = RC.base
+    with pytest.raises(cc.CutcellError) as e:
+        cc.RefinedModel(b, [(32, 32, 16, 15, 16)])  # odd offset
+    assert e.value.status == cc.CC_EINVAL
+    with pytest.raises(cc.CutcellError) as e:
+        cc.RefinedModel(b, [(32, 32, 16, 2, 16)])  # covered box touches the coarse edge region
+    assert e.value.status == cc.CC_EINVAL
+    m = cc.RefinedModel(b, RC.boxes)
+    h = np.zeros((32, 32))
+    h[2, 2] = 10.0  # terrain near a box edge
+    with pytest.raises(cc.CutcellError) as e:
+        m.set_terrain(2, h)
+    assert e.value.status == cc.CC_EINVAL
+    hc = np.zeros((32, 32))
+    hc[16, 16] = 5.0  # coarse terrain next to the covered box
+    m.set_terrain(0, hc)
+    m.set_terrain(1, np.zeros((32, 32)))
+    m.set_terrain(2, RC.finest_heights())
+    with pytest.raises(cc.CutcellError) as e:
+        m.build_geometry()
+    assert e.value.status == cc.CC_EGEOM
+    m.close()
