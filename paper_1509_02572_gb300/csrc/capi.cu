@@ -7,6 +7,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <string>
 #include <type_traits>
 #include <vector>
@@ -291,7 +292,7 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
     }
     double *h, *vf, *ax, *ay, *az, *ba, *bb, *bn, *mg;
     int8_t *cls, *vcls;
-    int32_t *root, *kug, *bK, *bI, *bJ, *mK, *ktop;
+    int32_t *root, *kug, *bK, *bI, *bJ, *mK, *ktop, *kb;
     if ((e = dalloc(H.allocs, &h, ncol * 8, m->st)) ||
         (e = dalloc(H.allocs, &vf, ncell * 8, m->st)) || (e = dalloc(H.allocs, &ax, ncell * 8, m->st)) ||
         (e = dalloc(H.allocs, &ay, ncell * 8, m->st)) ||
@@ -302,11 +303,12 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
         (e = dalloc(H.allocs, &bJ, npc * 4, m->st)) || (e = dalloc(H.allocs, &ba, npc * 8, m->st)) ||
         (e = dalloc(H.allocs, &bb, npc * 8, m->st)) || (e = dalloc(H.allocs, &bn, 3 * npc * 8, m->st)) ||
         (e = dalloc(H.allocs, &mK, D.ncellp * 4, m->st)) || (e = dalloc(H.allocs, &mg, D.ncellp * 8, m->st)) ||
-        (e = dalloc(H.allocs, &ktop, npc * 4, m->st)))
+        (e = dalloc(H.allocs, &ktop, npc * 4, m->st)) || (e = dalloc(H.allocs, &kb, npc * 4, m->st)))
       return bail(e, "geometry alloc");
     D.h = h; D.vf = vf; D.ax = ax; D.ay = ay; D.az = az; D.cls = cls; D.root = root; D.kug = kug;
     D.vcls = vcls; D.bK = bK; D.bI = bI; D.bJ = bJ; D.ba = ba; D.bb = bb; D.bn = bn; D.mK = mK; D.mg = mg;
     D.ktop = ktop;
+    D.kb = kb;
     if ((e = launch_base(D, precision, c.theta0, c.N, c.p_surf, c.sponge_frac, c.tau_max, m->st)) != cudaSuccess)
       return bail(e, "base state");
     max_stage = std::max(max_stage, (size_t)(ncol * (c.nz + 1 + 2 * HOST_GZ)));
@@ -403,28 +405,41 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
             int dd = std::min({Ic - K.x0, K.x1 - Ic, Jc - K.y0, K.y1 - Jc, K.z1 - Kc});
             if (dd <= GH) rcorn.push_back(pidx(C, Ic, Jc, Kc));
           }
-      // interface faces (x low, x high, y low, y high, top) and the coarse
-      // cell outside the box that each one bounds
+      // interface faces (x low, x high, y low, y high, top); the coarse cells
+      // on both sides of each one take the register flux through it (the
+      // covered side is restricted afterwards, but the velocity diagnosis of
+      // the corners on the box boundary reads its new density first)
       std::vector<IfaceFace> faces;
       std::vector<IfaceCell> icells;
-      auto add = [&](int ax, int fi, int fj, int fk, int ci, int cj, int ck, int side) {
-        IfaceCell ic{};
-        ic.i = ci; ic.j = cj; ic.k = ck;
-        for (int q = 0; q < 6; q++) ic.slot[q] = -1;
-        ic.slot[ax * 2 + side] = (int)faces.size();
+      std::map<long long, int> where;
+      auto touch = [&](int ci, int cj, int ck, int slot, int q) {
+        long long key = pidx(C, ci, cj, ck);
+        auto it = where.find(key);
+        if (it == where.end()) {
+          IfaceCell ic{};
+          ic.i = ci; ic.j = cj; ic.k = ck;
+          for (int a = 0; a < 6; a++) ic.slot[a] = -1;
+          it = where.emplace(key, (int)icells.size()).first;
+          icells.push_back(ic);
+        }
+        icells[it->second].slot[slot] = q;
+      };
+      // face of axis ax between coarse cells lo (below) and hi (above)
+      auto add = [&](int ax, int fi, int fj, int fk, int hi_i, int hi_j, int hi_k) {
+        int q = (int)faces.size();
         faces.push_back(IfaceFace{ax, fi, fj, fk});
-        icells.push_back(ic);
+        int lo_i = hi_i - (ax == 0), lo_j = hi_j - (ax == 1), lo_k = hi_k - (ax == 2);
+        touch(lo_i, lo_j, lo_k, ax * 2 + 1, q);
+        touch(hi_i, hi_j, hi_k, ax * 2 + 0, q);
       };
       for (int sd = 0; sd < 2; sd++)
         for (int kc = 0; kc < K.z1; kc++)
-          for (int jc = K.y0; jc < K.y1; jc++)
-            add(0, sd ? b.nx : 0, 2 * jc - b.oy, 2 * kc, sd ? K.x1 : K.x0 - 1, jc, kc, sd ? 0 : 1);
+          for (int jc = K.y0; jc < K.y1; jc++) add(0, sd ? b.nx : 0, 2 * jc - b.oy, 2 * kc, sd ? K.x1 : K.x0, jc, kc);
       for (int sd = 0; sd < 2; sd++)
         for (int kc = 0; kc < K.z1; kc++)
-          for (int ic = K.x0; ic < K.x1; ic++)
-            add(1, 2 * ic - b.ox, sd ? b.ny : 0, 2 * kc, ic, sd ? K.y1 : K.y0 - 1, kc, sd ? 0 : 1);
+          for (int ic = K.x0; ic < K.x1; ic++) add(1, 2 * ic - b.ox, sd ? b.ny : 0, 2 * kc, ic, sd ? K.y1 : K.y0, kc);
       for (int jc = K.y0; jc < K.y1; jc++)
-        for (int ic = K.x0; ic < K.x1; ic++) add(2, 2 * ic - b.ox, 2 * jc - b.oy, b.nz, ic, jc, K.z1, 0);
+        for (int ic = K.x0; ic < K.x1; ic++) add(2, 2 * ic - b.ox, 2 * jc - b.oy, b.nz, ic, jc, K.z1);
       LevelLink &L = K.L;
       L.dc = m->d_doms + (l - 1);
       L.df = m->d_doms + l;

@@ -17,6 +17,7 @@ constexpr int TILE_Y_F32 = 8, TILE_Y_F64 = 8;      // tile height (y) per precis
 // cell classes and corner classes
 enum : int8_t { C_UG = 0, C_FULL = 1, C_CUT = 2, C_ABS = 3 };
 enum : int8_t { V_UG = 0, V_PRED = 1, V_MF = 2, V_LID = 3 };
+constexpr int KB_NONE = -1000;
 
 // Device-side description of one domain.  Pointers are device pointers;
 // field arrays are of the model's precision (double or float).
@@ -60,6 +61,10 @@ struct DomDev {
   const int32_t *mK;         // padded corner layout
   const double *mg;          // padded corner layout
   const int32_t *ktop;       // padded columns: highest non-predicted corner level below the top
+  // padded columns: corners K <= kb lie at or below the terrain and move with
+  // the boundary-point velocity u_B of their column; KB_NONE where the column's
+  // corners are not integrated (frame of a refined box)
+  const int32_t *kb;
 };
 
 // (block, tile) work item of the full-cell stencil
@@ -105,7 +110,7 @@ struct IfaceFace {
   int ax;          // 0, 1, 2
   int fi, fj, fk;  // fine face: the x-face of fine cell (fi, fj, fk) etc.
 };
-// coarse cell next to the box with up to three interface faces
+// coarse cell on either side of a box boundary, with up to three interface faces
 struct IfaceCell {
   int i, j, k;     // coarse cell
   int slot[6];     // register slot of face (ax*2 + side), -1 if not an interface face

@@ -508,6 +508,24 @@ __global__ void k_flat_columns(DomDev D) {
   for (int K = -GH; K < D.nz + GH; K++) vcls[pidx(D, I, J, K)] = K <= 0 ? V_UG : V_PRED;
 }
 
+// Highest corner level at or below the terrain per padded column (the test
+// K dz <= h of the velocity-point classes); KB_NONE outside the integrated
+// corner columns of a refined box.  A box's frame lies over flat floor.
+__global__ void k_kb(DomDev D, int32_t *kb) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)D.px * D.py) return;
+  int I = (int)(t % D.px) - GH, J = (int)(t / D.px) - GH;
+  if (!D.periodic && !(I >= D.qi0 && I < D.ci1 && J >= D.qj0 && J < D.cj1)) {
+    kb[t] = KB_NONE;
+    return;
+  }
+  bool inside = I >= 0 && I < D.nx && J >= 0 && J < D.ny;
+  double h = (D.periodic || inside) ? hcorner(D, I, J) : 0.0;
+  int K = -GH;
+  while (K + 1 < D.nz + GH && (K + 1) * D.dz <= h) K++;
+  kb[t] = K;
+}
+
 }  // namespace
 
 cudaError_t launch_flat_columns(const DomDev &D, cudaStream_t st) {
@@ -609,6 +627,7 @@ cudaError_t geom_build_one(DomDev &D, cudaStream_t st, int dom, int *d_err, int3
                                            const_cast<double *>(D.bn), d_err);
     k_mstencil<<<nblk(ncorner), TPB, 0, st>>>(D, vcls, mK, mg, d_err);
     k_ktop<<<nblk(ncol), TPB, 0, st>>>(D, vcls, const_cast<int32_t *>(D.ktop));
+    k_kb<<<nblk((long long)D.px * D.py), TPB, 0, st>>>(D, const_cast<int32_t *>(D.kb));
     if ((err = cudaGetLastError()) != cudaSuccess) {
       cudaFree(members);
       cudaFree(recs);

@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
   // (periodic domains wrap the lateral coordinates; a refined box reads its
   // ghost frame, clamped to the padding where no computed point needs it)
   long long loff[NLP];
-  int lpt[NLP];
+  int lpt[NLP], kbv[NLP];
   const int py = D.py;
 #pragma unroll
   for (int s = 0; s < NLP; s++) {
@@ -262,7 +262,9 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
       gj = min(max(gj, -GH), py - GH - 1);
     }
     loff[s] = (long long)(gj + GH) * px + (gi + GH);
+    kbv[s] = p < PL ? D.kb[loff[s]] : KB_NONE;
   }
+  const T *__restrict__ ubC = (const T *)D.ub[rC];
   const int kmaxp = D.pz - GH - 1;  // highest plane inside the padding
   // issue the asynchronous copies of every raw field of plane kk (the
   // current-level momentum only when with_m: its ring has four slots)
@@ -301,7 +303,9 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
       }
     }
   };
-  // corner velocity of plane K = momentum / mean density of the 8 cells around
+  // corner velocity of plane K = momentum / mean density of the 8 cells
+  // around; corners at or below the terrain take the boundary-point velocity
+  // of their column
   auto velocity = [&](int K) {
     const int sl = s4(K - 1), sh = s4(K), su = s3(K), sm = s4(K);
 #pragma unroll
@@ -309,12 +313,19 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
       const int p = lpt[s];
       const int hx = p % HX, hy = p / HX;
       if (p < PL && hx != 0 && hy != 0) {
-        const T *lo = S.rh[sl], *hi = S.rh[sh];
-        const int q00 = p - HX - 1, q01 = p - HX, q10 = p - 1, q11 = p;
-        T iv = rinv(rho8(lo[q00], lo[q01], lo[q10], lo[q11], hi[q00], hi[q01], hi[q10], hi[q11]));
-        S.uu[su][0][p] = S.cm[sm][0][p] * iv;
-        S.uu[su][1][p] = S.cm[sm][1][p] * iv;
-        S.uu[su][2][p] = S.cm[sm][2][p] * iv;
+        if (K <= kbv[s]) {
+          const T *u = ubC + 3 * loff[s];
+          S.uu[su][0][p] = u[0];
+          S.uu[su][1][p] = u[1];
+          S.uu[su][2][p] = u[2];
+        } else {
+          const T *lo = S.rh[sl], *hi = S.rh[sh];
+          const int q00 = p - HX - 1, q01 = p - HX, q10 = p - 1, q11 = p;
+          T iv = rinv(rho8(lo[q00], lo[q01], lo[q10], lo[q11], hi[q00], hi[q01], hi[q10], hi[q11]));
+          S.uu[su][0][p] = S.cm[sm][0][p] * iv;
+          S.uu[su][1][p] = S.cm[sm][1][p] * iv;
+          S.uu[su][2][p] = S.cm[sm][2][p] * iv;
+        }
       }
     }
   };
@@ -513,10 +524,26 @@ __device__ __forceinline__ T corner_rho(const DomDev &D, const T *rp, const T *r
               cell_rho(D, rp, rhob, I - 1, J, K), cell_rho(D, rp, rhob, I, J, K));
 }
 
-// corner velocity (the same operations as the full-cell stencil)
+// padded column of corner (I, J), wrapped on periodic domains
+__device__ __forceinline__ long long wqidx(const DomDev &D, int I, int J) {
+  return D.periodic ? qidx(D, wrapi(I, D.nx), wrapi(J, D.ny)) : qidx(D, I, J);
+}
+
+// corner velocity (the same operations as the full-cell stencil): the
+// boundary-point velocity ub for corners at or below the terrain (when ub is
+// given), else momentum / corner density
 template <typename T>
-__device__ __forceinline__ void corner_u(const DomDev &D, const T *rp, const T *const *M, const T *rhob, int I,
-                                         int J, int K, T u[3]) {
+__device__ __forceinline__ void corner_u(const DomDev &D, const T *rp, const T *const *M, const T *rhob,
+                                         const T *ub, int I, int J, int K, T u[3]) {
+  if (ub) {
+    const long long q = wqidx(D, I, J);
+    if (K <= D.kb[q]) {
+      u[0] = ub[3 * q];
+      u[1] = ub[3 * q + 1];
+      u[2] = ub[3 * q + 2];
+      return;
+    }
+  }
   T iv = rinv(corner_rho(D, rp, rhob, I, J, K));
   long long o = widx(D, I, J, K);
   u[0] = M[0][o] * iv;
@@ -538,6 +565,7 @@ __global__ void k_groups(const DomDev *__restrict__ doms, const GroupRec *__rest
   const T *rpC = (const T *)D.f[rC][0];
   const T *ppC = (const T *)D.f[rC][1];
   const T *MC[3] = {(const T *)D.f[rC][2], (const T *)D.f[rC][3], (const T *)D.f[rC][4]};
+  const T *ubC = (const T *)D.ub[rC];
   const T *rpO = (const T *)D.f[rO][0];
   const T *ppO = (const T *)D.f[rO][1];
   const T *rhob = (const T *)D.rhob, *pb = (const T *)D.pb, *thb = (const T *)D.thb, *pik = (const T *)D.pik;
@@ -582,7 +610,7 @@ __global__ void k_groups(const DomDev *__restrict__ doms, const GroupRec *__rest
         long long nb = cid(D, wrapi(ni, nx), wrapi(nj, ny), nk);
         if (D.cls[nb] != C_UG && D.root[nb] == R.host) continue;  // face inside the group
         T uc[4][3];
-        for (int s = 0; s < 4; s++) corner_u(D, rpC, MC, rhob, cI[s], cJ[s], cK[s], uc[s]);
+        for (int s = 0; s < 4; s++) corner_u(D, rpC, MC, rhob, ubC, cI[s], cJ[s], cK[s], uc[s]);
         T phm = cell_rho(D, rpC, rhob, i, j, k), phn = cell_rho(D, rpC, rhob, ni, nj, nk);
         T thm = theta_tot(D, thb, pb, ipb, k + GH, ppC[widx(D, i, j, k)]);
         T thn = theta_tot(D, thb, pb, ipb, nk + GH, ppC[widx(D, ni, nj, nk)]);
@@ -651,7 +679,7 @@ __global__ void k_diag(const DomDev *__restrict__ doms, const ColItem *__restric
   for (int s = 0; s < 4; s++) {
     if (w[s] == T(0)) continue;
     T u[3];
-    corner_u(D, rp, Mc, rhob, ci[s], cj[s], K, u);
+    corner_u<T>(D, rp, Mc, rhob, nullptr, ci[s], cj[s], K, u);
     for (int d = 0; d < 3; d++) uN[d] += w[s] * u[d];
   }
   T n[3] = {(T)D.bn[3 * q], (T)D.bn[3 * q + 1], (T)D.bn[3 * q + 2]};
@@ -693,14 +721,14 @@ __global__ void k_diag(const DomDev *__restrict__ doms, const ColItem *__restric
       int ka = D.mK[p];
       T gm = (T)D.mg[p];
       T ua[3];
-      corner_u(D, rp, Mc, rhob, I, J, ka, ua);
+      corner_u<T>(D, rp, Mc, rhob, nullptr, I, J, ka, ua);
       for (int d = 0; d < 3; d++) u[d] = gm * ua[d] + (T(1) - gm) * ub[d];
     }
     store(KK, u);
   }
   if (D.lid) {
     T ul[3];
-    corner_u(D, rp, Mc, rhob, I, J, D.nz - 1, ul);
+    corner_u<T>(D, rp, Mc, rhob, nullptr, I, J, D.nz - 1, ul);
     ul[2] = 0;
     for (int KK = D.nz; KK < D.nz + GH; KK++) store(KK, ul);
   }
@@ -932,10 +960,12 @@ __device__ __forceinline__ void face_fluxes(const DomDev &D, int rC, int ax, int
     cI[2] = I; cJ[2] = J + 1; cK[2] = K;
     cI[3] = I + 1; cJ[3] = J + 1; cK[3] = K;
   }
+  const T *ub = (const T *)D.ub[rC];
   T u[4];
   for (int s = 0; s < 4; s++) {
-    T iv = rinv(corner_rho(D, rp, rhob, cI[s], cJ[s], cK[s]));
-    u[s] = M[ax][widx(D, cI[s], cJ[s], cK[s])] * iv;
+    T uc[3];
+    corner_u(D, rp, M, rhob, ub, cI[s], cJ[s], cK[s], uc);
+    u[s] = uc[ax];
   }
   T ra = cell_rho(D, rp, rhob, li, lj, lk), rb = cell_rho(D, rp, rhob, I, J, K);
   T ta = theta_tot(D, thb, pb, ipb, lk + GH, pp[widx(D, li, lj, lk)]);
