@@ -6,9 +6,15 @@ Workloads (synthetic, seeded; the paper's hills sampled at grid corners):
              instances advance together in one launch per stage in the FP32
              perturbation form; the plain FP64 form loops over the instances.
   hemisphere the 128x128x64 grid of 50 m cells over the 1 km hemisphere.
+  refined    three block-structured levels (200 m over 64x32x16 km, 100 m and
+             50 m boxes around the 1 km hemisphere), FP32 perturbation form;
+             a step is one cycle of level 0 (2 steps of level 1, 4 of level 2).
+The default run (ensemble) also measures the refined workload and adds it as
+the "refined" object of the line.
 
 A step is one leapfrog step of every domain of the workload (all stages:
-full-cell stencil, cut-cell groups, velocity diagnosis, ghost fill).
+full-cell stencil, cut-cell groups, velocity diagnosis, and for the refined
+workload the flux register, restriction and prolongation).
 """
 from __future__ import annotations
 
@@ -38,7 +44,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "hemisphere"])
+    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "hemisphere", "refined"])
+    ap.add_argument("--no-refined", action="store_true", help="skip the refined object of the default run")
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-e2e", action="store_true")
@@ -181,25 +188,139 @@ def cpu_baseline(cfgs, seconds):
             "sample": "; ".join(inst) + f" ({t_used:.1f} s, single-threaded FP64 oracle)"}
 
 
+def make_refined(cc, rc, prec):
+    m = cc.RefinedModel(rc.base, rc.boxes, prec)
+    for l, c in enumerate(m.cfgs):
+        m.set_terrain(l, rc.finest_heights() if l == m.nlev - 1 else np.zeros((c.ny, c.nx)))
+    m.build_geometry()
+    m.init_state()
+    return m
+
+
+def refined_cell_updates(model):
+    """Cell updates of one cycle of level 0: the fluid cells of level l times
+    its 2^l substeps."""
+    n = 0
+    for l in range(model.nlev):
+        n += int((model.geometry(l)["cls"] != 0).sum()) * 2 ** l
+    return n
+
+
+def refined_kfull_bytes(model, dtype):
+    """Algorithmic bytes of the full-cell stencil over one cycle (interior
+    cells of every level times its substeps)."""
+    return sum(BYTES_PER_CELL[dtype] * c.nx * c.ny * c.nz * 2 ** l for l, c in enumerate(model.cfgs))
+
+
+def bench_refined(cc, torch, args, hbm, peak_kind, barrier, world):
+    """The refined workload: FP32 cycles timed on the device, k_full roofline
+    over all levels, the plain FP64 form and the FP32 error against it."""
+    rc = W.C4_REFINED
+    m = make_refined(cc, rc, cc.CC_FP32)
+    upd = refined_cell_updates(m)
+    clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
+    barrier()
+    m.profile(True)
+    m.profile_reset()
+    clocks.start()
+    ms, launches = time_steps(torch, m, args.steps, args.warmup)
+    clk = clocks.stop()
+    barrier()
+    kms, kn = m.profile_read(cc.CC_K_FULL)
+    stages = {cc.KERNEL_NAMES[k]: dict(zip(("ms_total", "launches"), m.profile_read(k))) for k in range(5)}
+    m.profile(False)
+    kbytes = refined_kfull_bytes(m, "f32") * args.steps
+    achieved = kbytes / (kms / 1e3) / 1e9
+    out = {"workload": rc.name, "levels": [list(b) for b in rc.boxes], "value": upd * args.steps * world / (ms / 1e3),
+           "unit": METRIC, "ms_per_step": ms / args.steps, "cell_updates_per_step": upd, "dtype": "f32",
+           "gpu_launches": launches, "clocks": clk, "stages": stages,
+           "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
+                        "traffic": None, "kernel": "k_full", "kernel_ms": kms / max(1, kn), "launches": kn,
+                        "peak_kind": f"{peak_kind} hbm_gbs",
+                        "bytes_per_cell": BYTES_PER_CELL["f32"],
+                        "how": "interior cells of every level times its substeps, per launch averaged over levels"}}
+    if not args.no_fp64:
+        m64 = make_refined(cc, rc, cc.CC_FP64)
+        ks = max(2, min(args.steps, 5))
+        m64.step(args.warmup)
+        torch.cuda.synchronize()
+        st = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(st)
+        m64.step(ks)
+        e1.record(st)
+        e1.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        m64.step(args.steps - ks)
+        errs = {}
+        for fname, f in (("rho'", cc.CC_RHOP), ("p'", cc.CC_PP), ("rho u", cc.CC_MX), ("rho v", cc.CC_MY),
+                         ("rho w", cc.CC_MZ)):
+            num = den = linf = scale = 0.0
+            for l in range(m.nlev):
+                a, b = m.download(l, f), m64.download(l, f)
+                num += float(((a - b) ** 2).sum())
+                den += float((b ** 2).sum())
+                linf = max(linf, float(np.abs(a - b).max()))
+                scale = max(scale, float(np.abs(b).max()))
+            errs[fname] = {"rel_l2": (num / den) ** 0.5 if den > 0 else 0.0,
+                           "rel_linf": linf / scale if scale > 0 else 0.0}
+        out["fp64_plain"] = {"value": upd * ks / (ms64 / 1e3), "unit": METRIC, "dtype": "f64",
+                             "ms_per_step": ms64 / ks, "steps": ks}
+        out["l2_error"] = {"vs": "plain FP64 GPU form", "after_steps": args.warmup + args.steps, "fields": errs}
+        m64.close()
+    m.close()
+    return out
+
+
+def cpu_baseline_refined(seconds):
+    """The FP64 oracle's refinement driver as it stands, on a bounded sample:
+    the three-level 32x32x16 hemisphere (400/200/100 m), cycles of level 0
+    until about `seconds` of CPU work."""
+    import oracle
+    rc = W.SMALL_REFINED
+    R = oracle.Refine(rc.base, rc.boxes, rc.finest_heights(pad=4))
+    upd = 0
+    for l, lev in enumerate(R.levels):
+        upd += int((lev.geometry()["cls"] != 0).sum()) * 2 ** l
+    R.init_state()
+    R.step(1)
+    s = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < seconds and s < 200:
+        R.step(1)
+        s += 1
+    dt = time.perf_counter() - t0
+    return {"value": upd * s / dt, "unit": METRIC, "cores": 1, "kind": "oracle",
+            "sample": f"{rc.name} x {s} cycles ({dt:.1f} s, single-threaded FP64 oracle)"}
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    name, cfgs = workload_configs(args)
     import oracle
     oracle.build()
     # each step: a bounded sample of the workload on the oracle
     per = max(2.0, 60.0 / max(1, args.steps + args.warmup))
     vals = []
-    for s in range(args.warmup + args.steps):
-        r = cpu_baseline(cfgs[s % len(cfgs):] + cfgs[:s % len(cfgs)], per)
-        if s >= args.warmup:
-            vals.append(r)
+    if args.workload == "refined":
+        name, ninst = W.C4_REFINED.name, 1
+        for s in range(args.warmup + args.steps):
+            r = cpu_baseline_refined(per)
+            if s >= args.warmup:
+                vals.append(r)
+    else:
+        name, cfgs = workload_configs(args)
+        ninst = len(cfgs)
+        for s in range(args.warmup + args.steps):
+            r = cpu_baseline(cfgs[s % len(cfgs):] + cfgs[:s % len(cfgs)], per)
+            if s >= args.warmup:
+                vals.append(r)
     v = statistics.median(x["value"] for x in vals)
     line = {"metric": METRIC, "value": v, "unit": METRIC, "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": name, "instances": len(cfgs)},
+            "config": {"workload": name, "instances": ninst},
             "cpu_baseline": {"value": v, "unit": METRIC, "cores": 1, "kind": "oracle",
                              "sample": vals[-1]["sample"]},
             "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -224,17 +345,45 @@ def main():
     B.build()
     from paper_1509_02572_gb300 import cutcell as cc
 
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    hbm, peak_kind = peaks()
+    if args.workload == "refined":
+        r = bench_refined(cc, torch, args, hbm, peak_kind, barrier, world)
+        t = torch.tensor([r["ms_per_step"]], device="cuda")
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        msps = float(t.item())
+        line = {"metric": METRIC, "value": r["cell_updates_per_step"] * world / (msps / 1e3), "unit": METRIC,
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": msps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+                "data": "synthetic",
+                "config": {"workload": r["workload"], "levels": r["levels"],
+                           "cell_updates_per_step": r["cell_updates_per_step"],
+                           "precision": "fp32 perturbations, fp64 geometry and base state",
+                           "l2": "inputs larger than L2 (state of all levels)"},
+                "gpu_launches": r["gpu_launches"], "roofline": r["roofline"], "stages": r["stages"],
+                "clocks": r["clocks"]}
+        for k in ("fp64_plain", "l2_error"):
+            if k in r:
+                line[k] = r[k]
+        if rank == 0 and world == 1 and not args.no_cpu:
+            line["cpu_baseline"] = cpu_baseline_refined(args.cpu_seconds)
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
     name, cfgs = workload_configs(args)
     prec_main = cc.CC_FP32 if args.workload == "ensemble" else cc.CC_FP64
     dtype = "f32" if prec_main == cc.CC_FP32 else "f64"
     model = make_model(cc, cfgs, prec_main)
     nfluid = fluid_cells(model, cfgs)
     ninterior = sum(c.cells for c in cfgs)
-
-    def barrier():
-        if world > 1:
-            dist.barrier()
-        torch.cuda.synchronize()
 
     # ---- timed region (device time, CUDA events on the model's stream)
     clocks = Clocks(local)
@@ -246,7 +395,7 @@ def main():
     clk = clocks.stop()
     barrier()
     kfull_ms, kfull_n = model.profile_read(cc.CC_K_FULL)
-    stage = {cc.KERNEL_NAMES[k]: model.profile_read(k) for k in range(4)}
+    stage = {cc.KERNEL_NAMES[k]: model.profile_read(k) for k in range(5)}
     model.profile(False)
     t = torch.tensor([ms], device="cuda")
     if world > 1:
@@ -254,7 +403,6 @@ def main():
     ms = float(t.item())
     value = nfluid * args.steps * world / (ms / 1e3)
 
-    hbm, peak_kind = peaks()
     kavg = kfull_ms / max(1, kfull_n)
     achieved = BYTES_PER_CELL[dtype] * ninterior / (kavg / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
@@ -346,6 +494,8 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(cfgs, args.cpu_seconds)
     model.close()
+    if args.workload == "ensemble" and not args.no_refined:
+        line["refined"] = bench_refined(cc, torch, args, hbm, peak_kind, barrier, world)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
