@@ -82,8 +82,10 @@ typedef struct cc_model cc_model;
 /* Create a model of n independent domains (cfgs[0..n-1]) computing in
  * precision CC_FP64 or CC_FP32 (FP32 perturbations about an FP64-evaluated
  * hydrostatic base state; geometry always FP64).  stream: a cudaStream_t or
- * NULL for the default stream.  Allocates all device memory.  *out receives
- * the model; on failure *out is NULL and the status says why. */
+ * NULL for the default stream.  Allocates all device memory.  The domains
+ * share the physical constants R, cp and p0 (CC_EINVAL otherwise; the other
+ * parameters are free per domain).  *out receives the model; on failure *out
+ * is NULL and the status says why. */
 cc_status cc_create(const cc_config *cfgs, int n, int precision, void *stream, cc_model **out);
 
 /* Release every device and host resource of the model.  Null is accepted. */

@@ -61,6 +61,7 @@ struct cc_model {
   long long ghost_points = 0;
   bool refined = false;
   std::vector<LinkHost> link;  // link[l] for level l >= 1 of a refined model
+  Eos eos{};                   // equation-of-state coefficients of every domain
   long long last_launches = 0;
   bool geom = false, state = false;
   // kernel timing with CUDA events on the model's stream (cc_profile_*)
@@ -164,6 +165,7 @@ StepLaunch make_launch(const cc_model *m, int d = -1) {
   L.ndom = m->ndom;
   L.ghost_points = m->ghost_points;
   L.ghost_off = nullptr;
+  L.eos = m->eos;
   if (d >= 0) {
     const DomHost &H = m->dom[d];
     L.items = m->d_items + H.item0;
@@ -314,6 +316,17 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
     max_stage = std::max(max_stage, (size_t)(ncol * (c.nz + 1 + 2 * HOST_GZ)));
     max_stage = std::max(max_stage, (size_t)(ncol * (c.nz + 1)));
     max_stage = std::max(max_stage, (size_t)(3 * ncol));
+  }
+  {
+    const DomDev &D0 = m->dom[0].D;
+    for (int a = 0; a < 8; a++) {
+      m->eos.sth[a] = D0.sth[a];
+      m->eos.sex[a] = D0.sex[a];
+    }
+    m->eos.p0 = D0.p0;
+    m->eos.p0R = D0.p0 / D0.R;
+    m->eos.cvcp = D0.cvcp;
+    m->eos.kap = D0.kap;
   }
   // device domain table
   if ((e = dalloc(m->allocs, &m->d_doms, sizeof(DomDev) * n, m->st)) != cudaSuccess) return bail(e, "domain table");
@@ -496,6 +509,8 @@ cc_status cc_create(const cc_config *cfgs, int n, int precision, void *stream, c
   for (int d = 0; d < n; d++) {
     std::string why;
     if (!valid_cfg(cfgs[d], why)) return fail(nullptr, CC_EINVAL, "domain " + std::to_string(d) + ": " + why);
+    if (cfgs[d].R != cfgs[0].R || cfgs[d].cp != cfgs[0].cp || cfgs[d].p0 != cfgs[0].p0)
+      return fail(nullptr, CC_EINVAL, "all domains of a model share R, cp and p0");
     kinds[d] = DomKind{1, 1, cfgs[d].nz * cfgs[d].dz};
   }
   return create_impl(cv, kinds, {}, precision, stream, out);

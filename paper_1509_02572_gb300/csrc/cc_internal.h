@@ -147,6 +147,13 @@ cudaError_t launch_flat_columns(const DomDev &D, cudaStream_t st);
 cudaError_t geom_build_one(DomDev &D, cudaStream_t st, int dom, int *d_err, int32_t **members_out,
                            GroupRec **recs_out, int *ng_out, int *nm_out);
 
+// Equation-of-state coefficients shared by every domain of a model (R, cp
+// and p0 are the same for all), passed to the step kernels as parameters
+struct Eos {
+  float sth[8], sex[8];  // binomial coefficients of (1+x)^(cv/cp) - 1 and (1+x)^(R/cp) - 1, then the exponent
+  double p0, p0R, cvcp, kap;
+};
+
 // step kernels (step.cu)
 struct StepLaunch {
   const DomDev *d_doms;
@@ -160,6 +167,7 @@ struct StepLaunch {
   int ndom;
   long long ghost_points;  // lateral ghost points over all domains (per level and field)
   const long long *ghost_off;  // per-domain prefix of ghost points (device)
+  Eos eos;
 };
 cudaError_t launch_base(const DomDev &D, int prec, double theta0, double N, double p_surf,
                         double sponge_frac, double tau_max, cudaStream_t st);

@@ -111,6 +111,69 @@ __device__ __forceinline__ float exner_fac(const DomDev &D, const float *pik, co
   return fmaf(pik[kp], pow1pm1(__fmul_rn(pp, ipb[kp]), D.sex), pik[kp]);
 }
 
+// The same equation-of-state operations on per-level base values already in
+// registers and on coefficients passed as kernel parameters (constant bank):
+// bit-identical to the functions above.
+__device__ __forceinline__ float pow1pm1_e(float x, const float (&c)[8]) {
+  if (fabsf(x) < 0.0625f) {
+    float s = c[6];
+    s = fmaf(s, x, c[5]);
+    s = fmaf(s, x, c[4]);
+    s = fmaf(s, x, c[3]);
+    s = fmaf(s, x, c[2]);
+    s = fmaf(s, x, c[1]);
+    s = fmaf(s, x, c[0]);
+    return __fmul_rn(s, x);
+  }
+  return expm1f(__fmul_rn(c[7], log1pf(x)));
+}
+__device__ __forceinline__ float theta_pert_e(const Eos &E, float thb, float ipb, float pp) {
+  return __fmul_rn(thb, pow1pm1_e(__fmul_rn(pp, ipb), E.sth));
+}
+__device__ __forceinline__ float theta_tot_e(const Eos &E, float thb, float ipb, float pp) {
+  return __fadd_rn(thb, theta_pert_e(E, thb, ipb, pp));
+}
+__device__ __forceinline__ float exner_e(const Eos &E, float pik, float ipb, float pp) {
+  return fmaf(pik, pow1pm1_e(__fmul_rn(pp, ipb), E.sex), pik);
+}
+__device__ __forceinline__ double theta_tot_e(const Eos &E, double pb, double pp) {
+  return __dmul_rn(E.p0R, pow((pb + pp) / E.p0, E.cvcp));
+}
+__device__ __forceinline__ double theta_pert_e(const Eos &E, double thb, double pb, double pp) {
+  return __dsub_rn(theta_tot_e(E, pb, pp), thb);
+}
+__device__ __forceinline__ double exner_e(const Eos &E, double pb, double pp) {
+  return pow((pb + pp) / E.p0, E.kap);
+}
+// per-precision adapters of one cell level kp
+template <typename T>
+struct EosK;
+template <>
+struct EosK<float> {
+  float thb, ipb, pik;
+  __device__ __forceinline__ void load(const float *thb_, const float *pb_, const float *ipb_, const float *pik_,
+                                       int kp) {
+    thb = thb_[kp];
+    ipb = ipb_[kp];
+    pik = pik_[kp];
+  }
+  __device__ __forceinline__ float tot(const Eos &E, float pp) const { return theta_tot_e(E, thb, ipb, pp); }
+  __device__ __forceinline__ float pert(const Eos &E, float pp) const { return theta_pert_e(E, thb, ipb, pp); }
+  __device__ __forceinline__ float exner(const Eos &E, float pp) const { return exner_e(E, pik, ipb, pp); }
+};
+template <>
+struct EosK<double> {
+  double thb, pb;
+  __device__ __forceinline__ void load(const double *thb_, const double *pb_, const double *, const double *,
+                                       int kp) {
+    thb = thb_[kp];
+    pb = pb_[kp];
+  }
+  __device__ __forceinline__ double tot(const Eos &E, double pp) const { return theta_tot_e(E, pb, pp); }
+  __device__ __forceinline__ double pert(const Eos &E, double pp) const { return theta_pert_e(E, thb, pb, pp); }
+  __device__ __forceinline__ double exner(const Eos &E, double pp) const { return exner_e(E, pb, pp); }
+};
+
 __device__ __forceinline__ double d4(double a, double b, double c, double d, double e) {
   return a - 4.0 * b + 6.0 * c - 4.0 * d + e;
 }
@@ -173,14 +236,16 @@ struct FullCfg {
 };
 
 // Shared-memory rings of haloed planes.  Raw planes arrive by asynchronous
-// copies issued three planes ahead; derived planes (total density, total rho
-// theta, corner velocity) are formed one plane ahead of their use.
+// copies issued three planes ahead (after the barrier that ends the previous
+// plane, so a slot is rewritten only once no thread reads it); derived planes
+// (total density, total rho theta, corner velocity) are formed one plane ahead
+// of their use.  Each ring holds exactly the planes still read at plane k.
 template <typename T, int PLn>
 struct FullSmem {
-  T cr[6][PLn], cp[6][PLn];  // raw rho', p' (current level), planes k-2 .. k+3
+  T cr[5][PLn], cp[5][PLn];  // raw rho', p' (current level), planes k-1 .. k+3
   T cm[4][3][PLn];           // raw momentum (current level), planes k-1 .. k+2 (+ in flight)
-  T op[5][PLn];              // raw p' at n-1, planes k-1 .. k+3
-  T om[5][3][PLn];           // raw momentum at n-1, planes k-1 .. k+3
+  T op[4][PLn];              // raw p' at n-1, planes k .. k+3
+  T om[4][3][PLn];           // raw momentum at n-1, planes k .. k+3
   T rh[4][PLn], th[4][PLn];  // total density and total rho theta, planes k-1 .. k+2
   T uu[3][3][PLn];           // corner velocity, planes k-1 .. k+1
   T to[PLn];                 // (rho theta)' at n-1, plane k
@@ -210,7 +275,7 @@ __device__ __forceinline__ void await_groups() {
 template <typename T, int TYv>
 __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict__ doms,
                                                         const WorkItem *__restrict__ items, int rO, int rC,
-                                                        int rN, int rF, int first) {
+                                                        int rN, int rF, int first, const Eos E) {
   using A = Ar<T>;
   using C = FullCfg<T, TYv>;
   constexpr int TX = C::TX, NT = C::NT, HX = C::HX, PL = C::PL, NLP = C::NLP;
@@ -266,40 +331,44 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
   }
   const T *__restrict__ ubC = (const T *)D.ub[rC];
   const int kmaxp = D.pz - GH - 1;  // highest plane inside the padding
-  // issue the asynchronous copies of every raw field of plane kk (the
-  // current-level momentum only when with_m: its ring has four slots)
-  auto issue = [&](int kk, bool with_m) {
+  // asynchronous copies of the raw fields of plane kk: the current-level
+  // momentum when with_m (its ring has four slots), the n-1 fields when with_o
+  auto issue = [&](int kk, bool with_m, bool with_o) {
     const long long zo = (long long)(min(kk, kmaxp) + GH) * plane;  // planes past the top are never used
-    const int a6 = s6(kk), a4 = s4(kk), a5 = s5(kk);
+    const int a5 = s5(kk), a4 = s4(kk);
 #pragma unroll
     for (int s = 0; s < NLP; s++) {
       const int p = lpt[s];
       if (p < PL) {
         const long long g = zo + loff[s];
-        acopy(&S.cr[a6][p], rpC + g);
-        acopy(&S.cp[a6][p], ppC + g);
+        acopy(&S.cr[a5][p], rpC + g);
+        acopy(&S.cp[a5][p], ppC + g);
         if (with_m) {
           acopy(&S.cm[a4][0][p], mC0 + g);
           acopy(&S.cm[a4][1][p], mC1 + g);
           acopy(&S.cm[a4][2][p], mC2 + g);
         }
-        acopy(&S.op[a5][p], ppO + g);
-        acopy(&S.om[a5][0][p], mO0 + g);
-        acopy(&S.om[a5][1][p], mO1 + g);
-        acopy(&S.om[a5][2][p], mO2 + g);
+        if (with_o) {
+          acopy(&S.op[a4][p], ppO + g);
+          acopy(&S.om[a4][0][p], mO0 + g);
+          acopy(&S.om[a4][1][p], mO1 + g);
+          acopy(&S.om[a4][2][p], mO2 + g);
+        }
       }
     }
   };
   // totals of plane kk from its raw plane
   auto derive = [&](int kk) {
-    const int a6 = s6(kk), a4 = s4(kk), kp = kk + GH;
+    const int a5 = s5(kk), a4 = s4(kk), kp = kk + GH;
     const T rb = rhob[kp];
+    EosK<T> ek;
+    ek.load(thb, pb, ipb, pik, kp);
 #pragma unroll
     for (int s = 0; s < NLP; s++) {
       const int p = lpt[s];
       if (p < PL) {
-        S.rh[a4][p] = A::add(rb, S.cr[a6][p]);
-        S.th[a4][p] = theta_tot(D, thb, pb, ipb, kp, S.cp[a6][p]);
+        S.rh[a4][p] = A::add(rb, S.cr[a5][p]);
+        S.th[a4][p] = ek.tot(E, S.cp[a5][p]);
       }
     }
   };
@@ -331,11 +400,13 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
   };
   // (rho theta)' at n-1 of plane kk (in-plane diffusion stencil)
   auto derive_old = [&](int kk) {
-    const int a5 = s5(kk), kp = kk + GH;
+    const int a4 = s4(kk), kp = kk + GH;
+    EosK<T> ek;
+    ek.load(thb, pb, ipb, pik, kp);
 #pragma unroll
     for (int s = 0; s < NLP; s++) {
       const int p = lpt[s];
-      if (p < PL) S.to[p] = theta_pert(D, thb, pb, ipb, kp, S.op[a5][p]);
+      if (p < PL) S.to[p] = ek.pert(E, S.op[a4][p]);
     }
   };
 
@@ -355,31 +426,43 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
   // own column at n-1 for the vertical diffusion stencils, levels k-2 .. k+2
   T treg[5], mreg[5][3];
   auto own_old = [&](int a, int kk) {
-    const int a5 = s5(kk);
-    treg[a] = theta_pert(D, thb, pb, ipb, kk + GH, S.op[a5][c]);
-    mreg[a][0] = S.om[a5][0][c];
-    mreg[a][1] = S.om[a5][1][c];
-    mreg[a][2] = S.om[a5][2][c];
+    const int a4 = s4(kk);
+    EosK<T> ek;
+    ek.load(thb, pb, ipb, pik, kk + GH);
+    treg[a] = ek.pert(E, S.op[a4][c]);
+    mreg[a][0] = S.om[a4][0][c];
+    mreg[a][1] = S.om[a4][1][c];
+    mreg[a][2] = S.om[a4][2][c];
   };
 
-  // prologue: raw planes k0-2 .. k0+2, totals k0-2 .. k0+1, velocities k0-1, k0
-  // (momentum of plane k0-2 is not needed and would share a ring slot with k0+2)
-  for (int kk = k0 - 2; kk <= k0 + 2; kk++) issue(kk, kk != k0 - 2);
+  // prologue: raw planes k0-2 .. k0+2 (momentum from k0-1, n-1 fields from
+  // k0-1: their rings have four slots), totals k0-2 .. k0+1, velocities
+  // k0-1, k0; the own column at n-1 of plane k0-2 straight from memory
+  for (int kk = k0 - 2; kk <= k0 + 2; kk++) issue(kk, kk != k0 - 2, kk != k0 - 2);
   acommit();
+  {
+    const long long o2 = (long long)(k0 - 2 + GH) * plane + own;
+    EosK<T> ek;
+    ek.load(thb, pb, ipb, pik, k0 - 2 + GH);
+    treg[0] = ek.pert(E, ppO[o2]);
+    mreg[0][0] = mO0[o2];
+    mreg[0][1] = mO1[o2];
+    mreg[0][2] = mO2[o2];
+  }
   await_groups<0>();
   __syncthreads();
   for (int kk = k0 - 2; kk <= k0 + 1; kk++) derive(kk);
 #pragma unroll
-  for (int a = 0; a < 4; a++) own_old(a, k0 - 2 + a);
+  for (int a = 1; a < 4; a++) own_old(a, k0 - 2 + a);
   __syncthreads();
   velocity(k0 - 1);
   velocity(k0);
 
   for (int k = k0; k < k1; k++) {
-    // phase 1: copies for plane k+3 in flight; totals of plane k+2,
-    // velocities of plane k+1, the n-1 fields of plane k
-    issue(k + 3, true);
-    acommit();
+    // phase 1: wait for plane k+2; once every thread is past the previous
+    // plane (the barrier), the ring slots it read last are free and the
+    // copies of plane k+3 go in flight; then the totals of plane k+2, the
+    // velocities of plane k+1 and the n-1 fields of plane k
     T rO_ = 0, mcur[3] = {0, 0, 0};
     const long long o = (long long)(k + GH) * plane + own;
     if (active) {
@@ -388,8 +471,10 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
       mcur[1] = mC1[o];
       mcur[2] = mC2[o];
     }
-    await_groups<1>();
+    await_groups<0>();
     __syncthreads();
+    issue(k + 3, true, true);
+    acommit();
     derive(k + 2);
     velocity(k + 1);
     derive_old(k);
@@ -398,7 +483,7 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
     // phase 2: the cell and corner of this thread on plane k
     if (active) {
       const int sk = s4(k), skm = s4(k - 1), skp = s4(k + 1);
-      const int ck = s6(k), ckm = s6(k - 1);
+      const int ck = s5(k), ckm = s5(k - 1);
       const T *R0 = S.rh[sk], *Rm = S.rh[skm], *Rp = S.rh[skp];
       const T *H0 = S.th[sk], *Hm = S.th[skm], *Hp = S.th[skp];
       const int uk = s3(k), ukp = s3(k + 1), ukm = s3(k - 1);
@@ -428,10 +513,12 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
              d4(treg[0], treg[1], treg[2], treg[3], treg[4]);
       T Dth = -kdif * dd;
       const int kp = k + GH;
+      EosK<T> ek;
+      ek.load(thb, pb, ipb, pik, kp);
       T rC_ = S.cr[ck][c], pC_ = S.cp[ck][c];
-      T pO_ = S.op[s5(k)][c];
+      T pO_ = S.op[s4(k)][c];
       T rN_ = rO_ - dt2 * (RM * v0inv);
-      T pN_ = pO_ - dt2 * Cp * exner_fac(D, pik, pb, ipb, kp, pC_) * (RH * v0inv - Dth);
+      T pN_ = pO_ - dt2 * Cp * ek.exner(E, pC_) * (RH * v0inv - Dth);
       if (k < kug) { rN_ = 0; pN_ = 0; }
       T rF_ = rC_ + nu * (rN_ - T(2) * rC_ + rO_);
       T pF_ = pC_ + nu * (pN_ - T(2) * pC_ + pO_);
@@ -470,22 +557,23 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
       T r8 = (Q0[c - HX - 1] + Q0[c - HX] + Q0[c - 1] + Q0[c]) + (Qm[c - HX - 1] + Qm[c - HX] + Qm[c - 1] + Qm[c]);
       T pg[3] = {T(0.25) * (pE - pW) / dx, T(0.25) * (pNn - pS) / dy, T(0.25) * (pT - pB) / dz};
       const T tk = tau[kp];
-      const int ok5 = s5(k);
+      const T rbc[5] = {rhobc[kp - 2] * U, rhobc[kp - 1] * U, rhobc[kp] * U, rhobc[kp + 1] * U, rhobc[kp + 2] * U};
+      const int ok4 = s4(k);
 #pragma unroll
       for (int d = 0; d < 3; d++) {
         T adv = fE * T(0.5) * (u0[d] + uE[d]) - fW * T(0.5) * (uW[d] + u0[d]) + fN * T(0.5) * (u0[d] + uN[d]) -
                 fS * T(0.5) * (uS[d] + u0[d]) + fT * T(0.5) * (u0[d] + uT[d]) - fB * T(0.5) * (uB[d] + u0[d]);
         T tend = -adv * v0inv - pg[d];
         if (d == 2) tend -= g * r8 * T(0.125);
-        const T *Mk = S.om[ok5][d];
+        const T *Mk = S.om[ok4][d];
         // diffusion of the departure from the reference momentum (rho_bar U, 0, 0)
-        T ref0 = d == 0 ? rhobc[kp] * U : T(0);
+        T ref0 = d == 0 ? rbc[2] : T(0);
         T dm = d4(Mk[c - 2] - ref0, Mk[c - 1] - ref0, Mk[c] - ref0, Mk[c + 1] - ref0, Mk[c + 2] - ref0) +
                d4(Mk[c - 2 * HX] - ref0, Mk[c - HX] - ref0, Mk[c] - ref0, Mk[c + HX] - ref0,
                   Mk[c + 2 * HX] - ref0);
         if (d == 0)
-          dm += d4(mreg[0][0] - rhobc[kp - 2] * U, mreg[1][0] - rhobc[kp - 1] * U, mreg[2][0] - ref0,
-                   mreg[3][0] - rhobc[kp + 1] * U, mreg[4][0] - rhobc[kp + 2] * U);
+          dm += d4(mreg[0][0] - rbc[0], mreg[1][0] - rbc[1], mreg[2][0] - ref0, mreg[3][0] - rbc[3],
+                   mreg[4][0] - rbc[4]);
         else
           dm += d4(mreg[0][d], mreg[1][d], mreg[2][d], mreg[3][d], mreg[4][d]);
         T mold = mreg[2][d];
@@ -1120,7 +1208,7 @@ cudaError_t full_t(const StepLaunch &L, int rO, int rC, int rN, int rF, int firs
   }
   if (L.nitems > 0)
     k_full<T, TYv><<<L.nitems, TILE_X * TYv, full_smem<T, TYv>(), st>>>(L.d_doms, L.items, rO, rC, rN, rF,
-                                                                        first);
+                                                                        first, L.eos);
   return cudaGetLastError();
 }
 
