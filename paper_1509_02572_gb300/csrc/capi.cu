@@ -251,7 +251,7 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
     const cc_config &c = H.cfg;
     DomDev &D = H.D;
     D.nx = c.nx; D.ny = c.ny; D.nz = c.nz;
-    D.px = c.nx + 2 * GH; D.py = c.ny + 2 * GH; D.pz = c.nz + 2 * GH;
+    D.px = (c.nx + GX + 4 + 7) / 8 * 8; D.py = c.ny + 2 * GH; D.pz = c.nz + 2 * GH;
     D.plane = (long long)D.px * D.py;
     D.ncellp = D.plane * D.pz;
     D.dx = c.dx; D.dy = c.dy; D.dz = c.dz; D.dt = c.dt;
@@ -344,7 +344,7 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
   {
     const int TILE_Y = full_tile_y(precision);
     auto tiles_of = [&](const DomDev &D) {
-      return (long long)((D.ci1 - D.ci0 + TILE_X - 1) / TILE_X) * ((D.cj1 - D.cj0 + TILE_Y - 1) / TILE_Y);
+      return (long long)((D.ci1 - D.ci0 + 3 + TILE_X - 1) / TILE_X) * ((D.cj1 - D.cj0 + TILE_Y - 1) / TILE_Y);
     };
     long long all_tiles = 0;
     for (auto &H : m->dom) all_tiles += tiles_of(H.D);
@@ -358,9 +358,11 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
       long long splits = std::max(1LL, (want + tiles - 1) / tiles);
       int chunk = (int)std::max(8LL, (D.ck1 + splits - 1) / splits);
       H.item0 = (int)items.size();
+      // tiles start at multiples of 4 in x (16-byte halo rows)
+      const int ib = D.ci0 - ((D.ci0 % 4) + 4) % 4;
       for (int k0 = 0; k0 < D.ck1; k0 += chunk)
         for (int j0 = D.cj0; j0 < D.cj1; j0 += TILE_Y)
-          for (int i0 = D.ci0; i0 < D.ci1; i0 += TILE_X) {
+          for (int i0 = ib; i0 < D.ci1; i0 += TILE_X) {
             WorkItem w{};
             w.dom = d; w.i0 = i0; w.j0 = j0; w.k0 = k0; w.k1 = std::min(D.ck1, k0 + chunk);
             items.push_back(w);

@@ -7,12 +7,16 @@
 
 namespace cc {
 
-constexpr int GH = 4;          // ghost width of every padded array (x, y and z)
+constexpr int GH = 4;          // ghost width of every padded array (y and z; at least this in x)
+// x offset of cell 0 in a padded row: with it, and rows of a multiple of 4
+// values, the halo row of a tile (cells i0-2 .. for i0 a multiple of 4) starts
+// on a 16-byte boundary
+constexpr int GX = 6;
 constexpr int HOST_GZ = 2;     // corner levels below floor / above lid in host arrays
 constexpr int NFIELD = 5;      // rho', p', rho u, rho v, rho w
 constexpr int NBUF = 4;        // rotating time levels
 constexpr int TILE_X = 32;                          // full-cell stencil tile width (x)
-constexpr int TILE_Y_F32 = 8, TILE_Y_F64 = 8;      // tile height (y) per precision
+constexpr int TILE_Y_F32 = 16, TILE_Y_F64 = 8;     // tile height (y) per precision
 
 // cell classes and corner classes
 enum : int8_t { C_UG = 0, C_FULL = 1, C_CUT = 2, C_ABS = 3 };
@@ -23,7 +27,7 @@ constexpr int KB_NONE = -1000;
 // field arrays are of the model's precision (double or float).
 struct DomDev {
   int nx, ny, nz;
-  int px, py, pz;            // padded extents (n + 2*GH)
+  int px, py, pz;            // padded extents: px = nx + GX + 4 rounded up to a multiple of 8 (32-byte FP32 rows), py = ny + 2*GH, pz = nz + 2*GH
   long long plane;           // px*py
   long long ncellp;          // px*py*pz
   double dx, dy, dz, dt;
@@ -87,7 +91,7 @@ struct GroupRec {
 };
 
 __host__ __device__ inline long long pidx(const DomDev &D, int i, int j, int k) {
-  return ((long long)(k + GH) * D.py + (j + GH)) * D.px + (i + GH);
+  return ((long long)(k + GH) * D.py + (j + GH)) * D.px + (i + GX);
 }
 __host__ __device__ inline int wrapi(int i, int n) {
   int r = i % n;
@@ -98,7 +102,7 @@ __host__ __device__ inline long long cid(const DomDev &D, int i, int j, int k) {
 }
 // padded column index
 __host__ __device__ inline long long qidx(const DomDev &D, int I, int J) {
-  return (long long)(J + GH) * D.px + (I + GH);
+  return (long long)(J + GH) * D.px + (I + GX);
 }
 
 // ---- refinement (step.cu)

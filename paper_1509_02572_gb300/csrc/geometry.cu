@@ -491,7 +491,7 @@ __global__ void k_ktop(DomDev D, const int8_t *vcls, int32_t *ktop) {
 __global__ void k_flat_columns(DomDev D) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)D.px * D.py) return;
-  int I = (int)(t % D.px) - GH, J = (int)(t / D.px) - GH;
+  int I = (int)(t % D.px) - GX, J = (int)(t / D.px) - GH;
   if (I >= 0 && I < D.nx && J >= 0 && J < D.ny) return;
   const_cast<int32_t *>(D.kug)[t] = 0;
   const_cast<int32_t *>(D.bK)[t] = 1;
@@ -514,7 +514,7 @@ __global__ void k_flat_columns(DomDev D) {
 __global__ void k_kb(DomDev D, int32_t *kb) {
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)D.px * D.py) return;
-  int I = (int)(t % D.px) - GH, J = (int)(t / D.px) - GH;
+  int I = (int)(t % D.px) - GX, J = (int)(t / D.px) - GH;
   if (!D.periodic && !(I >= D.qi0 && I < D.ci1 && J >= D.qj0 && J < D.cj1)) {
     kb[t] = KB_NONE;
     return;

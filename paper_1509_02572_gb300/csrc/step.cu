@@ -59,10 +59,15 @@ __device__ __forceinline__ T rho8(T a, T b, T c, T d, T e, T f, T g, T h) {
   return A::mul(A::add(A::add(A::add(A::add(A::add(A::add(A::add(a, b), c), d), e), f), g), h), T(0.125));
 }
 
-// reciprocal of the corner density; the velocity is momentum times it
-template <typename T>
-__device__ __forceinline__ T rinv(T rc) {
-  return T(1) / rc;
+// reciprocal of the corner density; the velocity is momentum times it.
+// FP32: the hardware reciprocal approximation (relative error below 2^-22,
+// under the FP32 form's other rounding); every kernel uses this same function,
+// so a corner velocity has the same bits in each
+__device__ __forceinline__ double rinv(double rc) { return 1.0 / rc; }
+__device__ __forceinline__ float rinv(float rc) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(rc));
+  return r;
 }
 
 // rho*theta as a function of pressure (equation of state, Sec 2.1:
@@ -266,6 +271,12 @@ __device__ __forceinline__ void acopy(T *dst, const T *src) {
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
+// asynchronous global -> shared copy of 16 bytes (both addresses 16-byte aligned)
+template <typename T>
+__device__ __forceinline__ void acopy16(T *dst, const T *src) {
+  unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+}
 __device__ __forceinline__ void acommit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void await_groups() {
@@ -310,51 +321,61 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
   // per-thread plane points of the haloed tile and their in-plane offsets
   // (periodic domains wrap the lateral coordinates; a refined box reads its
   // ghost frame, clamped to the padding where no computed point needs it)
-  long long loff[NLP];
-  int lpt[NLP], kbv[NLP];
-  const int py = D.py;
+  auto col_x = [&](int gi) { return D.periodic ? wrapi(gi, nx) : min(max(gi, -GX), px - GX - 1); };
+  auto row_y = [&](int gj) { return D.periodic ? wrapi(gj, ny) : min(max(gj, -GH), D.py - GH - 1); };
+  int loff[NLP], lpt[NLP], kbv[NLP];
 #pragma unroll
   for (int s = 0; s < NLP; s++) {
     int p = tid + s * NT;
     lpt[s] = p;
     int hx = p % HX, hy = p / HX;
-    int gi = i0 - 2 + hx, gj = j0 - 2 + hy;
-    if (D.periodic) {
-      gi = wrapi(gi, nx);
-      gj = wrapi(gj, ny);
-    } else {
-      gi = min(max(gi, -GH), px - GH - 1);
-      gj = min(max(gj, -GH), py - GH - 1);
-    }
-    loff[s] = (long long)(gj + GH) * px + (gi + GH);
+    loff[s] = (row_y(j0 - 2 + hy) + GH) * px + (col_x(i0 - 2 + hx) + GX);
     kbv[s] = p < PL ? D.kb[loff[s]] : KB_NONE;
   }
+  // 16-byte chunks of the haloed rows (i0 is a multiple of 4, so a row of the
+  // tile starts on a 16-byte boundary): this thread copies chunk tid of each
+  // field, whole where it lies inside the row, element by element (wrapped or
+  // clamped) where it crosses the periodic seam or the end of the padding
+  constexpr int VEC = 16 / sizeof(T), CPR = HX / VEC, NCH = CPR * C::HY;
+  static_assert(HX % VEC == 0, "halo rows are whole chunks");
+  static_assert(NCH <= NT, "one chunk per thread and field");
+  const bool has_chunk = tid < NCH;
+  const int ch_row = tid / CPR, ch_col = tid % CPR;
+  const int ch_x = i0 - 2 + VEC * ch_col;
+  const int ch_dst = ch_row * HX + VEC * ch_col;
+  const int ch_rowoff = (row_y(j0 - 2 + ch_row) + GH) * px;
+  const bool ch_whole = D.periodic ? (ch_x >= 0 && ch_x + VEC <= nx) : (ch_x >= -GX && ch_x + VEC <= px - GX);
+  int ch_e[VEC];  // in-plane offsets of the elements of a chunk copied one by one
+#pragma unroll
+  for (int e = 0; e < VEC; e++) ch_e[e] = ch_rowoff + col_x(ch_x + e) + GX;
   const T *__restrict__ ubC = (const T *)D.ub[rC];
   const int kmaxp = D.pz - GH - 1;  // highest plane inside the padding
+  auto chunk = [&](T *dst, const T *src) {
+    if (ch_whole) {
+      acopy16(dst + ch_dst, src + ch_e[0]);
+    } else {
+#pragma unroll
+      for (int e = 0; e < VEC; e++) acopy(dst + ch_dst + e, src + ch_e[e]);
+    }
+  };
   // asynchronous copies of the raw fields of plane kk: the current-level
   // momentum when with_m (its ring has four slots), the n-1 fields when with_o
   auto issue = [&](int kk, bool with_m, bool with_o) {
+    if (!has_chunk) return;
     const long long zo = (long long)(min(kk, kmaxp) + GH) * plane;  // planes past the top are never used
     const int a5 = s5(kk), a4 = s4(kk);
-#pragma unroll
-    for (int s = 0; s < NLP; s++) {
-      const int p = lpt[s];
-      if (p < PL) {
-        const long long g = zo + loff[s];
-        acopy(&S.cr[a5][p], rpC + g);
-        acopy(&S.cp[a5][p], ppC + g);
-        if (with_m) {
-          acopy(&S.cm[a4][0][p], mC0 + g);
-          acopy(&S.cm[a4][1][p], mC1 + g);
-          acopy(&S.cm[a4][2][p], mC2 + g);
-        }
-        if (with_o) {
-          acopy(&S.op[a4][p], ppO + g);
-          acopy(&S.om[a4][0][p], mO0 + g);
-          acopy(&S.om[a4][1][p], mO1 + g);
-          acopy(&S.om[a4][2][p], mO2 + g);
-        }
-      }
+    chunk(S.cr[a5], rpC + zo);
+    chunk(S.cp[a5], ppC + zo);
+    if (with_m) {
+      chunk(S.cm[a4][0], mC0 + zo);
+      chunk(S.cm[a4][1], mC1 + zo);
+      chunk(S.cm[a4][2], mC2 + zo);
+    }
+    if (with_o) {
+      chunk(S.op[a4], ppO + zo);
+      chunk(S.om[a4][0], mO0 + zo);
+      chunk(S.om[a4][1], mO1 + zo);
+      chunk(S.om[a4][2], mO2 + zo);
     }
   };
   // totals of plane kk from its raw plane
@@ -412,12 +433,12 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
 
   const int tx = tid % TX, ty = tid / TX;
   const int i = i0 + tx, j = j0 + ty;
-  const bool active = i < D.ci1 && j < D.cj1;
+  const bool active = i >= D.ci0 && i < D.ci1 && j < D.cj1;
   // corners of a refined box outside -1 .. n+1 are ghost values from the coarser level
   const bool corner_active = active && i >= D.qi0 && j >= D.qj0;
   const int c = (ty + 2) * HX + (tx + 2);
-  const long long own = active ? (long long)(j + GH) * px + (i + GH) : 0;
-  const T dx = (T)D.dx, dy = (T)D.dy, dz = (T)D.dz;
+  const long long own = active ? (long long)(j + GH) * px + (i + GX) : 0;
+  const T qdx = (T)(0.25 / D.dx), qdy = (T)(0.25 / D.dy), qdz = (T)(0.25 / D.dz);  // 1/4 of the pressure-gradient quotient
   const T Sx = (T)(D.dy * D.dz), Sy = (T)(D.dx * D.dz), Sz = (T)(D.dx * D.dy);
   const T v0inv = (T)(1.0 / (D.dx * D.dy * D.dz));
   const T kdif = (T)D.kdif, Cp = (T)D.Cp, g = (T)D.g, U = (T)D.U;
@@ -463,14 +484,9 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
     // plane (the barrier), the ring slots it read last are free and the
     // copies of plane k+3 go in flight; then the totals of plane k+2, the
     // velocities of plane k+1 and the n-1 fields of plane k
-    T rO_ = 0, mcur[3] = {0, 0, 0};
+    T rO_ = 0;
     const long long o = (long long)(k + GH) * plane + own;
-    if (active) {
-      rO_ = rpO[o];
-      mcur[0] = mC0[o];
-      mcur[1] = mC1[o];
-      mcur[2] = mC2[o];
-    }
+    if (active) rO_ = rpO[o];
     await_groups<0>();
     __syncthreads();
     issue(k + 3, true, true);
@@ -516,6 +532,7 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
       EosK<T> ek;
       ek.load(thb, pb, ipb, pik, kp);
       T rC_ = S.cr[ck][c], pC_ = S.cp[ck][c];
+      const T mcur[3] = {S.cm[sk][0][c], S.cm[sk][1][c], S.cm[sk][2][c]};
       T pO_ = S.op[s4(k)][c];
       T rN_ = rO_ - dt2 * (RM * v0inv);
       T pN_ = pO_ - dt2 * Cp * ek.exner(E, pC_) * (RH * v0inv - Dth);
@@ -555,7 +572,7 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
       T pB = Pm[c - HX - 1] + Pm[c - HX] + Pm[c - 1] + Pm[c];
       const T *Q0 = S.cr[ck], *Qm = S.cr[ckm];
       T r8 = (Q0[c - HX - 1] + Q0[c - HX] + Q0[c - 1] + Q0[c]) + (Qm[c - HX - 1] + Qm[c - HX] + Qm[c - 1] + Qm[c]);
-      T pg[3] = {T(0.25) * (pE - pW) / dx, T(0.25) * (pNn - pS) / dy, T(0.25) * (pT - pB) / dz};
+      T pg[3] = {(pE - pW) * qdx, (pNn - pS) * qdy, (pT - pB) * qdz};
       const T tk = tau[kp];
       const T rbc[5] = {rhobc[kp - 2] * U, rhobc[kp - 1] * U, rhobc[kp] * U, rhobc[kp + 1] * U, rhobc[kp + 2] * U};
       const int ok4 = s4(k);
@@ -926,7 +943,7 @@ __global__ void k_diag_final(const double *part, int nb, double *out) {
 
 // ------------------------------------------------------------------ refinement (Sec 2.2)
 __device__ __forceinline__ void decode(const DomDev &D, long long off, int &i, int &j, int &k) {
-  i = (int)(off % D.px) - GH;
+  i = (int)(off % D.px) - GX;
   j = (int)((off / D.px) % D.py) - GH;
   k = (int)(off / D.plane) - GH;
 }
