@@ -680,44 +680,42 @@ __global__ void k_groups(const DomDev *__restrict__ doms, const GroupRec *__rest
   for (int a = 0; a < R.count; a++) {
     int m = members[R.start + a];
     int i = m % nx, j = (m / nx) % ny, k = m / (nx * ny);
+    // the eight corner velocities of the cell, [dk][dj][di]
+    T uc8[2][2][2][3];
+#pragma unroll
+    for (int dk = 0; dk < 2; dk++)
+#pragma unroll
+      for (int dj = 0; dj < 2; dj++)
+#pragma unroll
+        for (int di = 0; di < 2; di++) corner_u(D, rpC, MC, rhob, ubC, i + di, j + dj, k + dk, uc8[dk][dj][di]);
+    const T phm = cell_rho(D, rpC, rhob, i, j, k);
+    const T thm = theta_tot(D, thb, pb, ipb, k + GH, ppC[widx(D, i, j, k)]);
     for (int ax = 0; ax < 3; ax++)
       for (int sd = 0; sd <= 1; sd++) {
         int ni = i, nj = j, nk = k;
         double Ap;
-        int cI[4], cJ[4], cK[4];
+        const T *uc[4];
         if (ax == 0) {
           int I = i + sd;
           ni = i + (sd ? 1 : -1);
           Ap = D.ax[cid(D, wrapi(I, nx), j, k)];
-          cI[0] = I; cJ[0] = j; cK[0] = k;
-          cI[1] = I; cJ[1] = j + 1; cK[1] = k;
-          cI[2] = I; cJ[2] = j; cK[2] = k + 1;
-          cI[3] = I; cJ[3] = j + 1; cK[3] = k + 1;
+          uc[0] = uc8[0][0][sd]; uc[1] = uc8[0][1][sd]; uc[2] = uc8[1][0][sd]; uc[3] = uc8[1][1][sd];
         } else if (ax == 1) {
           int J = j + sd;
           nj = j + (sd ? 1 : -1);
           Ap = D.ay[cid(D, i, wrapi(J, ny), k)];
-          cI[0] = i; cJ[0] = J; cK[0] = k;
-          cI[1] = i + 1; cJ[1] = J; cK[1] = k;
-          cI[2] = i; cJ[2] = J; cK[2] = k + 1;
-          cI[3] = i + 1; cJ[3] = J; cK[3] = k + 1;
+          uc[0] = uc8[0][sd][0]; uc[1] = uc8[0][sd][1]; uc[2] = uc8[1][sd][0]; uc[3] = uc8[1][sd][1];
         } else {
           int K = k + sd;
           nk = k + (sd ? 1 : -1);
           Ap = D.az[((long long)K * ny + j) * nx + i];
-          cI[0] = i; cJ[0] = j; cK[0] = K;
-          cI[1] = i + 1; cJ[1] = j; cK[1] = K;
-          cI[2] = i; cJ[2] = j + 1; cK[2] = K;
-          cI[3] = i + 1; cJ[3] = j + 1; cK[3] = K;
+          uc[0] = uc8[sd][0][0]; uc[1] = uc8[sd][0][1]; uc[2] = uc8[sd][1][0]; uc[3] = uc8[sd][1][1];
         }
         if (Ap == 0.0) continue;
         if (nk < 0 || nk >= nz) continue;
         long long nb = cid(D, wrapi(ni, nx), wrapi(nj, ny), nk);
         if (D.cls[nb] != C_UG && D.root[nb] == R.host) continue;  // face inside the group
-        T uc[4][3];
-        for (int s = 0; s < 4; s++) corner_u(D, rpC, MC, rhob, ubC, cI[s], cJ[s], cK[s], uc[s]);
-        T phm = cell_rho(D, rpC, rhob, i, j, k), phn = cell_rho(D, rpC, rhob, ni, nj, nk);
-        T thm = theta_tot(D, thb, pb, ipb, k + GH, ppC[widx(D, i, j, k)]);
+        T phn = cell_rho(D, rpC, rhob, ni, nj, nk);
         T thn = theta_tot(D, thb, pb, ipb, nk + GH, ppC[widx(D, ni, nj, nk)]);
         T S = (Ap == 1.0) ? Sfull[ax] : (T)(Ap * (double)Sfull[ax]);
         T fm, fh;
