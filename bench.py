@@ -64,6 +64,33 @@ def workload_configs(args):
     return name, cfgs
 
 
+def kfull_source_hash():
+    """Hash of the full-cell stencil's source (the kernel, its shared-memory
+    layout and tile shape): the DRAM counters recorded under profiles/ apply
+    only while it is unchanged."""
+    import hashlib
+    src = open(os.path.join(ROOT, "paper_1509_02572_gb300", "csrc", "step.cu")).read()
+    hdr = open(os.path.join(ROOT, "paper_1509_02572_gb300", "csrc", "cc_internal.h")).read()
+    a = src.index("struct FullCfg")
+    b = src.index("await_groups<0>();\n}", src.index("k_full(")) 
+    tiles = [ln for ln in hdr.splitlines() if "TILE_" in ln or "constexpr int GX" in ln]
+    return hashlib.sha256((src[a:b] + "\n".join(tiles)).encode()).hexdigest()[:16]
+
+
+def kfull_traffic(dtype, cells):
+    """DRAM bytes of one k_full launch over `cells` interior cells, scaled
+    from the committed ncu capture (per interior cell), or None when the
+    kernel changed since the capture or the precision differs."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_full_traffic.json")) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    if t.get("source_hash") != kfull_source_hash() or t.get("precision") != {"f32": "fp32", "f64": "fp64"}[dtype]:
+        return None
+    return t["dram_bytes_per_interior_cell"] * cells
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -406,7 +433,7 @@ def main():
     kavg = kfull_ms / max(1, kfull_n)
     achieved = BYTES_PER_CELL[dtype] * ninterior / (kavg / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": None, "kernel": "k_full", "kernel_ms": kavg, "peak_kind": f"{peak_kind} hbm_gbs",
+            "traffic": kfull_traffic(dtype, ninterior), "traffic_unit": "bytes per launch", "kernel": "k_full", "kernel_ms": kavg, "peak_kind": f"{peak_kind} hbm_gbs",
             "bytes_per_cell": BYTES_PER_CELL[dtype], "cells_per_launch": ninterior}
     stages = {k: {"ms_total": v[0], "launches": v[1]} for k, v in stage.items()}
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
