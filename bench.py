@@ -77,7 +77,7 @@ def kfull_source_hash():
     return hashlib.sha256((src[a:b] + "\n".join(tiles)).encode()).hexdigest()[:16]
 
 
-def kfull_traffic(dtype, cells):
+def kfull_traffic(dtype, cells, schedule):
     """DRAM bytes of one k_full launch over `cells` interior cells, scaled
     from the committed ncu capture (per interior cell), or None when the
     kernel changed since the capture or the precision differs."""
@@ -87,6 +87,8 @@ def kfull_traffic(dtype, cells):
     except Exception:
         return None
     if t.get("source_hash") != kfull_source_hash() or t.get("precision") != {"f32": "fp32", "f64": "fp64"}[dtype]:
+        return None
+    if list(t.get("schedule", [])) != list(schedule):
         return None
     return t["dram_bytes_per_interior_cell"] * cells
 
@@ -160,12 +162,14 @@ def fluid_cells(model, cfgs):
     return n
 
 
-def make_model(cc, cfgs, prec):
+def make_model(cc, cfgs, prec, tune=True):
     m = cc.Model(cfgs, prec)
     for d, c in enumerate(cfgs):
         m.set_terrain(d, c.heights())
     m.build_geometry()
     m.init_state()
+    if tune:
+        m.autotune(3)
     return m
 
 
@@ -221,6 +225,7 @@ def make_refined(cc, rc, prec):
         m.set_terrain(l, rc.finest_heights() if l == m.nlev - 1 else np.zeros((c.ny, c.nx)))
     m.build_geometry()
     m.init_state()
+    m.autotune(3)
     return m
 
 
@@ -259,6 +264,7 @@ def bench_refined(cc, torch, args, hbm, peak_kind, barrier, world):
     kbytes = refined_kfull_bytes(m, "f32") * args.steps
     achieved = kbytes / (kms / 1e3) / 1e9
     out = {"workload": rc.name, "levels": [list(b) for b in rc.boxes], "value": upd * args.steps * world / (ms / 1e3),
+           "schedule": [list(m.schedule(l)) for l in range(m.nlev)],
            "unit": METRIC, "ms_per_step": ms / args.steps, "cell_updates_per_step": upd, "dtype": "f32",
            "gpu_launches": launches, "clocks": clk, "stages": stages,
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
@@ -388,7 +394,7 @@ def main():
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": msps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
-                "config": {"workload": r["workload"], "levels": r["levels"],
+                "config": {"workload": r["workload"], "levels": r["levels"], "schedule": r["schedule"],
                            "cell_updates_per_step": r["cell_updates_per_step"],
                            "precision": "fp32 perturbations, fp64 geometry and base state",
                            "l2": "inputs larger than L2 (state of all levels)"},
@@ -433,13 +439,14 @@ def main():
     kavg = kfull_ms / max(1, kfull_n)
     achieved = BYTES_PER_CELL[dtype] * ninterior / (kavg / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": kfull_traffic(dtype, ninterior), "traffic_unit": "bytes per launch", "kernel": "k_full", "kernel_ms": kavg, "peak_kind": f"{peak_kind} hbm_gbs",
+            "traffic": kfull_traffic(dtype, ninterior, model.schedule(0)), "traffic_unit": "bytes per launch", "kernel": "k_full", "kernel_ms": kavg, "peak_kind": f"{peak_kind} hbm_gbs",
             "bytes_per_cell": BYTES_PER_CELL[dtype], "cells_per_launch": ninterior}
     stages = {k: {"ms_total": v[0], "launches": v[1]} for k, v in stage.items()}
     line = {"metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": name, "instances": len(cfgs), "interior_cells": ninterior,
+                       "schedule": list(model.schedule(0)),
                        "fluid_cells": nfluid, "precision": ("fp32 perturbations, fp64 geometry and base state"
                                                             if dtype == "f32" else "fp64"),
                        "l2": "inputs larger than L2 (state of all domains)" if ninterior * 80 > 129e6 else

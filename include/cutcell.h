@@ -162,6 +162,22 @@ cc_status cc_synchronize(cc_model *m);
 /* Number of kernels the last cc_step launched (for launch accounting). */
 long long cc_last_launch_count(const cc_model *m);
 
+/* Schedule of the full-cell stencil (no counterpart in the paper): tile
+ * height in y (FP32: 16 or 8, FP64: 8 or 4; tiles are 32 cells wide) and the
+ * number of work items one launch aims for (304 or 912; the z-columns are cut
+ * into chunks to reach it).  The schedule changes only how the work is
+ * distributed over thread blocks, never the result (bit for bit).
+ * cc_autotune times every schedule reps times on the model's current state
+ * and keeps the fastest, for the whole ensemble or for each level of a
+ * refined model; the state is left unchanged (the stencil writes only the
+ * levels the next step overwrites).  Needs cc_init_state; synchronises.
+ * cc_get_schedule / cc_set_schedule read or set the schedule of domain d
+ * (of an ensemble: the one shared by all domains); CC_EINVAL for a pair not
+ * in the list. */
+cc_status cc_autotune(cc_model *m, int reps);
+cc_status cc_get_schedule(const cc_model *m, int d, int *tile_y, int *items_per_launch);
+cc_status cc_set_schedule(cc_model *m, int d, int tile_y, int items_per_launch);
+
 /* Kernel timing for measurement (no counterpart in the paper).  When enabled,
  * cc_step brackets each stage with CUDA events on the model's stream;
  * cc_profile_read synchronises and returns the summed device time (ms) and the

@@ -29,7 +29,8 @@ struct DomHost {
   int r[4] = {0, 1, 2, 3};  // roles: old (filtered n-1), current, new, filtered n
   long long nsteps = 0;
   // this domain's ranges of the model-wide work, group and column lists
-  int item0 = 0, nitem = 0, group0 = 0, ngroup = 0, col0 = 0, ncol = 0;
+  int item0[NSCHED] = {}, nitem[NSCHED] = {}, group0 = 0, ngroup = 0, col0 = 0, ncol = 0;
+  int sched = 0;  // full-cell schedule of this level (refined models)
 };
 
 // Coarse-fine link of refined level l >= 1 with level l-1 (host side; the
@@ -51,8 +52,10 @@ struct cc_model {
   cudaStream_t st = nullptr;
   std::vector<DomHost> dom;
   DomDev *d_doms = nullptr;
-  WorkItem *d_items = nullptr;
-  int nitems = 0;
+  WorkItem *d_items[NSCHED] = {};  // work list of every full-cell schedule
+  int nitems[NSCHED] = {};
+  int sched = 0;                   // schedule of the ensemble launch
+  bool tuned = false;
   GroupRec *d_groups = nullptr;
   int ngroups = 0;
   int32_t *d_members = nullptr;
@@ -155,8 +158,9 @@ inline unsigned nb256(long long n) { return (unsigned)((n + 255) / 256); }
 StepLaunch make_launch(const cc_model *m, int d = -1) {
   StepLaunch L{};
   L.d_doms = m->d_doms;
-  L.items = m->d_items;
-  L.nitems = m->nitems;
+  L.items = m->d_items[m->sched];
+  L.nitems = m->nitems[m->sched];
+  L.ty = sched_tile_y(m->prec, m->sched);
   L.groups = m->d_groups;
   L.ngroups = m->ngroups;
   L.members = m->d_members;
@@ -168,8 +172,9 @@ StepLaunch make_launch(const cc_model *m, int d = -1) {
   L.eos = m->eos;
   if (d >= 0) {
     const DomHost &H = m->dom[d];
-    L.items = m->d_items + H.item0;
-    L.nitems = H.nitem;
+    L.items = m->d_items[H.sched] + H.item0[H.sched];
+    L.nitems = H.nitem[H.sched];
+    L.ty = sched_tile_y(m->prec, H.sched);
     L.groups = m->d_groups + H.group0;
     L.ngroups = H.ngroup;
     L.cols = m->d_cols + H.col0;
@@ -337,48 +342,56 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
       return bail(e, "domain table copy");
     if ((e = cudaStreamSynchronize(m->st)) != cudaSuccess) return bail(e, "sync");
   }
-  // (domain, tile, z-chunk) work list of the full-cell stencil over each
-  // domain's computed region; z is split so that every SM gets several work
-  // items per launch (all domains of an ensemble share one launch, each level
-  // of a refined model has its own)
+  // (domain, tile, z-chunk) work lists of the full-cell stencil over each
+  // domain's computed region, one per schedule (tile height, items per
+  // launch): z is split so that every SM gets several work items per launch
+  // (all domains of an ensemble share one launch, each level of a refined
+  // model has its own)
   {
-    const int TILE_Y = full_tile_y(precision);
-    auto tiles_of = [&](const DomDev &D) {
-      return (long long)((D.ci1 - D.ci0 + 3 + TILE_X - 1) / TILE_X) * ((D.cj1 - D.cj0 + TILE_Y - 1) / TILE_Y);
-    };
-    long long all_tiles = 0;
-    for (auto &H : m->dom) all_tiles += tiles_of(H.D);
-    const long long want = 2 * 152;
-    std::vector<WorkItem> items;
     std::vector<ColItem> cols;
+    for (int sc = 0; sc < NSCHED; sc++) {
+      const int TY = sched_tile_y(precision, sc);
+      auto tiles_of = [&](const DomDev &D) {
+        return (long long)((D.ci1 - D.ci0 + 3 + TILE_X - 1) / TILE_X) * ((D.cj1 - D.cj0 + TY - 1) / TY);
+      };
+      long long all_tiles = 0;
+      for (auto &H : m->dom) all_tiles += tiles_of(H.D);
+      const long long want = SCHED_ITEMS[sc];
+      std::vector<WorkItem> items;
+      for (int d = 0; d < n; d++) {
+        DomHost &H = m->dom[d];
+        const DomDev &D = H.D;
+        long long tiles = m->refined ? tiles_of(D) : all_tiles;
+        long long splits = std::max(1LL, (want + tiles - 1) / tiles);
+        int chunk = (int)std::max(8LL, (D.ck1 + splits - 1) / splits);
+        H.item0[sc] = (int)items.size();
+        // tiles start at multiples of 4 in x (16-byte halo rows)
+        const int ib = D.ci0 - ((D.ci0 % 4) + 4) % 4;
+        for (int k0 = 0; k0 < D.ck1; k0 += chunk)
+          for (int j0 = D.cj0; j0 < D.cj1; j0 += TY)
+            for (int i0 = ib; i0 < D.ci1; i0 += TILE_X) {
+              WorkItem w{};
+              w.dom = d; w.i0 = i0; w.j0 = j0; w.k0 = k0; w.k1 = std::min(D.ck1, k0 + chunk);
+              items.push_back(w);
+            }
+        H.nitem[sc] = (int)items.size() - H.item0[sc];
+      }
+      m->nitems[sc] = (int)items.size();
+      if ((e = dalloc(m->allocs, &m->d_items[sc], sizeof(WorkItem) * items.size(), m->st)) != cudaSuccess)
+        return bail(e, "work list");
+      if ((e = cudaMemcpyAsync(m->d_items[sc], items.data(), sizeof(WorkItem) * items.size(),
+                               cudaMemcpyHostToDevice, m->st)) != cudaSuccess)
+        return bail(e, "work list copy");
+      if ((e = cudaStreamSynchronize(m->st)) != cudaSuccess) return bail(e, "sync");
+    }
     for (int d = 0; d < n; d++) {
       DomHost &H = m->dom[d];
       const DomDev &D = H.D;
-      long long tiles = m->refined ? tiles_of(D) : all_tiles;
-      long long splits = std::max(1LL, (want + tiles - 1) / tiles);
-      int chunk = (int)std::max(8LL, (D.ck1 + splits - 1) / splits);
-      H.item0 = (int)items.size();
-      // tiles start at multiples of 4 in x (16-byte halo rows)
-      const int ib = D.ci0 - ((D.ci0 % 4) + 4) % 4;
-      for (int k0 = 0; k0 < D.ck1; k0 += chunk)
-        for (int j0 = D.cj0; j0 < D.cj1; j0 += TILE_Y)
-          for (int i0 = ib; i0 < D.ci1; i0 += TILE_X) {
-            WorkItem w{};
-            w.dom = d; w.i0 = i0; w.j0 = j0; w.k0 = k0; w.k1 = std::min(D.ck1, k0 + chunk);
-            items.push_back(w);
-          }
-      H.nitem = (int)items.size() - H.item0;
       H.col0 = (int)cols.size();
       for (int J = D.qj0; J < D.cj1; J++)
         for (int I = D.qi0; I < D.ci1; I++) cols.push_back(ColItem{d, I, J, 0});
       H.ncol = (int)cols.size() - H.col0;
     }
-    m->nitems = (int)items.size();
-    if ((e = dalloc(m->allocs, &m->d_items, sizeof(WorkItem) * items.size(), m->st)) != cudaSuccess)
-      return bail(e, "work list");
-    if ((e = cudaMemcpyAsync(m->d_items, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice,
-                             m->st)) != cudaSuccess)
-      return bail(e, "work list copy");
     m->ncols = (int)cols.size();
     if ((e = dalloc(m->allocs, &m->d_cols, sizeof(ColItem) * cols.size(), m->st)) != cudaSuccess)
       return bail(e, "column list");
@@ -1021,6 +1034,79 @@ cc_status cc_refine_mass(cc_model *m, int both, double *out) {
   }
   *out = tot;
   return CC_OK;
+}
+
+cc_status cc_autotune(cc_model *m, int reps) {
+  if (!m) return fail(m, CC_EINVAL, "null model");
+  if (reps < 1 || reps > 100) return fail(m, CC_EINVAL, "reps must be 1 .. 100");
+  if (!m->state) return fail(m, CC_ESTATE, "state not initialised");
+  cudaEvent_t a = nullptr, b = nullptr;
+  CK(m, cudaEventCreate(&a), "event");
+  if (cudaEventCreate(&b) != cudaSuccess) {
+    cudaEventDestroy(a);
+    return fail(m, CC_ECUDA, "event");
+  }
+  cc_status res = CC_OK;
+  // launch groups: the whole ensemble, or each level of a refined model
+  const int ngroup = m->refined ? m->ndom : 1;
+  for (int g = 0; g < ngroup && res == CC_OK; g++) {
+    const int d = m->refined ? g : -1;
+    DomHost &H = m->dom[m->refined ? g : 0];
+    const int first = H.nsteps == 0;
+    const int rO = first ? H.r[1] : H.r[0], rC = H.r[1], rN = H.r[2], rF = H.r[3];
+    int best = 0;
+    float best_ms = 0;
+    for (int sc = 0; sc < NSCHED && res == CC_OK; sc++) {
+      if (m->refined) H.sched = sc;
+      else m->sched = sc;
+      StepLaunch L = make_launch(m, d);
+      // the stencil writes only the new and filtered levels, which the next
+      // step overwrites with the same values: timing it leaves the state alone
+      cudaError_t e = launch_full(L, m->prec, rO, rC, rN, rF, first, m->st);
+      if (e == cudaSuccess) e = cudaEventRecord(a, m->st);
+      for (int r = 0; r < reps && e == cudaSuccess; r++) e = launch_full(L, m->prec, rO, rC, rN, rF, first, m->st);
+      if (e == cudaSuccess) e = cudaEventRecord(b, m->st);
+      if (e == cudaSuccess) e = cudaEventSynchronize(b);
+      float ms = 0;
+      if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+      if (e != cudaSuccess) {
+        res = cuda_fail(m, e, "autotune");
+        break;
+      }
+      if (sc == 0 || ms < best_ms) {
+        best = sc;
+        best_ms = ms;
+      }
+    }
+    if (m->refined) H.sched = best;
+    else m->sched = best;
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (res == CC_OK) m->tuned = true;
+  return res;
+}
+
+cc_status cc_get_schedule(const cc_model *mc, int d, int *tile_y, int *items_per_launch) {
+  cc_model *m = const_cast<cc_model *>(mc);
+  if (!m || !tile_y || !items_per_launch) return fail(m, CC_EINVAL, "null argument");
+  if (d < 0 || d >= m->ndom) return fail(m, CC_EINVAL, "domain index out of range");
+  const int sc = m->refined ? m->dom[d].sched : m->sched;
+  *tile_y = sched_tile_y(m->prec, sc);
+  *items_per_launch = SCHED_ITEMS[sc];
+  return CC_OK;
+}
+
+cc_status cc_set_schedule(cc_model *m, int d, int tile_y, int items_per_launch) {
+  if (!m) return fail(m, CC_EINVAL, "null model");
+  if (d < 0 || d >= m->ndom) return fail(m, CC_EINVAL, "domain index out of range");
+  for (int sc = 0; sc < NSCHED; sc++)
+    if (sched_tile_y(m->prec, sc) == tile_y && SCHED_ITEMS[sc] == items_per_launch) {
+      if (m->refined) m->dom[d].sched = sc;
+      else m->sched = sc;
+      return CC_OK;
+    }
+  return fail(m, CC_EINVAL, "no such schedule");
 }
 
 cc_status cc_synchronize(cc_model *m) {

@@ -16,7 +16,13 @@ constexpr int HOST_GZ = 2;     // corner levels below floor / above lid in host 
 constexpr int NFIELD = 5;      // rho', p', rho u, rho v, rho w
 constexpr int NBUF = 4;        // rotating time levels
 constexpr int TILE_X = 32;                          // full-cell stencil tile width (x)
-constexpr int TILE_Y_F32 = 16, TILE_Y_F64 = 8;     // tile height (y) per precision
+// full-cell stencil schedules: tile height (y) and the number of work items
+// to aim for per launch (the z-chunk length follows); the autotuner times them
+// on the model's own state and keeps the fastest per launch group
+constexpr int NSCHED = 4;
+constexpr int SCHED_TY_F32[NSCHED] = {16, 8, 16, 8};
+constexpr int SCHED_TY_F64[NSCHED] = {8, 4, 8, 4};
+constexpr int SCHED_ITEMS[NSCHED] = {2 * 152, 2 * 152, 6 * 152, 6 * 152};
 
 // cell classes and corner classes
 enum : int8_t { C_UG = 0, C_FULL = 1, C_CUT = 2, C_ABS = 3 };
@@ -172,6 +178,7 @@ struct StepLaunch {
   long long ghost_points;  // lateral ghost points over all domains (per level and field)
   const long long *ghost_off;  // per-domain prefix of ghost points (device)
   Eos eos;
+  int ty;                  // tile height of the work items
 };
 cudaError_t launch_base(const DomDev &D, int prec, double theta0, double N, double p_surf,
                         double sponge_frac, double tau_max, cudaStream_t st);
@@ -181,7 +188,7 @@ cudaError_t launch_groups(const StepLaunch &L, int prec, int rO, int rC, int rN,
                           cudaStream_t st);
 cudaError_t launch_diagnose(const StepLaunch &L, int prec, int rV, int rC, int rO, int rF, int first,
                             int filter, cudaStream_t st);
-int full_tile_y(int prec);
+int sched_tile_y(int prec, int s);
 cudaError_t launch_init_momentum(const DomDev &D, const DomDev *d_dom, int prec, int r, double U,
                                  cudaStream_t st);
 cudaError_t launch_diag_reduce(const DomDev &D, const DomDev *d_dom, int prec, int r, double *d_out,

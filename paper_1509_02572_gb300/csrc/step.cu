@@ -283,8 +283,15 @@ __device__ __forceinline__ void await_groups() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
+// blocks per SM the register budget is sized for: FP32 tiles of 256 threads
+// run two per SM (128 registers), everything else one
 template <typename T, int TYv>
-__global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict__ doms,
+struct FullOcc {
+  static constexpr int MINB = (sizeof(T) == 4 && TILE_X * TYv <= 256) ? 2 : 1;
+};
+
+template <typename T, int TYv>
+__global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(const DomDev *__restrict__ doms,
                                                         const WorkItem *__restrict__ items, int rO, int rC,
                                                         int rN, int rF, int first, const Eos E) {
   using A = Ar<T>;
@@ -333,35 +340,42 @@ __global__ void __launch_bounds__(TILE_X * TYv) k_full(const DomDev *__restrict_
     kbv[s] = p < PL ? D.kb[loff[s]] : KB_NONE;
   }
   // 16-byte chunks of the haloed rows (i0 is a multiple of 4, so a row of the
-  // tile starts on a 16-byte boundary): this thread copies chunk tid of each
-  // field, whole where it lies inside the row, element by element (wrapped or
-  // clamped) where it crosses the periodic seam or the end of the padding
-  constexpr int VEC = 16 / sizeof(T), CPR = HX / VEC, NCH = CPR * C::HY;
+  // tile starts on a 16-byte boundary): this thread copies chunks tid,
+  // tid + NT, .. of each field, whole where a chunk lies inside the row,
+  // element by element (wrapped or clamped) where it crosses the periodic
+  // seam or the end of the padding
+  constexpr int VEC = 16 / sizeof(T), CPR = HX / VEC, NCH = CPR * C::HY, NCQ = (NCH + NT - 1) / NT;
   static_assert(HX % VEC == 0, "halo rows are whole chunks");
-  static_assert(NCH <= NT, "one chunk per thread and field");
-  const bool has_chunk = tid < NCH;
-  const int ch_row = tid / CPR, ch_col = tid % CPR;
-  const int ch_x = i0 - 2 + VEC * ch_col;
-  const int ch_dst = ch_row * HX + VEC * ch_col;
-  const int ch_rowoff = (row_y(j0 - 2 + ch_row) + GH) * px;
-  const bool ch_whole = D.periodic ? (ch_x >= 0 && ch_x + VEC <= nx) : (ch_x >= -GX && ch_x + VEC <= px - GX);
-  int ch_e[VEC];  // in-plane offsets of the elements of a chunk copied one by one
+  int ch_dst[NCQ], ch_e[NCQ][VEC];  // destination, and source offsets of the elements
+  bool ch_whole[NCQ];
 #pragma unroll
-  for (int e = 0; e < VEC; e++) ch_e[e] = ch_rowoff + col_x(ch_x + e) + GX;
+  for (int q = 0; q < NCQ; q++) {
+    const int t = tid + q * NT;
+    const int row = t / CPR, col = t % CPR;
+    const int x = i0 - 2 + VEC * col;
+    const int rowoff = (row_y(j0 - 2 + row) + GH) * px;
+    ch_dst[q] = t < NCH ? row * HX + VEC * col : -1;
+    ch_whole[q] = D.periodic ? (x >= 0 && x + VEC <= nx) : (x >= -GX && x + VEC <= px - GX);
+#pragma unroll
+    for (int e = 0; e < VEC; e++) ch_e[q][e] = rowoff + col_x(x + e) + GX;
+  }
   const T *__restrict__ ubC = (const T *)D.ub[rC];
   const int kmaxp = D.pz - GH - 1;  // highest plane inside the padding
   auto chunk = [&](T *dst, const T *src) {
-    if (ch_whole) {
-      acopy16(dst + ch_dst, src + ch_e[0]);
-    } else {
 #pragma unroll
-      for (int e = 0; e < VEC; e++) acopy(dst + ch_dst + e, src + ch_e[e]);
+    for (int q = 0; q < NCQ; q++) {
+      if (ch_dst[q] < 0) continue;
+      if (ch_whole[q]) {
+        acopy16(dst + ch_dst[q], src + ch_e[q][0]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VEC; e++) acopy(dst + ch_dst[q] + e, src + ch_e[q][e]);
+      }
     }
   };
   // asynchronous copies of the raw fields of plane kk: the current-level
   // momentum when with_m (its ring has four slots), the n-1 fields when with_o
   auto issue = [&](int kk, bool with_m, bool with_o) {
-    if (!has_chunk) return;
     const long long zo = (long long)(min(kk, kmaxp) + GH) * plane;  // planes past the top are never used
     const int a5 = s5(kk), a4 = s4(kk);
     chunk(S.cr[a5], rpC + zo);
@@ -1236,7 +1250,7 @@ cudaError_t groups_t(const StepLaunch &L, int rO, int rC, int rN, int rF, int fi
 }
 }  // namespace
 
-int full_tile_y(int prec) { return prec == CC_FP64 ? TILE_Y_F64 : TILE_Y_F32; }
+int sched_tile_y(int prec, int s) { return prec == CC_FP64 ? SCHED_TY_F64[s] : SCHED_TY_F32[s]; }
 
 cudaError_t launch_base(const DomDev &D, int prec, double theta0, double N, double p_surf, double sponge_frac,
                         double tau_max, cudaStream_t st) {
@@ -1254,8 +1268,14 @@ cudaError_t launch_base(const DomDev &D, int prec, double theta0, double N, doub
 
 cudaError_t launch_full(const StepLaunch &L, int prec, int rO, int rC, int rN, int rF, int first,
                         cudaStream_t st) {
-  return prec == CC_FP64 ? full_t<double, TILE_Y_F64>(L, rO, rC, rN, rF, first, st)
-                         : full_t<float, TILE_Y_F32>(L, rO, rC, rN, rF, first, st);
+  if (prec == CC_FP64) {
+    if (L.ty == 8) return full_t<double, 8>(L, rO, rC, rN, rF, first, st);
+    if (L.ty == 4) return full_t<double, 4>(L, rO, rC, rN, rF, first, st);
+  } else {
+    if (L.ty == 16) return full_t<float, 16>(L, rO, rC, rN, rF, first, st);
+    if (L.ty == 8) return full_t<float, 8>(L, rO, rC, rN, rF, first, st);
+  }
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_groups(const StepLaunch &L, int prec, int rO, int rC, int rN, int rF, int first,

@@ -26,7 +26,8 @@ EXPORTS = ("cc_create", "cc_destroy", "cc_last_error", "cc_set_terrain", "cc_bui
            "cc_get_geometry", "cc_get_stencils", "cc_get_groups", "cc_init_state", "cc_upload_state",
            "cc_download_state", "cc_step", "cc_diagnostics", "cc_synchronize", "cc_last_launch_count",
            "cc_profile_enable", "cc_profile_read", "cc_profile_reset", "cc_create_refined",
-           "cc_refine_mass", "cc_domain_count", "cc_mass_sum_noalloc", "cc_noalloc_last_error")
+           "cc_refine_mass", "cc_domain_count", "cc_autotune", "cc_get_schedule", "cc_set_schedule",
+           "cc_mass_sum_noalloc", "cc_noalloc_last_error")
 CC_NOALLOC_MAX_PARTS = 1024
 CC_K_FULL, CC_K_GROUPS, CC_K_DIAGNOSE, CC_K_GHOST, CC_K_REFINE = range(5)
 KERNEL_NAMES = {CC_K_FULL: "k_full", CC_K_GROUPS: "k_groups", CC_K_DIAGNOSE: "k_diag", CC_K_GHOST: "k_ghost",
@@ -96,6 +97,9 @@ def load(path: str = LIB_PATH):
     L.cc_refine_mass.argtypes = [vp, i, ct.POINTER(d)]
     L.cc_domain_count.restype = i
     L.cc_domain_count.argtypes = [vp]
+    L.cc_autotune.argtypes = [vp, i]
+    L.cc_get_schedule.argtypes = [vp, i, ct.POINTER(i), ct.POINTER(i)]
+    L.cc_set_schedule.argtypes = [vp, i, i, i]
     L.cc_mass_sum_noalloc.argtypes = [vp, i, vp, ct.c_longlong, i, vp, vp]
     L.cc_noalloc_last_error.restype = ct.c_char_p
     L.cc_noalloc_last_error.argtypes = []
@@ -269,6 +273,20 @@ class Model:
 
     def profile_reset(self):
         self._check(self.L.cc_profile_reset(self.h))
+
+    def autotune(self, reps: int = 3) -> list:
+        """Time every full-cell schedule on the current state and keep the
+        fastest (per level of a refined model); returns the schedules."""
+        self._check(self.L.cc_autotune(self.h, int(reps)))
+        return [self.schedule(d) for d in range(len(self.cfgs))]
+
+    def schedule(self, d: int = 0) -> tuple:
+        ty, items = ct.c_int(), ct.c_int()
+        self._check(self.L.cc_get_schedule(self.h, d, ct.byref(ty), ct.byref(items)))
+        return ty.value, items.value
+
+    def set_schedule(self, d: int, tile_y: int, items_per_launch: int):
+        self._check(self.L.cc_set_schedule(self.h, d, int(tile_y), int(items_per_launch)))
 
     def profile_read(self, kernel: int):
         ms, n = ct.c_double(), ct.c_longlong()

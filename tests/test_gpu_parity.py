@@ -242,3 +242,39 @@ def test_v_shaped_valley_is_a_geometry_error(cc, oracle_mod):
         m.build_geometry()
     assert e.value.status == cc.CC_EGEOM
     m.close()
+
+
+def test_schedules_give_identical_bits_and_autotune_keeps_state(cc):
+    """Every full-cell schedule (tile height, items per launch) distributes
+    the same arithmetic: the states agree bit for bit; timing the schedules
+    leaves the state unchanged."""
+    a = W.SMALL_HEMI
+    b = W.C1_BELL.replace(nx=48, ny=40, nz=20, U=7.0, N=0.012, dt=0.12)
+    for prec, tys in ((cc.CC_FP32, (16, 8)), (cc.CC_FP64, (8, 4))):
+        ref = None
+        for ty in tys:
+            for items in (304, 912):
+                m = gpu_model(cc, [a, b], prec)
+                m.init_state()
+                m.set_schedule(0, ty, items)
+                assert m.schedule(0) == (ty, items)
+                m.step(7)
+                out = [m.download(d, f) for d in range(2) for f in (cc.CC_RHOP, cc.CC_PP, cc.CC_MX, cc.CC_MZ)]
+                if ref is None:
+                    ref = out
+                else:
+                    for x, y in zip(out, ref):
+                        assert np.array_equal(x, y), (prec, ty, items)
+                m.close()
+        m = gpu_model(cc, [a, b], prec)
+        m.init_state()
+        m.step(3)
+        m.autotune(2)
+        assert m.schedule(0)[0] in tys
+        m.step(4)
+        out = [m.download(d, f) for d in range(2) for f in (cc.CC_RHOP, cc.CC_PP, cc.CC_MX, cc.CC_MZ)]
+        for x, y in zip(out, ref):
+            assert np.array_equal(x, y), (prec, "autotuned")
+        with pytest.raises(cc.CutcellError):
+            m.set_schedule(0, 5, 304)
+        m.close()

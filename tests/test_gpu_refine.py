@@ -195,3 +195,23 @@ def test_refined_error_paths(cc):
         m.build_geometry()
     assert e.value.status == cc.CC_EGEOM
     m.close()
+
+
+def test_refined_autotune_per_level_keeps_bits(cc):
+    """Each level picks its own schedule; the result is the same bits as the
+    default schedules."""
+    m = gpu_refined(cc, RC, cc.CC_FP32)
+    m.init_state()
+    m.step(3)
+    ref = [m.download(l, f) for l in range(m.nlev) for f in (cc.CC_RHOP, cc.CC_PP, cc.CC_MX)]
+    m.close()
+    m = gpu_refined(cc, RC, cc.CC_FP32)
+    m.init_state()
+    m.step(1)
+    sched = m.autotune(2)
+    assert len(sched) == m.nlev and all(s[0] in (16, 8) for s in sched)
+    m.step(2)
+    out = [m.download(l, f) for l in range(m.nlev) for f in (cc.CC_RHOP, cc.CC_PP, cc.CC_MX)]
+    for x, y in zip(out, ref):
+        assert np.array_equal(x, y)
+    m.close()
