@@ -152,6 +152,14 @@ cc_status cc_download_state(const cc_model *m, int d, int field, int level, doub
  * cc_init_state is forward Euler).  Asynchronous on the model's stream. */
 cc_status cc_step(cc_model *m, int n);
 
+/* CUDA graphs (no counterpart in the paper): with graphs on (the default),
+ * cc_step captures the launches of one step (one cycle of level 0 of a
+ * refined model) once per arrangement of time levels and schedules, on a
+ * private stream, and replays the graph on the model's stream; the results
+ * are the same bits as launching the kernels one by one.  Forward-Euler
+ * starts and steps taken with profiling on always launch directly. */
+cc_status cc_graphs_enable(cc_model *m, int on);
+
 /* Diagnostics of domain d at the current level; synchronises the stream.
  * Returns CC_ENUMERIC when non-finite values are present. */
 cc_status cc_diagnostics(cc_model *m, int d, cc_diag *out);

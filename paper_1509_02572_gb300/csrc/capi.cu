@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -56,6 +57,18 @@ struct cc_model {
   int nitems[NSCHED] = {};
   int sched = 0;                   // schedule of the ensemble launch
   bool tuned = false;
+  // CUDA graphs of one step (one cycle of level 0 for a refined model), keyed
+  // by the time-level roles and schedules of every domain; captured on a
+  // private stream, launched on the model's stream
+  struct GraphEnt {
+    std::vector<int> key;
+    cudaGraphExec_t exec = nullptr;
+    long long launches = 0;
+  };
+  std::vector<GraphEnt> graphs;
+  bool graphs_on = true;
+  bool dry = false;  // bookkeeping only (roles, step counts): the graph does the work
+  cudaStream_t cap = nullptr;
   GroupRec *d_groups = nullptr;
   int ngroups = 0;
   int32_t *d_members = nullptr;
@@ -250,6 +263,7 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
     return fail(nullptr, ee == cudaErrorMemoryAllocation ? CC_ENOMEM : CC_ECUDA, msg);
   };
   size_t max_stage = 16;
+  if ((e = full_prepare(precision)) != cudaSuccess) return bail(e, "kernel attributes");
   for (int d = 0; d < n; d++) {
     DomHost &H = m->dom[d];
     H.cfg = cfgs[d];
@@ -583,6 +597,8 @@ cc_status cc_destroy(cc_model *m) {
     cudaEventDestroy(e.b);
   }
   for (auto e : m->ev_pool) cudaEventDestroy(e);
+  for (auto &g : m->graphs) cudaGraphExecDestroy(g.exec);
+  if (m->cap) cudaStreamDestroy(m->cap);
   delete m;
   return CC_OK;
 }
@@ -896,6 +912,7 @@ static cudaEvent_t ev_get(cc_model *m) {
 // launch one stage, bracketed by events when profiling is on
 template <typename F>
 static cudaError_t timed(cc_model *m, int kid, F &&launch) {
+  if (m->dry) return cudaSuccess;
   if (!m->prof) return launch();
   cudaEvent_t a = ev_get(m), b = ev_get(m);
   if (!a || !b) return cudaErrorMemoryAllocation;
@@ -982,15 +999,94 @@ static cc_status cycle(cc_model *m, int l, long long &nl) {
 
 extern "C" {
 
+static cc_status one_step(cc_model *m, long long &nl) { return m->refined ? cycle(m, 0, nl) : step_domains(m, -1, nl); }
+
+static std::vector<int> graph_key(const cc_model *m) {
+  std::vector<int> k;
+  k.push_back(m->sched);
+  for (const auto &H : m->dom) {
+    for (int a = 0; a < 4; a++) k.push_back(H.r[a]);
+    k.push_back(H.sched);
+  }
+  return k;
+}
+
+// One step through a CUDA graph: the launches of the step are captured once
+// per key on the private stream and replayed on the model's stream; a replay
+// advances the host bookkeeping without launching.
+static cc_status graph_step(cc_model *m, long long &nl) {
+  const std::vector<int> key = graph_key(m);
+  for (auto &g : m->graphs)
+    if (g.key == key) {
+      m->dry = true;
+      long long dummy = 0;
+      cc_status r = one_step(m, dummy);
+      m->dry = false;
+      if (r != CC_OK) return r;
+      CK(m, cudaGraphLaunch(g.exec, m->st), "graph launch");
+      nl += g.launches;
+      return CC_OK;
+    }
+  if (!m->cap) CK(m, cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking), "capture stream");
+  // the capture stream starts after the work already queued on the model's stream
+  std::vector<std::array<int, 4>> roles;
+  std::vector<long long> steps;
+  for (const auto &H : m->dom) {
+    roles.push_back({H.r[0], H.r[1], H.r[2], H.r[3]});
+    steps.push_back(H.nsteps);
+  }
+  auto restore = [&]() {
+    for (size_t d = 0; d < m->dom.size(); d++) {
+      for (int a = 0; a < 4; a++) m->dom[d].r[a] = roles[d][a];
+      m->dom[d].nsteps = steps[d];
+    }
+  };
+  cudaStream_t saved = m->st;
+  CK(m, cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal), "begin capture");
+  m->st = m->cap;
+  long long cl = 0;
+  cc_status r = one_step(m, cl);
+  m->st = saved;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(m->cap, &graph);
+  if (r != CC_OK || e != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    restore();
+    return r != CC_OK ? r : cuda_fail(m, e, "end capture");
+  }
+  cudaGraphExec_t exec = nullptr;
+  e = cudaGraphInstantiate(&exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    restore();
+    return cuda_fail(m, e, "graph instantiate");
+  }
+  m->graphs.push_back({key, exec, cl});
+  CK(m, cudaGraphLaunch(exec, m->st), "graph launch");
+  nl += cl;
+  return CC_OK;
+}
+
 cc_status cc_step(cc_model *m, int n) {
   if (!m) return fail(m, CC_EINVAL, "null model");
   if (n < 0) return fail(m, CC_EINVAL, "negative step count");
   if (!m->state) return fail(m, CC_ESTATE, "state not initialised");
   long long nl = 0;
   cc_status r = CC_OK;
-  for (int s = 0; s < n && r == CC_OK; s++) r = m->refined ? cycle(m, 0, nl) : step_domains(m, -1, nl);
+  for (int s = 0; s < n && r == CC_OK; s++) {
+    // forward-Euler starts and profiled steps run eagerly
+    bool graph = m->graphs_on && !m->prof;
+    for (const auto &H : m->dom) graph = graph && H.nsteps > 0;
+    r = graph ? graph_step(m, nl) : one_step(m, nl);
+  }
   m->last_launches = nl;
   return r;
+}
+
+cc_status cc_graphs_enable(cc_model *m, int on) {
+  if (!m) return fail(m, CC_EINVAL, "null model");
+  m->graphs_on = on != 0;
+  return CC_OK;
 }
 
 cc_status cc_diagnostics(cc_model *m, int d, cc_diag *out) {

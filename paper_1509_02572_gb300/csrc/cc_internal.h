@@ -189,6 +189,8 @@ cudaError_t launch_groups(const StepLaunch &L, int prec, int rO, int rC, int rN,
 cudaError_t launch_diagnose(const StepLaunch &L, int prec, int rV, int rC, int rO, int rF, int first,
                             int filter, cudaStream_t st);
 int sched_tile_y(int prec, int s);
+// shared-memory limits of every full-cell kernel variant (before any capture)
+cudaError_t full_prepare(int prec);
 cudaError_t launch_init_momentum(const DomDev &D, const DomDev *d_dom, int prec, int r, double U,
                                  cudaStream_t st);
 cudaError_t launch_diag_reduce(const DomDev &D, const DomDev *d_dom, int prec, int r, double *d_out,

@@ -1252,6 +1252,19 @@ cudaError_t groups_t(const StepLaunch &L, int rO, int rC, int rN, int rF, int fi
 
 int sched_tile_y(int prec, int s) { return prec == CC_FP64 ? SCHED_TY_F64[s] : SCHED_TY_F32[s]; }
 
+cudaError_t full_prepare(int prec) {
+  auto set = [](auto kern, size_t bytes) {
+    return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  };
+  cudaError_t e;
+  if (prec == CC_FP64) {
+    if ((e = set(k_full<double, 8>, full_smem<double, 8>())) != cudaSuccess) return e;
+    return set(k_full<double, 4>, full_smem<double, 4>());
+  }
+  if ((e = set(k_full<float, 16>, full_smem<float, 16>())) != cudaSuccess) return e;
+  return set(k_full<float, 8>, full_smem<float, 8>());
+}
+
 cudaError_t launch_base(const DomDev &D, int prec, double theta0, double N, double p_surf, double sponge_frac,
                         double tau_max, cudaStream_t st) {
   unsigned nb = (unsigned)((D.pz + 127) / 128);

@@ -27,6 +27,7 @@ EXPORTS = ("cc_create", "cc_destroy", "cc_last_error", "cc_set_terrain", "cc_bui
            "cc_download_state", "cc_step", "cc_diagnostics", "cc_synchronize", "cc_last_launch_count",
            "cc_profile_enable", "cc_profile_read", "cc_profile_reset", "cc_create_refined",
            "cc_refine_mass", "cc_domain_count", "cc_autotune", "cc_get_schedule", "cc_set_schedule",
+           "cc_graphs_enable",
            "cc_mass_sum_noalloc", "cc_noalloc_last_error")
 CC_NOALLOC_MAX_PARTS = 1024
 CC_K_FULL, CC_K_GROUPS, CC_K_DIAGNOSE, CC_K_GHOST, CC_K_REFINE = range(5)
@@ -98,6 +99,7 @@ def load(path: str = LIB_PATH):
     L.cc_domain_count.restype = i
     L.cc_domain_count.argtypes = [vp]
     L.cc_autotune.argtypes = [vp, i]
+    L.cc_graphs_enable.argtypes = [vp, i]
     L.cc_get_schedule.argtypes = [vp, i, ct.POINTER(i), ct.POINTER(i)]
     L.cc_set_schedule.argtypes = [vp, i, i, i]
     L.cc_mass_sum_noalloc.argtypes = [vp, i, vp, ct.c_longlong, i, vp, vp]
@@ -279,6 +281,9 @@ class Model:
         fastest (per level of a refined model); returns the schedules."""
         self._check(self.L.cc_autotune(self.h, int(reps)))
         return [self.schedule(d) for d in range(len(self.cfgs))]
+
+    def graphs(self, on: bool = True):
+        self._check(self.L.cc_graphs_enable(self.h, 1 if on else 0))
 
     def schedule(self, d: int = 0) -> tuple:
         ty, items = ct.c_int(), ct.c_int()

@@ -215,3 +215,19 @@ def test_refined_autotune_per_level_keeps_bits(cc):
     for x, y in zip(out, ref):
         assert np.array_equal(x, y)
     m.close()
+
+
+def test_refined_graph_replay_equals_direct_launches(cc):
+    outs = []
+    for on in (False, True):
+        m = gpu_refined(cc, RC, cc.CC_FP32)
+        m.graphs(on)
+        m.init_state()
+        for _ in range(6):
+            m.step(1)
+        launches = m.last_launch_count
+        outs.append([m.download(l, f) for l in range(m.nlev) for f in (cc.CC_RHOP, cc.CC_PP, cc.CC_MX, cc.CC_MZ)])
+        m.close()
+        assert launches > 20
+    for x, y in zip(*outs):
+        assert np.array_equal(x, y)
