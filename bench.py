@@ -190,6 +190,21 @@ def time_steps(torch, model, steps, warmup):
     return e0.elapsed_time(e1), launches
 
 
+def time_graphs(torch, model, steps):
+    """The same steps replayed from CUDA graphs, without per-stage events."""
+    model.profile(False)
+    model.graphs(True)
+    model.step(4)  # capture the four arrangements of the time levels
+    model.synchronize()
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    model.step(steps)
+    e1.record(st)
+    e1.synchronize()
+    return e0.elapsed_time(e1) / steps
+
+
 def cpu_baseline(cfgs, seconds):
     """The FP64 oracle as it stands on the host cores, on a bounded sample of
     the workload: whole instances, stepped until about `seconds` of CPU work."""
@@ -261,12 +276,15 @@ def bench_refined(cc, torch, args, hbm, peak_kind, barrier, world):
     kms, kn = m.profile_read(cc.CC_K_FULL)
     stages = {cc.KERNEL_NAMES[k]: dict(zip(("ms_total", "launches"), m.profile_read(k))) for k in range(5)}
     m.profile(False)
+    gms = time_graphs(torch, m, args.steps)
     kbytes = refined_kfull_bytes(m, "f32") * args.steps
     achieved = kbytes / (kms / 1e3) / 1e9
     out = {"workload": rc.name, "levels": [list(b) for b in rc.boxes], "value": upd * args.steps * world / (ms / 1e3),
            "schedule": [list(m.schedule(l)) for l in range(m.nlev)],
            "unit": METRIC, "ms_per_step": ms / args.steps, "cell_updates_per_step": upd, "dtype": "f32",
            "gpu_launches": launches, "clocks": clk, "stages": stages,
+           "graphs": {"ms_per_step": gms, "value": upd * world / (gms / 1e3), "unit": METRIC,
+                      "how": "the same cycles replayed from CUDA graphs, no per-stage events"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
                         "traffic": None, "kernel": "k_full", "kernel_ms": kms / max(1, kn), "launches": kn,
                         "peak_kind": f"{peak_kind} hbm_gbs",
@@ -284,7 +302,8 @@ def bench_refined(cc, torch, args, hbm, peak_kind, barrier, world):
         e1.record(st)
         e1.synchronize()
         ms64 = e0.elapsed_time(e1)
-        m64.step(args.steps - ks)
+        n32 = int(m.diagnostics(0, check=False)["steps"])  # steps the FP32 model has taken
+        m64.step(n32 - args.warmup - ks)
         errs = {}
         for fname, f in (("rho'", cc.CC_RHOP), ("p'", cc.CC_PP), ("rho u", cc.CC_MX), ("rho v", cc.CC_MY),
                          ("rho w", cc.CC_MZ)):
@@ -299,7 +318,7 @@ def bench_refined(cc, torch, args, hbm, peak_kind, barrier, world):
                            "rel_linf": linf / scale if scale > 0 else 0.0}
         out["fp64_plain"] = {"value": upd * ks / (ms64 / 1e3), "unit": METRIC, "dtype": "f64",
                              "ms_per_step": ms64 / ks, "steps": ks}
-        out["l2_error"] = {"vs": "plain FP64 GPU form", "after_steps": args.warmup + args.steps, "fields": errs}
+        out["l2_error"] = {"vs": "plain FP64 GPU form", "after_steps": n32, "fields": errs}
         m64.close()
     m.close()
     return out
@@ -430,6 +449,7 @@ def main():
     kfull_ms, kfull_n = model.profile_read(cc.CC_K_FULL)
     stage = {cc.KERNEL_NAMES[k]: model.profile_read(k) for k in range(5)}
     model.profile(False)
+    gms = time_graphs(torch, model, args.steps)
     t = torch.tensor([ms], device="cuda")
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -451,7 +471,9 @@ def main():
                                                             if dtype == "f32" else "fp64"),
                        "l2": "inputs larger than L2 (state of all domains)" if ninterior * 80 > 129e6 else
                        "working set may fit in L2"},
-            "gpu_launches": launches, "roofline": roof, "stages": stages, "clocks": clk}
+            "gpu_launches": launches, "roofline": roof, "stages": stages, "clocks": clk,
+            "graphs": {"ms_per_step": gms, "value": nfluid * world / (gms / 1e3), "unit": METRIC,
+                       "how": "the same steps replayed from CUDA graphs, no per-stage events"}}
 
     # ---- plain FP64 form on the same workload, one domain at a time
     if not args.no_fp64 and args.workload == "ensemble":
@@ -472,7 +494,7 @@ def main():
         v64 = nfluid * ksteps / (ms64 / 1e3)
         # error of the FP32 batched state against the FP64 runs after the same
         # number of steps (both started from the same initial state)
-        n32 = args.warmup + args.steps
+        n32 = int(model.diagnostics(0, check=False)["steps"])  # steps the FP32 model has taken
         n64 = args.warmup + ksteps
         for s in singles:
             s.step(n32 - n64)
