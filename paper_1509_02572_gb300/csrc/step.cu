@@ -454,6 +454,7 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
   const long long own = active ? (long long)(j + GH) * px + (i + GX) : 0;
   const T qdx = (T)(0.25 / D.dx), qdy = (T)(0.25 / D.dy), qdz = (T)(0.25 / D.dz);  // 1/4 of the pressure-gradient quotient
   const T Sx = (T)(D.dy * D.dz), Sy = (T)(D.dx * D.dz), Sz = (T)(D.dx * D.dy);
+  const T hSx = (T)(0.25 * D.dy * D.dz), hSy = (T)(0.25 * D.dx * D.dz), hSz = (T)(0.25 * D.dx * D.dy);
   const T v0inv = (T)(1.0 / (D.dx * D.dy * D.dz));
   const T kdif = (T)D.kdif, Cp = (T)D.Cp, g = (T)D.g, U = (T)D.U;
   const int kug = active ? D.kug[qidx(D, i, j)] : 0;
@@ -493,6 +494,7 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
   velocity(k0 - 1);
   velocity(k0);
 
+  T fz_carry = 0, hz_carry = 0;  // high z-face fluxes of the previous plane
   for (int k = k0; k < k1; k++) {
     // phase 1: wait for plane k+2; once every thread is past the previous
     // plane (the barrier), the ring slots it read last are free and the
@@ -524,14 +526,18 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
       T fxp = face_flux(R0[c], R0[c + 1], ux0[c + 1], ux0[c + 1 + HX], uxp[c + 1], uxp[c + 1 + HX], Sx);
       T fym = face_flux(R0[c - HX], R0[c], uy0[c], uy0[c + 1], uyp[c], uyp[c + 1], Sy);
       T fyp = face_flux(R0[c], R0[c + HX], uy0[c + HX], uy0[c + HX + 1], uyp[c + HX], uyp[c + HX + 1], Sy);
-      T fzm = face_flux(Rm[c], R0[c], uz0[c], uz0[c + 1], uz0[c + HX], uz0[c + HX + 1], Sz);
+      // the low z-face of this cell is the high z-face of the cell below,
+      // computed on the previous plane from the same values (same bits)
+      T fzm = k > k0 ? fz_carry : face_flux(Rm[c], R0[c], uz0[c], uz0[c + 1], uz0[c + HX], uz0[c + HX + 1], Sz);
       T fzp = face_flux(R0[c], Rp[c], uzp[c], uzp[c + 1], uzp[c + HX], uzp[c + HX + 1], Sz);
       T hxm = face_flux(H0[c - 1], H0[c], ux0[c], ux0[c + HX], uxp[c], uxp[c + HX], Sx);
       T hxp = face_flux(H0[c], H0[c + 1], ux0[c + 1], ux0[c + 1 + HX], uxp[c + 1], uxp[c + 1 + HX], Sx);
       T hym = face_flux(H0[c - HX], H0[c], uy0[c], uy0[c + 1], uyp[c], uyp[c + 1], Sy);
       T hyp = face_flux(H0[c], H0[c + HX], uy0[c + HX], uy0[c + HX + 1], uyp[c + HX], uyp[c + HX + 1], Sy);
-      T hzm = face_flux(Hm[c], H0[c], uz0[c], uz0[c + 1], uz0[c + HX], uz0[c + HX + 1], Sz);
+      T hzm = k > k0 ? hz_carry : face_flux(Hm[c], H0[c], uz0[c], uz0[c + 1], uz0[c + HX], uz0[c + HX + 1], Sz);
       T hzp = face_flux(H0[c], Hp[c], uzp[c], uzp[c + 1], uzp[c + HX], uzp[c + HX + 1], Sz);
+      fz_carry = fzp;
+      hz_carry = hzp;
       if (k == 0) { fzm = 0; hzm = 0; }                  // floor
       if (D.lid && k == nz - 1) { fzp = 0; hzp = 0; }    // rigid lid
       T RM = A::add(A::add(A::sub(fxp, fxm), A::sub(fyp, fym)), A::sub(fzp, fzm));
@@ -560,12 +566,15 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
       ((T *)D.f[rF][1])[o] = pF_;
 
       // ---- velocity cell centred on corner (i,j,K=k): Eqs. momentum_u_d .. w_d
-      T rE = (Rm[c - HX] + Rm[c] + R0[c - HX] + R0[c]) * T(0.25);
-      T rW = (Rm[c - HX - 1] + Rm[c - 1] + R0[c - HX - 1] + R0[c - 1]) * T(0.25);
-      T rNn = (Rm[c - 1] + Rm[c] + R0[c - 1] + R0[c]) * T(0.25);
-      T rS = (Rm[c - HX - 1] + Rm[c - HX] + R0[c - HX - 1] + R0[c - HX]) * T(0.25);
-      T rT = (R0[c - HX - 1] + R0[c - HX] + R0[c - 1] + R0[c]) * T(0.25);
-      T rB = (Rm[c - HX - 1] + Rm[c - HX] + Rm[c - 1] + Rm[c]) * T(0.25);
+      // face densities and pressures of the velocity cell: means over the 4
+      // cells touching each face, from the vertical pair sums of the 4
+      // cell columns around the corner
+      const int cW = c - 1, cS = c - HX, cSW = c - HX - 1;
+      const T v00 = Rm[cSW] + R0[cSW], v10 = Rm[cS] + R0[cS], v01 = Rm[cW] + R0[cW], v11 = Rm[c] + R0[c];
+      const T rE = (v10 + v11) * T(0.25), rW = (v00 + v01) * T(0.25);
+      const T rNn = (v01 + v11) * T(0.25), rS = (v00 + v10) * T(0.25);
+      const T rT = ((R0[cSW] + R0[cS]) + (R0[cW] + R0[c])) * T(0.25);
+      const T rB = ((Rm[cSW] + Rm[cS]) + (Rm[cW] + Rm[c])) * T(0.25);
       const T *uxm = S.uu[ukm][0], *uym = S.uu[ukm][1], *uzm = S.uu[ukm][2];
       T u0[3] = {ux0[c], uy0[c], uz0[c]};
       T uE[3] = {ux0[c + 1], uy0[c + 1], uz0[c + 1]};
@@ -574,26 +583,27 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
       T uS[3] = {ux0[c - HX], uy0[c - HX], uz0[c - HX]};
       T uT[3] = {uxp[c], uyp[c], uzp[c]};
       T uB[3] = {uxm[c], uym[c], uzm[c]};
-      T fE = rE * T(0.5) * (u0[0] + uE[0]) * Sx, fW = rW * T(0.5) * (uW[0] + u0[0]) * Sx;
-      T fN = rNn * T(0.5) * (u0[1] + uN[1]) * Sy, fS = rS * T(0.5) * (uS[1] + u0[1]) * Sy;
-      T fT = rT * T(0.5) * (u0[2] + uT[2]) * Sz, fB = rB * T(0.5) * (uB[2] + u0[2]) * Sz;
+      // half the mass flux through each face (face density x mean normal
+      // velocity x area); the advected value is the mean of the two corners:
+      // sum_f g_f (u0 + u_f) = u0 sum_f g_f + sum_f g_f u_f
+      const T gE = rE * (u0[0] + uE[0]) * hSx, gW = rW * (uW[0] + u0[0]) * hSx;
+      const T gN = rNn * (u0[1] + uN[1]) * hSy, gS = rS * (uS[1] + u0[1]) * hSy;
+      const T gT = rT * (u0[2] + uT[2]) * hSz, gB = rB * (uB[2] + u0[2]) * hSz;
+      const T gsum = ((gE - gW) + (gN - gS)) + (gT - gB);
       const T *P0 = S.cp[ck], *Pm = S.cp[ckm];
-      T pE = Pm[c - HX] + Pm[c] + P0[c - HX] + P0[c];
-      T pW = Pm[c - HX - 1] + Pm[c - 1] + P0[c - HX - 1] + P0[c - 1];
-      T pNn = Pm[c - 1] + Pm[c] + P0[c - 1] + P0[c];
-      T pS = Pm[c - HX - 1] + Pm[c - HX] + P0[c - HX - 1] + P0[c - HX];
-      T pT = P0[c - HX - 1] + P0[c - HX] + P0[c - 1] + P0[c];
-      T pB = Pm[c - HX - 1] + Pm[c - HX] + Pm[c - 1] + Pm[c];
+      const T w00 = Pm[cSW] + P0[cSW], w10 = Pm[cS] + P0[cS], w01 = Pm[cW] + P0[cW], w11 = Pm[c] + P0[c];
+      const T pE = w10 + w11, pW = w00 + w01, pNn = w01 + w11, pS = w00 + w10;
+      const T pT = (P0[cSW] + P0[cS]) + (P0[cW] + P0[c]);
+      const T pB = (Pm[cSW] + Pm[cS]) + (Pm[cW] + Pm[c]);
       const T *Q0 = S.cr[ck], *Qm = S.cr[ckm];
-      T r8 = (Q0[c - HX - 1] + Q0[c - HX] + Q0[c - 1] + Q0[c]) + (Qm[c - HX - 1] + Qm[c - HX] + Qm[c - 1] + Qm[c]);
+      T r8 = (Q0[cSW] + Q0[cS] + Q0[cW] + Q0[c]) + (Qm[cSW] + Qm[cS] + Qm[cW] + Qm[c]);
       T pg[3] = {(pE - pW) * qdx, (pNn - pS) * qdy, (pT - pB) * qdz};
       const T tk = tau[kp];
       const T rbc[5] = {rhobc[kp - 2] * U, rhobc[kp - 1] * U, rhobc[kp] * U, rhobc[kp + 1] * U, rhobc[kp + 2] * U};
       const int ok4 = s4(k);
 #pragma unroll
       for (int d = 0; d < 3; d++) {
-        T adv = fE * T(0.5) * (u0[d] + uE[d]) - fW * T(0.5) * (uW[d] + u0[d]) + fN * T(0.5) * (u0[d] + uN[d]) -
-                fS * T(0.5) * (uS[d] + u0[d]) + fT * T(0.5) * (u0[d] + uT[d]) - fB * T(0.5) * (uB[d] + u0[d]);
+        T adv = u0[d] * gsum + (((gE * uE[d] - gW * uW[d]) + (gN * uN[d] - gS * uS[d])) + (gT * uT[d] - gB * uB[d]));
         T tend = -adv * v0inv - pg[d];
         if (d == 2) tend -= g * r8 * T(0.125);
         const T *Mk = S.om[ok4][d];
