@@ -819,12 +819,26 @@ __global__ void k_diag(const DomDev *__restrict__ doms, const ColItem *__restric
   }
   T *ubv = (T *)D.ub[rV];
   for (int d = 0; d < 3; d++) ubv[3 * q + d] = ub[d];
-  T *mcur[3] = {(T *)D.f[rC][2], (T *)D.f[rC][3], (T *)D.f[rC][4]};
-  T *mold[3] = {(T *)D.f[rO][2], (T *)D.f[rO][3], (T *)D.f[rO][4]};
-  T *mflt[3] = {(T *)D.f[rF][2], (T *)D.f[rF][3], (T *)D.f[rF][4]};
-  auto store = [&](int KK, const T u[3]) {
-    long long o = pidx(D, I, J, KK);
-    T rc = corner_rho(D, rp, rhob, I, J, KK);
+  const T *__restrict__ mcur[3] = {(const T *)D.f[rC][2], (const T *)D.f[rC][3], (const T *)D.f[rC][4]};
+  const T *__restrict__ mold[3] = {(const T *)D.f[rO][2], (const T *)D.f[rO][3], (const T *)D.f[rO][4]};
+  T *__restrict__ mflt[3] = {(T *)D.f[rF][2], (T *)D.f[rF][3], (T *)D.f[rF][4]};
+  // the four cell columns around the corner column, in the order of the
+  // corner density (i-1,j-1), (i,j-1), (i-1,j), (i,j); totals of cell level k
+  // are carried from one corner level to the next
+  const long long plane = D.plane;
+  const long long oc[4] = {widx(D, I - 1, J - 1, -GH), widx(D, I, J - 1, -GH), widx(D, I - 1, J, -GH),
+                           widx(D, I, J, -GH)};
+  const long long own = pidx(D, I, J, -GH);
+  auto level = [&](int k, T r[4]) {
+    const T rb = rhob[k + GH];
+    const long long z = (long long)(k + GH) * plane;
+#pragma unroll
+    for (int s = 0; s < 4; s++) r[s] = Ar<T>::add(rb, rp[oc[s] + z]);
+  };
+  auto store = [&](int KK, const T lo[4], const T hi[4], const T u[3]) {
+    const long long o = own + (long long)(KK + GH) * plane;
+    const T rc = rho8(lo[0], lo[1], lo[2], lo[3], hi[0], hi[1], hi[2], hi[3]);
+#pragma unroll
     for (int d = 0; d < 3; d++) {
       T mv = rc * u[d];
       M[d][o] = mv;
@@ -837,27 +851,39 @@ __global__ void k_diag(const DomDev *__restrict__ doms, const ColItem *__restric
   // corner levels from -GH+1: the density of corner K averages cell levels
   // K-1 and K, and the lowest padded cell level is -GH
   const int kt = D.ktop[q];
+  T lo[4], hi[4];
+  level(-GH, lo);
   for (int KK = -GH + 1; KK <= kt; KK++) {
-    long long p = pidx(D, I, J, KK);
-    int8_t v = D.vcls[p];
-    if (v == V_PRED) continue;
-    T u[3];
-    if (v == V_UG) {
-      u[0] = ub[0]; u[1] = ub[1]; u[2] = ub[2];
-    } else {
-      int ka = D.mK[p];
-      T gm = (T)D.mg[p];
-      T ua[3];
-      corner_u<T>(D, rp, Mc, rhob, nullptr, I, J, ka, ua);
-      for (int d = 0; d < 3; d++) u[d] = gm * ua[d] + (T(1) - gm) * ub[d];
+    level(KK, hi);
+    const long long p = own + (long long)(KK + GH) * plane;
+    const int8_t v = D.vcls[p];
+    if (v != V_PRED) {
+      T u[3];
+      if (v == V_UG) {
+        u[0] = ub[0]; u[1] = ub[1]; u[2] = ub[2];
+      } else {
+        int ka = D.mK[p];
+        T gm = (T)D.mg[p];
+        T ua[3];
+        corner_u<T>(D, rp, Mc, rhob, nullptr, I, J, ka, ua);
+        for (int d = 0; d < 3; d++) u[d] = gm * ua[d] + (T(1) - gm) * ub[d];
+      }
+      store(KK, lo, hi, u);
     }
-    store(KK, u);
+#pragma unroll
+    for (int s = 0; s < 4; s++) lo[s] = hi[s];
   }
   if (D.lid) {
     T ul[3];
     corner_u<T>(D, rp, Mc, rhob, nullptr, I, J, D.nz - 1, ul);
     ul[2] = 0;
-    for (int KK = D.nz; KK < D.nz + GH; KK++) store(KK, ul);
+    level(D.nz - 1, lo);
+    for (int KK = D.nz; KK < D.nz + GH; KK++) {
+      level(KK, hi);
+      store(KK, lo, hi, ul);
+#pragma unroll
+      for (int s = 0; s < 4; s++) lo[s] = hi[s];
+    }
   }
 }
 
