@@ -1136,15 +1136,41 @@ __global__ void k_reg_add(LevelLink L, int rF) {
   if (q >= L.nfaces) return;
   const IfaceFace f = L.faces[q];
   const DomDev &F = *L.df;
+  const int ax = f.ax;
+  const T *rp = (const T *)F.f[rF][0];
+  const T *pp = (const T *)F.f[rF][1];
+  const T *M[3] = {(const T *)F.f[rF][2], (const T *)F.f[rF][3], (const T *)F.f[rF][4]};
+  const T *rhob = (const T *)F.rhob, *pb = (const T *)F.pb, *thb = (const T *)F.thb, *ipb = (const T *)F.ipb;
+  const T *ub = (const T *)F.ub[rF];
+  // the two in-face directions (a, b) of the 2x2 fine faces, as in the face
+  // flux of the full-cell stencil: x-face (y, z), y-face (x, z), z-face (x, y)
+  const int da_i = ax == 0 ? 0 : 1, da_j = ax == 0 ? 1 : 0, da_k = 0;
+  const int db_i = 0, db_j = ax == 2 ? 1 : 0, db_k = ax == 2 ? 0 : 1;
+  // normal velocity at the 3x3 corners of the fine faces (one evaluation each)
+  T un[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; a++)
+#pragma unroll
+    for (int b = 0; b < 3; b++) {
+      T uc[3];
+      corner_u(F, rp, M, rhob, ub, f.fi + a * da_i + b * db_i, f.fj + a * da_j + b * db_j,
+               f.fk + a * da_k + b * db_k, uc);
+      un[a][b] = uc[ax];
+    }
+  const T S = (T)(ax == 0 ? F.dy * F.dz : (ax == 1 ? F.dx * F.dz : F.dx * F.dy));
+  const int li = ax == 0 ? -1 : 0, lj = ax == 1 ? -1 : 0, lk = ax == 2 ? -1 : 0;
   T sm = 0, sh = 0;
+#pragma unroll
   for (int a = 0; a < 2; a++)
+#pragma unroll
     for (int b = 0; b < 2; b++) {
-      int I = f.fi, J = f.fj, K = f.fk;
-      if (f.ax == 0) { J += a; K += b; }
-      else if (f.ax == 1) { I += a; K += b; }
-      else { I += a; J += b; }
-      T fm, fh;
-      face_fluxes<T>(F, rF, f.ax, I, J, K, fm, fh);
+      const int I = f.fi + a * da_i + b * db_i, J = f.fj + a * da_j + b * db_j, K = f.fk + a * da_k + b * db_k;
+      T ra = cell_rho(F, rp, rhob, I + li, J + lj, K + lk), rb = cell_rho(F, rp, rhob, I, J, K);
+      T ta = theta_tot(F, thb, pb, ipb, K + lk + GH, pp[widx(F, I + li, J + lj, K + lk)]);
+      T tb = theta_tot(F, thb, pb, ipb, K + GH, pp[widx(F, I, J, K)]);
+      // corners of the face in the full-cell stencil's order: (0,0), (+a), (+b), (+a+b)
+      T fm = face_flux(ra, rb, un[a][b], un[a + 1][b], un[a][b + 1], un[a + 1][b + 1], S);
+      T fh = face_flux(ta, tb, un[a][b], un[a + 1][b], un[a][b + 1], un[a + 1][b + 1], S);
       sm = Ar<T>::add(sm, fm);
       sh = Ar<T>::add(sh, fh);
     }
@@ -1175,8 +1201,27 @@ __global__ void k_iface(LevelLink L, int rO, int rC, int rN, int rF, int first) 
   const T nu = (T)(first ? 0.0 : D.ra_nu);
   const int i = ic.i, j = ic.j, k = ic.k;
   const T *rm_ = (const T *)L.regm, *rh_ = (const T *)L.regh;
+  const T *rp = (const T *)D.f[rC][0];
+  const T *pp = (const T *)D.f[rC][1];
+  const T *M[3] = {(const T *)D.f[rC][2], (const T *)D.f[rC][3], (const T *)D.f[rC][4]};
+  const T *rhob_ = (const T *)D.rhob, *pbv = (const T *)D.pb, *thbv = (const T *)D.thb, *ipbv = (const T *)D.ipb;
+  const T *ub = (const T *)D.ub[rC];
+  // the eight corner velocities of the cell, [dk][dj][di], and the totals of
+  // the cell and its six neighbours (the operations of the full-cell stencil)
+  T uc8[2][2][2][3];
+#pragma unroll
+  for (int dk = 0; dk < 2; dk++)
+#pragma unroll
+    for (int dj = 0; dj < 2; dj++)
+#pragma unroll
+      for (int di = 0; di < 2; di++) corner_u(D, rp, M, rhob_, ub, i + di, j + dj, k + dk, uc8[dk][dj][di]);
+  const T r0 = cell_rho(D, rp, rhob_, i, j, k);
+  const T t0 = theta_tot(D, thbv, pbv, ipbv, k + GH, pp[widx(D, i, j, k)]);
+  const T Sf[3] = {(T)(D.dy * D.dz), (T)(D.dx * D.dz), (T)(D.dx * D.dy)};
   T fl[6], hl[6];
+#pragma unroll
   for (int ax = 0; ax < 3; ax++)
+#pragma unroll
     for (int sd = 0; sd < 2; sd++) {
       int sl = ic.slot[ax * 2 + sd];
       T fm, fh;
@@ -1184,8 +1229,22 @@ __global__ void k_iface(LevelLink L, int rO, int rC, int rN, int rF, int first) 
         fm = A::mul(T(0.5), rm_[sl]);
         fh = A::mul(T(0.5), rh_[sl]);
       } else {
-        int I = i + (ax == 0 ? sd : 0), J = j + (ax == 1 ? sd : 0), K = k + (ax == 2 ? sd : 0);
-        face_fluxes<T>(D, rC, ax, I, J, K, fm, fh);
+        const int ni = i + (ax == 0 ? 2 * sd - 1 : 0), nj = j + (ax == 1 ? 2 * sd - 1 : 0),
+                  nk = k + (ax == 2 ? 2 * sd - 1 : 0);
+        const T rn = cell_rho(D, rp, rhob_, ni, nj, nk);
+        const T tn = theta_tot(D, thbv, pbv, ipbv, nk + GH, pp[widx(D, ni, nj, nk)]);
+        const T *u0, *u1, *u2, *u3;  // the face's corners in the full-cell stencil's order
+        if (ax == 0) {
+          u0 = uc8[0][0][sd]; u1 = uc8[0][1][sd]; u2 = uc8[1][0][sd]; u3 = uc8[1][1][sd];
+        } else if (ax == 1) {
+          u0 = uc8[0][sd][0]; u1 = uc8[0][sd][1]; u2 = uc8[1][sd][0]; u3 = uc8[1][sd][1];
+        } else {
+          u0 = uc8[sd][0][0]; u1 = uc8[sd][0][1]; u2 = uc8[sd][1][0]; u3 = uc8[sd][1][1];
+        }
+        // lower-index cell first
+        const T ra = sd ? r0 : rn, rb = sd ? rn : r0, ta = sd ? t0 : tn, tb = sd ? tn : t0;
+        fm = face_flux(ra, rb, u0[ax], u1[ax], u2[ax], u3[ax], Sf[ax]);
+        fh = face_flux(ta, tb, u0[ax], u1[ax], u2[ax], u3[ax], Sf[ax]);
       }
       fl[ax * 2 + sd] = fm;
       hl[ax * 2 + sd] = fh;
