@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--schedule", default=None,
+                    help="TILE_Y,ITEMS: fixed full-cell schedule instead of the autotuner (profiling runs)")
     return ap.parse_args()
 
 
@@ -73,7 +75,7 @@ def kfull_source_hash():
     hdr = open(os.path.join(ROOT, "paper_1509_02572_gb300", "csrc", "cc_internal.h")).read()
     a = src.index("struct FullCfg")
     b = src.index("await_groups<0>();\n}", src.index("k_full(")) 
-    tiles = [ln for ln in hdr.splitlines() if "TILE_" in ln or "constexpr int GX" in ln]
+    tiles = [ln for ln in hdr.splitlines() if "TILE_" in ln or "SCHED_" in ln or "constexpr int GX" in ln]
     return hashlib.sha256((src[a:b] + "\n".join(tiles)).encode()).hexdigest()[:16]
 
 
@@ -88,9 +90,8 @@ def kfull_traffic(dtype, cells, schedule):
         return None
     if t.get("source_hash") != kfull_source_hash() or t.get("precision") != {"f32": "fp32", "f64": "fp64"}[dtype]:
         return None
-    if list(t.get("schedule", [])) != list(schedule):
-        return None
-    return t["dram_bytes_per_interior_cell"] * cells
+    per = t.get("dram_bytes_per_interior_cell_by_tile_y", {}).get(str(schedule[0]))
+    return None if per is None else per * cells
 
 
 def peaks():
@@ -162,13 +163,18 @@ def fluid_cells(model, cfgs):
     return n
 
 
+SCHEDULE = None  # fixed (tile_y, items) from --schedule
+
+
 def make_model(cc, cfgs, prec, tune=True):
     m = cc.Model(cfgs, prec)
     for d, c in enumerate(cfgs):
         m.set_terrain(d, c.heights())
     m.build_geometry()
     m.init_state()
-    if tune:
+    if SCHEDULE and prec == cc.CC_FP32:
+        m.set_schedule(0, *SCHEDULE)
+    elif tune:
         m.autotune(3)
     return m
 
@@ -380,7 +386,10 @@ def run_reference(args):
 
 
 def main():
+    global SCHEDULE
     args = parse()
+    if args.schedule:
+        SCHEDULE = tuple(int(x) for x in args.schedule.split(","))
     if args.impl == "reference":
         run_reference(args)
         return
