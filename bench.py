@@ -94,6 +94,17 @@ def kfull_traffic(dtype, cells, schedule):
     return None if per is None else per * cells
 
 
+def job_time_and_rate(ms, units_per_rank, world, dist=None, device="cuda"):
+    """Whole-job timing over the ranks: the slowest rank's time (max over
+    ranks) and the units all ranks processed divided by it."""
+    import torch
+    t = torch.tensor([float(ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    msmax = float(t.item())
+    return msmax, units_per_rank * world / (msmax / 1e3)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -414,11 +425,8 @@ def main():
     hbm, peak_kind = peaks()
     if args.workload == "refined":
         r = bench_refined(cc, torch, args, hbm, peak_kind, barrier, world)
-        t = torch.tensor([r["ms_per_step"]], device="cuda")
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        msps = float(t.item())
-        line = {"metric": METRIC, "value": r["cell_updates_per_step"] * world / (msps / 1e3), "unit": METRIC,
+        msps, rate = job_time_and_rate(r["ms_per_step"], r["cell_updates_per_step"], world, dist)
+        line = {"metric": METRIC, "value": rate, "unit": METRIC,
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": msps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
@@ -459,11 +467,7 @@ def main():
     stage = {cc.KERNEL_NAMES[k]: model.profile_read(k) for k in range(5)}
     model.profile(False)
     gms = time_graphs(torch, model, args.steps)
-    t = torch.tensor([ms], device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms = float(t.item())
-    value = nfluid * args.steps * world / (ms / 1e3)
+    ms, value = job_time_and_rate(ms, nfluid * args.steps, world, dist)
 
     kavg = kfull_ms / max(1, kfull_n)
     achieved = BYTES_PER_CELL[dtype] * ninterior / (kavg / 1e3) / 1e9
