@@ -291,7 +291,7 @@ def bench_refined(cc, torch, args, hbm, peak_kind, barrier, world):
     clk = clocks.stop()
     barrier()
     kms, kn = m.profile_read(cc.CC_K_FULL)
-    stages = {cc.KERNEL_NAMES[k]: dict(zip(("ms_total", "launches"), m.profile_read(k))) for k in range(5)}
+    stages = {cc.KERNEL_NAMES[k]: dict(zip(("ms_total", "launches"), m.profile_read(k))) for k in cc.KERNEL_NAMES}
     m.profile(False)
     gms = time_graphs(torch, m, args.steps)
     kbytes = refined_kfull_bytes(m, "f32") * args.steps
@@ -464,7 +464,7 @@ def main():
     clk = clocks.stop()
     barrier()
     kfull_ms, kfull_n = model.profile_read(cc.CC_K_FULL)
-    stage = {cc.KERNEL_NAMES[k]: model.profile_read(k) for k in range(5)}
+    stage = {cc.KERNEL_NAMES[k]: model.profile_read(k) for k in cc.KERNEL_NAMES}
     model.profile(False)
     gms = time_graphs(torch, model, args.steps)
     ms, value = job_time_and_rate(ms, nfluid * args.steps, world, dist)

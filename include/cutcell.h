@@ -190,7 +190,7 @@ cc_status cc_set_schedule(cc_model *m, int d, int tile_y, int items_per_launch);
  * cc_step brackets each stage with CUDA events on the model's stream;
  * cc_profile_read synchronises and returns the summed device time (ms) and the
  * number of timed launches of one stage since the last cc_profile_reset. */
-enum { CC_K_FULL = 0, CC_K_GROUPS = 1, CC_K_DIAGNOSE = 2, CC_K_GHOST = 3, CC_K_REFINE = 4 };
+enum { CC_K_FULL = 0, CC_K_GROUPS = 1, CC_K_DIAGNOSE = 2, CC_K_REFINE = 3 };
 cc_status cc_profile_enable(cc_model *m, int on);
 cc_status cc_profile_read(cc_model *m, int kernel, double *total_ms, long long *launches);
 cc_status cc_profile_reset(cc_model *m);

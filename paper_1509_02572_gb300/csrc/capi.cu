@@ -74,7 +74,6 @@ struct cc_model {
   int32_t *d_members = nullptr;
   ColItem *d_cols = nullptr;
   int ncols = 0;
-  long long ghost_points = 0;
   bool refined = false;
   std::vector<LinkHost> link;  // link[l] for level l >= 1 of a refined model
   Eos eos{};                   // equation-of-state coefficients of every domain
@@ -180,8 +179,6 @@ StepLaunch make_launch(const cc_model *m, int d = -1) {
   L.cols = m->d_cols;
   L.ncols = m->ncols;
   L.ndom = m->ndom;
-  L.ghost_points = m->ghost_points;
-  L.ghost_off = nullptr;
   L.eos = m->eos;
   if (d >= 0) {
     const DomHost &H = m->dom[d];

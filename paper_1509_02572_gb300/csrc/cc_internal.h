@@ -175,8 +175,6 @@ struct StepLaunch {
   const ColItem *cols;
   int ncols;
   int ndom;
-  long long ghost_points;  // lateral ghost points over all domains (per level and field)
-  const long long *ghost_off;  // per-domain prefix of ghost points (device)
   Eos eos;
   int ty;                  // tile height of the work items
 };

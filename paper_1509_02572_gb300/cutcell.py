@@ -30,9 +30,8 @@ EXPORTS = ("cc_create", "cc_destroy", "cc_last_error", "cc_set_terrain", "cc_bui
            "cc_graphs_enable",
            "cc_mass_sum_noalloc", "cc_noalloc_last_error")
 CC_NOALLOC_MAX_PARTS = 1024
-CC_K_FULL, CC_K_GROUPS, CC_K_DIAGNOSE, CC_K_GHOST, CC_K_REFINE = range(5)
-KERNEL_NAMES = {CC_K_FULL: "k_full", CC_K_GROUPS: "k_groups", CC_K_DIAGNOSE: "k_diag", CC_K_GHOST: "k_ghost",
-                CC_K_REFINE: "refinement"}
+CC_K_FULL, CC_K_GROUPS, CC_K_DIAGNOSE, CC_K_REFINE = range(4)
+KERNEL_NAMES = {CC_K_FULL: "k_full", CC_K_GROUPS: "k_groups", CC_K_DIAGNOSE: "k_diag", CC_K_REFINE: "refinement"}
 
 
 class CCConfig(ct.Structure):
