@@ -5,7 +5,9 @@ Workloads (synthetic, seeded; the paper's hills sampled at grid corners):
              192x192x96), seed 1509, bell or half-ellipsoid hills; all
              instances advance together in one launch per stage in the FP32
              perturbation form; the plain FP64 form loops over the instances.
-  hemisphere the 128x128x64 grid of 50 m cells over the 1 km hemisphere.
+  hemisphere the 128x128x64 grid of 50 m cells over the 1 km hemisphere (FP64).
+  bell512    the 512x512x128 grid (100 m, dz 50 m) over the 400 m / 2 km bell,
+             FP32 against its FP64 run (--error-steps for long comparisons).
   refined    three block-structured levels (200 m over 64x32x16 km, 100 m and
              50 m boxes around the 1 km hemisphere), FP32 perturbation form;
              a step is one cycle of level 0 (2 steps of level 1, 4 of level 2).
@@ -44,7 +46,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "hemisphere", "refined"])
+    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "hemisphere", "bell512", "refined"])
+    ap.add_argument("--error-steps", type=int, default=0,
+                    help="extra untimed steps of the FP32 and FP64 runs before their difference is taken")
     ap.add_argument("--no-refined", action="store_true", help="skip the refined object of the default run")
     ap.add_argument("--instances", type=int, default=64)
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
@@ -60,6 +64,9 @@ def workload_configs(args):
     if args.workload == "ensemble":
         cfgs = W.ensemble_configs(args.instances, 1509)
         name = f"ensemble-{len(cfgs)}x(64^3..192x192x96)-seed1509"
+    elif args.workload == "bell512":
+        cfgs = [W.C3_BELL]
+        name = W.C3_BELL.name
     else:
         cfgs = [W.C2_HEMI]
         name = W.C2_HEMI.name
@@ -448,7 +455,7 @@ def main():
         return
 
     name, cfgs = workload_configs(args)
-    prec_main = cc.CC_FP32 if args.workload == "ensemble" else cc.CC_FP64
+    prec_main = cc.CC_FP64 if args.workload == "hemisphere" else cc.CC_FP32
     dtype = "f32" if prec_main == cc.CC_FP32 else "f64"
     model = make_model(cc, cfgs, prec_main)
     nfluid = fluid_cells(model, cfgs)
@@ -489,7 +496,7 @@ def main():
                        "how": "the same steps replayed from CUDA graphs, no per-stage events"}}
 
     # ---- plain FP64 form on the same workload, one domain at a time
-    if not args.no_fp64 and args.workload == "ensemble":
+    if not args.no_fp64 and prec_main == cc.CC_FP32:
         singles = [make_model(cc, [c], cc.CC_FP64) for c in cfgs]
         ksteps = max(2, min(args.steps, 5))
         for s in singles:
@@ -507,6 +514,8 @@ def main():
         v64 = nfluid * ksteps / (ms64 / 1e3)
         # error of the FP32 batched state against the FP64 runs after the same
         # number of steps (both started from the same initial state)
+        if args.error_steps > 0:
+            model.step(args.error_steps)
         n32 = int(model.diagnostics(0, check=False)["steps"])  # steps the FP32 model has taken
         n64 = args.warmup + ksteps
         for s in singles:

@@ -300,3 +300,21 @@ def test_graph_replay_equals_direct_launches(cc):
         m.close()
     for x, y in zip(*outs):
         assert np.array_equal(x, y)
+
+
+def test_full_size_hemisphere_rest_state_2000_steps(cc):
+    """The 128x128x64 hemisphere (71 degree slopes, vertical and horizontal
+    merges) at rest for 2000 FP64 steps: no spurious velocity and no mass
+    change at all (the hydrostatic base state is exactly balanced)."""
+    cfg = W.C2_HEMI.replace(U=0.0)
+    m = gpu_model(cc, cfg, cc.CC_FP64)
+    m.init_state()
+    d0 = m.diagnostics()
+    m.step(2000)
+    d1 = m.diagnostics()
+    assert d1["steps"] == 2000 and d1["nonfinite"] == 0
+    assert d1["max_u"] == 0.0 and d1["max_w"] == 0.0
+    assert d1["mass"] == d0["mass"] == 0.0
+    for f in (cc.CC_RHOP, cc.CC_PP, cc.CC_MX, cc.CC_MY, cc.CC_MZ):
+        assert np.abs(m.download(0, f)).max() == 0.0
+    m.close()
