@@ -148,6 +148,15 @@ cc_status cc_upload_state(cc_model *m, int d, int field, int level, const double
 /* Copy one field of domain d at level 0 or 1 to a host array (same layout). */
 cc_status cc_download_state(const cc_model *m, int d, int field, int level, double *host);
 
+/* The same transfers queued on the model's stream without waiting (no
+ * counterpart in the paper; for callers that move whole states every step):
+ * the host buffer must stay valid and unchanged (upload) or unread
+ * (download) until the stream has passed the transfer (cc_synchronize).
+ * With pinned host buffers the copies run asynchronously; transfers, steps
+ * and other calls on the model stay in stream order. */
+cc_status cc_upload_state_async(cc_model *m, int d, int field, int level, const double *host);
+cc_status cc_download_state_async(const cc_model *m, int d, int field, int level, double *host);
+
 /* Advance every domain by n steps (leapfrog; the first step after
  * cc_init_state is forward Euler).  Asynchronous on the model's stream. */
 cc_status cc_step(cc_model *m, int n);

@@ -842,7 +842,12 @@ static long long field_elems(const DomDev &D, int field, int *nlev, int *kfirst)
   return ncol * (*nlev);
 }
 
-cc_status cc_upload_state(cc_model *m, int d, int field, int level, const double *host) {
+}  // extern "C"
+
+// Transfers through the model's device staging buffer, in the model's
+// stream order (the staging buffer is reused only after the previous
+// transfer's kernel or copy, so no host wait is needed between them).
+static cc_status upload(cc_model *m, int d, int field, int level, const double *host, bool sync) {
   if (!m || !host) return fail(m, CC_EINVAL, "null argument");
   if (d < 0 || d >= m->ndom) return fail(m, CC_EINVAL, "domain index out of range");
   if (field < 0 || field > CC_UB || level < 0 || level > 1) return fail(m, CC_EINVAL, "bad field or level");
@@ -861,12 +866,11 @@ cc_status cc_upload_state(cc_model *m, int d, int field, int level, const double
     else k_scatter<float><<<nb256(n), 256, 0, m->st>>>(m->d_stage, (float *)dst, D, nlev, kfirst);
   }
   CK(m, cudaGetLastError(), "upload scatter");
-  CK(m, cudaStreamSynchronize(m->st), "upload sync");
+  if (sync) CK(m, cudaStreamSynchronize(m->st), "upload sync");
   return CC_OK;
 }
 
-cc_status cc_download_state(const cc_model *mc, int d, int field, int level, double *host) {
-  cc_model *m = const_cast<cc_model *>(mc);
+static cc_status download(cc_model *m, int d, int field, int level, double *host, bool sync) {
   if (!m || !host) return fail(m, CC_EINVAL, "null argument");
   if (d < 0 || d >= m->ndom) return fail(m, CC_EINVAL, "domain index out of range");
   if (field < 0 || field > CC_UB || level < 0 || level > 1) return fail(m, CC_EINVAL, "bad field or level");
@@ -889,8 +893,26 @@ cc_status cc_download_state(const cc_model *mc, int d, int field, int level, dou
   }
   CK(m, cudaGetLastError(), "download gather");
   CK(m, cudaMemcpyAsync(host, m->d_stage, n * 8, cudaMemcpyDeviceToHost, m->st), "download");
-  CK(m, cudaStreamSynchronize(m->st), "download sync");
+  if (sync) CK(m, cudaStreamSynchronize(m->st), "download sync");
   return CC_OK;
+}
+
+extern "C" {
+
+cc_status cc_upload_state(cc_model *m, int d, int field, int level, const double *host) {
+  return upload(m, d, field, level, host, true);
+}
+
+cc_status cc_download_state(const cc_model *m, int d, int field, int level, double *host) {
+  return download(const_cast<cc_model *>(m), d, field, level, host, true);
+}
+
+cc_status cc_upload_state_async(cc_model *m, int d, int field, int level, const double *host) {
+  return upload(m, d, field, level, host, false);
+}
+
+cc_status cc_download_state_async(const cc_model *m, int d, int field, int level, double *host) {
+  return download(const_cast<cc_model *>(m), d, field, level, host, false);
 }
 
 }  // extern "C"

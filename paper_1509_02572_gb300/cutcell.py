@@ -27,7 +27,7 @@ EXPORTS = ("cc_create", "cc_destroy", "cc_last_error", "cc_set_terrain", "cc_bui
            "cc_download_state", "cc_step", "cc_diagnostics", "cc_synchronize", "cc_last_launch_count",
            "cc_profile_enable", "cc_profile_read", "cc_profile_reset", "cc_create_refined",
            "cc_refine_mass", "cc_domain_count", "cc_autotune", "cc_get_schedule", "cc_set_schedule",
-           "cc_graphs_enable",
+           "cc_graphs_enable", "cc_upload_state_async", "cc_download_state_async",
            "cc_mass_sum_noalloc", "cc_noalloc_last_error")
 CC_NOALLOC_MAX_PARTS = 1024
 CC_K_FULL, CC_K_GROUPS, CC_K_DIAGNOSE, CC_K_REFINE = range(4)
@@ -85,6 +85,8 @@ def load(path: str = LIB_PATH):
     L.cc_init_state.argtypes = [vp]
     L.cc_upload_state.argtypes = [vp, i, i, i, vp]
     L.cc_download_state.argtypes = [vp, i, i, i, vp]
+    L.cc_upload_state_async.argtypes = [vp, i, i, i, vp]
+    L.cc_download_state_async.argtypes = [vp, i, i, i, vp]
     L.cc_step.argtypes = [vp, i]
     L.cc_diagnostics.argtypes = [vp, i, ct.POINTER(CCDiag)]
     L.cc_synchronize.argtypes = [vp]
@@ -240,16 +242,18 @@ class Model:
         self._check(self.L.cc_download_state(self.h, d, field, level, _p(out)))
         return out
 
-    def download_ptr(self, d: int, field: int, level: int, ptr: int):
-        self._check(self.L.cc_download_state(self.h, d, field, level, ct.c_void_p(ptr)))
+    def download_ptr(self, d: int, field: int, level: int, ptr: int, wait: bool = True):
+        fn = self.L.cc_download_state if wait else self.L.cc_download_state_async
+        self._check(fn(self.h, d, field, level, ct.c_void_p(ptr)))
 
     def upload(self, d: int, field: int, level: int, a: np.ndarray):
         a = np.ascontiguousarray(a, dtype=np.float64)
         assert a.shape == self._shape(d, field)
         self._check(self.L.cc_upload_state(self.h, d, field, level, _p(a)))
 
-    def upload_ptr(self, d: int, field: int, level: int, ptr: int):
-        self._check(self.L.cc_upload_state(self.h, d, field, level, ct.c_void_p(ptr)))
+    def upload_ptr(self, d: int, field: int, level: int, ptr: int, wait: bool = True):
+        fn = self.L.cc_upload_state if wait else self.L.cc_upload_state_async
+        self._check(fn(self.h, d, field, level, ct.c_void_p(ptr)))
 
     def step(self, n: int = 1):
         self._check(self.L.cc_step(self.h, int(n)))

@@ -318,3 +318,32 @@ def test_full_size_hemisphere_rest_state_2000_steps(cc):
     for f in (cc.CC_RHOP, cc.CC_PP, cc.CC_MX, cc.CC_MY, cc.CC_MZ):
         assert np.abs(m.download(0, f)).max() == 0.0
     m.close()
+
+
+def test_async_transfers_match_synchronous(cc, oracle_mod):
+    """Queued uploads and downloads (one wait at the end) give the same
+    state as the waiting ones."""
+    torch = pytest.importorskip("torch")
+    cfg = W.SMALL_HEMI
+    om = oracle_mod.Model(cfg)
+    om.init_state()
+    om.step(5)
+    pairs = [(cc.CC_RHOP, oracle_mod.F_RHOP), (cc.CC_PP, oracle_mod.F_PP), (cc.CC_MX, oracle_mod.F_MX),
+             (cc.CC_MY, oracle_mod.F_MY), (cc.CC_MZ, oracle_mod.F_MZ)]
+    outs = []
+    for wait in (True, False):
+        m = gpu_model(cc, cfg)
+        m.init_state()
+        m.step(1)
+        host = {(f, lev): torch.from_numpy(om.field(fo, lev)).pin_memory() for f, fo in pairs for lev in (0, 1)}
+        for (f, lev), a in host.items():
+            m.upload_ptr(0, f, lev, a.data_ptr(), wait=wait)
+        m.step(3)
+        res = {f: torch.empty(tuple(m._shape(0, f)), dtype=torch.float64).pin_memory() for f, _ in pairs}
+        for f, r in res.items():
+            m.download_ptr(0, f, 1, r.data_ptr(), wait=wait)
+        m.synchronize()
+        outs.append([res[f].numpy().copy() for f, _ in pairs])
+        m.close()
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
