@@ -560,10 +560,6 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
       T rF_ = rC_ + nu * (rN_ - T(2) * rC_ + rO_);
       T pF_ = pC_ + nu * (pN_ - T(2) * pC_ + pO_);
       if (k < kug) { rF_ = 0; pF_ = 0; }
-      ((T *)D.f[rN][0])[o] = rN_;
-      ((T *)D.f[rN][1])[o] = pN_;
-      ((T *)D.f[rF][0])[o] = rF_;
-      ((T *)D.f[rF][1])[o] = pF_;
 
       // ---- velocity cell centred on corner (i,j,K=k): Eqs. momentum_u_d .. w_d
       // face densities and pressures of the velocity cell: means over the 4
@@ -600,6 +596,7 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
       T pg[3] = {(pE - pW) * qdx, (pNn - pS) * qdy, (pT - pB) * qdz};
       const T tk = tau[kp];
       const T rbc[5] = {rhobc[kp - 2] * U, rhobc[kp - 1] * U, rhobc[kp] * U, rhobc[kp + 1] * U, rhobc[kp + 2] * U};
+      T mnew[3], mflt[3];
       const int ok4 = s4(k);
 #pragma unroll
       for (int d = 0; d < 3; d++) {
@@ -619,11 +616,20 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
           dm += d4(mreg[0][d], mreg[1][d], mreg[2][d], mreg[3][d], mreg[4][d]);
         T mold = mreg[2][d];
         tend += -kdif * dm - tk * (mold - ref0);
-        T mnew = mold + dt2 * tend;
-        T mf = mcur[d] + nu * (mnew - T(2) * mcur[d] + mold);
-        if (corner_active) {
-          ((T *)D.f[rN][2 + d])[o] = mnew;
-          ((T *)D.f[rF][2 + d])[o] = mf;
+        mnew[d] = mold + dt2 * tend;
+        mflt[d] = mcur[d] + nu * (mnew[d] - T(2) * mcur[d] + mold);
+      }
+      // every store after every shared-memory read of the plane (a store
+      // through a generic pointer would otherwise order the later reads)
+      ((T *)D.f[rN][0])[o] = rN_;
+      ((T *)D.f[rN][1])[o] = pN_;
+      ((T *)D.f[rF][0])[o] = rF_;
+      ((T *)D.f[rF][1])[o] = pF_;
+      if (corner_active) {
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          ((T *)D.f[rN][2 + d])[o] = mnew[d];
+          ((T *)D.f[rF][2 + d])[o] = mflt[d];
         }
       }
     }
