@@ -443,7 +443,7 @@ def main():
                            "l2": "inputs larger than L2 (state of all levels)"},
                 "gpu_launches": r["gpu_launches"], "roofline": r["roofline"], "stages": r["stages"],
                 "clocks": r["clocks"]}
-        for k in ("fp64_plain", "l2_error"):
+        for k in ("fp64_plain", "l2_error", "graphs"):
             if k in r:
                 line[k] = r[k]
         if rank == 0 and world == 1 and not args.no_cpu:
