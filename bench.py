@@ -269,11 +269,16 @@ def make_refined(cc, rc, prec):
 
 
 def refined_cell_updates(model):
-    """Cell updates of one cycle of level 0: the fluid cells of level l times
-    its 2^l substeps."""
+    """Cell updates of one cycle of level 0: the fluid cells of level l that
+    the next finer level does not cover, times its 2^l substeps (the covered
+    cells are computed too, but the finer level's values stand for them)."""
     n = 0
     for l in range(model.nlev):
-        n += int((model.geometry(l)["cls"] != 0).sum()) * 2 ** l
+        fluid = model.geometry(l)["cls"] != 0
+        if l + 1 < model.nlev:
+            nx, ny, nz, ox, oy = model.boxes[l]
+            fluid[:nz // 2, oy // 2:(oy + ny) // 2, ox // 2:(ox + nx) // 2] = False
+        n += int(fluid.sum()) * 2 ** l
     return n
 
 
@@ -357,7 +362,11 @@ def cpu_baseline_refined(seconds):
     R = oracle.Refine(rc.base, rc.boxes, rc.finest_heights(pad=4))
     upd = 0
     for l, lev in enumerate(R.levels):
-        upd += int((lev.geometry()["cls"] != 0).sum()) * 2 ** l
+        fluid = lev.geometry()["cls"] != 0
+        if l + 1 < len(R.levels):
+            nx, ny, nz, ox, oy = rc.boxes[l]
+            fluid[:nz // 2, oy // 2:(oy + ny) // 2, ox // 2:(ox + nx) // 2] = False
+        upd += int(fluid.sum()) * 2 ** l
     R.init_state()
     R.step(1)
     s = 0
