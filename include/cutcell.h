@@ -157,6 +157,20 @@ cc_status cc_download_state(const cc_model *m, int d, int field, int level, doub
 cc_status cc_upload_state_async(cc_model *m, int d, int field, int level, const double *host);
 cc_status cc_download_state_async(const cc_model *m, int d, int field, int level, double *host);
 
+/* Checkpoint and resume (no counterpart in the paper; long runs are split
+ * over several jobs).  cc_save writes the whole state of every domain -- all
+ * four time levels of the five fields and of the boundary-point velocity in
+ * the device layout and the model's precision, with the time-level roles and
+ * step counts -- to the file `path` (synchronises the stream).  cc_load reads
+ * it into a model created with the same configurations and precision whose
+ * geometry is built; the model then continues bit for bit as the saved one
+ * would.  CC_EINVAL when the file is not a checkpoint, is truncated, cannot be
+ * opened, or does not match the model's precision, domain count or sizes;
+ * a file found truncated after the header checks leaves the model without a
+ * state (CC_ESTATE on cc_step until cc_init_state or a good cc_load). */
+cc_status cc_save(const cc_model *m, const char *path);
+cc_status cc_load(cc_model *m, const char *path);
+
 /* Advance every domain by n steps (leapfrog; the first step after
  * cc_init_state is forward Euler).  Asynchronous on the model's stream. */
 cc_status cc_step(cc_model *m, int n);

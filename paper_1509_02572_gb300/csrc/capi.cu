@@ -1108,6 +1108,123 @@ cc_status cc_graphs_enable(cc_model *m, int on) {
   return CC_OK;
 }
 
+// Checkpoint file: a header (magic, version, precision, domain count and
+// sizes, time-level roles and step counts) followed, per domain, by the raw
+// device arrays of all four time levels (five fields and the boundary-point
+// velocity, padded layout, model precision).
+namespace {
+const char kMagic[8] = {'C', 'U', 'T', 'C', 'E', 'L', 'L', '1'};
+struct CkptDom {
+  int32_t nx, ny, nz, px, py, pz, r[4];
+  int64_t nsteps;
+};
+}  // namespace
+
+cc_status cc_save(const cc_model *mc, const char *path) {
+  cc_model *m = const_cast<cc_model *>(mc);
+  if (!m || !path) return fail(m, CC_EINVAL, "null argument");
+  if (!m->state) return fail(m, CC_ESTATE, "state not initialised");
+  CK(m, cudaStreamSynchronize(m->st), "save sync");
+  FILE *f = std::fopen(path, "wb");
+  if (!f) return fail(m, CC_EINVAL, std::string("cannot open ") + path + " for writing");
+  bool ok = std::fwrite(kMagic, 1, 8, f) == 8;
+  int32_t hdr[4] = {1, m->prec, m->ndom, m->refined ? 1 : 0};
+  ok = ok && std::fwrite(hdr, sizeof(hdr), 1, f) == 1;
+  for (const auto &H : m->dom) {
+    CkptDom c{H.D.nx, H.D.ny, H.D.nz, H.D.px, H.D.py, H.D.pz, {H.r[0], H.r[1], H.r[2], H.r[3]}, H.nsteps};
+    ok = ok && std::fwrite(&c, sizeof(c), 1, f) == 1;
+  }
+  std::vector<char> buf;
+  for (const auto &H : m->dom) {
+    const size_t nf = (size_t)H.D.ncellp * m->esz, nu = (size_t)3 * H.D.plane * m->esz;
+    buf.resize(std::max(nf, nu));
+    for (int b = 0; b < NBUF && ok; b++) {
+      for (int fl = 0; fl < NFIELD && ok; fl++) {
+        cudaError_t e = cudaMemcpy(buf.data(), H.D.f[b][fl], nf, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) {
+          std::fclose(f);
+          return cuda_fail(m, e, "save copy");
+        }
+        ok = std::fwrite(buf.data(), 1, nf, f) == nf;
+      }
+      if (!ok) break;
+      cudaError_t e = cudaMemcpy(buf.data(), H.D.ub[b], nu, cudaMemcpyDeviceToHost);
+      if (e != cudaSuccess) {
+        std::fclose(f);
+        return cuda_fail(m, e, "save copy");
+      }
+      ok = std::fwrite(buf.data(), 1, nu, f) == nu;
+    }
+  }
+  ok = (std::fclose(f) == 0) && ok;
+  if (!ok) return fail(m, CC_EINVAL, std::string("write to ") + path + " failed");
+  return CC_OK;
+}
+
+cc_status cc_load(cc_model *m, const char *path) {
+  if (!m || !path) return fail(m, CC_EINVAL, "null argument");
+  if (!m->geom) return fail(m, CC_ESTATE, "geometry not built");
+  FILE *f = std::fopen(path, "rb");
+  if (!f) return fail(m, CC_EINVAL, std::string("cannot open ") + path);
+  auto bad = [&](const std::string &why) {
+    std::fclose(f);
+    return fail(m, CC_EINVAL, std::string(path) + ": " + why);
+  };
+  char magic[8];
+  int32_t hdr[4];
+  if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, kMagic, 8) != 0) return bad("not a checkpoint file");
+  if (std::fread(hdr, sizeof(hdr), 1, f) != 1 || hdr[0] != 1) return bad("unknown checkpoint version");
+  if (hdr[1] != m->prec || hdr[2] != m->ndom || hdr[3] != (m->refined ? 1 : 0))
+    return bad("precision, domain count or refinement differ from the model");
+  std::vector<CkptDom> cd(m->ndom);
+  for (int d = 0; d < m->ndom; d++) {
+    if (std::fread(&cd[d], sizeof(CkptDom), 1, f) != 1) return bad("truncated header");
+    const DomDev &D = m->dom[d].D;
+    if (cd[d].nx != D.nx || cd[d].ny != D.ny || cd[d].nz != D.nz || cd[d].px != D.px || cd[d].py != D.py ||
+        cd[d].pz != D.pz)
+      return bad("domain " + std::to_string(d) + " has other sizes than the model's");
+    for (int a = 0; a < 4; a++)
+      if (cd[d].r[a] < 0 || cd[d].r[a] >= NBUF) return bad("invalid time-level roles");
+  }
+  std::vector<char> buf;
+  m->state = false;  // until every array has been read
+  for (int d = 0; d < m->ndom; d++) {
+    const DomDev &D = m->dom[d].D;
+    const size_t nf = (size_t)D.ncellp * m->esz, nu = (size_t)3 * D.plane * m->esz;
+    buf.resize(std::max(nf, nu));
+    for (int b = 0; b < NBUF; b++) {
+      for (int fl = 0; fl < NFIELD; fl++) {
+        if (std::fread(buf.data(), 1, nf, f) != nf) return bad("truncated data");
+        cudaError_t e = cudaMemcpy(D.f[b][fl], buf.data(), nf, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+          std::fclose(f);
+          return cuda_fail(m, e, "load copy");
+        }
+      }
+      if (std::fread(buf.data(), 1, nu, f) != nu) return bad("truncated data");
+      cudaError_t e = cudaMemcpy(D.ub[b], buf.data(), nu, cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        std::fclose(f);
+        return cuda_fail(m, e, "load copy");
+      }
+    }
+  }
+  std::fclose(f);
+  for (int d = 0; d < m->ndom; d++) {
+    for (int a = 0; a < 4; a++) m->dom[d].r[a] = cd[d].r[a];
+    m->dom[d].nsteps = cd[d].nsteps;
+  }
+  // the flux registers are empty between steps
+  for (int l = 1; l < (int)m->link.size(); l++) {
+    const LevelLink &K = m->link[l].L;
+    CK(m, cudaMemsetAsync(K.regm, 0, K.nfaces * m->esz, m->st), "register reset");
+    CK(m, cudaMemsetAsync(K.regh, 0, K.nfaces * m->esz, m->st), "register reset");
+  }
+  CK(m, cudaStreamSynchronize(m->st), "load sync");
+  m->state = true;
+  return CC_OK;
+}
+
 cc_status cc_diagnostics(cc_model *m, int d, cc_diag *out) {
   if (!m || !out) return fail(m, CC_EINVAL, "null argument");
   if (d < 0 || d >= m->ndom) return fail(m, CC_EINVAL, "domain index out of range");

@@ -27,7 +27,7 @@ EXPORTS = ("cc_create", "cc_destroy", "cc_last_error", "cc_set_terrain", "cc_bui
            "cc_download_state", "cc_step", "cc_diagnostics", "cc_synchronize", "cc_last_launch_count",
            "cc_profile_enable", "cc_profile_read", "cc_profile_reset", "cc_create_refined",
            "cc_refine_mass", "cc_domain_count", "cc_autotune", "cc_get_schedule", "cc_set_schedule",
-           "cc_graphs_enable", "cc_upload_state_async", "cc_download_state_async",
+           "cc_graphs_enable", "cc_upload_state_async", "cc_download_state_async", "cc_save", "cc_load",
            "cc_mass_sum_noalloc", "cc_noalloc_last_error")
 CC_NOALLOC_MAX_PARTS = 1024
 CC_K_FULL, CC_K_GROUPS, CC_K_DIAGNOSE, CC_K_REFINE = range(4)
@@ -101,6 +101,8 @@ def load(path: str = LIB_PATH):
     L.cc_domain_count.argtypes = [vp]
     L.cc_autotune.argtypes = [vp, i]
     L.cc_graphs_enable.argtypes = [vp, i]
+    L.cc_save.argtypes = [vp, ct.c_char_p]
+    L.cc_load.argtypes = [vp, ct.c_char_p]
     L.cc_get_schedule.argtypes = [vp, i, ct.POINTER(i), ct.POINTER(i)]
     L.cc_set_schedule.argtypes = [vp, i, i, i]
     L.cc_mass_sum_noalloc.argtypes = [vp, i, vp, ct.c_longlong, i, vp, vp]
@@ -284,6 +286,14 @@ class Model:
         fastest (per level of a refined model); returns the schedules."""
         self._check(self.L.cc_autotune(self.h, int(reps)))
         return [self.schedule(d) for d in range(len(self.cfgs))]
+
+    def save(self, path: str):
+        """Checkpoint the whole state to a file (cc_save)."""
+        self._check(self.L.cc_save(self.h, os.fsencode(path)))
+
+    def load(self, path: str):
+        """Resume from a checkpoint written by a model of the same set-up."""
+        self._check(self.L.cc_load(self.h, os.fsencode(path)))
 
     def graphs(self, on: bool = True):
         self._check(self.L.cc_graphs_enable(self.h, 1 if on else 0))
