@@ -18,6 +18,8 @@ SRC = os.path.join(HERE, "oracle.c")
 
 OK, EINVAL, EGEOM = 0, 1, 3
 F_RHOP, F_PP, F_MX, F_MY, F_MZ, F_UB = range(6)
+# derived output fields: corner velocity components, cell theta'
+D_U, D_V, D_W, D_THETA = range(4)
 # cell classes and corner classes
 C_UG, C_FULL, C_CUT, C_ABS = 0, 1, 2, 3
 V_UG, V_PRED, V_MF, V_LID = 0, 1, 2, 3
@@ -71,6 +73,9 @@ def lib():
             L.oc_mass.restype = ct.c_double
             L.oc_mass.argtypes = [ct.c_void_p, ct.c_int]
             L.oc_nsteps.argtypes = [ct.c_void_p]
+            L.oc_heat.restype = ct.c_double
+            L.oc_heat.argtypes = [ct.c_void_p, ct.c_int]
+            L.oc_get_derived.argtypes = [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p]
             L.oc_line_int.restype = ct.c_double
             L.oc_line_int.argtypes = [ct.c_double] * 4
             L.oc_line_frac.restype = ct.c_double
@@ -216,6 +221,18 @@ class Model:
 
     def mass(self, level: int = 1) -> float:
         return lib().oc_mass(self._m, level)
+
+    def heat(self, level: int = 1) -> float:
+        return lib().oc_heat(self._m, level)
+
+    def derived(self, which: int, level: int = 1) -> np.ndarray:
+        c = self.cfg
+        shape = self.cell_shape if which == D_THETA else (c.nz + 1, c.ny, c.nx)
+        a = np.zeros(int(np.prod(shape)))
+        st = lib().oc_get_derived(self._m, which, level, _ptr(a))
+        if st != OK:
+            raise OracleError(f"get_derived {which} {level} -> {st}")
+        return a.reshape(shape)
 
 
 def line_int(z, ha, hb, length):

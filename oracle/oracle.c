@@ -1066,6 +1066,57 @@ double oc_mass(const oc_model *m, int level) {
 
 int oc_nsteps(const oc_model *m) { return m->nsteps; }
 
+/* Heat content of the interior: sum over merge groups of V_G (rho theta)'_G,
+ * where (rho theta)' is rho theta of the total pressure minus that of the
+ * base pressure, both from the equation of state (Sec 2.1).  The scheme does
+ * not conserve it (the pressure equation is not in flux form); it is a
+ * diagnostic. */
+double oc_heat(const oc_model *m, int level) {
+  double s = 0.0;
+  for (int k = 0; k < m->nz; k++)
+    for (int j = 0; j < m->ny; j++)
+      for (int i = 0; i < m->nx; i++) {
+        long c = CI(m, i, j, k);
+        if (m->cls[c] != C_UG && m->root[c] == c) {
+          double p = pb_k(m, k);
+          s += m->vg[c] * (rhotheta_of_p(&m->P, p + m->pp[level][c]) - rhotheta_of_p(&m->P, p));
+        }
+      }
+  return s;
+}
+
+/* Derived output fields of time level `level` (0 filtered previous, 1
+ * current).  OC_D_U, OC_D_V, OC_D_W: the corner velocity every flux formula
+ * uses (corner_velocity above), corners K = 0 .. nz, (nz+1)*ny*nx values.
+ * OC_D_THETA: potential-temperature perturbation of every cell,
+ * theta' = (rho theta)(p_bar + p') / (rho_bar + rho') - (rho theta)(p_bar) / rho_bar,
+ * nz*ny*nx values (absorbed cells carry their group's state, cells below the
+ * terrain give 0). */
+int oc_get_derived(const oc_model *m, int which, int level, double *out) {
+  if (level < 0 || level > 1 || which < OC_D_U || which > OC_D_THETA) return OC_EINVAL;
+  int nx = m->nx, ny = m->ny, nz = m->nz;
+  long h = 0;
+  if (which == OC_D_THETA) {
+    for (int k = 0; k < nz; k++)
+      for (int j = 0; j < ny; j++)
+        for (int i = 0; i < nx; i++, h++) {
+          long c = CI(m, i, j, k);
+          double p = pb_k(m, k), r = rhob_k(m, k);
+          out[h] = rhotheta_of_p(&m->P, p + m->pp[level][c]) / (r + m->rp[level][c]) -
+                   rhotheta_of_p(&m->P, p) / r;
+        }
+    return OC_OK;
+  }
+  for (int K = 0; K <= nz; K++)
+    for (int J = 0; J < ny; J++)
+      for (int I = 0; I < nx; I++, h++) {
+        double u[3];
+        corner_velocity(m, level, I, J, K, u);
+        out[h] = u[which - OC_D_U];
+      }
+  return OC_OK;
+}
+
 /* ================================================================== */
 /* Block-structured refinement (Sec 2.2).                              */
 /* Level 0 is the periodic domain with the lid; level l >= 1 is a box of */

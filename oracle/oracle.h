@@ -6,6 +6,8 @@
 
 enum { OC_OK = 0, OC_EINVAL = 1, OC_EGEOM = 3 };
 enum { OC_F_RHOP = 0, OC_F_PP = 1, OC_F_MX = 2, OC_F_MY = 3, OC_F_MZ = 4, OC_F_UB = 5 };
+/* derived output fields */
+enum { OC_D_U = 0, OC_D_V = 1, OC_D_W = 2, OC_D_THETA = 3 };
 
 typedef struct {
   int nx, ny, nz;
@@ -38,6 +40,8 @@ int oc_base_len(const oc_model *m);
 int oc_get_base(const oc_model *m, double *rhob, double *pb, int *koff, int *nb);
 double oc_mass(const oc_model *m, int level);
 int oc_nsteps(const oc_model *m);
+double oc_heat(const oc_model *m, int level);
+int oc_get_derived(const oc_model *m, int which, int level, double *out);
 
 double oc_line_int(double z, double ha, double hb, double len);
 double oc_line_frac(double z, double ha, double hb);
