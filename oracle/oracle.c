@@ -1086,14 +1086,17 @@ double oc_heat(const oc_model *m, int level) {
 }
 
 /* Derived output fields of time level `level` (0 filtered previous, 1
- * current).  OC_D_U, OC_D_V, OC_D_W: the corner velocity every flux formula
- * uses (corner_velocity above), corners K = 0 .. nz, (nz+1)*ny*nx values.
+ * current).  OC_D_U, OC_D_V, OC_D_W (level 1 only: the boundary-point
+ * velocity is diagnosed for the current level alone): the corner velocity
+ * every flux formula uses (corner_velocity above), corners K = 0 .. nz,
+ * (nz+1)*ny*nx values.
  * OC_D_THETA: potential-temperature perturbation of every cell,
  * theta' = (rho theta)(p_bar + p') / (rho_bar + rho') - (rho theta)(p_bar) / rho_bar,
  * nz*ny*nx values (absorbed cells carry their group's state, cells below the
  * terrain give 0). */
 int oc_get_derived(const oc_model *m, int which, int level, double *out) {
   if (level < 0 || level > 1 || which < OC_D_U || which > OC_D_THETA) return OC_EINVAL;
+  if (which != OC_D_THETA && level != 1) return OC_EINVAL;
   int nx = m->nx, ny = m->ny, nz = m->nz;
   long h = 0;
   if (which == OC_D_THETA) {

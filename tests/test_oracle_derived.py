@@ -5,6 +5,7 @@ state rho theta = (p0/R)(p/p0)^(cv/cp) (Sec 2.1) and known momentum fields."""
 import math
 
 import numpy as np
+import pytest
 
 from paper_1509_02572_gb300 import workloads as W
 
@@ -96,6 +97,8 @@ def test_corner_velocity_of_known_momentum(oracle_mod):
         w = np.broadcast_to(want[c], (len(K), ny, nx))[gz:gz + nz + 1]
         np.testing.assert_allclose(got[1:], w[1:], rtol=1e-13, atol=1e-13)
         assert np.array_equal(got[0], ub[:, :, c])
+        with pytest.raises(oracle_mod.OracleError):
+            om.derived(which, 0)  # the boundary velocity exists for the current level only
 
 
 def test_corner_velocity_of_initial_state_over_a_hill(oracle_mod):
