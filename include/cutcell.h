@@ -75,6 +75,9 @@ typedef struct {
   double max_w;       /* max |w| over corners above the terrain (m/s)       */
   long long nonfinite;/* number of non-finite prognostic values             */
   long long steps;    /* steps taken since cc_init_state                    */
+  double heat;        /* sum over merged cells of V_G (rho theta)'_G (kg K);
+                         the scheme does not conserve it (diagnostic)       */
+  double heat_comp;   /* compensation term of its Neumaier sum              */
 } cc_diag;
 
 typedef struct cc_model cc_model;
@@ -99,6 +102,26 @@ const char *cc_last_error(const cc_model *m);
  * (periodic), ny*nx doubles x fastest, every value >= 0 and below the lid.
  * Copied to the device; Sec 2.3, Eq. bilin and its coefficients. */
 cc_status cc_set_terrain(cc_model *m, int d, const double *corner_h);
+
+/* Analytic terrain shapes of cc_set_terrain_analytic. */
+enum { CC_HILL_BELL = 0, CC_HILL_ELLIPSOID = 1, CC_HILL_COSINE = 2 };
+
+/* Terrain of domain d from an analytic hill evaluated on the GPU at the
+ * corners (I dx, J dy), I < nx, J < ny.  params = {h0, a, xc, yc}: height,
+ * half-width (bell) or radius (ellipsoid, cosine), and the centre in metres
+ * from corner (0, 0); r is the horizontal distance from the centre.
+ *   CC_HILL_BELL       h0 / (1 + r^2/a^2)^(3/2)          (Sec 3.1.1)
+ *   CC_HILL_ELLIPSOID  h0 sqrt(max(0, 1 - r^2/a^2))      (Sec 3.1.2; the
+ *                      hemisphere when h0 = a)
+ *   CC_HILL_COSINE     h0 (1 + cos(pi r / a)) / 2 for r < a, else 0 (appendix)
+ * The heights then pass the checks of cc_set_terrain; when one fails the
+ * domain is left without terrain (CC_EINVAL).  CC_EINVAL also for an
+ * unknown kind, h0 < 0, a <= 0 or non-finite parameters. */
+cc_status cc_set_terrain_analytic(cc_model *m, int d, int kind, const double *params);
+
+/* Corner heights of domain d as last set, ny*nx doubles x fastest, into a
+ * host array.  CC_ESTATE before the domain has terrain. */
+cc_status cc_get_terrain(const cc_model *m, int d, double *corner_h);
 
 /* Build the cut-cell geometry of every domain on the GPU in FP64 (Sec 2.3 and
  * 2.4): column gradients (Eqs. xgrad, ygrad), volumes and apertures by exact
@@ -147,6 +170,26 @@ cc_status cc_upload_state(cc_model *m, int d, int field, int level, const double
 
 /* Copy one field of domain d at level 0 or 1 to a host array (same layout). */
 cc_status cc_download_state(const cc_model *m, int d, int field, int level, double *host);
+
+/* Derived output fields of cc_download_derived. */
+enum { CC_U = 0, CC_V = 1, CC_W = 2, CC_THETA_P = 3 };
+
+/* A derived field of domain d at level 0 or 1 into a host array.
+ *   CC_U, CC_V, CC_W (level 1 only: the boundary-point velocity is
+ *     diagnosed for the current level alone): the velocity at the corners
+ *     K = 0 .. nz,
+ *     (nz+1)*ny*nx doubles x fastest, as every flux formula uses it (Sec 2.4):
+ *     at corners at or below the terrain the boundary-point velocity of the
+ *     column, elsewhere momentum over the corner density (the mean total
+ *     density of the 8 cells around the corner), in the model's arithmetic;
+ *   CC_THETA_P: the potential-temperature perturbation theta - theta_bar of
+ *     every cell, nz*ny*nx doubles, with theta = rho theta / rho and rho theta
+ *     from the pressure by the equation of state (Sec 2.1), evaluated in FP64
+ *     from the stored perturbations; absorbed cells carry their group's
+ *     state, cells below the terrain give 0.
+ * Computed on the GPU; synchronous with respect to the model's stream.
+ * CC_EINVAL for a bad domain, field or level, CC_ESTATE before a state. */
+cc_status cc_download_derived(const cc_model *m, int d, int which, int level, double *host);
 
 /* The same transfers queued on the model's stream without waiting (no
  * counterpart in the paper; for callers that move whole states every step):

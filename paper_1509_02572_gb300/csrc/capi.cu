@@ -512,7 +512,7 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
       if ((e = cudaStreamSynchronize(m->st)) != cudaSuccess) return bail(e, "sync");
     }
   }
-  if ((e = dalloc(m->allocs, &m->d_diag, sizeof(double) * (8 + 5 * 256), m->st)) != cudaSuccess) return bail(e, "diag");
+  if ((e = dalloc(m->allocs, &m->d_diag, sizeof(double) * (8 + 7 * 256), m->st)) != cudaSuccess) return bail(e, "diag");
   if ((e = dalloc(m->allocs, &m->d_stage, sizeof(double) * max_stage, m->st)) != cudaSuccess) return bail(e, "stage");
   m->stage_elems = max_stage;
   if ((e = dalloc(m->allocs, &m->d_err, sizeof(int), m->st)) != cudaSuccess) return bail(e, "err flag");
@@ -605,10 +605,9 @@ const char *cc_last_error(const cc_model *m) {
   return m->err.c_str();
 }
 
-cc_status cc_set_terrain(cc_model *m, int d, const double *corner_h) {
-  if (!m || !corner_h) return fail(m, CC_EINVAL, "null argument");
-  if (d < 0 || d >= m->ndom) return fail(m, CC_EINVAL, "domain index out of range");
-  DomHost &H = m->dom[d];
+// The heights every terrain must satisfy: finite, >= 0, below the top; a
+// box level flat within FLAT_MARGIN corners of its edges.
+static cc_status check_terrain(cc_model *m, const DomHost &H, const double *corner_h) {
   const int nx = H.cfg.nx, ny = H.cfg.ny;
   long long ncol = (long long)nx * ny;
   double top = H.cfg.nz * H.cfg.dz;
@@ -625,12 +624,56 @@ cc_status cc_set_terrain(cc_model *m, int d, const double *corner_h) {
           return fail(m, CC_EINVAL, "terrain of a refined box must be zero within 8 corners of its edges");
       }
   }
+  return CC_OK;
+}
+
+cc_status cc_set_terrain(cc_model *m, int d, const double *corner_h) {
+  if (!m || !corner_h) return fail(m, CC_EINVAL, "null argument");
+  if (d < 0 || d >= m->ndom) return fail(m, CC_EINVAL, "domain index out of range");
+  DomHost &H = m->dom[d];
+  long long ncol = (long long)H.cfg.nx * H.cfg.ny;
+  cc_status r = check_terrain(m, H, corner_h);
+  if (r != CC_OK) return r;
   CK(m, cudaMemcpyAsync((void *)H.D.h, corner_h, ncol * 8, cudaMemcpyHostToDevice, m->st), "terrain copy");
   CK(m, cudaStreamSynchronize(m->st), "terrain sync");
   H.hh.assign(corner_h, corner_h + ncol);
   H.terrain = true;
   m->geom = false;
   m->state = false;
+  return CC_OK;
+}
+
+cc_status cc_set_terrain_analytic(cc_model *m, int d, int kind, const double *params) {
+  if (!m || !params) return fail(m, CC_EINVAL, "null argument");
+  if (d < 0 || d >= m->ndom) return fail(m, CC_EINVAL, "domain index out of range");
+  if (kind < CC_HILL_BELL || kind > CC_HILL_COSINE) return fail(m, CC_EINVAL, "unknown hill kind");
+  for (int a = 0; a < 4; a++)
+    if (!std::isfinite(params[a])) return fail(m, CC_EINVAL, "non-finite hill parameter");
+  if (params[0] < 0.0 || params[1] <= 0.0) return fail(m, CC_EINVAL, "hill height < 0 or width <= 0");
+  DomHost &H = m->dom[d];
+  long long ncol = (long long)H.cfg.nx * H.cfg.ny;
+  H.terrain = false;
+  m->geom = false;
+  m->state = false;
+  CK(m, launch_hill((double *)H.D.h, H.cfg.nx, H.cfg.ny, H.cfg.dx, H.cfg.dy, kind, params[0], params[1], params[2],
+                    params[3], m->st), "hill");
+  std::vector<double> hh(ncol);
+  CK(m, cudaMemcpyAsync(hh.data(), H.D.h, ncol * 8, cudaMemcpyDeviceToHost, m->st), "hill copy");
+  CK(m, cudaStreamSynchronize(m->st), "hill sync");
+  cc_status r = check_terrain(m, H, hh.data());
+  if (r != CC_OK) return r;
+  H.hh.swap(hh);
+  H.terrain = true;
+  return CC_OK;
+}
+
+cc_status cc_get_terrain(const cc_model *mc, int d, double *corner_h) {
+  cc_model *m = const_cast<cc_model *>(mc);
+  if (!m || !corner_h) return fail(m, CC_EINVAL, "null argument");
+  if (d < 0 || d >= m->ndom) return fail(m, CC_EINVAL, "domain index out of range");
+  const DomHost &H = m->dom[d];
+  if (!H.terrain) return fail(m, CC_ESTATE, "terrain not set");
+  std::memcpy(corner_h, H.hh.data(), H.hh.size() * sizeof(double));
   return CC_OK;
 }
 
@@ -905,6 +948,22 @@ cc_status cc_upload_state(cc_model *m, int d, int field, int level, const double
 
 cc_status cc_download_state(const cc_model *m, int d, int field, int level, double *host) {
   return download(const_cast<cc_model *>(m), d, field, level, host, true);
+}
+
+cc_status cc_download_derived(const cc_model *mc, int d, int which, int level, double *host) {
+  cc_model *m = const_cast<cc_model *>(mc);
+  if (!m || !host) return fail(m, CC_EINVAL, "null argument");
+  if (d < 0 || d >= m->ndom) return fail(m, CC_EINVAL, "domain index out of range");
+  if (which < CC_U || which > CC_THETA_P || level < 0 || level > 1 || (which != CC_THETA_P && level != 1))
+    return fail(m, CC_EINVAL, "bad field or level (velocities: level 1 only)");
+  if (!m->state) return fail(m, CC_ESTATE, "state not initialised");
+  const DomHost &H = m->dom[d];
+  const long long n = (long long)H.D.nx * H.D.ny * (which == CC_THETA_P ? H.D.nz : H.D.nz + 1);
+  const int buf = level == 0 ? H.r[0] : H.r[1];
+  CK(m, launch_derived(H.D, m->d_doms + d, m->prec, buf, which, m->d_stage, m->st), "derived");
+  CK(m, cudaMemcpyAsync(host, m->d_stage, n * 8, cudaMemcpyDeviceToHost, m->st), "derived copy");
+  CK(m, cudaStreamSynchronize(m->st), "derived sync");
+  return CC_OK;
 }
 
 cc_status cc_upload_state_async(cc_model *m, int d, int field, int level, const double *host) {
@@ -1231,8 +1290,9 @@ cc_status cc_diagnostics(cc_model *m, int d, cc_diag *out) {
   if (!m->state) return fail(m, CC_ESTATE, "state not initialised");
   const DomHost &H = m->dom[d];
   CK(m, launch_diag_reduce(H.D, m->d_doms + d, m->prec, H.r[1], m->d_diag, m->st), "diagnostics");
+  CK(m, launch_heat(m->d_doms + d, m->prec, H.r[1], m->d_diag + 5, m->d_diag + 8 + 5 * 256, m->st), "heat");
   double h[8];
-  CK(m, cudaMemcpyAsync(h, m->d_diag, sizeof(double) * 5, cudaMemcpyDeviceToHost, m->st), "diag copy");
+  CK(m, cudaMemcpyAsync(h, m->d_diag, sizeof(double) * 7, cudaMemcpyDeviceToHost, m->st), "diag copy");
   CK(m, cudaStreamSynchronize(m->st), "diag sync");
   out->mass = h[0];
   out->mass_comp = h[1];
@@ -1240,6 +1300,8 @@ cc_status cc_diagnostics(cc_model *m, int d, cc_diag *out) {
   out->max_w = h[3];
   out->nonfinite = (long long)h[4];
   out->steps = H.nsteps;
+  out->heat = h[5];
+  out->heat_comp = h[6];
   if (out->nonfinite > 0) return fail(m, CC_ENUMERIC, "non-finite values in the state");
   return CC_OK;
 }

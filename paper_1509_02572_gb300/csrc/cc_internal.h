@@ -191,6 +191,15 @@ int sched_tile_y(int prec, int s);
 cudaError_t full_prepare(int prec);
 cudaError_t launch_init_momentum(const DomDev &D, const DomDev *d_dom, int prec, int r, double U,
                                  cudaStream_t st);
+// derived output: corner velocity component which = 0..2 (K = 0 .. nz) or the
+// cell potential-temperature perturbation (which = 3), FP64 host layout
+cudaError_t launch_derived(const DomDev &D, const DomDev *d_dom, int prec, int r, int which, double *d_out,
+                           cudaStream_t st);
+// heat content: d_out[0] sum, d_out[1] compensation; d_part 2 * 256 doubles
+cudaError_t launch_heat(const DomDev *d_dom, int prec, int r, double *d_out, double *d_part, cudaStream_t st);
+// analytic hill at the corners (I dx - xc, J dy - yc), ny*nx doubles
+cudaError_t launch_hill(double *h, int nx, int ny, double dx, double dy, int kind, double h0, double a, double xc,
+                        double yc, cudaStream_t st);
 cudaError_t launch_diag_reduce(const DomDev &D, const DomDev *d_dom, int prec, int r, double *d_out,
                                cudaStream_t st);
 

@@ -528,6 +528,37 @@ __global__ void k_kb(DomDev D, int32_t *kb) {
 
 }  // namespace
 
+// Analytic hill at the corners (I dx, J dy) relative to its centre (xc, yc):
+// the bell-shaped hill h0 / (1 + r^2/a^2)^(3/2) (Sec 3.1.1), the half-
+// ellipsoid h0 sqrt(1 - r^2/a^2) (the hemisphere of Sec 3.1.2 when h0 = a)
+// and the cosine hill h0 (1 + cos(pi r / a)) / 2 for r < a (appendix).  This
+// unit is compiled without contraction, so every operation rounds as written.
+__global__ void k_hill(double *h, int nx, int ny, double dx, double dy, int kind, double h0, double a, double xc,
+                       double yc) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nx * ny) return;
+  const int I = (int)(t % nx), J = (int)(t / nx);
+  const double x = (double)I * dx - xc, y = (double)J * dy - yc;
+  const double r2 = x * x + y * y;
+  double v = 0.0;
+  if (kind == CC_HILL_BELL) {
+    v = h0 / pow(1.0 + r2 / (a * a), 1.5);
+  } else if (kind == CC_HILL_ELLIPSOID) {
+    v = h0 * sqrt(fmax(0.0, 1.0 - r2 / (a * a)));
+  } else if (kind == CC_HILL_COSINE) {
+    const double r = sqrt(r2);
+    v = r < a ? 0.5 * h0 * (1.0 + cos(M_PI * r / a)) : 0.0;
+  }
+  h[t] = v;
+}
+
+cudaError_t launch_hill(double *h, int nx, int ny, double dx, double dy, int kind, double h0, double a, double xc,
+                        double yc, cudaStream_t st) {
+  long long n = (long long)nx * ny;
+  k_hill<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(h, nx, ny, dx, dy, kind, h0, a, xc, yc);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_flat_columns(const DomDev &D, cudaStream_t st) {
   k_flat_columns<<<nblk((long long)D.px * D.py), TPB, 0, st>>>(D);
   return cudaGetLastError();

@@ -995,6 +995,83 @@ __global__ void k_diag_final(const double *part, int nb, double *out) {
 }
 
 
+// ------------------------------------------------------------------ derived output (not on the step path)
+// Corner velocity for corners K = 0 .. nz (the velocity every flux uses:
+// the boundary-point value at or below the terrain, else momentum / corner
+// density) or, for which == 3, the potential-temperature perturbation of each
+// cell, theta' = ((rho theta)' - theta_bar rho') / (rho_bar + rho') with
+// theta_bar = (rho theta)_bar / rho_bar; FP64 host layout.
+template <typename T>
+__global__ void k_derived(const DomDev *__restrict__ dom, int r, int which, double *__restrict__ out) {
+  const DomDev &D = *dom;
+  const long long ncol = (long long)D.nx * D.ny;
+  const long long n = ncol * (which == 3 ? D.nz : D.nz + 1);
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const int i = (int)(t % D.nx), j = (int)((t / D.nx) % D.ny), k = (int)(t / ncol);
+  const T *rp = (const T *)D.f[r][0];
+  const T *rhob = (const T *)D.rhob;
+  if (which == 3) {
+    const long long o = pidx(D, i, j, k);
+    const int kp = k + GH;
+    const T *thb = (const T *)D.thb;
+    const double X = (double)theta_pert(D, thb, (const T *)D.pb, (const T *)D.ipb, kp, ((const T *)D.f[r][1])[o]);
+    const double rb = (double)rhob[kp], rv = (double)rp[o];
+    out[t] = (X - (double)thb[kp] / rb * rv) / (rb + rv);
+    return;
+  }
+  const T *M[3] = {(const T *)D.f[r][2], (const T *)D.f[r][3], (const T *)D.f[r][4]};
+  T u[3];
+  corner_u<T>(D, rp, M, rhob, (const T *)D.ub[r], i, j, k, u);
+  out[t] = (double)u[which];
+}
+
+// Heat content sum_G V_G (rho theta)'_G: every member cell of a merge group
+// adds its volume times the host's (rho theta)' (evaluated at the host's
+// level); cells below the terrain have no volume.  Neumaier sums in FP64,
+// fixed block count and order.
+template <typename T>
+__global__ void k_heat_partial(const DomDev *__restrict__ dom, int r, double *part) {
+  const DomDev &D = *dom;
+  const T *pp = (const T *)D.f[r][1];
+  const double V0 = D.dx * D.dy * D.dz;
+  const long long ncol = (long long)D.nx * D.ny, n = ncol * D.nz;
+  NSum<double> acc{0, 0};
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int32_t h = D.root[t];
+    if (h < 0 || D.vf[t] == 0.0) continue;
+    const int ih = (int)(h % D.nx), jh = (int)((h / D.nx) % D.ny), kh = (int)(h / ncol);
+    const T x = theta_pert(D, (const T *)D.thb, (const T *)D.pb, (const T *)D.ipb, kh + GH, pp[pidx(D, ih, jh, kh)]);
+    acc.add(D.vf[t] * V0 * (double)x);
+  }
+  __shared__ double sh[2][DIAG_TPB];
+  sh[0][threadIdx.x] = acc.s;
+  sh[1][threadIdx.x] = acc.c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    NSum<double> S{0, 0};
+    double cc = 0;
+    for (int a = 0; a < DIAG_TPB; a++) {
+      S.add(sh[0][a]);
+      cc += sh[1][a];
+    }
+    part[2 * blockIdx.x] = S.s;
+    part[2 * blockIdx.x + 1] = S.c + cc;
+  }
+}
+
+__global__ void k_heat_final(const double *part, int nb, double *out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  NSum<double> S{0, 0};
+  double cc = 0;
+  for (int b = 0; b < nb; b++) {
+    S.add(part[2 * b]);
+    cc += part[2 * b + 1];
+  }
+  out[0] = S.s + (S.c + cc);
+  out[1] = S.c + cc;
+}
+
 // ------------------------------------------------------------------ refinement (Sec 2.2)
 __device__ __forceinline__ void decode(const DomDev &D, long long off, int &i, int &j, int &k) {
   i = (int)(off % D.px) - GX;
@@ -1428,6 +1505,21 @@ cudaError_t launch_diag_reduce(const DomDev &D, const DomDev *d_dom, int prec, i
 
 namespace {
 inline unsigned nb256(long long n) { return (unsigned)((n + 255) / 256); }
+}
+
+cudaError_t launch_derived(const DomDev &D, const DomDev *d_dom, int prec, int r, int which, double *d_out,
+                           cudaStream_t st) {
+  long long n = (long long)D.nx * D.ny * (which == 3 ? D.nz : D.nz + 1);
+  if (prec == CC_FP64) k_derived<double><<<nb256(n), 256, 0, st>>>(d_dom, r, which, d_out);
+  else k_derived<float><<<nb256(n), 256, 0, st>>>(d_dom, r, which, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_heat(const DomDev *d_dom, int prec, int r, double *d_out, double *d_part, cudaStream_t st) {
+  if (prec == CC_FP64) k_heat_partial<double><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(d_dom, r, d_part);
+  else k_heat_partial<float><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(d_dom, r, d_part);
+  k_heat_final<<<1, 32, 0, st>>>(d_part, DIAG_BLOCKS, d_out);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_prolong(const LevelLink &L, int prec, int rC, cudaStream_t st) {

@@ -28,8 +28,14 @@ EXPORTS = ("cc_create", "cc_destroy", "cc_last_error", "cc_set_terrain", "cc_bui
            "cc_profile_enable", "cc_profile_read", "cc_profile_reset", "cc_create_refined",
            "cc_refine_mass", "cc_domain_count", "cc_autotune", "cc_get_schedule", "cc_set_schedule",
            "cc_graphs_enable", "cc_upload_state_async", "cc_download_state_async", "cc_save", "cc_load",
+           "cc_set_terrain_analytic", "cc_get_terrain", "cc_download_derived",
            "cc_mass_sum_noalloc", "cc_noalloc_last_error")
 CC_NOALLOC_MAX_PARTS = 1024
+CC_HILL_BELL, CC_HILL_ELLIPSOID, CC_HILL_COSINE = range(3)
+HILL_KINDS = {"bell": CC_HILL_BELL, "ellipsoid": CC_HILL_ELLIPSOID, "hemisphere": CC_HILL_ELLIPSOID,
+              "cosine": CC_HILL_COSINE}
+# derived output fields: corner velocity components, cell theta'
+CC_U, CC_V, CC_W, CC_THETA_P = range(4)
 CC_K_FULL, CC_K_GROUPS, CC_K_DIAGNOSE, CC_K_REFINE = range(4)
 KERNEL_NAMES = {CC_K_FULL: "k_full", CC_K_GROUPS: "k_groups", CC_K_DIAGNOSE: "k_diag", CC_K_REFINE: "refinement"}
 
@@ -51,7 +57,8 @@ class CCBox(ct.Structure):
 
 class CCDiag(ct.Structure):
     _fields_ = [("mass", ct.c_double), ("mass_comp", ct.c_double), ("max_u", ct.c_double),
-                ("max_w", ct.c_double), ("nonfinite", ct.c_longlong), ("steps", ct.c_longlong)]
+                ("max_w", ct.c_double), ("nonfinite", ct.c_longlong), ("steps", ct.c_longlong),
+                ("heat", ct.c_double), ("heat_comp", ct.c_double)]
 
 
 class CutcellError(RuntimeError):
@@ -78,6 +85,9 @@ def load(path: str = LIB_PATH):
     L.cc_last_error.restype = ct.c_char_p
     L.cc_last_error.argtypes = [vp]
     L.cc_set_terrain.argtypes = [vp, i, vp]
+    L.cc_set_terrain_analytic.argtypes = [vp, i, i, vp]
+    L.cc_get_terrain.argtypes = [vp, i, vp]
+    L.cc_download_derived.argtypes = [vp, i, i, i, vp]
     L.cc_build_geometry.argtypes = [vp]
     L.cc_get_geometry.argtypes = [vp, i] + [vp] * 7
     L.cc_get_stencils.argtypes = [vp, i] + [vp] * 8
@@ -191,6 +201,23 @@ class Model:
         assert h.shape == (c.ny, c.nx)
         self._check(self.L.cc_set_terrain(self.h, d, _p(h)))
 
+    def set_terrain_analytic(self, d: int, kind, h0: float, a: float, xc: float | None = None,
+                             yc: float | None = None):
+        """Hill evaluated on the GPU at the corners of domain d (centred on the
+        domain by default); kind is CC_HILL_* or a name of HILL_KINDS."""
+        c = self.cfgs[d]
+        k = HILL_KINDS[kind] if isinstance(kind, str) else int(kind)
+        xc = 0.5 * c.nx * c.dx if xc is None else xc
+        yc = 0.5 * c.ny * c.dy if yc is None else yc
+        prm = np.array([h0, a, xc, yc], np.float64)
+        self._check(self.L.cc_set_terrain_analytic(self.h, d, k, _p(prm)))
+
+    def terrain(self, d: int = 0) -> np.ndarray:
+        c = self.cfgs[d]
+        out = np.zeros((c.ny, c.nx))
+        self._check(self.L.cc_get_terrain(self.h, d, _p(out)))
+        return out
+
     def build_geometry(self):
         self._check(self.L.cc_build_geometry(self.h))
 
@@ -244,6 +271,15 @@ class Model:
         self._check(self.L.cc_download_state(self.h, d, field, level, _p(out)))
         return out
 
+    def derived(self, d: int, which: int, level: int = 1) -> np.ndarray:
+        """Corner velocity component (CC_U, CC_V, CC_W; corners K = 0 .. nz)
+        or the cell potential-temperature perturbation (CC_THETA_P)."""
+        c = self.cfgs[d]
+        shape = (c.nz, c.ny, c.nx) if which == CC_THETA_P else (c.nz + 1, c.ny, c.nx)
+        out = np.zeros(shape)
+        self._check(self.L.cc_download_derived(self.h, d, which, level, _p(out)))
+        return out
+
     def download_ptr(self, d: int, field: int, level: int, ptr: int, wait: bool = True):
         fn = self.L.cc_download_state if wait else self.L.cc_download_state_async
         self._check(fn(self.h, d, field, level, ct.c_void_p(ptr)))
@@ -269,7 +305,7 @@ class Model:
         if check:
             self._check(st)
         return dict(mass=g.mass, mass_comp=g.mass_comp, max_u=g.max_u, max_w=g.max_w,
-                    nonfinite=g.nonfinite, steps=g.steps, status=st)
+                    nonfinite=g.nonfinite, steps=g.steps, heat=g.heat, heat_comp=g.heat_comp, status=st)
 
     @property
     def last_launch_count(self) -> int:
