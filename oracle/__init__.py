@@ -76,6 +76,7 @@ def lib():
             L.oc_heat.restype = ct.c_double
             L.oc_heat.argtypes = [ct.c_void_p, ct.c_int]
             L.oc_get_derived.argtypes = [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p]
+            L.oc_error_norms.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_int, ct.c_double, ct.c_void_p]
             L.oc_line_int.restype = ct.c_double
             L.oc_line_int.argtypes = [ct.c_double] * 4
             L.oc_line_frac.restype = ct.c_double
@@ -233,6 +234,16 @@ class Model:
         if st != OK:
             raise OracleError(f"get_derived {which} {level} -> {st}")
         return a.reshape(shape)
+
+
+def error_norms(a: Model, b: Model, which: int, zmin: float):
+    """(L1, L2, N) of a corner velocity component of model a against the
+    finer model b at the coincident corners above zmin."""
+    out = np.zeros(3)
+    st = lib().oc_error_norms(a._m, b._m, which, float(zmin), _ptr(out))
+    if st != OK:
+        raise OracleError(f"error_norms -> {st}")
+    return out[0], out[1], int(out[2])
 
 
 def line_int(z, ha, hb, length):

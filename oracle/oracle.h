@@ -42,6 +42,7 @@ double oc_mass(const oc_model *m, int level);
 int oc_nsteps(const oc_model *m);
 double oc_heat(const oc_model *m, int level);
 int oc_get_derived(const oc_model *m, int which, int level, double *out);
+int oc_error_norms(const oc_model *a, const oc_model *b, int which, double zmin, double *out);
 
 double oc_line_int(double z, double ha, double hb, double len);
 double oc_line_frac(double z, double ha, double hb);

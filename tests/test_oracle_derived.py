@@ -165,3 +165,55 @@ def test_heat_over_a_hill_uses_merged_volumes(oracle_mod):
     assert abs(om.heat() - want) <= 1e-9 * abs(want)
     # merging moves volume between cells but keeps the fluid volume
     assert abs(np.sum(g["vg"][host]) - np.sum(g["vf"]) * cfg.dx * cfg.dy * cfg.dz) <= 1e-9 * np.sum(g["vg"][host])
+
+
+def _set_u(oracle_mod, om, fu):
+    """Momentum rho_c * fu(I, J, K) on every corner level of a flat-floor
+    model at rest density (rho_c = mean base density of the levels K-1, K)."""
+    rhob, pb, koff, _ = _levels(om)
+    nz, ny, nx = om.cell_shape
+    K = np.arange(-om.gz, nz + om.gz + 1)
+    rc = 0.5 * (rhob[K - 1 + koff] + rhob[K + koff])
+    I = np.arange(nx)[None, None, :]
+    J = np.arange(ny)[None, :, None]
+    om.set_field(oracle_mod.F_MX, 1, rc[:, None, None] * fu(I, J, K[:, None, None]))
+
+
+def test_error_norms_of_a_known_difference(oracle_mod):
+    """The appendix's L1 and L2 norms: a coarse model holding u = U and a
+    model refined by 2 holding U + delta at the coincident corners give the
+    mean of |delta| and the root mean square of delta over the coarse
+    corners above zmin; equal fields give zero."""
+    a = oracle_mod.Model(_flat(8, 6, 10, 200.0))
+    b = oracle_mod.Model(_flat(16, 12, 20, 100.0))
+    a.init_state()
+    b.init_state()
+    U = 7.0
+    _set_u(oracle_mod, a, lambda I, J, K: U + 0.0 * (I + J + K))
+    _set_u(oracle_mod, b, lambda I, J, K: U + 0.0 * (I + J + K))
+    l1, l2, n = oracle_mod.error_norms(a, b, oracle_mod.D_U, 250.0)
+    assert n == 8 * 6 * 9  # corner levels K = 2 .. 10 lie above 250 m
+    assert l1 <= 4e-16 * U and l2 <= 4e-16 * U
+    assert oracle_mod.error_norms(a, b, oracle_mod.D_W, 250.0)[:2] == (0.0, 0.0)
+
+    def delta(I, J, K):
+        return 1e-2 * np.sin(0.7 * I + 1.3 * J) * np.cos(0.4 * K) + 1e-3 * (I % 3)
+
+    _set_u(oracle_mod, b, lambda I, J, K: U + delta(I, J, K))
+    Ia, Ja, Ka = np.meshgrid(np.arange(8), np.arange(6), np.arange(2, 11), indexing="ij")
+    d = delta(2 * Ia, 2 * Ja, 2 * Ka)
+    l1, l2, n = oracle_mod.error_norms(a, b, oracle_mod.D_U, 250.0)
+    assert n == d.size
+    assert abs(l1 - np.mean(np.abs(d))) <= 1e-12 * np.mean(np.abs(d))
+    assert abs(l2 - np.sqrt(np.mean(d ** 2))) <= 1e-12 * np.sqrt(np.mean(d ** 2))
+    # every level above the floor when zmin is below it
+    assert oracle_mod.error_norms(a, b, oracle_mod.D_U, -1.0)[2] == 8 * 6 * 11
+
+
+def test_error_norms_reject_incommensurate_grids(oracle_mod):
+    a = oracle_mod.Model(_flat(8, 6, 10, 200.0))
+    for b in (oracle_mod.Model(_flat(12, 9, 15, 133.33)), oracle_mod.Model(_flat(16, 12, 18, 100.0))):
+        with pytest.raises(oracle_mod.OracleError):
+            oracle_mod.error_norms(a, b, oracle_mod.D_U, 0.0)
+    with pytest.raises(oracle_mod.OracleError):
+        oracle_mod.error_norms(a, a, oracle_mod.D_THETA, 0.0)
