@@ -191,6 +191,20 @@ enum { CC_U = 0, CC_V = 1, CC_W = 2, CC_THETA_P = 3 };
  * CC_EINVAL for a bad domain, field or level, CC_ESTATE before a state. */
 cc_status cc_download_derived(const cc_model *m, int d, int which, int level, double *host);
 
+/* Global error norms of the appendix accuracy test ("Estimation of global
+ * accuracy"): the corner velocity component `which` (CC_U, CC_V, CC_W) of the
+ * current level of domain da of model a against domain db of model b, a
+ * finer solution of the same problem taken as exact, at the coincident
+ * corners, over the N corners of a with K dz > zmin (the grid points above
+ * the hill top; zmin = -inf takes every corner level 0 .. nz):
+ *   out[0] = L1 = (1/N) sum |psi_a - psi_b|,
+ *   out[1] = L2 = ((1/N) sum (psi_a - psi_b)^2)^(1/2),   out[2] = N.
+ * b's spacing must be a's divided by one integer r >= 1 in x, y and z over
+ * the same extents (CC_EINVAL otherwise); the models may differ in
+ * precision.  Both on the current device; waits for b's stream, computes on
+ * a's and synchronises it.  Errors are reported on a. */
+cc_status cc_error_norms(const cc_model *a, int da, const cc_model *b, int db, int which, double zmin, double *out);
+
 /* The same transfers queued on the model's stream without waiting (no
  * counterpart in the paper; for callers that move whole states every step):
  * the host buffer must stay valid and unchanged (upload) or unread

@@ -966,6 +966,37 @@ cc_status cc_download_derived(const cc_model *mc, int d, int which, int level, d
   return CC_OK;
 }
 
+cc_status cc_error_norms(const cc_model *ac, int da, const cc_model *bc, int db, int which, double zmin,
+                         double *out) {
+  cc_model *a = const_cast<cc_model *>(ac), *b = const_cast<cc_model *>(bc);
+  if (!a || !b || !out) return fail(a, CC_EINVAL, "null argument");
+  if (da < 0 || da >= a->ndom || db < 0 || db >= b->ndom) return fail(a, CC_EINVAL, "domain index out of range");
+  if (which < CC_U || which > CC_W) return fail(a, CC_EINVAL, "error norms are of a velocity component");
+  if (!std::isfinite(zmin) && !(zmin < 0)) return fail(a, CC_EINVAL, "zmin must be finite or -inf");
+  if (!a->state || !b->state) return fail(a, CC_ESTATE, "state not initialised");
+  const DomHost &A = a->dom[da], &B = b->dom[db];
+  const cc_config &ca = A.cfg, &cb = B.cfg;
+  const int r = (int)std::floor(ca.dx / cb.dx + 0.5);
+  if (r < 1 || std::fabs(r * cb.dx - ca.dx) > 1e-9 * ca.dx || std::fabs(r * cb.dy - ca.dy) > 1e-9 * ca.dy ||
+      std::fabs(r * cb.dz - ca.dz) > 1e-9 * ca.dz || ca.nx * r != cb.nx || ca.ny * r != cb.ny || ca.nz * r != cb.nz)
+    return fail(a, CC_EINVAL, "the second model must refine the first by one integer ratio over the same domain");
+  int kmin = 0;
+  while (kmin <= ca.nz && !(kmin * ca.dz > zmin)) kmin++;
+  double h[2] = {0.0, 0.0};
+  const long long n = (long long)ca.nx * ca.ny * (ca.nz + 1 - kmin);
+  if (n > 0) {
+    CK(a, cudaStreamSynchronize(b->st), "norms: sync of the finer model");
+    CK(a, launch_norms(a->d_doms + da, a->prec, A.r[1], b->d_doms + db, b->prec, B.r[1], which, r, kmin, a->d_diag,
+                       a->d_diag + 8, a->st), "norms");
+    CK(a, cudaMemcpyAsync(h, a->d_diag, sizeof(h), cudaMemcpyDeviceToHost, a->st), "norms copy");
+    CK(a, cudaStreamSynchronize(a->st), "norms sync");
+  }
+  out[0] = n > 0 ? h[0] / n : 0.0;
+  out[1] = n > 0 ? std::sqrt(h[1] / n) : 0.0;
+  out[2] = (double)n;
+  return CC_OK;
+}
+
 cc_status cc_upload_state_async(cc_model *m, int d, int field, int level, const double *host) {
   return upload(m, d, field, level, host, false);
 }

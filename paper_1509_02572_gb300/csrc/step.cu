@@ -1072,6 +1072,64 @@ __global__ void k_heat_final(const double *part, int nb, double *out) {
   out[1] = S.c + cc;
 }
 
+// Global error norms (appendix accuracy test): the corner velocity component
+// `which` of model A against the finer model B at the coincident corners
+// (r I, r J, r K), over the corners K >= kmin of A; Neumaier sums of |d| and
+// d^2 in FP64, fixed block count and order.
+template <typename TA, typename TB>
+__global__ void k_norms(const DomDev *__restrict__ A, int ra, const DomDev *__restrict__ B, int rb, int which, int r,
+                        int kmin, double *part) {
+  const DomDev &Da = *A, &Db = *B;
+  const long long ncol = (long long)Da.nx * Da.ny, n = ncol * (Da.nz + 1 - kmin);
+  const TA *Ma[3] = {(const TA *)Da.f[ra][2], (const TA *)Da.f[ra][3], (const TA *)Da.f[ra][4]};
+  const TB *Mb[3] = {(const TB *)Db.f[rb][2], (const TB *)Db.f[rb][3], (const TB *)Db.f[rb][4]};
+  NSum<double> s1{0, 0}, s2{0, 0};
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const int I = (int)(t % Da.nx), J = (int)((t / Da.nx) % Da.ny), K = kmin + (int)(t / ncol);
+    TA ua[3];
+    TB ub[3];
+    corner_u<TA>(Da, (const TA *)Da.f[ra][0], Ma, (const TA *)Da.rhob, (const TA *)Da.ub[ra], I, J, K, ua);
+    corner_u<TB>(Db, (const TB *)Db.f[rb][0], Mb, (const TB *)Db.rhob, (const TB *)Db.ub[rb], r * I, r * J, r * K, ub);
+    const double d = (double)ua[which] - (double)ub[which];
+    s1.add(fabs(d));
+    s2.add(d * d);
+  }
+  __shared__ double sh[4][DIAG_TPB];
+  sh[0][threadIdx.x] = s1.s;
+  sh[1][threadIdx.x] = s1.c;
+  sh[2][threadIdx.x] = s2.s;
+  sh[3][threadIdx.x] = s2.c;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    NSum<double> S1{0, 0}, S2{0, 0};
+    double c1 = 0, c2 = 0;
+    for (int a = 0; a < DIAG_TPB; a++) {
+      S1.add(sh[0][a]);
+      c1 += sh[1][a];
+      S2.add(sh[2][a]);
+      c2 += sh[3][a];
+    }
+    part[4 * blockIdx.x] = S1.s;
+    part[4 * blockIdx.x + 1] = S1.c + c1;
+    part[4 * blockIdx.x + 2] = S2.s;
+    part[4 * blockIdx.x + 3] = S2.c + c2;
+  }
+}
+
+__global__ void k_norms_final(const double *part, int nb, double *out) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  NSum<double> S1{0, 0}, S2{0, 0};
+  double c1 = 0, c2 = 0;
+  for (int b = 0; b < nb; b++) {
+    S1.add(part[4 * b]);
+    c1 += part[4 * b + 1];
+    S2.add(part[4 * b + 2]);
+    c2 += part[4 * b + 3];
+  }
+  out[0] = S1.s + (S1.c + c1);
+  out[1] = S2.s + (S2.c + c2);
+}
+
 // ------------------------------------------------------------------ refinement (Sec 2.2)
 __device__ __forceinline__ void decode(const DomDev &D, long long off, int &i, int &j, int &k) {
   i = (int)(off % D.px) - GX;
@@ -1512,6 +1570,20 @@ cudaError_t launch_derived(const DomDev &D, const DomDev *d_dom, int prec, int r
   long long n = (long long)D.nx * D.ny * (which == 3 ? D.nz : D.nz + 1);
   if (prec == CC_FP64) k_derived<double><<<nb256(n), 256, 0, st>>>(d_dom, r, which, d_out);
   else k_derived<float><<<nb256(n), 256, 0, st>>>(d_dom, r, which, d_out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norms(const DomDev *a, int prec_a, int ra, const DomDev *b, int prec_b, int rb, int which, int r,
+                         int kmin, double *d_out, double *d_part, cudaStream_t st) {
+  if (prec_a == CC_FP64 && prec_b == CC_FP64)
+    k_norms<double, double><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(a, ra, b, rb, which, r, kmin, d_part);
+  else if (prec_a == CC_FP64)
+    k_norms<double, float><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(a, ra, b, rb, which, r, kmin, d_part);
+  else if (prec_b == CC_FP64)
+    k_norms<float, double><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(a, ra, b, rb, which, r, kmin, d_part);
+  else
+    k_norms<float, float><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(a, ra, b, rb, which, r, kmin, d_part);
+  k_norms_final<<<1, 32, 0, st>>>(d_part, DIAG_BLOCKS, d_out);
   return cudaGetLastError();
 }
 

@@ -28,7 +28,7 @@ EXPORTS = ("cc_create", "cc_destroy", "cc_last_error", "cc_set_terrain", "cc_bui
            "cc_profile_enable", "cc_profile_read", "cc_profile_reset", "cc_create_refined",
            "cc_refine_mass", "cc_domain_count", "cc_autotune", "cc_get_schedule", "cc_set_schedule",
            "cc_graphs_enable", "cc_upload_state_async", "cc_download_state_async", "cc_save", "cc_load",
-           "cc_set_terrain_analytic", "cc_get_terrain", "cc_download_derived",
+           "cc_set_terrain_analytic", "cc_get_terrain", "cc_download_derived", "cc_error_norms",
            "cc_mass_sum_noalloc", "cc_noalloc_last_error")
 CC_NOALLOC_MAX_PARTS = 1024
 CC_HILL_BELL, CC_HILL_ELLIPSOID, CC_HILL_COSINE = range(3)
@@ -88,6 +88,7 @@ def load(path: str = LIB_PATH):
     L.cc_set_terrain_analytic.argtypes = [vp, i, i, vp]
     L.cc_get_terrain.argtypes = [vp, i, vp]
     L.cc_download_derived.argtypes = [vp, i, i, i, vp]
+    L.cc_error_norms.argtypes = [vp, i, vp, i, i, d, vp]
     L.cc_build_geometry.argtypes = [vp]
     L.cc_get_geometry.argtypes = [vp, i] + [vp] * 7
     L.cc_get_stencils.argtypes = [vp, i] + [vp] * 8
@@ -346,6 +347,15 @@ class Model:
         ms, n = ct.c_double(), ct.c_longlong()
         self._check(self.L.cc_profile_read(self.h, kernel, ct.byref(ms), ct.byref(n)))
         return ms.value, n.value
+
+
+def error_norms(a: "Model", da: int, b: "Model", db: int, which: int, zmin: float = float("-inf")):
+    """(L1, L2, N) of a corner velocity component of domain da of model a
+    against the finer domain db of model b at the coincident corners above
+    zmin (cc_error_norms)."""
+    out = np.zeros(3)
+    a._check(a.L.cc_error_norms(a.h, da, b.h, db, which, float(zmin), _p(out)))
+    return out[0], out[1], int(out[2])
 
 
 class _Level:
