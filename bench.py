@@ -565,17 +565,20 @@ def main():
         ke = max(2, min(args.steps, 5))
         barrier()
         t0 = time.perf_counter()
+        iter_ms = []
         for _ in range(ke):
+            ti = time.perf_counter()
             for (d, f, lev), a in host.items():
                 model.upload_ptr(d, f, lev, a.data_ptr(), wait=False)
             model.step(1)
             for d in range(len(cfgs)):
                 model.download_ptr(d, cc.CC_PP, 1, outs[d].data_ptr(), wait=False)
             model.synchronize()  # the step's result is on the host
+            iter_ms.append(round(1e3 * (time.perf_counter() - ti), 2))
         barrier()
         te = time.perf_counter() - t0
         line["e2e"] = {"value": nfluid * ke * world / te, "unit": METRIC, "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": d2h, "steps": ke,
+                       "d2h_bytes_per_step": d2h, "steps": ke, "iter_ms": iter_ms,
                        "how": "per step: upload both time levels of every prognostic field from pinned host "
                               "FP64 arrays, one step, download p' of every domain, then wait for it (transfers "
                               "queued on the model's stream, one host wait per step)"}

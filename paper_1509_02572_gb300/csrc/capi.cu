@@ -86,6 +86,14 @@ struct cc_model {
   std::vector<Ev> ev_used;
   double *d_diag = nullptr;     // 8 results + partials
   double *d_stage = nullptr;    // FP64 staging for host transfers
+  // state uploads and downloads alternate between d_stage and d_stage2; an
+  // upload's host copy runs on the transfer stream xs, so that it overlaps
+  // the conversion kernel of the previous transfer on the model's stream
+  double *d_stage2 = nullptr;
+  cudaStream_t xs = nullptr;
+  cudaEvent_t ev_copied[2] = {}, ev_staged[2] = {};
+  bool used_valid[2] = {false, false};
+  int xslot = 0;
   size_t stage_elems = 0;
   int *d_err = nullptr;
   std::string err;
@@ -596,6 +604,15 @@ cc_status cc_destroy(cc_model *m) {
   for (auto e : m->ev_pool) cudaEventDestroy(e);
   for (auto &g : m->graphs) cudaGraphExecDestroy(g.exec);
   if (m->cap) cudaStreamDestroy(m->cap);
+  if (m->xs) {
+    cudaStreamSynchronize(m->xs);
+    cudaStreamDestroy(m->xs);
+  }
+  for (int a = 0; a < 2; a++) {
+    if (m->ev_copied[a]) cudaEventDestroy(m->ev_copied[a]);
+    if (m->ev_staged[a]) cudaEventDestroy(m->ev_staged[a]);
+  }
+  cudaFree(m->d_stage2);
   delete m;
   return CC_OK;
 }
@@ -890,25 +907,55 @@ static long long field_elems(const DomDev &D, int field, int *nlev, int *kfirst)
 // Transfers through the model's device staging buffer, in the model's
 // stream order (the staging buffer is reused only after the previous
 // transfer's kernel or copy, so no host wait is needed between them).
+// The transfer stream, its events and the second staging buffer, made on
+// first use.
+static cc_status transfer_setup(cc_model *m) {
+  if (m->xs) return CC_OK;
+  CK(m, cudaStreamCreateWithFlags(&m->xs, cudaStreamNonBlocking), "transfer stream");
+  for (int a = 0; a < 2; a++) {
+    CK(m, cudaEventCreateWithFlags(&m->ev_copied[a], cudaEventDisableTiming), "transfer event");
+    CK(m, cudaEventCreateWithFlags(&m->ev_staged[a], cudaEventDisableTiming), "transfer event");
+  }
+  cudaError_t e = cudaMalloc(&m->d_stage2, sizeof(double) * m->stage_elems);
+  if (e != cudaSuccess) {
+    m->d_stage2 = nullptr;
+    return fail(m, e == cudaErrorMemoryAllocation ? CC_ENOMEM : CC_ECUDA, "second staging buffer");
+  }
+  return CC_OK;
+}
+
 static cc_status upload(cc_model *m, int d, int field, int level, const double *host, bool sync) {
   if (!m || !host) return fail(m, CC_EINVAL, "null argument");
   if (d < 0 || d >= m->ndom) return fail(m, CC_EINVAL, "domain index out of range");
   if (field < 0 || field > CC_UB || level < 0 || level > 1) return fail(m, CC_EINVAL, "bad field or level");
   if (!m->state) return fail(m, CC_ESTATE, "state not initialised");
+  cc_status r = transfer_setup(m);
+  if (r != CC_OK) return r;
   const DomDev &D = m->dom[d].D;
   int buf = level == 0 ? m->dom[d].r[0] : m->dom[d].r[1];
   int nlev, kfirst;
   long long n = field_elems(D, field, &nlev, &kfirst);
-  CK(m, cudaMemcpyAsync(m->d_stage, host, n * 8, cudaMemcpyHostToDevice, m->st), "upload");
+  // host -> staging on the transfer stream, once the model's stream is done
+  // with this staging buffer; the conversion into the field on the model's
+  // stream after the copy
+  const int sl = m->xslot;
+  m->xslot ^= 1;
+  double *stage = sl ? m->d_stage2 : m->d_stage;
+  if (m->used_valid[sl]) CK(m, cudaStreamWaitEvent(m->xs, m->ev_staged[sl], 0), "upload order");
+  CK(m, cudaMemcpyAsync(stage, host, n * 8, cudaMemcpyHostToDevice, m->xs), "upload");
+  CK(m, cudaEventRecord(m->ev_copied[sl], m->xs), "upload event");
+  CK(m, cudaStreamWaitEvent(m->st, m->ev_copied[sl], 0), "upload order");
   if (field == CC_UB) {
-    if (m->prec == CC_FP64) k_scatter_cols<double><<<nb256(n), 256, 0, m->st>>>(m->d_stage, (double *)D.ub[buf], D, 3);
-    else k_scatter_cols<float><<<nb256(n), 256, 0, m->st>>>(m->d_stage, (float *)D.ub[buf], D, 3);
+    if (m->prec == CC_FP64) k_scatter_cols<double><<<nb256(n), 256, 0, m->st>>>(stage, (double *)D.ub[buf], D, 3);
+    else k_scatter_cols<float><<<nb256(n), 256, 0, m->st>>>(stage, (float *)D.ub[buf], D, 3);
   } else {
     void *dst = D.f[buf][field];
-    if (m->prec == CC_FP64) k_scatter<double><<<nb256(n), 256, 0, m->st>>>(m->d_stage, (double *)dst, D, nlev, kfirst);
-    else k_scatter<float><<<nb256(n), 256, 0, m->st>>>(m->d_stage, (float *)dst, D, nlev, kfirst);
+    if (m->prec == CC_FP64) k_scatter<double><<<nb256(n), 256, 0, m->st>>>(stage, (double *)dst, D, nlev, kfirst);
+    else k_scatter<float><<<nb256(n), 256, 0, m->st>>>(stage, (float *)dst, D, nlev, kfirst);
   }
   CK(m, cudaGetLastError(), "upload scatter");
+  CK(m, cudaEventRecord(m->ev_staged[sl], m->st), "upload event");
+  m->used_valid[sl] = true;
   if (sync) CK(m, cudaStreamSynchronize(m->st), "upload sync");
   return CC_OK;
 }
@@ -918,24 +965,33 @@ static cc_status download(cc_model *m, int d, int field, int level, double *host
   if (d < 0 || d >= m->ndom) return fail(m, CC_EINVAL, "domain index out of range");
   if (field < 0 || field > CC_UB || level < 0 || level > 1) return fail(m, CC_EINVAL, "bad field or level");
   if (!m->state) return fail(m, CC_ESTATE, "state not initialised");
+  cc_status r = transfer_setup(m);
+  if (r != CC_OK) return r;
   const DomDev &D = m->dom[d].D;
   int buf = level == 0 ? m->dom[d].r[0] : m->dom[d].r[1];
   int nlev, kfirst;
   long long n = field_elems(D, field, &nlev, &kfirst);
+  // gather and copy on the model's stream (an upload's copy into this
+  // staging buffer is ordered before them by its conversion kernel)
+  const int sl = m->xslot;
+  m->xslot ^= 1;
+  double *stage = sl ? m->d_stage2 : m->d_stage;
   if (field == CC_UB) {
     if (m->prec == CC_FP64)
-      k_gather_cols_cvt<double><<<nb256(n), 256, 0, m->st>>>((const double *)D.ub[buf], m->d_stage, D, 3);
+      k_gather_cols_cvt<double><<<nb256(n), 256, 0, m->st>>>((const double *)D.ub[buf], stage, D, 3);
     else
-      k_gather_cols_cvt<float><<<nb256(n), 256, 0, m->st>>>((const float *)D.ub[buf], m->d_stage, D, 3);
+      k_gather_cols_cvt<float><<<nb256(n), 256, 0, m->st>>>((const float *)D.ub[buf], stage, D, 3);
   } else {
     const void *src = D.f[buf][field];
     if (m->prec == CC_FP64)
-      k_gather<double><<<nb256(n), 256, 0, m->st>>>((const double *)src, m->d_stage, D, nlev, kfirst);
+      k_gather<double><<<nb256(n), 256, 0, m->st>>>((const double *)src, stage, D, nlev, kfirst);
     else
-      k_gather<float><<<nb256(n), 256, 0, m->st>>>((const float *)src, m->d_stage, D, nlev, kfirst);
+      k_gather<float><<<nb256(n), 256, 0, m->st>>>((const float *)src, stage, D, nlev, kfirst);
   }
   CK(m, cudaGetLastError(), "download gather");
-  CK(m, cudaMemcpyAsync(host, m->d_stage, n * 8, cudaMemcpyDeviceToHost, m->st), "download");
+  CK(m, cudaMemcpyAsync(host, stage, n * 8, cudaMemcpyDeviceToHost, m->st), "download");
+  CK(m, cudaEventRecord(m->ev_staged[sl], m->st), "download event");
+  m->used_valid[sl] = true;
   if (sync) CK(m, cudaStreamSynchronize(m->st), "download sync");
   return CC_OK;
 }
