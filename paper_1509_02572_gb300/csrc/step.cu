@@ -393,11 +393,8 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
     }
   };
   // totals of plane kk from its raw plane
-  auto derive = [&](int kk) {
-    const int a5 = s5(kk), a4 = s4(kk), kp = kk + GH;
-    const T rb = rhob[kp];
-    EosK<T> ek;
-    ek.load(thb, pb, ipb, pik, kp);
+  auto derive_e = [&](int kk, const T rb, const EosK<T> ek) {
+    const int a5 = s5(kk), a4 = s4(kk);
 #pragma unroll
     for (int s = 0; s < NLP; s++) {
       const int p = lpt[s];
@@ -406,6 +403,11 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
         S.th[a4][p] = ek.tot(E, S.cp[a5][p]);
       }
     }
+  };
+  auto derive = [&](int kk) {
+    EosK<T> ek;
+    ek.load(thb, pb, ipb, pik, kk + GH);
+    derive_e(kk, rhob[kk + GH], ek);
   };
   // corner velocity of plane K = momentum / mean density of the 8 cells
   // around; corners at or below the terrain take the boundary-point velocity
@@ -434,10 +436,8 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
     }
   };
   // (rho theta)' at n-1 of plane kk (in-plane diffusion stencil)
-  auto derive_old = [&](int kk) {
-    const int a4 = s4(kk), kp = kk + GH;
-    EosK<T> ek;
-    ek.load(thb, pb, ipb, pik, kp);
+  auto derive_old_e = [&](int kk, const EosK<T> ek) {
+    const int a4 = s4(kk);
 #pragma unroll
     for (int s = 0; s < NLP; s++) {
       const int p = lpt[s];
@@ -461,14 +461,17 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
 
   // own column at n-1 for the vertical diffusion stencils, levels k-2 .. k+2
   T treg[5], mreg[5][3];
-  auto own_old = [&](int a, int kk) {
+  auto own_old_e = [&](int a, int kk, const EosK<T> ek) {
     const int a4 = s4(kk);
-    EosK<T> ek;
-    ek.load(thb, pb, ipb, pik, kk + GH);
     treg[a] = ek.pert(E, S.op[a4][c]);
     mreg[a][0] = S.om[a4][0][c];
     mreg[a][1] = S.om[a4][1][c];
     mreg[a][2] = S.om[a4][2][c];
+  };
+  auto own_old = [&](int a, int kk) {
+    EosK<T> ek;
+    ek.load(thb, pb, ipb, pik, kk + GH);
+    own_old_e(a, kk, ek);
   };
 
   // prologue: raw planes k0-2 .. k0+2 (momentum from k0-1, n-1 fields from
@@ -503,14 +506,22 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
     T rO_ = 0;
     const long long o = (long long)(k + GH) * plane + own;
     if (active) rO_ = rpO[o];
+    // base state of the levels this plane uses, loaded before the wait so
+    // that their latency hides behind it
+    EosK<T> ek0, ek2;
+    ek0.load(thb, pb, ipb, pik, k + GH);
+    ek2.load(thb, pb, ipb, pik, k + 2 + GH);
+    const T rb2 = rhob[k + 2 + GH], tk = tau[k + GH];
+    const T rbc[5] = {rhobc[k + GH - 2] * U, rhobc[k + GH - 1] * U, rhobc[k + GH] * U, rhobc[k + GH + 1] * U,
+                      rhobc[k + GH + 2] * U};
     await_groups<0>();
     __syncthreads();
     issue(k + 3, true, true);
     acommit();
-    derive(k + 2);
+    derive_e(k + 2, rb2, ek2);
     velocity(k + 1);
-    derive_old(k);
-    own_old(4, k + 2);
+    derive_old_e(k, ek0);
+    own_old_e(4, k + 2, ek2);
     __syncthreads();
     // phase 2: the cell and corner of this thread on plane k
     if (active) {
@@ -548,9 +559,7 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
              d4(Tk[c - 2 * HX], Tk[c - HX], Tk[c], Tk[c + HX], Tk[c + 2 * HX]) +
              d4(treg[0], treg[1], treg[2], treg[3], treg[4]);
       T Dth = -kdif * dd;
-      const int kp = k + GH;
-      EosK<T> ek;
-      ek.load(thb, pb, ipb, pik, kp);
+      const EosK<T> &ek = ek0;
       T rC_ = S.cr[ck][c], pC_ = S.cp[ck][c];
       const T mcur[3] = {S.cm[sk][0][c], S.cm[sk][1][c], S.cm[sk][2][c]};
       T pO_ = S.op[s4(k)][c];
@@ -594,8 +603,6 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
       const T *Q0 = S.cr[ck], *Qm = S.cr[ckm];
       T r8 = (Q0[cSW] + Q0[cS] + Q0[cW] + Q0[c]) + (Qm[cSW] + Qm[cS] + Qm[cW] + Qm[c]);
       T pg[3] = {(pE - pW) * qdx, (pNn - pS) * qdy, (pT - pB) * qdz};
-      const T tk = tau[kp];
-      const T rbc[5] = {rhobc[kp - 2] * U, rhobc[kp - 1] * U, rhobc[kp] * U, rhobc[kp + 1] * U, rhobc[kp + 2] * U};
       T mnew[3], mflt[3];
       const int ok4 = s4(k);
 #pragma unroll
