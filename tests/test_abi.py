@@ -63,3 +63,27 @@ def test_binding_fails_loudly_without_library(tmp_path):
             cutcell.load(str(tmp_path / "missing.so"))
     finally:
         cutcell._lib = saved
+
+
+def test_create_rejects_empty_and_inconsistent_inputs(lib):
+    """Empty and inconsistent inputs fail in the argument checks, before any
+    CUDA call: no domains, domains that disagree on R / cp / p0, refined
+    models with too few levels or odd box extents, a NULL result pointer."""
+    from paper_1509_02572_gb300 import cutcell, workloads as W
+    L = cutcell.load()
+    h = ctypes.c_void_p()
+    one = cutcell.config_from(W.C1_BELL)
+    assert L.cc_create(ctypes.byref(one), 0, cutcell.CC_FP64, None, ctypes.byref(h)) == cutcell.CC_EINVAL
+    assert b"at least one domain" in L.cc_last_error(None) and not h.value
+    two = (cutcell.CCConfig * 2)(cutcell.config_from(W.C1_BELL), cutcell.config_from(W.C1_BELL.replace(R=288.0)))
+    assert L.cc_create(two, 2, cutcell.CC_FP32, None, ctypes.byref(h)) == cutcell.CC_EINVAL
+    assert b"share R" in L.cc_last_error(None)
+    assert L.cc_create(ctypes.byref(one), 1, cutcell.CC_FP64, None, None) == cutcell.CC_EINVAL
+    base = cutcell.config_from(W.SMALL_REFINED.base)
+    boxes = (cutcell.CCBox * 1)(cutcell.CCBox(32, 32, 16, 16, 16))
+    assert L.cc_create_refined(ctypes.byref(base), 1, boxes, cutcell.CC_FP32, None,
+                               ctypes.byref(h)) == cutcell.CC_EINVAL
+    odd = (cutcell.CCBox * 1)(cutcell.CCBox(31, 32, 16, 16, 16))
+    assert L.cc_create_refined(ctypes.byref(base), 2, odd, cutcell.CC_FP32, None,
+                               ctypes.byref(h)) == cutcell.CC_EINVAL
+    assert b"even" in L.cc_last_error(None) and not h.value
