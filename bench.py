@@ -101,6 +101,24 @@ def kfull_traffic(dtype, cells, schedule):
     return None if per is None else per * cells
 
 
+def refined_kfull_traffic(dtype, workload, schedules):
+    """DRAM bytes of the full-cell stencil per launch, averaged over the
+    launches of one cycle (as the refined roofline averages its algorithmic
+    bytes), from the committed ncu capture of the refined workload; None when
+    the kernel, the precision, the workload or the tile heights of the levels
+    differ (the items per launch only split the z-columns)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_full_traffic.json")) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    r = t.get("refined")
+    if (r is None or t.get("source_hash") != kfull_source_hash() or dtype != "f32"
+            or r.get("workload") != workload or [x[0] for x in r.get("schedule", [])] != [x[0] for x in schedules]):
+        return None
+    return r["cycle_dram_bytes"] / r["cycle_launches"]
+
+
 def job_time_and_rate(ms, units_per_rank, world, dist=None, device="cuda"):
     """Whole-job timing over the ranks: the slowest rank's time (max over
     ranks) and the units all ranks processed divided by it."""
@@ -306,8 +324,12 @@ def bench_refined(cc, torch, args, hbm, peak_kind, barrier, world):
     stages = {cc.KERNEL_NAMES[k]: dict(zip(("ms_total", "launches"), m.profile_read(k))) for k in cc.KERNEL_NAMES}
     m.profile(False)
     gms = time_graphs(torch, m, args.steps)
-    kbytes = refined_kfull_bytes(m, "f32") * args.steps
-    achieved = kbytes / (kms / 1e3) / 1e9
+    # per launch, averaged over the launches of a cycle (the profiled launches
+    # include the warm-up cycles): one k_full launch per level and substep
+    per_cycle = sum(2 ** l for l in range(m.nlev))
+    kavg = kms / max(1, kn)
+    achieved = refined_kfull_bytes(m, "f32") / per_cycle / (kavg / 1e3) / 1e9
+    schedules = [list(m.schedule(l)) for l in range(m.nlev)]
     out = {"workload": rc.name, "levels": [list(b) for b in rc.boxes], "value": upd * args.steps * world / (ms / 1e3),
            "schedule": [list(m.schedule(l)) for l in range(m.nlev)],
            "unit": METRIC, "ms_per_step": ms / args.steps, "cell_updates_per_step": upd, "dtype": "f32",
@@ -315,7 +337,9 @@ def bench_refined(cc, torch, args, hbm, peak_kind, barrier, world):
            "graphs": {"ms_per_step": gms, "value": upd * world / (gms / 1e3), "unit": METRIC,
                       "how": "the same cycles replayed from CUDA graphs, no per-stage events"},
            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-                        "traffic": None, "kernel": "k_full", "kernel_ms": kms / max(1, kn), "launches": kn,
+                        "traffic": refined_kfull_traffic("f32", rc.name, schedules),
+                        "traffic_unit": "bytes per launch, averaged over a cycle",
+                        "kernel": "k_full", "kernel_ms": kavg, "launches": kn,
                         "peak_kind": f"{peak_kind} hbm_gbs",
                         "bytes_per_cell": BYTES_PER_CELL["f32"],
                         "how": "interior cells of every level times its substeps, per launch averaged over levels"}}
