@@ -1122,28 +1122,34 @@ int oc_get_derived(const oc_model *m, int which, int level, double *out) {
 
 /* Global error norms of the appendix accuracy test: the corner velocity
  * component `which` (OC_D_U, OC_D_V, OC_D_W) of level 1 of model a against
- * the finer model b at the coincident corners, over the corners of a above
- * the height zmin (the grid points above the hill top):
+ * the finer model b at the corners the two grids share, over those corners of
+ * a that lie above the height zmin (the grid points above the hill top):
  *   out[0] = L1 = (1/N) sum |psi_a - psi_b|,
  *   out[1] = L2 = ((1/N) sum (psi_a - psi_b)^2)^(1/2),   out[2] = N.
- * b's spacing must divide a's by the same integer r >= 1 in every direction
- * and both must cover the same domain. */
+ * The spacings must be in one ratio dx_a / dx_b = p / q (integers, lowest
+ * terms, q <= 16) in every direction over the same domain; corner I of a is
+ * corner I p / q of b when q divides I, and only those corners count. */
 int oc_error_norms(const oc_model *a, const oc_model *b, int which, double zmin, double *out) {
   if (which < OC_D_U || which > OC_D_W) return OC_EINVAL;
-  double rr = a->P.dx / b->P.dx;
-  int r = (int)floor(rr + 0.5);
-  if (r < 1 || fabs(r * b->P.dx - a->P.dx) > 1e-9 * a->P.dx || fabs(r * b->P.dy - a->P.dy) > 1e-9 * a->P.dy ||
-      fabs(r * b->P.dz - a->P.dz) > 1e-9 * a->P.dz || a->nx * r != b->nx || a->ny * r != b->ny || a->nz * r != b->nz)
+  int p = 0, q = 0;
+  for (int qq = 1; qq <= 16 && !p; qq++) {
+    double pp = a->P.dx / b->P.dx * qq;
+    int pi = (int)floor(pp + 0.5);
+    if (pi >= qq && fabs(pi - pp) <= 1e-9 * pp) { p = pi; q = qq; }
+  }
+  if (!p) return OC_EINVAL;
+  if (fabs(p * b->P.dy - q * a->P.dy) > 1e-9 * q * a->P.dy || fabs(p * b->P.dz - q * a->P.dz) > 1e-9 * q * a->P.dz ||
+      (long)a->nx * p != (long)b->nx * q || (long)a->ny * p != (long)b->ny * q || (long)a->nz * p != (long)b->nz * q)
     return OC_EINVAL;
   double s1 = 0.0, s2 = 0.0;
   long n = 0;
-  for (int K = 0; K <= a->nz; K++) {
+  for (int K = 0; K <= a->nz; K += q) {
     if (!(K * a->P.dz > zmin)) continue;
-    for (int J = 0; J < a->ny; J++)
-      for (int I = 0; I < a->nx; I++) {
+    for (int J = 0; J < a->ny; J += q)
+      for (int I = 0; I < a->nx; I += q) {
         double ua[3], ub[3];
         corner_velocity(a, 1, I, J, K, ua);
-        corner_velocity(b, 1, r * I, r * J, r * K, ub);
+        corner_velocity(b, 1, I / q * p, J / q * p, K / q * p, ub);
         double d = ua[which - OC_D_U] - ub[which - OC_D_U];
         s1 += fabs(d);
         s2 += d * d;

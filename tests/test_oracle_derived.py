@@ -217,3 +217,26 @@ def test_error_norms_reject_incommensurate_grids(oracle_mod):
             oracle_mod.error_norms(a, b, oracle_mod.D_U, 0.0)
     with pytest.raises(oracle_mod.OracleError):
         oracle_mod.error_norms(a, a, oracle_mod.D_THETA, 0.0)
+
+
+def test_error_norms_at_a_rational_ratio(oracle_mod):
+    """Spacings in the ratio 5/2 (250 m against 100 m, as in the appendix):
+    only every second coarse corner coincides with a fine corner (every
+    500 m), and the norms are taken over those."""
+    a = oracle_mod.Model(_flat(8, 6, 10, 250.0))
+    b = oracle_mod.Model(_flat(20, 15, 25, 100.0))
+    a.init_state()
+    b.init_state()
+    U = 5.0
+    _set_u(oracle_mod, a, lambda I, J, K: U + 0.0 * (I + J + K))
+
+    def delta(I, J, K):
+        return 1e-2 * np.cos(0.3 * I - 0.2 * J) * (1.0 + 0.1 * K)
+
+    _set_u(oracle_mod, b, lambda I, J, K: U + delta(I, J, K))
+    Ia, Ja, Ka = np.meshgrid(np.arange(0, 8, 2), np.arange(0, 6, 2), np.arange(2, 11, 2), indexing="ij")
+    d = delta(Ia // 2 * 5, Ja // 2 * 5, Ka // 2 * 5)
+    l1, l2, n = oracle_mod.error_norms(a, b, oracle_mod.D_U, 300.0)  # K dz > 300 m: K = 2, 4, .., 10
+    assert n == d.size == 4 * 3 * 5
+    assert abs(l1 - np.mean(np.abs(d))) <= 1e-12 * np.mean(np.abs(d))
+    assert abs(l2 - np.sqrt(np.mean(d ** 2))) <= 1e-12 * np.sqrt(np.mean(d ** 2))
