@@ -22,6 +22,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -46,7 +47,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="ensemble", choices=["ensemble", "hemisphere", "bell512", "refined"])
+    ap.add_argument("--workload", default="ensemble",
+                    choices=["ensemble", "hemisphere", "bell512", "refined", "convergence"])
+    ap.add_argument("--seconds", type=float, default=3600.0,
+                    help="simulated time of each run of the convergence workload")
     ap.add_argument("--error-steps", type=int, default=0,
                     help="extra untimed steps of the FP32 and FP64 runs before their difference is taken")
     ap.add_argument("--no-refined", action="store_true", help="skip the refined object of the default run")
@@ -436,6 +440,59 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_convergence(cc, torch, args):
+    """The appendix accuracy experiment on the paper's domain: flow over the
+    cosine hill (h_m = 400 m, a = 2 km, centred at (32, 16) km) on a periodic
+    64 x 32 x 16 km domain with equal spacing 400, 250, 200 and 100 m, U = 10
+    m/s, N = 0.01 1/s, Theta = 300 K, sponge above 10 km, FP32, for the same
+    simulated time; the L1 and L2 errors of u and w above the hill top against
+    the 100 m run, at the corners the grids share, and the orders between
+    successive spacings. One JSON line."""
+    h0, a = 400.0, 2000.0
+    res = [100.0, 400.0, 250.0, 200.0]  # the reference run first
+
+    def run(d):
+        nx, ny, nz = int(round(64000 / d)), int(round(32000 / d)), int(round(16000 / d))
+        cfg = W.RunConfig(f"cosine-{d:g}m", nx, ny, nz, d, d, d, 0.15 * d / 200.0, 1, "cosine", h0, a,
+                          theta0=300.0)
+        m = cc.Model([cfg], cc.CC_FP32)
+        m.set_terrain_analytic(0, "cosine", h0, a)
+        m.build_geometry()
+        m.init_state()
+        n = int(round(args.seconds / cfg.dt))
+        t0 = time.perf_counter()
+        m.step(n)
+        m.synchronize()
+        dg = m.diagnostics(0)
+        return m, cfg, n, time.perf_counter() - t0, dg
+
+    fine, fcfg, fn, fsec, fdg = run(res[0])
+    runs = {res[0]: {"grid": [fcfg.nx, fcfg.ny, fcfg.nz], "steps": fn, "wall_s": round(fsec, 2),
+                     "max_w": fdg["max_w"]}}
+    for d in res[1:]:
+        m, cfg, n, sec, dg = run(d)
+        e = {"grid": [cfg.nx, cfg.ny, cfg.nz], "steps": n, "wall_s": round(sec, 2), "max_w": dg["max_w"]}
+        for nm, w in (("u", cc.CC_U), ("w", cc.CC_W)):
+            l1, l2, cnt = cc.error_norms(m, 0, fine, 0, w, h0)
+            e[nm] = {"L1": l1, "L2": l2, "points": cnt}
+        runs[d] = e
+        m.close()
+    fine.close()
+    coarse = sorted(res[1:], reverse=True)
+    orders = {}
+    for nm in ("u", "w"):
+        for norm in ("L1", "L2"):
+            orders[f"{nm}_{norm}"] = [math.log(runs[x][nm][norm] / runs[y][nm][norm]) / math.log(x / y)
+                                      for x, y in zip(coarse, coarse[1:])]
+    line = {"metric": "global error of u and w against the 100 m run (L1, L2)", "unit": "m/s",
+            "workload": "convergence-cosine-64x32x16km", "seconds": args.seconds, "dtype": "f32",
+            "data": "synthetic", "n_gpus": 1, "zmin": h0,
+            "runs": {f"{k:g}m": v for k, v in runs.items()}, "orders": orders,
+            "how": "orders between successive spacings 400-250-200 m, log(e1/e2)/log(d1/d2); the paper's "
+                   "appendix reports second order"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     global SCHEDULE
     args = parse()
@@ -463,6 +520,12 @@ def main():
         torch.cuda.synchronize()
 
     hbm, peak_kind = peaks()
+    if args.workload == "convergence":
+        if rank == 0:
+            run_convergence(cc, torch, args)
+        if world > 1:
+            dist.destroy_process_group()
+        return
     if args.workload == "refined":
         r = bench_refined(cc, torch, args, hbm, peak_kind, barrier, world)
         msps, rate = job_time_and_rate(r["ms_per_step"], r["cell_updates_per_step"], world, dist)

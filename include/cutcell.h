@@ -194,14 +194,16 @@ cc_status cc_download_derived(const cc_model *m, int d, int which, int level, do
 /* Global error norms of the appendix accuracy test ("Estimation of global
  * accuracy"): the corner velocity component `which` (CC_U, CC_V, CC_W) of the
  * current level of domain da of model a against domain db of model b, a
- * finer solution of the same problem taken as exact, at the coincident
- * corners, over the N corners of a with K dz > zmin (the grid points above
- * the hill top; zmin = -inf takes every corner level 0 .. nz):
+ * finer solution of the same problem taken as exact, at the corners the two
+ * grids share, over the N shared corners of a with K dz > zmin (the grid
+ * points above the hill top; zmin = -inf takes every corner level 0 .. nz):
  *   out[0] = L1 = (1/N) sum |psi_a - psi_b|,
  *   out[1] = L2 = ((1/N) sum (psi_a - psi_b)^2)^(1/2),   out[2] = N.
- * b's spacing must be a's divided by one integer r >= 1 in x, y and z over
- * the same extents (CC_EINVAL otherwise); the models may differ in
- * precision.  Both on the current device; waits for b's stream, computes on
+ * The spacings must be in one ratio dx_a / dx_b = p / q >= 1 (integers in
+ * lowest terms, q <= 16) in x, y and z over the same extents (CC_EINVAL
+ * otherwise); corner I of a is corner I p / q of b when q divides I, and only
+ * those corners count (every corner for an integer ratio).  The models may
+ * differ in precision.  Both on the current device; waits for b's stream, computes on
  * a's and synchronises it.  Errors are reported on a. */
 cc_status cc_error_norms(const cc_model *a, int da, const cc_model *b, int db, int which, double zmin, double *out);
 

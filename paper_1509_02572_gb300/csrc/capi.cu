@@ -1032,17 +1032,24 @@ cc_status cc_error_norms(const cc_model *ac, int da, const cc_model *bc, int db,
   if (!a->state || !b->state) return fail(a, CC_ESTATE, "state not initialised");
   const DomHost &A = a->dom[da], &B = b->dom[db];
   const cc_config &ca = A.cfg, &cb = B.cfg;
-  const int r = (int)std::floor(ca.dx / cb.dx + 0.5);
-  if (r < 1 || std::fabs(r * cb.dx - ca.dx) > 1e-9 * ca.dx || std::fabs(r * cb.dy - ca.dy) > 1e-9 * ca.dy ||
-      std::fabs(r * cb.dz - ca.dz) > 1e-9 * ca.dz || ca.nx * r != cb.nx || ca.ny * r != cb.ny || ca.nz * r != cb.nz)
-    return fail(a, CC_EINVAL, "the second model must refine the first by one integer ratio over the same domain");
+  // spacing ratio dx_a / dx_b = p / q in lowest terms, q <= 16
+  int p = 0, q = 0;
+  for (int qq = 1; qq <= 16 && !p; qq++) {
+    const double pp = ca.dx / cb.dx * qq;
+    const int pi = (int)std::floor(pp + 0.5);
+    if (pi >= qq && std::fabs(pi - pp) <= 1e-9 * pp) { p = pi; q = qq; }
+  }
+  if (!p || std::fabs(p * cb.dy - q * ca.dy) > 1e-9 * q * ca.dy || std::fabs(p * cb.dz - q * ca.dz) > 1e-9 * q * ca.dz ||
+      (long long)ca.nx * p != (long long)cb.nx * q || (long long)ca.ny * p != (long long)cb.ny * q ||
+      (long long)ca.nz * p != (long long)cb.nz * q)
+    return fail(a, CC_EINVAL, "the second model must refine the first by one ratio p/q (q <= 16) over the same domain");
   int kmin = 0;
   while (kmin <= ca.nz && !(kmin * ca.dz > zmin)) kmin++;
   double h[2] = {0.0, 0.0};
-  const long long n = (long long)ca.nx * ca.ny * (ca.nz + 1 - kmin);
+  const long long n = (long long)((ca.nx + q - 1) / q) * ((ca.ny + q - 1) / q) * (ca.nz / q + 1 - (kmin + q - 1) / q);
   if (n > 0) {
     CK(a, cudaStreamSynchronize(b->st), "norms: sync of the finer model");
-    CK(a, launch_norms(a->d_doms + da, a->prec, A.r[1], b->d_doms + db, b->prec, B.r[1], which, r, kmin, a->d_diag,
+    CK(a, launch_norms(a->d_doms + da, a->prec, A.r[1], b->d_doms + db, b->prec, B.r[1], which, p, q, kmin, a->d_diag,
                        a->d_diag + 8, a->st), "norms");
     CK(a, cudaMemcpyAsync(h, a->d_diag, sizeof(h), cudaMemcpyDeviceToHost, a->st), "norms copy");
     CK(a, cudaStreamSynchronize(a->st), "norms sync");

@@ -197,10 +197,11 @@ cudaError_t launch_derived(const DomDev &D, const DomDev *d_dom, int prec, int r
                            cudaStream_t st);
 // heat content: d_out[0] sum, d_out[1] compensation; d_part 2 * 256 doubles
 cudaError_t launch_heat(const DomDev *d_dom, int prec, int r, double *d_out, double *d_part, cudaStream_t st);
-// error norms: d_out[0] = sum |d|, d_out[1] = sum d^2 over the corners K >= kmin
-// of a against b at (r I, r J, r K); d_part 4 * 256 doubles
-cudaError_t launch_norms(const DomDev *a, int prec_a, int ra, const DomDev *b, int prec_b, int rb, int which, int r,
-                         int kmin, double *d_out, double *d_part, cudaStream_t st);
+// error norms: d_out[0] = sum |d|, d_out[1] = sum d^2 over the corners of a
+// shared with b (spacing ratio p/q: corner q I' of a is corner p I' of b) with
+// K >= kmin; d_part 4 * 256 doubles
+cudaError_t launch_norms(const DomDev *a, int prec_a, int ra, const DomDev *b, int prec_b, int rb, int which, int p,
+                         int q, int kmin, double *d_out, double *d_part, cudaStream_t st);
 // analytic hill at the corners (I dx - xc, J dy - yc), ny*nx doubles
 cudaError_t launch_hill(double *h, int nx, int ny, double dx, double dy, int kind, double h0, double a, double xc,
                         double yc, cudaStream_t st);

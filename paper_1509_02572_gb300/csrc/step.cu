@@ -1080,23 +1080,27 @@ __global__ void k_heat_final(const double *part, int nb, double *out) {
 }
 
 // Global error norms (appendix accuracy test): the corner velocity component
-// `which` of model A against the finer model B at the coincident corners
-// (r I, r J, r K), over the corners K >= kmin of A; Neumaier sums of |d| and
-// d^2 in FP64, fixed block count and order.
+// `which` of model A against the finer model B at the corners the grids
+// share (spacing ratio p/q: corner q I' of A is corner p I' of B), over the
+// shared corners with K >= kmin of A; Neumaier sums of |d| and d^2 in FP64,
+// fixed block count and order.
 template <typename TA, typename TB>
-__global__ void k_norms(const DomDev *__restrict__ A, int ra, const DomDev *__restrict__ B, int rb, int which, int r,
-                        int kmin, double *part) {
+__global__ void k_norms(const DomDev *__restrict__ A, int ra, const DomDev *__restrict__ B, int rb, int which, int p,
+                        int q, int kmin, double *part) {
   const DomDev &Da = *A, &Db = *B;
-  const long long ncol = (long long)Da.nx * Da.ny, n = ncol * (Da.nz + 1 - kmin);
+  const int mx = (Da.nx + q - 1) / q, my = (Da.ny + q - 1) / q, k0 = (kmin + q - 1) / q;
+  const long long ncol = (long long)mx * my, n = ncol * (Da.nz / q + 1 - k0);
   const TA *Ma[3] = {(const TA *)Da.f[ra][2], (const TA *)Da.f[ra][3], (const TA *)Da.f[ra][4]};
   const TB *Mb[3] = {(const TB *)Db.f[rb][2], (const TB *)Db.f[rb][3], (const TB *)Db.f[rb][4]};
   NSum<double> s1{0, 0}, s2{0, 0};
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    const int I = (int)(t % Da.nx), J = (int)((t / Da.nx) % Da.ny), K = kmin + (int)(t / ncol);
+    const int Ip = (int)(t % mx), Jp = (int)((t / mx) % my), Kp = k0 + (int)(t / ncol);
     TA ua[3];
     TB ub[3];
-    corner_u<TA>(Da, (const TA *)Da.f[ra][0], Ma, (const TA *)Da.rhob, (const TA *)Da.ub[ra], I, J, K, ua);
-    corner_u<TB>(Db, (const TB *)Db.f[rb][0], Mb, (const TB *)Db.rhob, (const TB *)Db.ub[rb], r * I, r * J, r * K, ub);
+    corner_u<TA>(Da, (const TA *)Da.f[ra][0], Ma, (const TA *)Da.rhob, (const TA *)Da.ub[ra], q * Ip, q * Jp, q * Kp,
+                 ua);
+    corner_u<TB>(Db, (const TB *)Db.f[rb][0], Mb, (const TB *)Db.rhob, (const TB *)Db.ub[rb], p * Ip, p * Jp, p * Kp,
+                 ub);
     const double d = (double)ua[which] - (double)ub[which];
     s1.add(fabs(d));
     s2.add(d * d);
@@ -1580,16 +1584,16 @@ cudaError_t launch_derived(const DomDev &D, const DomDev *d_dom, int prec, int r
   return cudaGetLastError();
 }
 
-cudaError_t launch_norms(const DomDev *a, int prec_a, int ra, const DomDev *b, int prec_b, int rb, int which, int r,
-                         int kmin, double *d_out, double *d_part, cudaStream_t st) {
+cudaError_t launch_norms(const DomDev *a, int prec_a, int ra, const DomDev *b, int prec_b, int rb, int which, int p,
+                         int q, int kmin, double *d_out, double *d_part, cudaStream_t st) {
   if (prec_a == CC_FP64 && prec_b == CC_FP64)
-    k_norms<double, double><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(a, ra, b, rb, which, r, kmin, d_part);
+    k_norms<double, double><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(a, ra, b, rb, which, p, q, kmin, d_part);
   else if (prec_a == CC_FP64)
-    k_norms<double, float><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(a, ra, b, rb, which, r, kmin, d_part);
+    k_norms<double, float><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(a, ra, b, rb, which, p, q, kmin, d_part);
   else if (prec_b == CC_FP64)
-    k_norms<float, double><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(a, ra, b, rb, which, r, kmin, d_part);
+    k_norms<float, double><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(a, ra, b, rb, which, p, q, kmin, d_part);
   else
-    k_norms<float, float><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(a, ra, b, rb, which, r, kmin, d_part);
+    k_norms<float, float><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(a, ra, b, rb, which, p, q, kmin, d_part);
   k_norms_final<<<1, 32, 0, st>>>(d_part, DIAG_BLOCKS, d_out);
   return cudaGetLastError();
 }

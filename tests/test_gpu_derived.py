@@ -243,3 +243,27 @@ def test_cosine_hill_errors_fall_with_resolution(cc):
             assert e4[k] >= 1.5 * e2[k] > 0, (w, k, e4, e2)
     for m in runs.values():
         m.close()
+
+
+def test_error_norms_at_a_rational_ratio_match_oracle(cc, oracle_mod):
+    """250 m against 100 m (the appendix's 250 m run): the norms over the
+    corners the grids share (every 500 m) equal the oracle's."""
+    a_cfg = W.RunConfig("cosine-250m", 16, 12, 8, 250.0, 250.0, 250.0, 0.1875, 1, "cosine", 300.0, 1200.0)
+    b_cfg = a_cfg.replace(name="cosine-100m", nx=40, ny=30, nz=20, dx=100.0, dy=100.0, dz=100.0, dt=0.075)
+    oa, ob = oracle_mod.Model(a_cfg), oracle_mod.Model(b_cfg)
+    oa.init_state()
+    ob.init_state()
+    oa.step(160)
+    ob.step(400)
+    a, b = gpu_model(cc, a_cfg, cc.CC_FP64), gpu_model(cc, b_cfg, cc.CC_FP64)
+    a.init_state()
+    b.init_state()
+    a.step(160)
+    b.step(400)
+    for wg, wo in ((cc.CC_U, oracle_mod.D_U), (cc.CC_W, oracle_mod.D_W)):
+        l1, l2, n = cc.error_norms(a, 0, b, 0, wg, a_cfg.h0)
+        r1, r2, rn = oracle_mod.error_norms(oa, ob, wo, a_cfg.h0)
+        assert n == rn == 8 * 6 * 4  # corners K = 2, 4, 6, 8 lie above 300 m
+        assert abs(l1 - r1) <= 1e-9 * r1 and abs(l2 - r2) <= 1e-9 * r2, (wg, l1, r1, l2, r2)
+    a.close()
+    b.close()
