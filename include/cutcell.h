@@ -335,6 +335,36 @@ cc_status cc_refine_mass(cc_model *m, int both, double *out);
 /* Number of domains (ensemble members, or levels of a refined model). */
 int cc_domain_count(const cc_model *m);
 
+/* A cube of the block-structured layout: its refinement level and its index
+ * in cube units of that level (cube (ci, cj, ck) of level l covers cells
+ * ci*c .. (ci+1)*c - 1 of that level in x, and so on). */
+typedef struct {
+  int level, ci, cj, ck;
+} cc_cube;
+
+/* Block-structured cube layout (Sec 2.2, grid generation of the cube-based
+ * Cartesian mesh); host code, no GPU needed.  The level-0 domain of
+ * nx0 x ny0 x nz0 cells at spacing H is divided into cubes of cube^3 cells;
+ * cubes near the terrain are split into eight, level after level, up to
+ * level nlev-1 (spacing H / 2^l, every cube holding cube^3 cells); the sizes
+ * are then adjusted so that cubes touching across a face, an edge or a corner
+ * differ by at most one level (2:1); cubes completely inside the terrain are
+ * dropped.  Refinement test (the paper only says that cubes close to the
+ * terrain surface are split; this test gives its cube counts 64, 148, 232 for
+ * its hemisphere grids): a cube below the finest level is split when its
+ * bottom lies below the highest terrain point and its footprint lies within
+ * one cube width, horizontally, of a finest-level corner where the terrain
+ * is raised above its lowest value.  Lateral boundaries are periodic.
+ *   h_finest: corner heights of the finest level, (ny0 2^(nlev-1)) x
+ *             (nx0 2^(nlev-1)) doubles, x fastest (host array);
+ *   out:      capacity cubes, sorted by (level, ck, cj, ci), or NULL to get
+ *             the count only; *count receives the number of cubes.
+ * CC_EINVAL for extents that are not multiples of cube, nlev outside 1 .. 12,
+ * non-finite heights, or a capacity below the count (the count is still
+ * set). */
+cc_status cc_cbcm_cubes(int nx0, int ny0, int nz0, int cube, double H, int nlev, const double *h_finest,
+                        cc_cube *out, int capacity, int *count);
+
 /* Allocation-free mass sum (the paper has no counterpart; it is an entry
  * point for callers that cannot call cudaMalloc -- code running inside
  * another framework's memory pool, or a host application that reserves all

@@ -21,6 +21,7 @@ UNITS = {
     "step.cu": [],
     "capi.cu": [],
     "noalloc.cu": [],
+    "cbcm.cu": [],
 }
 
 

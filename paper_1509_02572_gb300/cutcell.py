@@ -28,7 +28,7 @@ EXPORTS = ("cc_create", "cc_destroy", "cc_last_error", "cc_set_terrain", "cc_bui
            "cc_profile_enable", "cc_profile_read", "cc_profile_reset", "cc_create_refined",
            "cc_refine_mass", "cc_domain_count", "cc_autotune", "cc_get_schedule", "cc_set_schedule",
            "cc_graphs_enable", "cc_upload_state_async", "cc_download_state_async", "cc_save", "cc_load",
-           "cc_set_terrain_analytic", "cc_get_terrain", "cc_download_derived", "cc_error_norms",
+           "cc_set_terrain_analytic", "cc_get_terrain", "cc_download_derived", "cc_error_norms", "cc_cbcm_cubes",
            "cc_mass_sum_noalloc", "cc_noalloc_last_error")
 CC_NOALLOC_MAX_PARTS = 1024
 CC_HILL_BELL, CC_HILL_ELLIPSOID, CC_HILL_COSINE = range(3)
@@ -61,6 +61,10 @@ class CCDiag(ct.Structure):
                 ("heat", ct.c_double), ("heat_comp", ct.c_double)]
 
 
+class CCCube(ct.Structure):
+    _fields_ = [("level", ct.c_int), ("ci", ct.c_int), ("cj", ct.c_int), ("ck", ct.c_int)]
+
+
 class CutcellError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -89,6 +93,7 @@ def load(path: str = LIB_PATH):
     L.cc_get_terrain.argtypes = [vp, i, vp]
     L.cc_download_derived.argtypes = [vp, i, i, i, vp]
     L.cc_error_norms.argtypes = [vp, i, vp, i, i, d, vp]
+    L.cc_cbcm_cubes.argtypes = [i, i, i, i, d, i, vp, vp, i, ct.POINTER(i)]
     L.cc_build_geometry.argtypes = [vp]
     L.cc_get_geometry.argtypes = [vp, i] + [vp] * 7
     L.cc_get_stencils.argtypes = [vp, i] + [vp] * 8
@@ -356,6 +361,22 @@ def error_norms(a: "Model", da: int, b: "Model", db: int, which: int, zmin: floa
     out = np.zeros(3)
     a._check(a.L.cc_error_norms(a.h, da, b.h, db, which, float(zmin), _p(out)))
     return out[0], out[1], int(out[2])
+
+
+def cbcm_cubes(nx0: int, ny0: int, nz0: int, cube: int, H: float, nlev: int, h_finest: np.ndarray):
+    """Block-structured cube layout (cc_cbcm_cubes): a list of (level, ci,
+    cj, ck), sorted by (level, ck, cj, ci)."""
+    L = load()
+    h = np.ascontiguousarray(h_finest, dtype=np.float64)
+    n = ct.c_int()
+    st = L.cc_cbcm_cubes(nx0, ny0, nz0, cube, H, nlev, _p(h), None, 0, ct.byref(n))
+    if st != CC_OK:
+        raise CutcellError(st, "cube layout: invalid arguments")
+    arr = (CCCube * max(1, n.value))()
+    st = L.cc_cbcm_cubes(nx0, ny0, nz0, cube, H, nlev, _p(h), ct.cast(arr, ct.c_void_p), n.value, ct.byref(n))
+    if st != CC_OK:
+        raise CutcellError(st, "cube layout failed")
+    return [(c.level, c.ci, c.cj, c.ck) for c in arr[:n.value]]
 
 
 class _Level:

@@ -87,3 +87,31 @@ def test_create_rejects_empty_and_inconsistent_inputs(lib):
     assert L.cc_create_refined(ctypes.byref(base), 2, odd, cutcell.CC_FP32, None,
                                ctypes.byref(h)) == cutcell.CC_EINVAL
     assert b"even" in L.cc_last_error(None) and not h.value
+
+
+def test_cube_layout_is_host_code_equal_to_the_oracle(lib):
+    """The library's cube layout (host code, no GPU) equals the oracle's on
+    the paper's hemisphere grids, a ridge that needs the balance pass and a
+    plateau that drops cubes."""
+    import numpy as np
+    from paper_1509_02572_gb300 import cutcell, workloads as W
+    from oracle import cbcm
+    cases = []
+    for nlev in (1, 2, 3):
+        d = 400.0 / (1 << (nlev - 1))
+        h = W.corner_heights("hemisphere", int(64000 / d), int(32000 / d), d, d, 1000.0, 1000.0)
+        cases.append((160, 80, 40, 20, 400.0, nlev, h))
+    nf = 8 * 8 * 8
+    ridge = np.zeros((nf // 2, nf))
+    ridge[:, nf // 2] = 50.0
+    cases.append((64, 32, 16, 8, 100.0, 4, ridge))
+    plateau = np.full((64, 128), 900.0)
+    plateau[10, 10] = 950.0
+    cases.append((64, 32, 32, 8, 100.0, 2, plateau))
+    bell = W.corner_heights("bell", 256, 128, 50.0, 50.0, 600.0, 1500.0)
+    cases.append((64, 32, 32, 16, 200.0, 3, bell))
+    for args in cases:
+        assert cutcell.cbcm_cubes(*args) == cbcm.cube_layout(*args), args[:6]
+    assert [len(cutcell.cbcm_cubes(*c)) for c in cases[:3]] == [64, 148, 232]
+    with pytest.raises(cutcell.CutcellError):
+        cutcell.cbcm_cubes(30, 20, 20, 20, 400.0, 1, np.zeros((20, 30)))  # 30 is not a multiple of 20
