@@ -315,6 +315,13 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
         o[nn - 1] = (float)cn;
       }
       o[7] = (float)a;
+      double *od = w == 0 ? D.dsth : D.dsex;
+      cn = 1.0;
+      for (int nn = 1; nn <= 12; nn++) {
+        cn = cn * (a - (nn - 1)) / nn;
+        od[nn - 1] = cn;
+      }
+      od[12] = a;
     }
     double *h, *vf, *ax, *ay, *az, *ba, *bb, *bn, *mg;
     int8_t *cls, *vcls;
@@ -346,6 +353,10 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
     for (int a = 0; a < 8; a++) {
       m->eos.sth[a] = D0.sth[a];
       m->eos.sex[a] = D0.sex[a];
+    }
+    for (int a = 0; a < 13; a++) {
+      m->eos.dsth[a] = D0.dsth[a];
+      m->eos.dsex[a] = D0.dsex[a];
     }
     m->eos.p0 = D0.p0;
     m->eos.p0R = D0.p0 / D0.R;

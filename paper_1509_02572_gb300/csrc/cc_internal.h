@@ -57,6 +57,8 @@ struct DomDev {
   // binomial-series coefficients C(a, 1..7) and the exponent a, for
   // (1 + x)^a - 1 with a = cv/cp (rho theta) and a = R/cp (Exner factor)
   float sth[8], sex[8];
+  // the same series in FP64: C(a, 1..12) and the exponent a
+  double dsth[13], dsex[13];
   // geometry (FP64 / int), padded cell layout unless noted
   const double *h;           // corner heights, ny*nx (periodic)
   const double *vf;          // nz*ny*nx interior layout (cell id)
@@ -161,6 +163,7 @@ cudaError_t geom_build_one(DomDev &D, cudaStream_t st, int dom, int *d_err, int3
 // and p0 are the same for all), passed to the step kernels as parameters
 struct Eos {
   float sth[8], sex[8];  // binomial coefficients of (1+x)^(cv/cp) - 1 and (1+x)^(R/cp) - 1, then the exponent
+  double dsth[13], dsex[13];  // the same in FP64, 12 terms
   double p0, p0R, cvcp, kap;
 };
 

@@ -71,20 +71,32 @@ __device__ __forceinline__ float rinv(float rc) {
 }
 
 // rho*theta as a function of pressure (equation of state, Sec 2.1:
-// rho theta = (p0/R)(p/p0)^(cv/cp)) and the Exner-type factor (p/p0)^(R/cp).
-// FP64: direct powers; the product is rounded before the subtraction of the
-// base value (no fused multiply-add), so a resting state gives exactly zero.
-__device__ __forceinline__ double theta_tot(const DomDev &D, const double *thb, const double *pb,
-                                            const double *ipb, int kp, double pp) {
-  return __dmul_rn(D.p0 / D.R, pow((pb[kp] + pp) / D.p0, D.cvcp));
+// rho theta = (p0/R)(p/p0)^(cv/cp)) and the Exner-type factor (p/p0)^(R/cp),
+// both about the per-level base values: with x = p'/p_bar,
+// (rho theta)' = (rho theta)_bar ((1 + x)^(cv/cp) - 1) and the Exner factor
+// pi_bar (1 + ((1 + x)^(R/cp) - 1)).  FP64: (1 + x)^a - 1 as the binomial
+// series sum_{n=1..12} C(a, n) x^n for |x| < 1/32 (truncation below 1e-17
+// relative), else through log1p / expm1; a resting state gives exactly zero.
+__device__ __forceinline__ double pow1pm1(double x, const double *c) {
+  if (fabs(x) < 0.03125) {
+    double s = c[11];
+#pragma unroll
+    for (int n = 10; n >= 0; n--) s = fma(s, x, c[n]);
+    return __dmul_rn(s, x);
+  }
+  return expm1(__dmul_rn(c[12], log1p(x)));
 }
 __device__ __forceinline__ double theta_pert(const DomDev &D, const double *thb, const double *pb,
                                              const double *ipb, int kp, double pp) {
-  return __dsub_rn(theta_tot(D, thb, pb, ipb, kp, pp), thb[kp]);
+  return __dmul_rn(thb[kp], pow1pm1(__dmul_rn(pp, ipb[kp]), D.dsth));
+}
+__device__ __forceinline__ double theta_tot(const DomDev &D, const double *thb, const double *pb,
+                                            const double *ipb, int kp, double pp) {
+  return __dadd_rn(thb[kp], theta_pert(D, thb, pb, ipb, kp, pp));
 }
 __device__ __forceinline__ double exner_fac(const DomDev &D, const double *pik, const double *pb,
                                             const double *ipb, int kp, double pp) {
-  return pow((pb[kp] + pp) / D.p0, D.kap);
+  return fma(pik[kp], pow1pm1(__dmul_rn(pp, ipb[kp]), D.dsex), pik[kp]);
 }
 // FP32 perturbation form: with x = p'/p_bar, (1 + x)^a - 1 is summed as the
 // binomial series sum_{n=1..7} C(a, n) x^n for |x| < 1/16 (truncation below
@@ -141,14 +153,23 @@ __device__ __forceinline__ float theta_tot_e(const Eos &E, float thb, float ipb,
 __device__ __forceinline__ float exner_e(const Eos &E, float pik, float ipb, float pp) {
   return fmaf(pik, pow1pm1_e(__fmul_rn(pp, ipb), E.sex), pik);
 }
-__device__ __forceinline__ double theta_tot_e(const Eos &E, double pb, double pp) {
-  return __dmul_rn(E.p0R, pow((pb + pp) / E.p0, E.cvcp));
+__device__ __forceinline__ double pow1pm1_e(double x, const double (&c)[13]) {
+  if (fabs(x) < 0.03125) {
+    double s = c[11];
+#pragma unroll
+    for (int n = 10; n >= 0; n--) s = fma(s, x, c[n]);
+    return __dmul_rn(s, x);
+  }
+  return expm1(__dmul_rn(c[12], log1p(x)));
 }
-__device__ __forceinline__ double theta_pert_e(const Eos &E, double thb, double pb, double pp) {
-  return __dsub_rn(theta_tot_e(E, pb, pp), thb);
+__device__ __forceinline__ double theta_pert_e(const Eos &E, double thb, double ipb, double pp) {
+  return __dmul_rn(thb, pow1pm1_e(__dmul_rn(pp, ipb), E.dsth));
 }
-__device__ __forceinline__ double exner_e(const Eos &E, double pb, double pp) {
-  return pow((pb + pp) / E.p0, E.kap);
+__device__ __forceinline__ double theta_tot_e(const Eos &E, double thb, double ipb, double pp) {
+  return __dadd_rn(thb, theta_pert_e(E, thb, ipb, pp));
+}
+__device__ __forceinline__ double exner_e(const Eos &E, double pik, double ipb, double pp) {
+  return fma(pik, pow1pm1_e(__dmul_rn(pp, ipb), E.dsex), pik);
 }
 // per-precision adapters of one cell level kp
 template <typename T>
@@ -168,15 +189,16 @@ struct EosK<float> {
 };
 template <>
 struct EosK<double> {
-  double thb, pb;
-  __device__ __forceinline__ void load(const double *thb_, const double *pb_, const double *, const double *,
-                                       int kp) {
+  double thb, ipb, pik;
+  __device__ __forceinline__ void load(const double *thb_, const double *pb_, const double *ipb_,
+                                       const double *pik_, int kp) {
     thb = thb_[kp];
-    pb = pb_[kp];
+    ipb = ipb_[kp];
+    pik = pik_[kp];
   }
-  __device__ __forceinline__ double tot(const Eos &E, double pp) const { return theta_tot_e(E, pb, pp); }
-  __device__ __forceinline__ double pert(const Eos &E, double pp) const { return theta_pert_e(E, thb, pb, pp); }
-  __device__ __forceinline__ double exner(const Eos &E, double pp) const { return exner_e(E, pb, pp); }
+  __device__ __forceinline__ double tot(const Eos &E, double pp) const { return theta_tot_e(E, thb, ipb, pp); }
+  __device__ __forceinline__ double pert(const Eos &E, double pp) const { return theta_pert_e(E, thb, ipb, pp); }
+  __device__ __forceinline__ double exner(const Eos &E, double pp) const { return exner_e(E, pik, ipb, pp); }
 };
 
 __device__ __forceinline__ double d4(double a, double b, double c, double d, double e) {
