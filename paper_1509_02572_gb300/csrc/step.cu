@@ -41,22 +41,22 @@ struct Ar<float> {
 };
 
 // Face flux phi_f * u_n * S with phi_f the mean of the two cells (lower index
-// first) and u_n the mean of the four corner values in a fixed order.  Every
+// first) and u_n the mean of the four corner values, summed pairwise.  Every
 // operation is rounded as written, so a face evaluated from either side, or
 // by either kernel, gives the same bits and cancels exactly in the sum.
 template <typename T>
 __device__ __forceinline__ T face_flux(T pa, T pb, T u1, T u2, T u3, T u4, T S) {
   using A = Ar<T>;
-  T un = A::mul(A::add(A::add(A::add(u1, u2), u3), u4), T(0.25));
+  T un = A::mul(A::add(A::add(u1, u2), A::add(u3, u4)), T(0.25));
   return A::mul(A::mul(A::mul(A::add(pa, pb), T(0.5)), un), S);
 }
 
-// Corner density: mean of the eight surrounding cell totals, fixed order
-// (dk outer, then dj, then di; -1 before 0).
+// Corner density: mean of the eight surrounding cell totals (dk outer, then
+// dj, then di; -1 before 0), summed pairwise.
 template <typename T>
 __device__ __forceinline__ T rho8(T a, T b, T c, T d, T e, T f, T g, T h) {
   using A = Ar<T>;
-  return A::mul(A::add(A::add(A::add(A::add(A::add(A::add(A::add(a, b), c), d), e), f), g), h), T(0.125));
+  return A::mul(A::add(A::add(A::add(a, b), A::add(c, d)), A::add(A::add(e, f), A::add(g, h))), T(0.125));
 }
 
 // reciprocal of the corner density; the velocity is momentum times it.
