@@ -21,6 +21,7 @@ workload the flux register, restriction and prolongation).
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import math
 import os
@@ -220,10 +221,13 @@ def make_model(cc, cfgs, prec, tune=True):
 
 
 def time_steps(torch, model, steps, warmup):
-    """W untimed steps, then K steps between events on the model's stream."""
+    """W untimed steps, then K steps between events on the model's stream
+    (Python's garbage collector paused while the steps are issued)."""
     for _ in range(warmup):
         model.step(1)
     model.synchronize()
+    gc.collect()
+    gc.disable()
     st = torch.cuda.current_stream()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     launches = 0
@@ -233,6 +237,7 @@ def time_steps(torch, model, steps, warmup):
         launches += model.last_launch_count
     e1.record(st)
     e1.synchronize()
+    gc.enable()
     return e0.elapsed_time(e1), launches
 
 
@@ -661,6 +666,8 @@ def main():
 
         for _ in range(max(1, min(args.warmup, 3))):  # untimed, as for the device-timed steps
             e2e_step()
+        gc.collect()
+        gc.disable()  # no collection pause inside the timed host loop
         barrier()
         t0 = time.perf_counter()
         iter_ms = []
@@ -670,6 +677,7 @@ def main():
             iter_ms.append(round(1e3 * (time.perf_counter() - ti), 2))
         barrier()
         te = time.perf_counter() - t0
+        gc.enable()
         line["e2e"] = {"value": nfluid * ke * world / te, "unit": METRIC, "h2d_bytes_per_step": h2d,
                        "d2h_bytes_per_step": d2h, "steps": ke, "iter_ms": iter_ms,
                        "how": "per step: upload both time levels of every prognostic field from pinned host "
