@@ -1233,8 +1233,10 @@ static void prolong(oc_model *c, oc_model *f, const oc_box *b) {
 
 /* Fine -> coarse (Sec 2.2): coarse cells of the covered box within G cells of
  * its boundary take the mean of the 8 fine cells they contain; coarse corners
- * strictly inside the covered box (within G) take the coincident fine corner.
- * All four time-level buffers of the coarse level receive the values. */
+ * inside the covered box or on its lateral and top faces (within G of them)
+ * take the coincident fine corner (reading C-18: a corner on the interface is
+ * covered by the fine level, so only one level computes it).  All four
+ * time-level buffers of the coarse level receive the values. */
 static void restrict_(oc_model *c, oc_model *f, const oc_box *b) {
   int x0, x1, y0, y1, z1;
   covered(b, &x0, &x1, &y0, &y1, &z1);
@@ -1261,9 +1263,9 @@ static void restrict_(oc_model *c, oc_model *f, const oc_box *b) {
           c->pp[L][pc] = sp / 8.0;
         }
       }
-  for (int Kc = 1; Kc < z1; Kc++)
-    for (int Jc = y0 + 1; Jc < y1; Jc++)
-      for (int Ic = x0 + 1; Ic < x1; Ic++) {
+  for (int Kc = 1; Kc <= z1; Kc++)
+    for (int Jc = y0; Jc <= y1; Jc++)
+      for (int Ic = x0; Ic <= x1; Ic++) {
         int d = Ic - x0;
         if (x1 - Ic < d) d = x1 - Ic;
         if (Jc - y0 < d) d = Jc - y0;

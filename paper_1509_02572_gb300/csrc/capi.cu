@@ -457,9 +457,9 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
             int dd = std::min({ic - K.x0, K.x1 - 1 - ic, jc - K.y0, K.y1 - 1 - jc, K.z1 - 1 - kc});
             if (dd < GH) rcell.push_back(pidx(C, ic, jc, kc));
           }
-      for (int Kc = 1; Kc < K.z1; Kc++)
-        for (int Jc = K.y0 + 1; Jc < K.y1; Jc++)
-          for (int Ic = K.x0 + 1; Ic < K.x1; Ic++) {
+      for (int Kc = 1; Kc <= K.z1; Kc++)
+        for (int Jc = K.y0; Jc <= K.y1; Jc++)
+          for (int Ic = K.x0; Ic <= K.x1; Ic++) {
             int dd = std::min({Ic - K.x0, K.x1 - Ic, Jc - K.y0, K.y1 - Jc, K.z1 - Kc});
             if (dd <= GH) rcorn.push_back(pidx(C, Ic, Jc, Kc));
           }

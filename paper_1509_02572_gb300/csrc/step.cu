@@ -1215,8 +1215,9 @@ __global__ void k_prolong(LevelLink L, int rC) {
 }
 
 // Fine -> coarse: coarse cells near the covered box boundary take the mean of
-// the 8 fine cells they contain; coarse corners inside it take the coincident
-// fine corner.  All four time-level buffers of the coarse level.
+// the 8 fine cells they contain; coarse corners inside it or on its lateral
+// and top faces take the coincident fine corner.  All four time-level
+// buffers of the coarse level.
 template <typename T>
 __global__ void k_restrict(LevelLink L, int rF) {
   const DomDev &C = *L.dc, &F = *L.df;
