@@ -1192,17 +1192,20 @@ static inline void covered(const oc_box *b, int *x0, int *x1, int *y0, int *y1, 
   *z1 = b->nz / 2;
 }
 
-/* Coarse -> fine (Sec 2.2): every fine ghost cell outside the region the fine
- * level integrates (cells -2 .. n+1) takes the value of the coarse cell that
- * covers it (injection); fine ghost corners outside the integrated corners
- * (-1 .. n+1) take the coarse momentum interpolated linearly along each axis
- * (coincident points copy; reading C-14).  All four
- * time-level buffers of the fine level receive the current coarse values. */
+/* Coarse -> fine (Sec 2.2): at every exchange each fine ghost cell (all four
+ * layers beyond the box) takes the value of the coarse cell that covers it
+ * (injection), and each fine ghost corner outside the box's corners 0 .. n
+ * (above nz at the top) the coarse momentum interpolated linearly along each
+ * axis (coincident points copy; reading C-14).  Between exchanges the fine
+ * level integrates the inner two ghost layers (cells -2 .. n+1, corners
+ * -1 .. n+1) so that its boundary stencils see updated values; the exchange
+ * then brings them back to the coarse solution.  All four time-level buffers
+ * of the fine level receive the current coarse values. */
 static void prolong(oc_model *c, oc_model *f, const oc_box *b) {
   for (int k = 0; k < f->nz + G; k++)
     for (int j = -G; j < f->ny + G; j++)
       for (int i = -G; i < f->nx + G; i++) {
-        if (i >= -2 && i < f->nx + 2 && j >= -2 && j < f->ny + 2 && k < f->nz + 2) continue;
+        if (i >= 0 && i < f->nx && j >= 0 && j < f->ny && k < f->nz) continue;
         int ic, jc, kc;
         parent(b, i, j, k, &ic, &jc, &kc);
         long pc = CI(c, ic, jc, kc), pf = CI(f, i, j, k);
@@ -1214,7 +1217,7 @@ static void prolong(oc_model *c, oc_model *f, const oc_box *b) {
   for (int K = -G + 1; K < f->nz + G; K++)
     for (int J = -G; J < f->ny + G; J++)
       for (int I = -G; I < f->nx + G; I++) {
-        if (I >= -1 && I < f->nx + 2 && J >= -1 && J < f->ny + 2 && K < f->nz + 2) continue;
+        if (I >= 0 && I <= f->nx && J >= 0 && J <= f->ny && K <= f->nz) continue;
         int X = I + b->ox, Y = J + b->oy;
         int xs[2] = {X >> 1, (X + 1) >> 1}, ys[2] = {Y >> 1, (Y + 1) >> 1}, zs[2] = {K >> 1, (K + 1) >> 1};
         double s[3] = {0, 0, 0};

@@ -445,11 +445,11 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
       for (int k = 0; k < F.nz + GH; k++)
         for (int j = -GH; j < F.ny + GH; j++)
           for (int i = -GH; i < F.nx + GH; i++)
-            if (!(i >= -2 && i < F.nx + 2 && j >= -2 && j < F.ny + 2 && k < F.nz + 2)) pcell.push_back(pidx(F, i, j, k));
+            if (!(i >= 0 && i < F.nx && j >= 0 && j < F.ny && k < F.nz)) pcell.push_back(pidx(F, i, j, k));
       for (int Kk = -GH + 1; Kk < F.nz + GH; Kk++)
         for (int J = -GH; J < F.ny + GH; J++)
           for (int I = -GH; I < F.nx + GH; I++)
-            if (!(I >= -1 && I < F.nx + 2 && J >= -1 && J < F.ny + 2 && Kk < F.nz + 2))
+            if (!(I >= 0 && I <= F.nx && J >= 0 && J <= F.ny && Kk <= F.nz))
               pcorn.push_back(pidx(F, I, J, Kk));
       for (int kc = 0; kc < K.z1; kc++)
         for (int jc = K.y0; jc < K.y1; jc++)

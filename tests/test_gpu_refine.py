@@ -234,23 +234,27 @@ def test_refined_graph_replay_equals_direct_launches(cc):
 
 
 @pytest.mark.timeout(900)
-def test_refined_paper_domain_stays_bounded_for_1000_steps(cc):
+@pytest.mark.parametrize("nbox", [1, 2], ids=["two-levels", "three-levels"])
+def test_refined_paper_domain_one_hour(cc, nbox):
     """The 1 km hemisphere on the paper's 64 x 32 x 16 km domain at 400 m with
-    a 200 m box (x 16-48 km, y 8-24 km, z 0-8 km), FP32, 1000 coarse steps
-    (5 simulated minutes): every level stays finite with |w| bounded. With the
-    corners on the box faces left to both levels, the coarse level's w on the
-    box top reached hundreds of m/s within these steps."""
+    a 200 m box (x 16-48 km, y 8-24 km, z 0-8 km) and, for three levels, a
+    100 m box (x 24-40 km, y 12-20 km, z 0-4 km), FP32, one hour (12,000
+    coarse steps): every level stays finite with |w| bounded. With the
+    corners on the box faces computed by both levels, or with the fine
+    level's integrated ghost layers never reset to the coarse solution, these
+    runs blew up within a quarter of the hour."""
     base = W.RunConfig("hemisphere-400m", 160, 80, 40, 400.0, 400.0, 400.0, 0.3, 1, "hemisphere", 1000.0, 1000.0,
                        theta0=300.0)
-    boxes = [(160, 80, 40, 80, 40)]
-    rc = W.RefinedConfig("paper-domain-2-levels", base, boxes)
+    boxes = [(160, 80, 40, 80, 40)] * nbox
+    rc = W.RefinedConfig("paper-domain", base, boxes)
     m = cc.RefinedModel(base, boxes, cc.CC_FP32)
     for l, c in enumerate(m.cfgs):
         m.set_terrain(l, rc.finest_heights() if l == m.nlev - 1 else np.zeros((c.ny, c.nx)))
     m.build_geometry()
     m.init_state()
-    m.step(1000)
-    d0, d1 = m.diagnostics(0, check=False), m.diagnostics(1, check=False)
+    m.step(12000)
+    ds = [m.diagnostics(l, check=False) for l in range(m.nlev)]
     m.close()
-    assert d0["nonfinite"] == 0 and d1["nonfinite"] == 0
-    assert d0["max_w"] < 3.0 and d1["max_w"] < 10.0, (d0["max_w"], d1["max_w"])
+    for l, d in enumerate(ds):
+        assert d["nonfinite"] == 0, l
+        assert d["max_w"] < 20.0, (l, d["max_w"])
