@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ensemble",
-                    choices=["ensemble", "hemisphere", "bell512", "refined", "convergence"])
+                    choices=["ensemble", "hemisphere", "bell512", "refined", "convergence", "refined-vs-uniform"])
     ap.add_argument("--seconds", type=float, default=3600.0,
                     help="simulated time of each run of the convergence workload")
     ap.add_argument("--error-steps", type=int, default=0,
@@ -498,6 +498,95 @@ def run_convergence(cc, torch, args):
     print(json.dumps(line), flush=True)
 
 
+def run_refined_vs_uniform(cc, torch, args):
+    """The paper's refined-grid test (Sec 3.2) with nested boxes in place of
+    its cube sets: flow over the 1 km hemisphere on the 64 x 32 x 16 km domain
+    (Theta = 300 K) for the same simulated time on a uniform 400 m grid, with
+    a 200 m box (x 16-48 km, y 8-24 km, z 0-8 km), and with a further 100 m
+    box (x 24-40 km, y 12-20 km, z 0-4 km); each against a uniform 100 m run.
+    The root-mean-square difference of w at z = 1200 m is taken at the points
+    of the 400 m lattice, from the finest level covering each point, in three
+    regions: inside the 100 m box, inside the 200 m box only, and outside
+    both (1 km margins). One JSON line."""
+    base = W.RunConfig("hemisphere-400m", 160, 80, 40, 400.0, 400.0, 400.0, 0.3, 1, "hemisphere", 1000.0, 1000.0,
+                       theta0=300.0)
+    box1, box2 = (160, 80, 40, 80, 40), (160, 80, 40, 80, 40)
+    z = 1200.0
+    t0 = time.perf_counter()
+
+    def finish(m, n):
+        m.step(n)
+        m.synchronize()
+
+    # the uniform runs
+    def uniform(d):
+        cfg = base.replace(name=f"hemisphere-{d:g}m", nx=int(64000 / d), ny=int(32000 / d), nz=int(16000 / d),
+                           dx=d, dy=d, dz=d, dt=0.15 * d / 200.0)
+        m = cc.Model([cfg], cc.CC_FP32)
+        m.set_terrain(0, cfg.heights())
+        m.build_geometry()
+        m.init_state()
+        finish(m, int(round(args.seconds / cfg.dt)))
+        w = m.derived(0, cc.CC_W)[int(round(z / d))]
+        m.close()
+        return w
+
+    ref = uniform(100.0)
+    lat = {"400m": [(0.0, 0.0, 400.0, uniform(400.0))]}  # (origin x, origin y, spacing, w plane) finest last
+    for name, boxes in (("400/200m", [box1]), ("400/200/100m", [box1, box2])):
+        rc = W.RefinedConfig(name, base, boxes)
+        m = cc.RefinedModel(base, boxes, cc.CC_FP32)
+        for l, c in enumerate(m.cfgs):
+            m.set_terrain(l, rc.finest_heights() if l == m.nlev - 1 else np.zeros((c.ny, c.nx)))
+        m.build_geometry()
+        m.init_state()
+        finish(m, int(round(args.seconds / base.dt)))
+        planes = []
+        for l, c in enumerate(m.cfgs):
+            ox, oy = rc.level_origin(l)
+            planes.append((ox, oy, c.dx, m.derived(l, cc.CC_W)[int(round(z / c.dx))]))
+        lat[name] = planes
+        m.close()
+
+    def value(planes, x, y):
+        """w at (x, y) from the finest level whose interior holds the point."""
+        for ox, oy, d, w in reversed(planes):
+            i, j = (x - ox) / d, (y - oy) / d
+            if 0 <= i < w.shape[1] and 0 <= j < w.shape[0] and abs(i - round(i)) < 1e-9:
+                return float(w[int(round(j)), int(round(i))])
+        raise AssertionError((x, y))
+
+    def region(x, y):
+        if 25000 <= x <= 39000 and 13000 <= y <= 19000:
+            return "inside the 100 m box"
+        if 17000 <= x <= 47000 and 9000 <= y <= 23000 and not (23000 <= x <= 41000 and 11000 <= y <= 21000):
+            return "inside the 200 m box only"
+        if x < 15000 or x > 49000 or y < 7000 or y > 25000:
+            return "outside both boxes"
+        return None
+
+    acc = {}
+    for b in range(80):
+        for a in range(160):
+            x, y = 400.0 * a, 400.0 * b
+            r = region(x, y)
+            if r is None:
+                continue
+            wr = float(ref[4 * b, 4 * a])
+            for name, planes in lat.items():
+                e = acc.setdefault(r, {}).setdefault(name, [0.0, 0])
+                e[0] += (value(planes, x, y) - wr) ** 2
+                e[1] += 1
+    out = {r: {name: {"rms": math.sqrt(v[0] / v[1]), "points": v[1]} for name, v in d.items()}
+           for r, d in acc.items()}
+    line = {"metric": "rms difference of w at z = 1200 m from the uniform 100 m run", "unit": "m/s",
+            "workload": "refined-vs-uniform-hemisphere-64x32x16km", "seconds": args.seconds, "dtype": "f32",
+            "data": "synthetic", "n_gpus": 1, "regions": out, "wall_s": round(time.perf_counter() - t0, 1),
+            "how": "grids 400 m; 400 m + 200 m box; 400 m + 200 m + 100 m boxes (nested boxes standing for the "
+                   "paper's cube sets); w at the 400 m lattice points, from the finest level holding each point"}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     global SCHEDULE
     args = parse()
@@ -525,9 +614,9 @@ def main():
         torch.cuda.synchronize()
 
     hbm, peak_kind = peaks()
-    if args.workload == "convergence":
+    if args.workload in ("convergence", "refined-vs-uniform"):
         if rank == 0:
-            run_convergence(cc, torch, args)
+            (run_convergence if args.workload == "convergence" else run_refined_vs_uniform)(cc, torch, args)
         if world > 1:
             dist.destroy_process_group()
         return
