@@ -65,6 +65,9 @@ def lib():
             L.oc_dims.argtypes = [ct.c_void_p] + [ct.POINTER(ct.c_long)] * 3 + [ct.POINTER(ct.c_int)]
             L.oc_get_state.argtypes = [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p]
             L.oc_set_state.argtypes = [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p]
+            L.oc_get_state_padded.argtypes = [ct.c_void_p, ct.c_int, ct.c_int, ct.c_void_p]
+            L.oc_padding.argtypes = [ct.c_void_p] + [ct.POINTER(ct.c_int)] * 4
+            L.oc_padding.restype = None
             L.oc_get_geometry.argtypes = [ct.c_void_p] + [ct.c_void_p] * 10
             L.oc_get_points.argtypes = [ct.c_void_p] + [ct.c_void_p] * 9
             L.oc_get_base.argtypes = [ct.c_void_p, ct.c_void_p, ct.c_void_p,
@@ -219,6 +222,18 @@ class Model:
         st = lib().oc_set_state(self._m, f, level, _ptr(a))
         if st != OK:
             raise OracleError(f"set_state {f} {level} -> {st}")
+
+    def padded(self, f: int, level: int = 1):
+        """The whole padded array of prognostic field f at time level `level`
+        ((nz + 2G, ny + 2G, nx + 2G); cell or corner (i, j, k) at
+        [k + G, j + G, i + G]) and the padding G."""
+        g, nx, ny, nz = (ct.c_int() for _ in range(4))
+        lib().oc_padding(self._m, ct.byref(g), ct.byref(nx), ct.byref(ny), ct.byref(nz))
+        a = np.zeros(nz.value * ny.value * nx.value)
+        st = lib().oc_get_state_padded(self._m, f, level, _ptr(a))
+        if st != OK:
+            raise OracleError(f"get_state_padded {f} {level} -> {st}")
+        return a.reshape((nz.value, ny.value, nx.value)), g.value
 
     def mass(self, level: int = 1) -> float:
         return lib().oc_mass(self._m, level)

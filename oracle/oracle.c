@@ -990,6 +990,22 @@ int oc_get_state(oc_model *m, int field, int level, double *out) {
   return OC_OK;
 }
 
+/* The whole padded array of a prognostic field (cells or corners, G = 4
+ * layers on every side, index ((k + G) * nyp + j + G) * nxp + i + G), ghost
+ * frame included: lets tests check the coarse-fine exchange cell by cell. */
+int oc_get_state_padded(oc_model *m, int field, int level, double *out) {
+  if (level < 0 || level > 1 || field == OC_F_UB) return OC_EINVAL;
+  double *a = level_array(m, field, level);
+  if (!a) return OC_EINVAL;
+  long n = (long)m->nxp * m->nyp * m->nzp;
+  for (long q = 0; q < n; q++) out[q] = a[q];
+  return OC_OK;
+}
+
+void oc_padding(const oc_model *m, int *g, int *nxp, int *nyp, int *nzp) {
+  *g = G; *nxp = m->nxp; *nyp = m->nyp; *nzp = m->nzp;
+}
+
 int oc_set_state(oc_model *m, int field, int level, const double *in) {
   if (level < 0 || level > 1) return OC_EINVAL;
   double *a = level_array(m, field, level);

@@ -32,6 +32,8 @@ void oc_step(oc_model *m, int nsteps);
 int oc_dims(const oc_model *m, long *ncell, long *ncorner, long *ncol, int *gz);
 int oc_get_state(oc_model *m, int field, int level, double *out);
 int oc_set_state(oc_model *m, int field, int level, const double *in);
+int oc_get_state_padded(oc_model *m, int field, int level, double *out);
+void oc_padding(const oc_model *m, int *g, int *nxp, int *nyp, int *nzp);
 int oc_get_geometry(const oc_model *m, double *vf, double *ax, double *ay, double *az, int8_t *cls,
                     int32_t *root, double *vg, double *hc, double *gx, double *gy);
 int oc_get_points(const oc_model *m, int8_t *vcls, int32_t *bK, int32_t *bI, int32_t *bJ, double *ba,

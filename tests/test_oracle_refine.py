@@ -110,3 +110,100 @@ def test_refined_run_is_stable(oracle_mod):
             assert np.isfinite(a).all()
     w = R.levels[-1].field(oracle_mod.F_MZ)
     assert 0.5 < np.abs(w).max() < 50.0
+
+
+def _pairs(R):
+    """(coarse level, fine level, box, coarse is the periodic base level)."""
+    for l in range(1, R.nlev):
+        yield R.levels[l - 1], R.levels[l], RC.boxes[l - 1], l == 1
+
+
+def _at(P, G, k, j, i, cshape, periodic):
+    if periodic:
+        j, i = j % cshape[1], i % cshape[2]
+    return P[k + G, j + G, i + G]
+
+
+def test_coarse_fine_exchange_follows_its_definition(oracle_mod):
+    """The exchange of Sec 2.2, point by point, after two full cycles with
+    wind, for both level pairs.  Coarse to fine: every fine ghost cell of the
+    four layers above the floor holds the value of the coarse cell covering it
+    (the same coarse value for its eight fine cells), in both time levels;
+    every fine ghost corner outside the box's corners 0 .. n (up to three
+    layers above its top) the mean of the coarse corners at the floor and the
+    ceiling of its half-index along each axis, i.e. linear interpolation with
+    coincident points copied.  Fine to coarse: covered coarse cells within
+    four cells of the lateral faces or the top hold the mean of their eight
+    fine cells and deeper ones their own values; covered coarse corners above
+    the floor, inside the box or on its lateral faces and top and within four
+    corners of them, hold the coincident fine corner."""
+    R = _refine(oracle_mod)
+    R.step(2)
+    O = oracle_mod
+    for C, F, (nx, ny, nz, ox, oy), periodic in _pairs(R):
+        cz, cy, cx = C.cfg.nz, C.cfg.ny, C.cfg.nx
+        cs = (cz, cy, cx)
+        # coarse to fine, cells
+        for f in (O.F_RHOP, O.F_PP):
+            Pc, G = C.padded(f, 1)
+            n_checked = 0
+            for lev in (0, 1):
+                Pf, _ = F.padded(f, lev)
+                for k in range(0, nz + G):
+                    for j in range(-G, ny + G):
+                        for i in range(-G, nx + G):
+                            if 0 <= i < nx and 0 <= j < ny and k < nz:
+                                continue
+                            want = _at(Pc, G, k // 2, (j + oy) // 2, (i + ox) // 2, cs, periodic)
+                            assert Pf[k + G, j + G, i + G] == want, (f, lev, i, j, k)
+                            n_checked += 1
+            assert n_checked > 0
+        # coarse to fine, corners
+        for f in (O.F_MX, O.F_MY, O.F_MZ):
+            Pc, G = C.padded(f, 1)
+            for lev in (0, 1):
+                Pf, _ = F.padded(f, lev)
+                for K in range(-G + 1, nz + G):
+                    for J in range(-G, ny + G):
+                        for I in range(-G, nx + G):
+                            if 0 <= I <= nx and 0 <= J <= ny and K <= nz:
+                                continue
+                            X, Y = I + ox, J + oy
+                            vals = [_at(Pc, G, z, y, x, cs, periodic)
+                                    for x in (X // 2, (X + 1) // 2) for y in (Y // 2, (Y + 1) // 2)
+                                    for z in (K // 2, (K + 1) // 2)]
+                            want = sum(vals) / 8.0
+                            got = Pf[K + G, J + G, I + G]
+                            assert abs(got - want) <= 1e-13 * (abs(want) + 1e-300), (f, lev, I, J, K, got, want)
+        # fine to coarse, cells
+        x0, x1, y0, y1, z1 = ox // 2, (ox + nx) // 2, oy // 2, (oy + ny) // 2, nz // 2
+        for f in (O.F_RHOP, O.F_PP):
+            Pc1, G = C.padded(f, 1)
+            Pc0, _ = C.padded(f, 0)
+            Pf, _ = F.padded(f, 1)
+            deep_differs = False
+            for kc in range(z1):
+                for jc in range(y0, y1):
+                    for ic in range(x0, x1):
+                        d = min(ic - x0, x1 - 1 - ic, jc - y0, y1 - 1 - jc, z1 - 1 - kc)
+                        kids = Pf[2 * kc + G:2 * kc + G + 2, 2 * jc - oy + G:2 * jc - oy + G + 2,
+                                  2 * ic - ox + G:2 * ic - ox + G + 2]
+                        mean = kids.sum() / 8.0
+                        got = Pc1[kc + G, jc + G, ic + G]
+                        if d < 4:
+                            assert abs(got - mean) <= 1e-13 * (abs(mean) + 1e-300), (f, ic, jc, kc, got, mean)
+                            assert Pc0[kc + G, jc + G, ic + G] == got
+                        elif abs(got - mean) > 1e-9 * (abs(mean) + 1e-12):
+                            deep_differs = True
+            assert deep_differs, "covered cells deeper than four cells must keep their own values"
+        # fine to coarse, corners
+        for f in (O.F_MX, O.F_MY, O.F_MZ):
+            Pc1, G = C.padded(f, 1)
+            Pf, _ = F.padded(f, 1)
+            for Kc in range(1, z1 + 1):
+                for Jc in range(y0, y1 + 1):
+                    for Ic in range(x0, x1 + 1):
+                        if min(Ic - x0, x1 - Ic, Jc - y0, y1 - Jc, z1 - Kc) > 4:
+                            continue
+                        assert Pc1[Kc + G, Jc + G, Ic + G] == Pf[2 * Kc + G, 2 * Jc - oy + G, 2 * Ic - ox + G], \
+                            (f, Ic, Jc, Kc)
