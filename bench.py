@@ -733,45 +733,58 @@ def main():
     # ---- end to end through the C ABI with host buffers
     if not args.no_e2e:
         fields = (cc.CC_RHOP, cc.CC_PP, cc.CC_MX, cc.CC_MY, cc.CC_MZ)
-        host = {}
-        for d in range(len(cfgs)):
-            for f in fields:
-                for lev in (0, 1):
-                    a = torch.from_numpy(model.download(d, f, lev)).pin_memory()
-                    host[(d, f, lev)] = a
-        outs = [torch.empty(tuple(model._shape(d, cc.CC_PP)), dtype=torch.float64).pin_memory()
-                for d in range(len(cfgs))]
-        h2d = sum(a.numel() * 8 for a in host.values())
-        d2h = sum(o.numel() * 8 for o in outs)
-        ke = max(3, min(args.steps, 8))
 
-        def e2e_step():
-            for (d, f, lev), a in host.items():
-                model.upload_ptr(d, f, lev, a.data_ptr(), wait=False)
-            model.step(1)
+        def e2e_run(f32):
+            """Pinned host buffers in FP32 (the model's own precision, copied
+            unchanged) or FP64; per step: upload, one step, download p'."""
+            np_dt, t_dt, es = (np.float32, torch.float32, 4) if f32 else (np.float64, torch.float64, 8)
+            host = {}
             for d in range(len(cfgs)):
-                model.download_ptr(d, cc.CC_PP, 1, outs[d].data_ptr(), wait=False)
-            model.synchronize()  # the step's result is on the host
+                for f in fields:
+                    for lev in (0, 1):
+                        host[(d, f, lev)] = torch.from_numpy(model.download(d, f, lev, dtype=np_dt)).pin_memory()
+            outs = [torch.empty(tuple(model._shape(d, cc.CC_PP)), dtype=t_dt).pin_memory() for d in range(len(cfgs))]
+            h2d = sum(a.numel() * es for a in host.values())
+            d2h = sum(o.numel() * es for o in outs)
+            ke = max(3, min(args.steps, 8))
 
-        for _ in range(max(1, min(args.warmup, 3))):  # untimed, as for the device-timed steps
-            e2e_step()
-        gc.collect()
-        gc.disable()  # no collection pause inside the timed host loop
-        barrier()
-        t0 = time.perf_counter()
-        iter_ms = []
-        for _ in range(ke):
-            ti = time.perf_counter()
-            e2e_step()
-            iter_ms.append(round(1e3 * (time.perf_counter() - ti), 2))
-        barrier()
-        te = time.perf_counter() - t0
-        gc.enable()
-        line["e2e"] = {"value": nfluid * ke * world / te, "unit": METRIC, "h2d_bytes_per_step": h2d,
-                       "d2h_bytes_per_step": d2h, "steps": ke, "iter_ms": iter_ms,
-                       "how": "per step: upload both time levels of every prognostic field from pinned host "
-                              "FP64 arrays, one step, download p' of every domain, then wait for it (transfers "
-                              "queued on the model's stream, one host wait per step); untimed warm-up steps first"}
+            def e2e_step():
+                for (d, f, lev), a in host.items():
+                    model.upload_ptr(d, f, lev, a.data_ptr(), wait=False, f32=f32)
+                model.step(1)
+                for d in range(len(cfgs)):
+                    model.download_ptr(d, cc.CC_PP, 1, outs[d].data_ptr(), wait=False, f32=f32)
+                model.synchronize()  # the step's result is on the host
+
+            for _ in range(max(1, min(args.warmup, 3))):  # untimed, as for the device-timed steps
+                e2e_step()
+            gc.collect()
+            gc.disable()  # no collection pause inside the timed host loop
+            barrier()
+            t0 = time.perf_counter()
+            iter_ms = []
+            for _ in range(ke):
+                ti = time.perf_counter()
+                e2e_step()
+                iter_ms.append(round(1e3 * (time.perf_counter() - ti), 2))
+            barrier()
+            te = time.perf_counter() - t0
+            gc.enable()
+            del host, outs
+            gc.collect()
+            return {"value": nfluid * ke * world / te, "unit": METRIC, "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h, "steps": ke, "iter_ms": iter_ms}
+
+        f32 = prec_main == cc.CC_FP32
+        line["e2e"] = e2e_run(f32)
+        line["e2e"]["how"] = ("per step: upload both time levels of every prognostic field from pinned host "
+                              + ("FP32 arrays (the model's precision, copied unchanged)" if f32 else "FP64 arrays")
+                              + ", one step, download p' of every domain, then wait for it (transfers queued on "
+                                "the model's stream, one host wait per step); untimed warm-up steps first")
+        if f32:
+            r = e2e_run(False)
+            line["e2e"]["fp64_host"] = {k: r[k] for k in ("value", "h2d_bytes_per_step", "d2h_bytes_per_step",
+                                                          "iter_ms")}
 
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(cfgs, args.cpu_seconds)

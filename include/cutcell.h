@@ -216,6 +216,15 @@ cc_status cc_error_norms(const cc_model *a, int da, const cc_model *b, int db, i
 cc_status cc_upload_state_async(cc_model *m, int d, int field, int level, const double *host);
 cc_status cc_download_state_async(const cc_model *m, int d, int field, int level, double *host);
 
+/* The same four transfers with FP32 host buffers (same layouts), for FP32
+ * models only, whose prognostic fields are FP32: the values are copied
+ * unchanged, with half the host-device bytes of the FP64 calls.  An FP64
+ * model returns CC_EINVAL.  The _async forms follow the rules above. */
+cc_status cc_upload_state_f32(cc_model *m, int d, int field, int level, const float *host);
+cc_status cc_download_state_f32(const cc_model *m, int d, int field, int level, float *host);
+cc_status cc_upload_state_f32_async(cc_model *m, int d, int field, int level, const float *host);
+cc_status cc_download_state_f32_async(const cc_model *m, int d, int field, int level, float *host);
+
 /* Checkpoint and resume (no counterpart in the paper; long runs are split
  * over several jobs).  cc_save writes the whole state of every domain -- all
  * four time levels of the five fields and of the boundary-point velocity in

@@ -146,22 +146,24 @@ bool valid_cfg(const cc_config &c, std::string &why) {
 }
 
 // ---------------------------------------------------------------- transfer kernels
-// host layout (interior, corner levels from -HOST_GZ) <-> padded layout
-template <typename T>
-__global__ void k_scatter(const double *src, T *dst, DomDev D, int nlev, int k_first) {
+// host layout (interior, corner levels from -HOST_GZ) <-> padded layout;
+// T the field's element type, H the host buffer's (FP64, or FP32 for FP32
+// models)
+template <typename T, typename H = double>
+__global__ void k_scatter(const H *src, T *dst, DomDev D, int nlev, int k_first) {
   long long n = (long long)D.nx * D.ny * nlev;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   int i = (int)(t % D.nx), j = (int)((t / D.nx) % D.ny), k = (int)(t / ((long long)D.nx * D.ny)) + k_first;
   dst[pidx(D, i, j, k)] = (T)src[t];
 }
-template <typename T>
-__global__ void k_gather(const T *src, double *dst, DomDev D, int nlev, int k_first) {
+template <typename T, typename H = double>
+__global__ void k_gather(const T *src, H *dst, DomDev D, int nlev, int k_first) {
   long long n = (long long)D.nx * D.ny * nlev;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   int i = (int)(t % D.nx), j = (int)((t / D.nx) % D.ny), k = (int)(t / ((long long)D.nx * D.ny)) + k_first;
-  dst[t] = (double)src[pidx(D, i, j, k)];
+  dst[t] = (H)src[pidx(D, i, j, k)];
 }
 template <typename P>
 __global__ void k_gather_raw(const P *src, P *dst, DomDev D, int nlev, int k_first) {
@@ -212,8 +214,8 @@ __global__ void k_gather_cols(const P *src, P *dst, DomDev D, int w) {
   int I = (int)(q % D.nx), J = (int)(q / D.nx);
   dst[t] = src[qidx(D, I, J) * w + c];
 }
-template <typename T>
-__global__ void k_scatter_cols(const double *src, T *dst, DomDev D, int w) {
+template <typename T, typename H = double>
+__global__ void k_scatter_cols(const H *src, T *dst, DomDev D, int w) {
   long long n = (long long)D.nx * D.ny * w;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
@@ -222,15 +224,15 @@ __global__ void k_scatter_cols(const double *src, T *dst, DomDev D, int w) {
   int I = (int)(q % D.nx), J = (int)(q / D.nx);
   dst[qidx(D, I, J) * w + c] = (T)src[t];
 }
-template <typename T>
-__global__ void k_gather_cols_cvt(const T *src, double *dst, DomDev D, int w) {
+template <typename T, typename H = double>
+__global__ void k_gather_cols_cvt(const T *src, H *dst, DomDev D, int w) {
   long long n = (long long)D.nx * D.ny * w;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= n) return;
   int c = (int)(t % w);
   long long q = t / w;
   int I = (int)(q % D.nx), J = (int)(q / D.nx);
-  dst[t] = (double)src[qidx(D, I, J) * w + c];
+  dst[t] = (H)src[qidx(D, I, J) * w + c];
 }
 
 // corner heights of a box level must vanish within this many corners of its
@@ -935,8 +937,11 @@ static cc_status transfer_setup(cc_model *m) {
   return CC_OK;
 }
 
-static cc_status upload(cc_model *m, int d, int field, int level, const double *host, bool sync) {
+// f32: the host buffer holds FP32 values (FP32 models only, where the
+// prognostic fields are FP32, so nothing is rounded either way)
+static cc_status upload(cc_model *m, int d, int field, int level, const void *host, bool sync, bool f32 = false) {
   if (!m || !host) return fail(m, CC_EINVAL, "null argument");
+  if (f32 && m->prec != CC_FP32) return fail(m, CC_EINVAL, "FP32 host buffers need an FP32 model");
   if (d < 0 || d >= m->ndom) return fail(m, CC_EINVAL, "domain index out of range");
   if (field < 0 || field > CC_UB || level < 0 || level > 1) return fail(m, CC_EINVAL, "bad field or level");
   if (!m->state) return fail(m, CC_ESTATE, "state not initialised");
@@ -953,15 +958,18 @@ static cc_status upload(cc_model *m, int d, int field, int level, const double *
   m->xslot ^= 1;
   double *stage = sl ? m->d_stage2 : m->d_stage;
   if (m->used_valid[sl]) CK(m, cudaStreamWaitEvent(m->xs, m->ev_staged[sl], 0), "upload order");
-  CK(m, cudaMemcpyAsync(stage, host, n * 8, cudaMemcpyHostToDevice, m->xs), "upload");
+  CK(m, cudaMemcpyAsync(stage, host, n * (f32 ? 4 : 8), cudaMemcpyHostToDevice, m->xs), "upload");
   CK(m, cudaEventRecord(m->ev_copied[sl], m->xs), "upload event");
   CK(m, cudaStreamWaitEvent(m->st, m->ev_copied[sl], 0), "upload order");
+  const float *stage32 = (const float *)stage;
   if (field == CC_UB) {
     if (m->prec == CC_FP64) k_scatter_cols<double><<<nb256(n), 256, 0, m->st>>>(stage, (double *)D.ub[buf], D, 3);
+    else if (f32) k_scatter_cols<float><<<nb256(n), 256, 0, m->st>>>(stage32, (float *)D.ub[buf], D, 3);
     else k_scatter_cols<float><<<nb256(n), 256, 0, m->st>>>(stage, (float *)D.ub[buf], D, 3);
   } else {
     void *dst = D.f[buf][field];
     if (m->prec == CC_FP64) k_scatter<double><<<nb256(n), 256, 0, m->st>>>(stage, (double *)dst, D, nlev, kfirst);
+    else if (f32) k_scatter<float><<<nb256(n), 256, 0, m->st>>>(stage32, (float *)dst, D, nlev, kfirst);
     else k_scatter<float><<<nb256(n), 256, 0, m->st>>>(stage, (float *)dst, D, nlev, kfirst);
   }
   CK(m, cudaGetLastError(), "upload scatter");
@@ -971,8 +979,9 @@ static cc_status upload(cc_model *m, int d, int field, int level, const double *
   return CC_OK;
 }
 
-static cc_status download(cc_model *m, int d, int field, int level, double *host, bool sync) {
+static cc_status download(cc_model *m, int d, int field, int level, void *host, bool sync, bool f32 = false) {
   if (!m || !host) return fail(m, CC_EINVAL, "null argument");
+  if (f32 && m->prec != CC_FP32) return fail(m, CC_EINVAL, "FP32 host buffers need an FP32 model");
   if (d < 0 || d >= m->ndom) return fail(m, CC_EINVAL, "domain index out of range");
   if (field < 0 || field > CC_UB || level < 0 || level > 1) return fail(m, CC_EINVAL, "bad field or level");
   if (!m->state) return fail(m, CC_ESTATE, "state not initialised");
@@ -987,20 +996,25 @@ static cc_status download(cc_model *m, int d, int field, int level, double *host
   const int sl = m->xslot;
   m->xslot ^= 1;
   double *stage = sl ? m->d_stage2 : m->d_stage;
+  float *stage32 = (float *)stage;
   if (field == CC_UB) {
     if (m->prec == CC_FP64)
       k_gather_cols_cvt<double><<<nb256(n), 256, 0, m->st>>>((const double *)D.ub[buf], stage, D, 3);
+    else if (f32)
+      k_gather_cols_cvt<float><<<nb256(n), 256, 0, m->st>>>((const float *)D.ub[buf], stage32, D, 3);
     else
       k_gather_cols_cvt<float><<<nb256(n), 256, 0, m->st>>>((const float *)D.ub[buf], stage, D, 3);
   } else {
     const void *src = D.f[buf][field];
     if (m->prec == CC_FP64)
       k_gather<double><<<nb256(n), 256, 0, m->st>>>((const double *)src, stage, D, nlev, kfirst);
+    else if (f32)
+      k_gather<float><<<nb256(n), 256, 0, m->st>>>((const float *)src, stage32, D, nlev, kfirst);
     else
       k_gather<float><<<nb256(n), 256, 0, m->st>>>((const float *)src, stage, D, nlev, kfirst);
   }
   CK(m, cudaGetLastError(), "download gather");
-  CK(m, cudaMemcpyAsync(host, stage, n * 8, cudaMemcpyDeviceToHost, m->st), "download");
+  CK(m, cudaMemcpyAsync(host, stage, n * (f32 ? 4 : 8), cudaMemcpyDeviceToHost, m->st), "download");
   CK(m, cudaEventRecord(m->ev_staged[sl], m->st), "download event");
   m->used_valid[sl] = true;
   if (sync) CK(m, cudaStreamSynchronize(m->st), "download sync");
@@ -1077,6 +1091,22 @@ cc_status cc_upload_state_async(cc_model *m, int d, int field, int level, const 
 
 cc_status cc_download_state_async(const cc_model *m, int d, int field, int level, double *host) {
   return download(const_cast<cc_model *>(m), d, field, level, host, false);
+}
+
+cc_status cc_upload_state_f32(cc_model *m, int d, int field, int level, const float *host) {
+  return upload(m, d, field, level, host, true, true);
+}
+
+cc_status cc_download_state_f32(const cc_model *m, int d, int field, int level, float *host) {
+  return download(const_cast<cc_model *>(m), d, field, level, host, true, true);
+}
+
+cc_status cc_upload_state_f32_async(cc_model *m, int d, int field, int level, const float *host) {
+  return upload(m, d, field, level, host, false, true);
+}
+
+cc_status cc_download_state_f32_async(const cc_model *m, int d, int field, int level, float *host) {
+  return download(const_cast<cc_model *>(m), d, field, level, host, false, true);
 }
 
 }  // extern "C"

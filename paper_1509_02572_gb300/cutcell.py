@@ -29,7 +29,8 @@ EXPORTS = ("cc_create", "cc_destroy", "cc_last_error", "cc_set_terrain", "cc_bui
            "cc_refine_mass", "cc_domain_count", "cc_autotune", "cc_get_schedule", "cc_set_schedule",
            "cc_graphs_enable", "cc_upload_state_async", "cc_download_state_async", "cc_save", "cc_load",
            "cc_set_terrain_analytic", "cc_get_terrain", "cc_download_derived", "cc_error_norms", "cc_cbcm_cubes",
-           "cc_mass_sum_noalloc", "cc_noalloc_last_error")
+           "cc_mass_sum_noalloc", "cc_noalloc_last_error", "cc_upload_state_f32", "cc_download_state_f32",
+           "cc_upload_state_f32_async", "cc_download_state_f32_async")
 CC_NOALLOC_MAX_PARTS = 1024
 CC_HILL_BELL, CC_HILL_ELLIPSOID, CC_HILL_COSINE = range(3)
 HILL_KINDS = {"bell": CC_HILL_BELL, "ellipsoid": CC_HILL_ELLIPSOID, "hemisphere": CC_HILL_ELLIPSOID,
@@ -103,6 +104,9 @@ def load(path: str = LIB_PATH):
     L.cc_download_state.argtypes = [vp, i, i, i, vp]
     L.cc_upload_state_async.argtypes = [vp, i, i, i, vp]
     L.cc_download_state_async.argtypes = [vp, i, i, i, vp]
+    for fn in ("cc_upload_state_f32", "cc_download_state_f32", "cc_upload_state_f32_async",
+               "cc_download_state_f32_async"):
+        getattr(L, fn).argtypes = [vp, i, i, i, vp]
     L.cc_step.argtypes = [vp, i]
     L.cc_diagnostics.argtypes = [vp, i, ct.POINTER(CCDiag)]
     L.cc_synchronize.argtypes = [vp]
@@ -269,12 +273,15 @@ class Model:
             return (c.ny, c.nx, 3)
         return (c.nz + 1 + 2 * HOST_GZ, c.ny, c.nx)
 
-    def download(self, d: int, field: int, level: int = 1, out: np.ndarray | None = None) -> np.ndarray:
+    def download(self, d: int, field: int, level: int = 1, out: np.ndarray | None = None,
+                 dtype=np.float64) -> np.ndarray:
+        """One field in the host layout, as FP64 or (FP32 models) FP32."""
         shape = self._shape(d, field)
         if out is None:
-            out = np.zeros(shape, np.float64)
-        assert out.shape == shape and out.dtype == np.float64 and out.flags.c_contiguous
-        self._check(self.L.cc_download_state(self.h, d, field, level, _p(out)))
+            out = np.zeros(shape, dtype)
+        assert out.shape == shape and out.dtype in (np.float64, np.float32) and out.flags.c_contiguous
+        fn = self.L.cc_download_state_f32 if out.dtype == np.float32 else self.L.cc_download_state
+        self._check(fn(self.h, d, field, level, _p(out)))
         return out
 
     def derived(self, d: int, which: int, level: int = 1) -> np.ndarray:
@@ -286,17 +293,28 @@ class Model:
         self._check(self.L.cc_download_derived(self.h, d, which, level, _p(out)))
         return out
 
-    def download_ptr(self, d: int, field: int, level: int, ptr: int, wait: bool = True):
-        fn = self.L.cc_download_state if wait else self.L.cc_download_state_async
+    def download_ptr(self, d: int, field: int, level: int, ptr: int, wait: bool = True, f32: bool = False):
+        if f32:
+            fn = self.L.cc_download_state_f32 if wait else self.L.cc_download_state_f32_async
+        else:
+            fn = self.L.cc_download_state if wait else self.L.cc_download_state_async
         self._check(fn(self.h, d, field, level, ct.c_void_p(ptr)))
 
     def upload(self, d: int, field: int, level: int, a: np.ndarray):
-        a = np.ascontiguousarray(a, dtype=np.float64)
+        """One field from a host array; FP32 arrays go through the FP32 calls
+        (FP32 models only), anything else as FP64."""
+        if a.dtype != np.float32:
+            a = np.ascontiguousarray(a, dtype=np.float64)
+        a = np.ascontiguousarray(a)
         assert a.shape == self._shape(d, field)
-        self._check(self.L.cc_upload_state(self.h, d, field, level, _p(a)))
+        fn = self.L.cc_upload_state_f32 if a.dtype == np.float32 else self.L.cc_upload_state
+        self._check(fn(self.h, d, field, level, _p(a)))
 
-    def upload_ptr(self, d: int, field: int, level: int, ptr: int, wait: bool = True):
-        fn = self.L.cc_upload_state if wait else self.L.cc_upload_state_async
+    def upload_ptr(self, d: int, field: int, level: int, ptr: int, wait: bool = True, f32: bool = False):
+        if f32:
+            fn = self.L.cc_upload_state_f32 if wait else self.L.cc_upload_state_f32_async
+        else:
+            fn = self.L.cc_upload_state if wait else self.L.cc_upload_state_async
         self._check(fn(self.h, d, field, level, ct.c_void_p(ptr)))
 
     def step(self, n: int = 1):
