@@ -685,6 +685,44 @@ void oc_init_state(oc_model *m) {
 }
 
 /* ------------------------------------------------------------------ */
+/* Artificial diffusion (Sec 2.1: fourth order in the horizontal and vertical
+ * directions; Sec 2.4: a second-order term, with the boundary conditions of the
+ * terrain surface, where the neighbouring fluid points a fourth-order term
+ * needs are missing).  Reading C-4, per axis of each point:
+ *   fluid points of a scalar stencil: cells owning their pressure point (full
+ *     or cut, not absorbed and not below the terrain) inside the level (above
+ *     the floor, below the rigid lid);
+ *   fluid points of a velocity stencil: corners above the terrain and below
+ *     the rigid lid;
+ *   all four neighbours at distance 1 and 2 fluid: the fourth difference
+ *     f(-2) - 4 f(-1) + 6 f(0) - 4 f(1) + f(2), with D = -K4 * (its sum over
+ *     the axes);
+ *   otherwise the second difference over the neighbours at distance 1 with
+ *     K2 = 4 K4 / d^2 (the same damping of the shortest, 2d, wave), entered as
+ *     -4 (f(-1) - 2 f(0) + f(1)) in that sum; a scalar neighbour that is not a
+ *     fluid point takes the centre value (no diffusive flux through the wall),
+ *     a velocity neighbour that is not a fluid point keeps its stored value
+ *     (the boundary-point velocity below the terrain, the free-slip value on
+ *     the lid). */
+static int cell_fluid(const oc_model *m, int i, int j, int k) {
+  if (k < 0 || k >= m->gk1) return 0;
+  int c = m->cls[CI(m, i, j, k)];
+  return c == C_FULL || c == C_CUT;
+}
+static int corner_fluid(const oc_model *m, int I, int J, int K) {
+  if (K <= 0 || (m->lid && K >= m->nz)) return 0;
+  return K * m->P.dz > HC(m, I, J);
+}
+/* the axis term of the diffusion sum for values f[0..4] at offsets -2..2 with
+ * fluid flags fl[0..4]; scalar selects the zero-gradient wall condition */
+static double diff_axis(const double f[5], const int fl[5], int scalar) {
+  if (fl[0] && fl[1] && fl[3] && fl[4]) return f[0] - 4 * f[1] + 6 * f[2] - 4 * f[3] + f[4];
+  double lo = (fl[1] || !scalar) ? f[1] : f[2];
+  double hi = (fl[3] || !scalar) ? f[3] : f[2];
+  return -4.0 * (lo - 2.0 * f[2] + hi);
+}
+
+/* ------------------------------------------------------------------ */
 static void scalar_residuals(oc_model *m);
 
 /* Cells of the computed region as (i,j,k) triplets */
@@ -757,16 +795,26 @@ void oc_step(oc_model *m, int nsteps) {
         rm += m->RM[m->gmem[a]]; rh += m->RH[m->gmem[a]];
       }
       double VG = m->vg[r];
-      /* fourth-order artificial diffusion of (rho theta)' at n-1 (reading C-4) */
+      /* artificial diffusion of (rho theta)' at n-1 at the host (reading C-4) */
       double d4 = 0.0;
       {
         double f[5];
-        for (int a = -2; a <= 2; a++) f[a + 2] = m->thp_o[CI(m, ir + a, jr, kr)];
-        d4 += f[0] - 4 * f[1] + 6 * f[2] - 4 * f[3] + f[4];
-        for (int a = -2; a <= 2; a++) f[a + 2] = m->thp_o[CI(m, ir, jr + a, kr)];
-        d4 += f[0] - 4 * f[1] + 6 * f[2] - 4 * f[3] + f[4];
-        for (int a = -2; a <= 2; a++) f[a + 2] = m->thp_o[CI(m, ir, jr, kr + a)];
-        d4 += f[0] - 4 * f[1] + 6 * f[2] - 4 * f[3] + f[4];
+        int fl[5];
+        for (int a = -2; a <= 2; a++) {
+          f[a + 2] = m->thp_o[CI(m, ir + a, jr, kr)];
+          fl[a + 2] = cell_fluid(m, ir + a, jr, kr);
+        }
+        d4 += diff_axis(f, fl, 1);
+        for (int a = -2; a <= 2; a++) {
+          f[a + 2] = m->thp_o[CI(m, ir, jr + a, kr)];
+          fl[a + 2] = cell_fluid(m, ir, jr + a, kr);
+        }
+        d4 += diff_axis(f, fl, 1);
+        for (int a = -2; a <= 2; a++) {
+          f[a + 2] = m->thp_o[CI(m, ir, jr, kr + a)];
+          fl[a + 2] = cell_fluid(m, ir, jr, kr + a);
+        }
+        d4 += diff_axis(f, fl, 1);
       }
       double Dth = -kdif * d4;
       double pn = pb_k(m, kr) + m->pp[1][r];
@@ -827,17 +875,23 @@ void oc_step(oc_model *m, int nsteps) {
       /* diffusion and sponge on the momentum departure from the reference
        * state (rho_bar U, 0, 0), level n-1 (readings C-4, C-5) */
       double *MO[3] = {m->mx[O], m->my[O], m->mz[O]};
+      int flx[5], fly[5], flz[5];
+      for (int a = -2; a <= 2; a++) {
+        flx[a + 2] = corner_fluid(m, I + a, J, K);
+        fly[a + 2] = corner_fluid(m, I, J + a, K);
+        flz[a + 2] = corner_fluid(m, I, J, K + a);
+      }
       for (int d = 0; d < 3; d++) {
         /* reference momentum (rho_bar_corner U, 0, 0) at corner level K */
         double ref0 = d == 0 ? m->rhobc[K + G] * P->U : 0.0;
         double f[5], d4 = 0.0;
         for (int a = -2; a <= 2; a++) f[a + 2] = MO[d][CI(m, I + a, J, K)] - ref0;
-        d4 += f[0] - 4 * f[1] + 6 * f[2] - 4 * f[3] + f[4];
+        d4 += diff_axis(f, flx, 0);
         for (int a = -2; a <= 2; a++) f[a + 2] = MO[d][CI(m, I, J + a, K)] - ref0;
-        d4 += f[0] - 4 * f[1] + 6 * f[2] - 4 * f[3] + f[4];
+        d4 += diff_axis(f, fly, 0);
         for (int a = -2; a <= 2; a++)
           f[a + 2] = MO[d][CI(m, I, J, K + a)] - (d == 0 ? m->rhobc[K + a + G] * P->U : 0.0);
-        d4 += f[0] - 4 * f[1] + 6 * f[2] - 4 * f[3] + f[4];
+        d4 += diff_axis(f, flz, 0);
         tend[d] += -kdif * d4 - m->tau[K + G] * (MO[d][p] - ref0);
       }
       double *MN[3] = {m->mx[2], m->my[2], m->mz[2]};

@@ -101,6 +101,16 @@ def _impulse_model(oracle_mod, **kw):
     return cfg, om
 
 
+def _tall_impulse_model(oracle_mod, **kw):
+    """12 levels: an impulse at level 5 and every point its diffusion reaches
+    (levels 3 .. 7) lie two or more points from the floor and the lid, so
+    every stencil involved is the fourth-order one."""
+    cfg = _flat(12, 10, 12, 100.0, 80.0, 50.0, 0.2, **kw)
+    om = oracle_mod.Model(cfg, np.zeros((cfg.ny, cfg.nx)))
+    om.init_state()
+    return cfg, om
+
+
 def test_buoyancy_impulse(oracle_mod):
     """A single-cell density perturbation at rest: after one forward step the
     eight corners of the cell carry w-momentum -dt g rho'/8 (the 8-point mean
@@ -149,12 +159,13 @@ def test_pressure_gradient_impulse(oracle_mod):
 
 
 def test_fourth_order_diffusion_impulse(oracle_mod):
-    """Artificial diffusion of (rho theta)': linearised about the base state the
-    pressure responds with the 5-point stencil (1,-4,6,-4,1) times c4/16 on each
-    axis (since (c_p R/c_v)(p/p0)^(R/c_p) d(rho theta)/dp = 1)."""
+    """Artificial diffusion of (rho theta)' away from every wall: linearised
+    about the base state the pressure responds with the 5-point stencil
+    (1,-4,6,-4,1) times c4/16 on each axis (since
+    (c_p R/c_v)(p/p0)^(R/c_p) d(rho theta)/dp = 1)."""
     c4 = 0.02
-    cfg, om = _impulse_model(oracle_mod, g=0.0, N=0.0, c4=c4)
-    i, j, k, dp = 6, 5, 4, 1e-2
+    cfg, om = _tall_impulse_model(oracle_mod, g=0.0, N=0.0, c4=c4)
+    i, j, k, dp = 6, 5, 5, 1e-2
     pp = np.zeros(om.cell_shape)
     pp[k, j, i] = dp
     om.set_field(oracle_mod.F_PP, 1, pp)
@@ -173,9 +184,9 @@ def test_fourth_order_diffusion_impulse(oracle_mod):
 
 def test_momentum_diffusion_impulse(oracle_mod):
     c4 = 0.02
-    cfg, om = _impulse_model(oracle_mod, g=0.0, N=0.0, c4=c4)
+    cfg, om = _tall_impulse_model(oracle_mod, g=0.0, N=0.0, c4=c4)
     gz = om.gz
-    I, J, K, dm = 6, 5, 4, 1e-7
+    I, J, K, dm = 6, 5, 5, 1e-7
     mx = np.zeros(om.corner_shape)
     mx[K + gz, J, I] = dm
     om.set_field(oracle_mod.F_MX, 1, mx)
