@@ -86,7 +86,7 @@ def kfull_source_hash():
     src = open(os.path.join(ROOT, "paper_1509_02572_gb300", "csrc", "step.cu")).read()
     hdr = open(os.path.join(ROOT, "paper_1509_02572_gb300", "csrc", "cc_internal.h")).read()
     a = src.index("struct FullCfg")
-    b = src.index("await_groups<0>();\n}", src.index("k_full(")) 
+    b = src.index("// ------------------------------------------------------------------ cut cells", a)
     tiles = [ln for ln in hdr.splitlines() if "TILE_" in ln or "SCHED_" in ln or "constexpr int GX" in ln]
     return hashlib.sha256((src[a:b] + "\n".join(tiles)).encode()).hexdigest()[:16]
 

@@ -40,7 +40,7 @@ typedef enum {
   CC_EINVAL = 1,    /* invalid argument (null pointer, bad size, bad index) */
   CC_ECUDA = 2,     /* a CUDA runtime call failed                           */
   CC_EGEOM = 3,     /* merge or boundary stencil cannot be formed           */
-  CC_ENUMERIC = 4,  /* NaN or Inf found by cc_diagnostics                   */
+  CC_ENUMERIC = 4,  /* NaN or Inf in the state (cc_diagnostics), or the step watchdog raised */
   CC_ENOMEM = 5,    /* device allocation failed                             */
   CC_ESTATE = 6     /* call out of order (e.g. step before geometry)        */
 } cc_status;
@@ -240,7 +240,16 @@ cc_status cc_save(const cc_model *m, const char *path);
 cc_status cc_load(cc_model *m, const char *path);
 
 /* Advance every domain by n steps (leapfrog; the first step after
- * cc_init_state is forward Euler).  Asynchronous on the model's stream. */
+ * cc_init_state is forward Euler).  Asynchronous on the model's stream.
+ *
+ * Step watchdog (no counterpart in the paper): every step's full-cell stencil
+ * raises a flag when it writes a non-finite value or when a corner's
+ * advective Courant number sum_d |u_d| dt / d_d exceeds 1 (the stability
+ * limit of centred leapfrog advection).  Each call queues a copy of the
+ * flags to the host after its steps; a later cc_step whose copy has arrived
+ * (checked without waiting) and cc_synchronize return CC_ENUMERIC, with the
+ * reason in cc_last_error, instead of stepping on.  cc_init_state and
+ * cc_load clear the flags. */
 cc_status cc_step(cc_model *m, int n);
 
 /* CUDA graphs (no counterpart in the paper): with graphs on (the default),
@@ -255,7 +264,9 @@ cc_status cc_graphs_enable(cc_model *m, int on);
  * Returns CC_ENUMERIC when non-finite values are present. */
 cc_status cc_diagnostics(cc_model *m, int d, cc_diag *out);
 
-/* Wait for all work queued on the model's stream. */
+/* Wait for all work queued on the model's stream; CC_ENUMERIC if the step
+ * watchdog (see cc_step) was raised by a step since the last cc_init_state
+ * or cc_load. */
 cc_status cc_synchronize(cc_model *m);
 
 /* Number of kernels the last cc_step launched (for launch accounting). */

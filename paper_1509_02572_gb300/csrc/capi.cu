@@ -96,6 +96,12 @@ struct cc_model {
   int xslot = 0;
   size_t stage_elems = 0;
   int *d_err = nullptr;
+  // step watchdog (flags of the full-cell stencil): the device word, its copy
+  // in pinned host memory, made after each cc_step call, and the event that
+  // marks the copy complete
+  unsigned *d_watch = nullptr, *h_watch = nullptr;
+  cudaEvent_t ev_watch = nullptr;
+  bool watch_pending = false;
   std::string err;
   std::vector<void *> allocs;
 };
@@ -118,6 +124,26 @@ cc_status cuda_fail(cc_model *m, cudaError_t e, const char *where) {
     cudaError_t e_ = (call);                        \
     if (e_ != cudaSuccess) return cuda_fail(m, e_, where); \
   } while (0)
+
+// The step watchdog's verdict from the host copy of its flags (valid once
+// ev_watch has completed).
+cc_status watch_verdict(cc_model *m) {
+  const unsigned w = *m->h_watch;
+  if (w & WATCH_NONFINITE) return fail(m, CC_ENUMERIC, "step watchdog: a step wrote a non-finite value");
+  if (w & WATCH_COURANT)
+    return fail(m, CC_ENUMERIC, "step watchdog: an advective Courant number sum |u_d| dt / d_d exceeded 1");
+  return CC_OK;
+}
+
+// Clears the watchdog (new state: initialisation, checkpoint load).
+cc_status watch_reset(cc_model *m) {
+  CK(m, cudaMemsetAsync(m->d_watch, 0, 16, m->st), "watchdog reset");
+  if (m->watch_pending) CK(m, cudaEventSynchronize(m->ev_watch), "watchdog reset");
+  *m->h_watch = 0;
+  m->watch_pending = false;
+  return CC_OK;
+}
+
 
 template <typename P>
 cudaError_t dalloc(std::vector<void *> &list, P **p, size_t bytes, cudaStream_t st) {
@@ -190,6 +216,7 @@ StepLaunch make_launch(const cc_model *m, int d = -1) {
   L.ncols = m->ncols;
   L.ndom = m->ndom;
   L.eos = m->eos;
+  L.watch = m->d_watch;
   if (d >= 0) {
     const DomHost &H = m->dom[d];
     L.items = m->d_items[H.sched] + H.item0[H.sched];
@@ -340,6 +367,9 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
         (e = dalloc(H.allocs, &mK, D.ncellp * 4, m->st)) || (e = dalloc(H.allocs, &mg, D.ncellp * 8, m->st)) ||
         (e = dalloc(H.allocs, &ktop, npc * 4, m->st)) || (e = dalloc(H.allocs, &kb, npc * 4, m->st)))
       return bail(e, "geometry alloc");
+    DiffCol *dcol;
+    if ((e = dalloc(H.allocs, &dcol, npc * sizeof(DiffCol), m->st)) != cudaSuccess) return bail(e, "geometry alloc");
+    D.dcol = dcol;
     D.h = h; D.vf = vf; D.ax = ax; D.ay = ay; D.az = az; D.cls = cls; D.root = root; D.kug = kug;
     D.vcls = vcls; D.bK = bK; D.bI = bI; D.bJ = bJ; D.ba = ba; D.bb = bb; D.bn = bn; D.mK = mK; D.mg = mg;
     D.ktop = ktop;
@@ -537,6 +567,12 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
   if ((e = dalloc(m->allocs, &m->d_stage, sizeof(double) * max_stage, m->st)) != cudaSuccess) return bail(e, "stage");
   m->stage_elems = max_stage;
   if ((e = dalloc(m->allocs, &m->d_err, sizeof(int), m->st)) != cudaSuccess) return bail(e, "err flag");
+  if ((e = dalloc(m->allocs, &m->d_watch, 16, m->st)) != cudaSuccess) return bail(e, "watchdog flag");
+  if ((e = cudaMemsetAsync(m->d_watch, 0, 16, m->st)) != cudaSuccess) return bail(e, "watchdog flag");
+  if ((e = cudaMallocHost(&m->h_watch, 16)) != cudaSuccess) return bail(e, "watchdog flag");
+  *m->h_watch = 0;
+  if ((e = cudaEventCreateWithFlags(&m->ev_watch, cudaEventDisableTiming)) != cudaSuccess)
+    return bail(e, "watchdog event");
   if ((e = cudaStreamSynchronize(m->st)) != cudaSuccess) return bail(e, "sync");
   *out = m;
   return CC_OK;
@@ -626,6 +662,8 @@ cc_status cc_destroy(cc_model *m) {
     if (m->ev_staged[a]) cudaEventDestroy(m->ev_staged[a]);
   }
   cudaFree(m->d_stage2);
+  if (m->h_watch) cudaFreeHost(m->h_watch);
+  if (m->ev_watch) cudaEventDestroy(m->ev_watch);
   delete m;
   return CC_OK;
 }
@@ -737,6 +775,7 @@ cc_status cc_build_geometry(cc_model *m) {
     cudaError_t e = geom_build_one(H.D, m->st, d, m->d_err, &mem, &recs, &ng, &nm);
     if (e != cudaSuccess) return cuda_fail(m, e, "geometry");
     if (!H.D.periodic) CK(m, launch_flat_columns(H.D, m->st), "frame columns");
+    CK(m, launch_diffcols(H.D, m->st), "diffusion stencils");
     int herr = 0;
     CK(m, cudaMemcpy(&herr, m->d_err, sizeof(int), cudaMemcpyDeviceToHost), "err read");
     std::vector<GroupRec> r(ng);
@@ -893,6 +932,8 @@ cc_status cc_init_state(cc_model *m) {
     CK(m, launch_restrict(K, m->prec, m->dom[l].r[1], m->st), "init restrict");
     CK(m, launch_prolong(K, m->prec, m->dom[l - 1].r[1], m->st), "init prolong");
   }
+  cc_status w = watch_reset(m);
+  if (w != CC_OK) return w;
   CK(m, cudaStreamSynchronize(m->st), "init sync");
   m->state = true;
   return CC_OK;
@@ -1284,6 +1325,11 @@ cc_status cc_step(cc_model *m, int n) {
   if (!m) return fail(m, CC_EINVAL, "null model");
   if (n < 0) return fail(m, CC_EINVAL, "negative step count");
   if (!m->state) return fail(m, CC_ESTATE, "state not initialised");
+  // the flags of the earlier calls, if their copy has arrived (no wait)
+  if (m->watch_pending && cudaEventQuery(m->ev_watch) == cudaSuccess) {
+    cc_status w = watch_verdict(m);
+    if (w != CC_OK) return w;
+  }
   long long nl = 0;
   cc_status r = CC_OK;
   for (int s = 0; s < n && r == CC_OK; s++) {
@@ -1293,6 +1339,11 @@ cc_status cc_step(cc_model *m, int n) {
     r = graph ? graph_step(m, nl) : one_step(m, nl);
   }
   m->last_launches = nl;
+  if (r == CC_OK && n > 0) {
+    CK(m, cudaMemcpyAsync(m->h_watch, m->d_watch, sizeof(unsigned), cudaMemcpyDeviceToHost, m->st), "watchdog copy");
+    CK(m, cudaEventRecord(m->ev_watch, m->st), "watchdog event");
+    m->watch_pending = true;
+  }
   return r;
 }
 
@@ -1308,10 +1359,34 @@ cc_status cc_graphs_enable(cc_model *m, int on) {
 // velocity, padded layout, model precision).
 namespace {
 const char kMagic[8] = {'C', 'U', 'T', 'C', 'E', 'L', 'L', '1'};
+constexpr int32_t kCkptVersion = 2;
 struct CkptDom {
   int32_t nx, ny, nz, px, py, pz, r[4];
   int64_t nsteps;
+  uint64_t fingerprint;  // the domain's configuration and terrain
 };
+
+// 64-bit FNV-1a over the domain's configuration (field by field, so that no
+// padding byte enters) and its corner heights: a checkpoint written for
+// another hill, spacing, time step or flow does not load.
+uint64_t fingerprint(const DomHost &H) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](const void *p, size_t n) {
+    const unsigned char *b = (const unsigned char *)p;
+    for (size_t a = 0; a < n; a++) {
+      h ^= b[a];
+      h *= 1099511628211ull;
+    }
+  };
+  const cc_config &c = H.cfg;
+  const int ints[4] = {c.nx, c.ny, c.nz, c.bc_slip};
+  const double dbl[16] = {c.dx, c.dy, c.dz, c.dt, c.U, c.N, c.theta0, c.p_surf,
+                          c.p0, c.g,  c.R,  c.cp, c.ra_nu, c.c4, c.sponge_frac, c.tau_max};
+  mix(ints, sizeof(ints));
+  mix(dbl, sizeof(dbl));
+  if (!H.hh.empty()) mix(H.hh.data(), H.hh.size() * sizeof(double));
+  return h;
+}
 }  // namespace
 
 cc_status cc_save(const cc_model *mc, const char *path) {
@@ -1322,10 +1397,11 @@ cc_status cc_save(const cc_model *mc, const char *path) {
   FILE *f = std::fopen(path, "wb");
   if (!f) return fail(m, CC_EINVAL, std::string("cannot open ") + path + " for writing");
   bool ok = std::fwrite(kMagic, 1, 8, f) == 8;
-  int32_t hdr[4] = {1, m->prec, m->ndom, m->refined ? 1 : 0};
+  int32_t hdr[4] = {kCkptVersion, m->prec, m->ndom, m->refined ? 1 : 0};
   ok = ok && std::fwrite(hdr, sizeof(hdr), 1, f) == 1;
   for (const auto &H : m->dom) {
-    CkptDom c{H.D.nx, H.D.ny, H.D.nz, H.D.px, H.D.py, H.D.pz, {H.r[0], H.r[1], H.r[2], H.r[3]}, H.nsteps};
+    CkptDom c{H.D.nx, H.D.ny, H.D.nz, H.D.px, H.D.py, H.D.pz, {H.r[0], H.r[1], H.r[2], H.r[3]}, H.nsteps,
+              fingerprint(H)};
     ok = ok && std::fwrite(&c, sizeof(c), 1, f) == 1;
   }
   std::vector<char> buf;
@@ -1367,7 +1443,7 @@ cc_status cc_load(cc_model *m, const char *path) {
   char magic[8];
   int32_t hdr[4];
   if (std::fread(magic, 1, 8, f) != 8 || std::memcmp(magic, kMagic, 8) != 0) return bad("not a checkpoint file");
-  if (std::fread(hdr, sizeof(hdr), 1, f) != 1 || hdr[0] != 1) return bad("unknown checkpoint version");
+  if (std::fread(hdr, sizeof(hdr), 1, f) != 1 || hdr[0] != kCkptVersion) return bad("unknown checkpoint version");
   if (hdr[1] != m->prec || hdr[2] != m->ndom || hdr[3] != (m->refined ? 1 : 0))
     return bad("precision, domain count or refinement differ from the model");
   std::vector<CkptDom> cd(m->ndom);
@@ -1377,8 +1453,14 @@ cc_status cc_load(cc_model *m, const char *path) {
     if (cd[d].nx != D.nx || cd[d].ny != D.ny || cd[d].nz != D.nz || cd[d].px != D.px || cd[d].py != D.py ||
         cd[d].pz != D.pz)
       return bad("domain " + std::to_string(d) + " has other sizes than the model's");
-    for (int a = 0; a < 4; a++)
+    int seen = 0;
+    for (int a = 0; a < 4; a++) {
       if (cd[d].r[a] < 0 || cd[d].r[a] >= NBUF) return bad("invalid time-level roles");
+      seen |= 1 << cd[d].r[a];
+    }
+    if (seen != (1 << NBUF) - 1) return bad("time-level roles of domain " + std::to_string(d) + " repeat a buffer");
+    if (cd[d].fingerprint != fingerprint(m->dom[d]))
+      return bad("domain " + std::to_string(d) + " was written for another configuration or terrain");
   }
   std::vector<char> buf;
   m->state = false;  // until every array has been read
@@ -1414,6 +1496,8 @@ cc_status cc_load(cc_model *m, const char *path) {
     CK(m, cudaMemsetAsync(K.regm, 0, K.nfaces * m->esz, m->st), "register reset");
     CK(m, cudaMemsetAsync(K.regh, 0, K.nfaces * m->esz, m->st), "register reset");
   }
+  cc_status w = watch_reset(m);
+  if (w != CC_OK) return w;
   CK(m, cudaStreamSynchronize(m->st), "load sync");
   m->state = true;
   return CC_OK;
@@ -1541,6 +1625,7 @@ cc_status cc_set_schedule(cc_model *m, int d, int tile_y, int items_per_launch) 
 cc_status cc_synchronize(cc_model *m) {
   if (!m) return fail(m, CC_EINVAL, "null model");
   CK(m, cudaStreamSynchronize(m->st), "synchronize");
+  if (m->watch_pending) return watch_verdict(m);
   return CC_OK;
 }
 

@@ -29,6 +29,22 @@ enum : int8_t { C_UG = 0, C_FULL = 1, C_CUT = 2, C_ABS = 3 };
 enum : int8_t { V_UG = 0, V_PRED = 1, V_MF = 2, V_LID = 3 };
 constexpr int KB_NONE = -1000;
 
+// Reach of the artificial-diffusion stencils in one padded column (Sec 2.1:
+// fourth order; Sec 2.4: second order where a cell lacks the neighbouring
+// fluid points the fourth-order term needs).  Fluid points: cells owning their
+// pressure point (full or cut) and corners above the terrain, below the lid.
+// In a column the cell classes run below-terrain, absorbed, cut, full from the
+// floor up, so a cell is a fluid point from the column's lowest full or cut
+// level on, and a corner from the lowest level above the terrain.
+struct DiffCol {
+  int16_t lo, hi;        // levels lo <= k < hi: the cell and the corner of this column take the
+                         // fourth-order term on every axis
+  int16_t ctop, vtop;    // cells k >= ctop and corners K >= vtop are not fluid points (the lid)
+  int16_t c0, v0;        // this column: lowest fluid cell level, lowest fluid corner level
+  int16_t cx[4], cy[4];  // lowest fluid cell level of the columns at offsets -2, -1, +1, +2 in x, in y
+  int16_t vx[4], vy[4];  // lowest fluid corner level of the same columns
+};
+
 // Device-side description of one domain.  Pointers are device pointers;
 // field arrays are of the model's precision (double or float).
 struct DomDev {
@@ -77,6 +93,7 @@ struct DomDev {
   // the boundary-point velocity u_B of their column; KB_NONE where the column's
   // corners are not integrated (frame of a refined box)
   const int32_t *kb;
+  const DiffCol *dcol;       // padded columns: reach of the diffusion stencils
 };
 
 // (block, tile) work item of the full-cell stencil
@@ -112,6 +129,67 @@ __host__ __device__ inline long long cid(const DomDev &D, int i, int j, int k) {
 __host__ __device__ inline long long qidx(const DomDev &D, int I, int J) {
   return (long long)(J + GH) * D.px + (I + GX);
 }
+
+// ---- deterministic compensated reductions (diagnostics, noalloc.cu)
+#ifdef __CUDACC__
+// Neumaier's running compensated sum of one thread's elements.
+template <typename T>
+struct NSum {
+  T s, c;
+  __device__ void add(T x) {
+    T t = s + x;
+    if (fabs((double)s) >= fabs((double)x)) c += (s - t) + x;
+    else c += (x - t) + s;
+    s = t;
+  }
+};
+// A compensated partial sum s + c.  Two partials combine by TwoSum (Knuth):
+// the rounding error of s1 + s2 is exact and symmetric in the operands, so a
+// xor-butterfly over a warp leaves the same bits in every lane, and the
+// whole reduction is the same on every run.
+struct CSum {
+  double s, c;
+};
+__device__ __forceinline__ CSum csum_add(CSum a, CSum b) {
+  const double t = a.s + b.s;
+  const double bp = t - a.s;
+  const double e = (a.s - (t - bp)) + (b.s - bp);
+  return CSum{t, (a.c + b.c) + e};
+}
+__device__ __forceinline__ CSum warp_csum(CSum v) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1)
+    v = csum_add(v, CSum{__shfl_xor_sync(0xffffffffu, v.s, m), __shfl_xor_sync(0xffffffffu, v.c, m)});
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int m = 16; m >= 1; m >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, m));
+  return v;
+}
+// Block of NT threads (a multiple of 32, at most 1024): the warps' sums, then
+// warp 0 over them; the result is valid in warp 0.  sh holds NT/32 entries.
+template <int NT>
+__device__ __forceinline__ CSum block_csum(CSum v, CSum *sh) {
+  v = warp_csum(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) v = warp_csum(l < NT / 32 ? sh[l] : CSum{0.0, 0.0});
+  __syncthreads();
+  return v;
+}
+template <int NT>
+__device__ __forceinline__ double block_max(double v, double *sh) {
+  v = warp_max(v);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (w == 0) v = warp_max(l < NT / 32 ? sh[l] : 0.0);
+  __syncthreads();
+  return v;
+}
+#endif
 
 // ---- refinement (step.cu)
 // A coarse face on the boundary of a refined box: the coarse cell on the
@@ -153,6 +231,8 @@ cudaError_t launch_iface(const LevelLink &L, int prec, int rO, int rC, int rN, i
 cudaError_t launch_mass_active(const DomDev &D, const DomDev *d_dom, int prec, int rC, int rO, int both,
                                int bx0, int bx1, int by0, int by1, int bz1, double *d_out, cudaStream_t st);
 cudaError_t launch_flat_columns(const DomDev &D, cudaStream_t st);
+// per-column reach of the diffusion stencils (after the classes and kb exist)
+cudaError_t launch_diffcols(const DomDev &D, cudaStream_t st);
 
 // geometry of one domain (geometry.cu); returns the group list of the domain
 // as device allocations owned by the caller
@@ -180,7 +260,11 @@ struct StepLaunch {
   int ndom;
   Eos eos;
   int ty;                  // tile height of the work items
+  unsigned *watch;         // step watchdog flags (CC_WATCH_*), or null
 };
+// step watchdog flags, set by the full-cell stencil
+constexpr unsigned WATCH_NONFINITE = 1u;  // a non-finite value was written
+constexpr unsigned WATCH_COURANT = 2u;    // advective Courant number sum_d |u_d| dt / d_d above 1
 cudaError_t launch_base(const DomDev &D, int prec, double theta0, double N, double p_surf,
                         double sponge_frac, double tau_max, cudaStream_t st);
 cudaError_t launch_full(const StepLaunch &L, int prec, int rO, int rC, int rN, int rF, int first,

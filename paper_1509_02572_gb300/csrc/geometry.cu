@@ -526,7 +526,69 @@ __global__ void k_kb(DomDev D, int32_t *kb) {
   kb[t] = K;
 }
 
+// Lowest fluid cell level of column (i, j) (full or cut: the classes of a
+// column run below-terrain, absorbed, cut, full upwards) and lowest fluid
+// corner level of corner column (I, J) (K dz above the terrain height, K >= 1).
+// A refined box's frame lies over flat floor.
+__device__ int first_fluid_cell(const DomDev &D, int i, int j) {
+  if (D.periodic) {
+    i = wrapi(i, D.nx);
+    j = wrapi(j, D.ny);
+  } else if (i < 0 || i >= D.nx || j < 0 || j >= D.ny) {
+    return 0;
+  }
+  for (int k = 0; k < D.nz; k++) {
+    const int8_t c = D.cls[cid(D, i, j, k)];
+    if (c == C_FULL || c == C_CUT) return k;
+  }
+  return D.nz;
+}
+__device__ int first_fluid_corner(const DomDev &D, int I, int J) {
+  const bool inside = I >= 0 && I < D.nx && J >= 0 && J < D.ny;
+  const double h = (D.periodic || inside) ? hcorner(D, I, J) : 0.0;
+  int K = 1;
+  while (K < D.nz + GH && K * D.dz <= h) K++;
+  return K;
+}
+
+// Reach of the diffusion stencils of every padded column (the descriptor of
+// the header): the lowest fluid levels of the column and of its neighbours at
+// -2 .. +2 along x and y, the lid, and the band of levels in which the cell
+// (x: its neighbours fluid; z: the two cells below fluid, the two above below
+// the lid) and the corner (likewise) both take the fourth-order term.
+__global__ void k_diffcols(DomDev D, DiffCol *out) {
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)D.px * D.py) return;
+  const int i = (int)(t % D.px) - GX, j = (int)(t / D.px) - GH;
+  const int off[4] = {-2, -1, 1, 2};
+  DiffCol q;
+  const int big = 16000;
+  q.ctop = (int16_t)(D.lid ? D.nz : big);
+  q.vtop = (int16_t)(D.lid ? D.nz : big);
+  int c0 = first_fluid_cell(D, i, j), v0 = first_fluid_corner(D, i, j);
+  q.c0 = (int16_t)c0;
+  q.v0 = (int16_t)v0;
+  int lo = max(c0 + 2, v0 + 2);
+  for (int a = 0; a < 4; a++) {
+    const int cxa = first_fluid_cell(D, i + off[a], j), cya = first_fluid_cell(D, i, j + off[a]);
+    const int vxa = first_fluid_corner(D, i + off[a], j), vya = first_fluid_corner(D, i, j + off[a]);
+    q.cx[a] = (int16_t)cxa;
+    q.cy[a] = (int16_t)cya;
+    q.vx[a] = (int16_t)vxa;
+    q.vy[a] = (int16_t)vya;
+    lo = max(lo, max(max(cxa, cya), max(vxa, vya)));
+  }
+  q.lo = (int16_t)lo;
+  q.hi = (int16_t)(D.lid ? D.nz - 2 : big);
+  out[t] = q;
+}
+
 }  // namespace
+
+cudaError_t launch_diffcols(const DomDev &D, cudaStream_t st) {
+  k_diffcols<<<nblk((long long)D.px * D.py), TPB, 0, st>>>(D, const_cast<DiffCol *>(D.dcol));
+  return cudaGetLastError();
+}
 
 // Analytic hill at the corners (I dx, J dy) relative to its centre (xc, yc):
 // the bell-shaped hill h0 / (1 + r^2/a^2)^(3/2) (Sec 3.1.1), the half-

@@ -33,52 +33,34 @@ double *g_addr[kMaxDevices] = {nullptr};
 
 thread_local char g_msg[256];  // fixed buffer: error reporting allocates nothing either
 
-template <typename T>
-struct Neu {
-  T s, c;
-  __device__ void add(T x) {
-    T t = s + x;
-    if (fabs((double)s) >= fabs((double)x)) c += (s - t) + x;
-    else c += (x - t) + s;
-    s = t;
-  }
-};
-
 // Each block writes its own slot; the final kernel reads exactly the slots
-// written by the same call, so nothing needs clearing between calls.
+// written by the same call, so nothing needs clearing between calls.  The
+// per-thread sums and the warp-shuffle trees are those of cc_diagnostics, so
+// with 256 partials (its block count) the two give the same bits.
 template <typename T>
 __global__ void k_mass_parts(const T *__restrict__ rho, const double *__restrict__ vol, long long n,
                              double *__restrict__ parts) {
-  Neu<T> acc{0, 0};
+  cc::NSum<T> acc{0, 0};
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
        i += (long long)gridDim.x * blockDim.x)
     acc.add((T)vol[i] * rho[i]);
-  __shared__ double sh[2][kThreads];
-  sh[0][threadIdx.x] = (double)acc.s;
-  sh[1][threadIdx.x] = (double)acc.c;
-  __syncthreads();
+  __shared__ cc::CSum sh[kThreads / 32];
+  const cc::CSum b = cc::block_csum<kThreads>(cc::CSum{(double)acc.s, (double)acc.c}, sh);
   if (threadIdx.x == 0) {
-    Neu<double> b{0, 0};
-    double cc = 0;
-    for (int a = 0; a < kThreads; a++) {
-      b.add(sh[0][a]);
-      cc += sh[1][a];
-    }
     parts[2 * blockIdx.x] = b.s;
-    parts[2 * blockIdx.x + 1] = b.c + cc;
+    parts[2 * blockIdx.x + 1] = b.c;
   }
 }
 
 __global__ void k_mass_final(const double *__restrict__ parts, int nparts, double *__restrict__ out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  Neu<double> b{0, 0};
-  double cc = 0;
-  for (int p = 0; p < nparts; p++) {
-    b.add(parts[2 * p]);
-    cc += parts[2 * p + 1];
+  cc::CSum b{0.0, 0.0};
+  for (int p = threadIdx.x; p < nparts; p += kThreads) b = cc::csum_add(b, cc::CSum{parts[2 * p], parts[2 * p + 1]});
+  __shared__ cc::CSum sh[kThreads / 32];
+  b = cc::block_csum<kThreads>(b, sh);
+  if (threadIdx.x == 0) {
+    out[0] = b.s + b.c;
+    out[1] = b.c;
   }
-  out[0] = b.s + (b.c + cc);
-  out[1] = b.c + cc;
 }
 
 cc_status fail(cc_status s, const char *what, const char *detail = "") {
@@ -113,12 +95,16 @@ extern "C" cc_status cc_mass_sum_noalloc(const void *rho_prime, int precision, c
     }
     parts = g_addr[dev];
   }
+  // an error left by an earlier, unrelated launch is reported, not cleared
+  // (it belongs to its caller), and nothing is launched on top of it
+  e = cudaPeekAtLastError();
+  if (e != cudaSuccess) return fail(CC_ECUDA, "a CUDA error from an earlier call is pending: ", cudaGetErrorString(e));
   cudaStream_t st = (cudaStream_t)stream;
   if (precision == CC_FP64)
     k_mass_parts<double><<<nparts, kThreads, 0, st>>>((const double *)rho_prime, volume, n, parts);
   else
     k_mass_parts<float><<<nparts, kThreads, 0, st>>>((const float *)rho_prime, volume, n, parts);
-  k_mass_final<<<1, 32, 0, st>>>(parts, nparts, out);
+  k_mass_final<<<1, kThreads, 0, st>>>(parts, nparts, out);
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(CC_ECUDA, "launch: ", cudaGetErrorString(e));
   return CC_OK;

@@ -208,6 +208,25 @@ __device__ __forceinline__ float d4(float a, float b, float c, float d, float e)
   return a - 4.0f * b + 6.0f * c - 4.0f * d + e;
 }
 
+// Artificial diffusion along one axis (Sec 2.1: fourth order; Sec 2.4: a
+// second-order term where the neighbouring fluid points the fourth-order term
+// needs are missing, with the boundary conditions of the terrain surface;
+// reading C-4), as the axis's term of the sum S in D = -K4 S: the fourth
+// difference where the neighbours at distance 1 and 2 (flags fa, fb, fd, fe)
+// are all fluid points, otherwise -4 times the second difference over the
+// distance-1 neighbours (K2 = 4 K4 / d^2).  A scalar neighbour that is not a
+// fluid point takes the centre value (no flux through the wall); a velocity
+// neighbour keeps its stored boundary value.
+template <typename T>
+__device__ __forceinline__ T diff_axis(T a, T b, T c, T d, T e, bool fa, bool fb, bool fd, bool fe,
+                                       bool scalar) {
+  if (fa && fb && fd && fe) return d4(a, b, c, d, e);
+  const T lo = (fb || !scalar) ? b : c;
+  const T hi = (fd || !scalar) ? d : c;
+  return T(-4) * ((lo - T(2) * c) + hi);
+}
+__device__ __forceinline__ bool fluid_at(int k, int lo, int top) { return k >= lo && k < top; }
+
 // padded index of a cell / corner; periodic domains wrap the lateral
 // coordinates, refined boxes read their ghost frame
 __device__ __forceinline__ long long widx(const DomDev &D, int i, int j, int k) {
@@ -315,7 +334,8 @@ struct FullOcc {
 template <typename T, int TYv>
 __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(const DomDev *__restrict__ doms,
                                                         const WorkItem *__restrict__ items, int rO, int rC,
-                                                        int rN, int rF, int first, const Eos E) {
+                                                        int rN, int rF, int first, const Eos E,
+                                                        unsigned *__restrict__ watch) {
   using A = Ar<T>;
   using C = FullCfg<T, TYv>;
   constexpr int TX = C::TX, NT = C::NT, HX = C::HX, PL = C::PL, NLP = C::NLP;
@@ -480,6 +500,9 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
   const T v0inv = (T)(1.0 / (D.dx * D.dy * D.dz));
   const T kdif = (T)D.kdif, Cp = (T)D.Cp, g = (T)D.g, U = (T)D.U;
   const int kug = active ? D.kug[qidx(D, i, j)] : 0;
+  // levels of this column whose cell and corner take the fourth-order
+  // diffusion on every axis; the others take the wall-aware form
+  const int dlo = active ? D.dcol[own].lo : 0, dhi = active ? D.dcol[own].hi : 0;
 
   // own column at n-1 for the vertical diffusion stencils, levels k-2 .. k+2
   T treg[5], mreg[5][3];
@@ -520,6 +543,11 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
   velocity(k0);
 
   T fz_carry = 0, hz_carry = 0;  // high z-face fluxes of the previous plane
+  // step watchdog: a non-finite value written, or the advective Courant
+  // number sum_d |u_d| dt / d_d of a corner above 1 (the stability limit of
+  // centred leapfrog advection)
+  unsigned wflag = 0;
+  const T cfx = (T)(D.dt / D.dx), cfy = (T)(D.dt / D.dy), cfz = (T)(D.dt / D.dz);
   for (int k = k0; k < k1; k++) {
     // phase 1: wait for plane k+2; once every thread is past the previous
     // plane (the barrier), the ring slots it read last are free and the
@@ -575,11 +603,62 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
       if (D.lid && k == nz - 1) { fzp = 0; hzp = 0; }    // rigid lid
       T RM = A::add(A::add(A::sub(fxp, fxm), A::sub(fyp, fym)), A::sub(fzp, fzm));
       T RH = A::add(A::add(A::sub(hxp, hxm), A::sub(hyp, hym)), A::sub(hzp, hzm));
-      // fourth-order diffusion of (rho theta)' at n-1
+      // artificial diffusion at n-1 of (rho theta)' and of the momentum
+      // departure from the reference (rho_bar U, 0, 0): fourth order inside
+      // the column's band, the wall-aware form next to the terrain and the lid
       const T *Tk = S.to;
-      T dd = d4(Tk[c - 2], Tk[c - 1], Tk[c], Tk[c + 1], Tk[c + 2]) +
+      const int ok4 = s4(k);
+      const bool wall = k < dlo || k >= dhi;
+      T dd, dmv[3];
+      if (!wall) {
+        dd = d4(Tk[c - 2], Tk[c - 1], Tk[c], Tk[c + 1], Tk[c + 2]) +
              d4(Tk[c - 2 * HX], Tk[c - HX], Tk[c], Tk[c + HX], Tk[c + 2 * HX]) +
              d4(treg[0], treg[1], treg[2], treg[3], treg[4]);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          const T *Mk = S.om[ok4][d];
+          const T ref0 = d == 0 ? rbc[2] : T(0);
+          T dm = d4(Mk[c - 2] - ref0, Mk[c - 1] - ref0, Mk[c] - ref0, Mk[c + 1] - ref0, Mk[c + 2] - ref0) +
+                 d4(Mk[c - 2 * HX] - ref0, Mk[c - HX] - ref0, Mk[c] - ref0, Mk[c + HX] - ref0,
+                    Mk[c + 2 * HX] - ref0);
+          if (d == 0)
+            dm += d4(mreg[0][0] - rbc[0], mreg[1][0] - rbc[1], mreg[2][0] - ref0, mreg[3][0] - rbc[3],
+                     mreg[4][0] - rbc[4]);
+          else
+            dm += d4(mreg[0][d], mreg[1][d], mreg[2][d], mreg[3][d], mreg[4][d]);
+          dmv[d] = dm;
+        }
+      } else {
+        const DiffCol &Q = D.dcol[own];
+        const int ct = Q.ctop, vt = Q.vtop;
+        dd = diff_axis(Tk[c - 2], Tk[c - 1], Tk[c], Tk[c + 1], Tk[c + 2], fluid_at(k, Q.cx[0], ct),
+                       fluid_at(k, Q.cx[1], ct), fluid_at(k, Q.cx[2], ct), fluid_at(k, Q.cx[3], ct), true) +
+             diff_axis(Tk[c - 2 * HX], Tk[c - HX], Tk[c], Tk[c + HX], Tk[c + 2 * HX], fluid_at(k, Q.cy[0], ct),
+                       fluid_at(k, Q.cy[1], ct), fluid_at(k, Q.cy[2], ct), fluid_at(k, Q.cy[3], ct), true) +
+             diff_axis(treg[0], treg[1], treg[2], treg[3], treg[4], fluid_at(k - 2, Q.c0, ct),
+                       fluid_at(k - 1, Q.c0, ct), fluid_at(k + 1, Q.c0, ct), fluid_at(k + 2, Q.c0, ct), true);
+        const bool fx0 = fluid_at(k, Q.vx[0], vt), fx1 = fluid_at(k, Q.vx[1], vt), fx2 = fluid_at(k, Q.vx[2], vt),
+                   fx3 = fluid_at(k, Q.vx[3], vt);
+        const bool fy0 = fluid_at(k, Q.vy[0], vt), fy1 = fluid_at(k, Q.vy[1], vt), fy2 = fluid_at(k, Q.vy[2], vt),
+                   fy3 = fluid_at(k, Q.vy[3], vt);
+        const bool fz0 = fluid_at(k - 2, Q.v0, vt), fz1 = fluid_at(k - 1, Q.v0, vt),
+                   fz2 = fluid_at(k + 1, Q.v0, vt), fz3 = fluid_at(k + 2, Q.v0, vt);
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          const T *Mk = S.om[ok4][d];
+          const T ref0 = d == 0 ? rbc[2] : T(0);
+          T dm = diff_axis(Mk[c - 2] - ref0, Mk[c - 1] - ref0, Mk[c] - ref0, Mk[c + 1] - ref0, Mk[c + 2] - ref0,
+                           fx0, fx1, fx2, fx3, false) +
+                 diff_axis(Mk[c - 2 * HX] - ref0, Mk[c - HX] - ref0, Mk[c] - ref0, Mk[c + HX] - ref0,
+                           Mk[c + 2 * HX] - ref0, fy0, fy1, fy2, fy3, false);
+          if (d == 0)
+            dm += diff_axis(mreg[0][0] - rbc[0], mreg[1][0] - rbc[1], mreg[2][0] - ref0, mreg[3][0] - rbc[3],
+                            mreg[4][0] - rbc[4], fz0, fz1, fz2, fz3, false);
+          else
+            dm += diff_axis(mreg[0][d], mreg[1][d], mreg[2][d], mreg[3][d], mreg[4][d], fz0, fz1, fz2, fz3, false);
+          dmv[d] = dm;
+        }
+      }
       T Dth = -kdif * dd;
       const EosK<T> &ek = ek0;
       T rC_ = S.cr[ck][c], pC_ = S.cp[ck][c];
@@ -626,27 +705,21 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
       T r8 = (Q0[cSW] + Q0[cS] + Q0[cW] + Q0[c]) + (Qm[cSW] + Qm[cS] + Qm[cW] + Qm[c]);
       T pg[3] = {(pE - pW) * qdx, (pNn - pS) * qdy, (pT - pB) * qdz};
       T mnew[3], mflt[3];
-      const int ok4 = s4(k);
 #pragma unroll
       for (int d = 0; d < 3; d++) {
         T adv = u0[d] * gsum + (((gE * uE[d] - gW * uW[d]) + (gN * uN[d] - gS * uS[d])) + (gT * uT[d] - gB * uB[d]));
         T tend = -adv * v0inv - pg[d];
         if (d == 2) tend -= g * r8 * T(0.125);
-        const T *Mk = S.om[ok4][d];
-        // diffusion of the departure from the reference momentum (rho_bar U, 0, 0)
-        T ref0 = d == 0 ? rbc[2] : T(0);
-        T dm = d4(Mk[c - 2] - ref0, Mk[c - 1] - ref0, Mk[c] - ref0, Mk[c + 1] - ref0, Mk[c + 2] - ref0) +
-               d4(Mk[c - 2 * HX] - ref0, Mk[c - HX] - ref0, Mk[c] - ref0, Mk[c + HX] - ref0,
-                  Mk[c + 2 * HX] - ref0);
-        if (d == 0)
-          dm += d4(mreg[0][0] - rbc[0], mreg[1][0] - rbc[1], mreg[2][0] - ref0, mreg[3][0] - rbc[3],
-                   mreg[4][0] - rbc[4]);
-        else
-          dm += d4(mreg[0][d], mreg[1][d], mreg[2][d], mreg[3][d], mreg[4][d]);
+        const T ref0 = d == 0 ? rbc[2] : T(0);
         T mold = mreg[2][d];
-        tend += -kdif * dm - tk * (mold - ref0);
+        tend += -kdif * dmv[d] - tk * (mold - ref0);
         mnew[d] = mold + dt2 * tend;
         mflt[d] = mcur[d] + nu * (mnew[d] - T(2) * mcur[d] + mold);
+      }
+      {
+        const T chk = ((rN_ + pN_) + (mnew[0] + mnew[1])) + mnew[2];
+        if (!isfinite(chk)) wflag |= WATCH_NONFINITE;
+        if (fabs(u0[0]) * cfx + fabs(u0[1]) * cfy + fabs(u0[2]) * cfz > T(1)) wflag |= WATCH_COURANT;
       }
       // every store after every shared-memory read of the plane (a store
       // through a generic pointer would otherwise order the later reads)
@@ -671,6 +744,8 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
     }
   }
   await_groups<0>();
+  wflag = __reduce_or_sync(0xffffffffu, wflag);
+  if (wflag && (tid & 31) == 0 && watch) atomicOr(watch, wflag);
 }
 
 // ------------------------------------------------------------------ cut cells and merge groups
@@ -713,6 +788,21 @@ __device__ __forceinline__ void corner_u(const DomDev &D, const T *rp, const T *
   u[0] = M[0][o] * iv;
   u[1] = M[1][o] * iv;
   u[2] = M[2][o] * iv;
+}
+
+// The diffusion sum S of a scalar cell (i, j, k) with the wall-aware axis
+// terms, from the column descriptor Q and a function f(i, j, k) giving the
+// diffused value at n-1.
+template <typename T, typename F>
+__device__ __forceinline__ T scalar_diffusion(const DiffCol &Q, int k, F &&f, int i, int j) {
+  const int ct = Q.ctop;
+  const T c = f(i, j, k);
+  return diff_axis(f(i - 2, j, k), f(i - 1, j, k), c, f(i + 1, j, k), f(i + 2, j, k), fluid_at(k, Q.cx[0], ct),
+                   fluid_at(k, Q.cx[1], ct), fluid_at(k, Q.cx[2], ct), fluid_at(k, Q.cx[3], ct), true) +
+         diff_axis(f(i, j - 2, k), f(i, j - 1, k), c, f(i, j + 1, k), f(i, j + 2, k), fluid_at(k, Q.cy[0], ct),
+                   fluid_at(k, Q.cy[1], ct), fluid_at(k, Q.cy[2], ct), fluid_at(k, Q.cy[3], ct), true) +
+         diff_axis(f(i, j, k - 2), f(i, j, k - 1), c, f(i, j, k + 1), f(i, j, k + 2), fluid_at(k - 2, Q.c0, ct),
+                   fluid_at(k - 1, Q.c0, ct), fluid_at(k + 1, Q.c0, ct), fluid_at(k + 2, Q.c0, ct), true);
 }
 
 template <typename T>
@@ -795,9 +885,8 @@ __global__ void k_groups(const DomDev *__restrict__ doms, const GroupRec *__rest
   int h = R.host;
   int ih = h % nx, jh = (h / nx) % ny, kh = h / (nx * ny);
   auto tho = [&](int ii, int jj, int kk) { return theta_pert(D, thb, pb, ipb, kk + GH, ppO[widx(D, ii, jj, kk)]); };
-  T dd = d4(tho(ih - 2, jh, kh), tho(ih - 1, jh, kh), tho(ih, jh, kh), tho(ih + 1, jh, kh), tho(ih + 2, jh, kh)) +
-         d4(tho(ih, jh - 2, kh), tho(ih, jh - 1, kh), tho(ih, jh, kh), tho(ih, jh + 1, kh), tho(ih, jh + 2, kh)) +
-         d4(tho(ih, jh, kh - 2), tho(ih, jh, kh - 1), tho(ih, jh, kh), tho(ih, jh, kh + 1), tho(ih, jh, kh + 2));
+  // wall-aware diffusion of (rho theta)' at n-1 at the host
+  T dd = scalar_diffusion<T>(D.dcol[qidx(D, ih, jh)], kh, tho, ih, jh);
   T Dth = -(T)D.kdif * dd;
   long long oh = pidx(D, ih, jh, kh);
   T rC_ = rpC[oh], pC_ = ppC[oh], rO_ = rpO[oh], pO_ = ppO[oh];
@@ -939,19 +1028,11 @@ __global__ void k_init_momentum(const DomDev *__restrict__ dom, int r, double U)
 }
 
 // ------------------------------------------------------------------ diagnostics
-// Neumaier-compensated mass sum and maxima; fixed block count and fixed
-// reduction order, so the result does not depend on scheduling.
-template <typename T>
-struct NSum {
-  T s, c;
-  __device__ void add(T x) {
-    T t = s + x;
-    if (fabs((double)s) >= fabs((double)x)) c += (s - t) + x;
-    else c += (x - t) + s;
-    s = t;
-  }
-};
-
+// Compensated sums and maxima (Sec 2.2: the mass the scheme conserves):
+// Neumaier per thread over a fixed grid-stride share of the cells, then
+// warp-shuffle TwoSum trees within each block and over the block partials.
+// Fixed block count and fixed order, so the result does not depend on
+// scheduling and repeats bit for bit.
 constexpr int DIAG_BLOCKS = 256, DIAG_TPB = 256;
 
 template <typename T>
@@ -980,47 +1061,44 @@ __global__ void k_diag_partial(const DomDev *__restrict__ dom, int r, double *pa
       mw = fmax(mw, ww);
     }
   }
-  __shared__ double sh[5][DIAG_TPB];
-  sh[0][threadIdx.x] = (double)acc.s;
-  sh[1][threadIdx.x] = (double)acc.c;
-  sh[2][threadIdx.x] = mu;
-  sh[3][threadIdx.x] = mw;
-  sh[4][threadIdx.x] = bad;
-  __syncthreads();
+  __shared__ CSum shc[DIAG_TPB / 32];
+  __shared__ double shm[DIAG_TPB / 32];
+  const CSum m = block_csum<DIAG_TPB>(CSum{(double)acc.s, (double)acc.c}, shc);
+  const CSum nb = block_csum<DIAG_TPB>(CSum{bad, 0.0}, shc);
+  const double a2 = block_max<DIAG_TPB>(mu, shm), a3 = block_max<DIAG_TPB>(mw, shm);
   if (threadIdx.x == 0) {
-    NSum<double> S{0, 0};
-    double cc = 0, a2 = 0, a3 = 0, a4 = 0;
-    for (int a = 0; a < DIAG_TPB; a++) {
-      S.add(sh[0][a]);
-      cc += sh[1][a];
-      a2 = fmax(a2, sh[2][a]);
-      a3 = fmax(a3, sh[3][a]);
-      a4 += sh[4][a];
-    }
-    part[5 * blockIdx.x + 0] = S.s;
-    part[5 * blockIdx.x + 1] = S.c + cc;
+    part[5 * blockIdx.x + 0] = m.s;
+    part[5 * blockIdx.x + 1] = m.c;
     part[5 * blockIdx.x + 2] = a2;
     part[5 * blockIdx.x + 3] = a3;
-    part[5 * blockIdx.x + 4] = a4;
+    part[5 * blockIdx.x + 4] = nb.s;
   }
 }
 
+// One block of DIAG_TPB threads over the nb block partials (thread t takes
+// partials t, t + DIAG_TPB, ..), then the same trees.
 __global__ void k_diag_final(const double *part, int nb, double *out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  NSum<double> S{0, 0};
-  double cc = 0, a2 = 0, a3 = 0, a4 = 0;
-  for (int b = 0; b < nb; b++) {
-    S.add(part[5 * b]);
-    cc += part[5 * b + 1];
+  CSum m{0.0, 0.0}, bad{0.0, 0.0};
+  double a2 = 0, a3 = 0;
+  for (int b = threadIdx.x; b < nb; b += DIAG_TPB) {
+    m = csum_add(m, CSum{part[5 * b], part[5 * b + 1]});
     a2 = fmax(a2, part[5 * b + 2]);
     a3 = fmax(a3, part[5 * b + 3]);
-    a4 += part[5 * b + 4];
+    bad = csum_add(bad, CSum{part[5 * b + 4], 0.0});
   }
-  out[0] = S.s + (S.c + cc);
-  out[1] = S.c + cc;
-  out[2] = a2;
-  out[3] = a3;
-  out[4] = a4;
+  __shared__ CSum shc[DIAG_TPB / 32];
+  __shared__ double shm[DIAG_TPB / 32];
+  m = block_csum<DIAG_TPB>(m, shc);
+  bad = block_csum<DIAG_TPB>(bad, shc);
+  a2 = block_max<DIAG_TPB>(a2, shm);
+  a3 = block_max<DIAG_TPB>(a3, shm);
+  if (threadIdx.x == 0) {
+    out[0] = m.s + m.c;
+    out[1] = m.c;
+    out[2] = a2;
+    out[3] = a3;
+    out[4] = bad.s;
+  }
 }
 
 
@@ -1073,32 +1151,23 @@ __global__ void k_heat_partial(const DomDev *__restrict__ dom, int r, double *pa
     const T x = theta_pert(D, (const T *)D.thb, (const T *)D.pb, (const T *)D.ipb, kh + GH, pp[pidx(D, ih, jh, kh)]);
     acc.add(D.vf[t] * V0 * (double)x);
   }
-  __shared__ double sh[2][DIAG_TPB];
-  sh[0][threadIdx.x] = acc.s;
-  sh[1][threadIdx.x] = acc.c;
-  __syncthreads();
+  __shared__ CSum shc[DIAG_TPB / 32];
+  const CSum h = block_csum<DIAG_TPB>(CSum{acc.s, acc.c}, shc);
   if (threadIdx.x == 0) {
-    NSum<double> S{0, 0};
-    double cc = 0;
-    for (int a = 0; a < DIAG_TPB; a++) {
-      S.add(sh[0][a]);
-      cc += sh[1][a];
-    }
-    part[2 * blockIdx.x] = S.s;
-    part[2 * blockIdx.x + 1] = S.c + cc;
+    part[2 * blockIdx.x] = h.s;
+    part[2 * blockIdx.x + 1] = h.c;
   }
 }
 
 __global__ void k_heat_final(const double *part, int nb, double *out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  NSum<double> S{0, 0};
-  double cc = 0;
-  for (int b = 0; b < nb; b++) {
-    S.add(part[2 * b]);
-    cc += part[2 * b + 1];
+  CSum h{0.0, 0.0};
+  for (int b = threadIdx.x; b < nb; b += DIAG_TPB) h = csum_add(h, CSum{part[2 * b], part[2 * b + 1]});
+  __shared__ CSum shc[DIAG_TPB / 32];
+  h = block_csum<DIAG_TPB>(h, shc);
+  if (threadIdx.x == 0) {
+    out[0] = h.s + h.c;
+    out[1] = h.c;
   }
-  out[0] = S.s + (S.c + cc);
-  out[1] = S.c + cc;
 }
 
 // Global error norms (appendix accuracy test): the corner velocity component
@@ -1127,40 +1196,30 @@ __global__ void k_norms(const DomDev *__restrict__ A, int ra, const DomDev *__re
     s1.add(fabs(d));
     s2.add(d * d);
   }
-  __shared__ double sh[4][DIAG_TPB];
-  sh[0][threadIdx.x] = s1.s;
-  sh[1][threadIdx.x] = s1.c;
-  sh[2][threadIdx.x] = s2.s;
-  sh[3][threadIdx.x] = s2.c;
-  __syncthreads();
+  __shared__ CSum shc[DIAG_TPB / 32];
+  const CSum a = block_csum<DIAG_TPB>(CSum{s1.s, s1.c}, shc);
+  const CSum b = block_csum<DIAG_TPB>(CSum{s2.s, s2.c}, shc);
   if (threadIdx.x == 0) {
-    NSum<double> S1{0, 0}, S2{0, 0};
-    double c1 = 0, c2 = 0;
-    for (int a = 0; a < DIAG_TPB; a++) {
-      S1.add(sh[0][a]);
-      c1 += sh[1][a];
-      S2.add(sh[2][a]);
-      c2 += sh[3][a];
-    }
-    part[4 * blockIdx.x] = S1.s;
-    part[4 * blockIdx.x + 1] = S1.c + c1;
-    part[4 * blockIdx.x + 2] = S2.s;
-    part[4 * blockIdx.x + 3] = S2.c + c2;
+    part[4 * blockIdx.x] = a.s;
+    part[4 * blockIdx.x + 1] = a.c;
+    part[4 * blockIdx.x + 2] = b.s;
+    part[4 * blockIdx.x + 3] = b.c;
   }
 }
 
 __global__ void k_norms_final(const double *part, int nb, double *out) {
-  if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  NSum<double> S1{0, 0}, S2{0, 0};
-  double c1 = 0, c2 = 0;
-  for (int b = 0; b < nb; b++) {
-    S1.add(part[4 * b]);
-    c1 += part[4 * b + 1];
-    S2.add(part[4 * b + 2]);
-    c2 += part[4 * b + 3];
+  CSum a{0.0, 0.0}, b{0.0, 0.0};
+  for (int q = threadIdx.x; q < nb; q += DIAG_TPB) {
+    a = csum_add(a, CSum{part[4 * q], part[4 * q + 1]});
+    b = csum_add(b, CSum{part[4 * q + 2], part[4 * q + 3]});
   }
-  out[0] = S1.s + (S1.c + c1);
-  out[1] = S2.s + (S2.c + c2);
+  __shared__ CSum shc[DIAG_TPB / 32];
+  a = block_csum<DIAG_TPB>(a, shc);
+  b = block_csum<DIAG_TPB>(b, shc);
+  if (threadIdx.x == 0) {
+    out[0] = a.s + a.c;
+    out[1] = b.s + b.c;
+  }
 }
 
 // ------------------------------------------------------------------ refinement (Sec 2.2)
@@ -1431,9 +1490,7 @@ __global__ void k_iface(LevelLink L, int rO, int rC, int rN, int rF, int first) 
   const T *ppO = (const T *)D.f[rO][1];
   const T *rhobp = (const T *)D.pb, *thb = (const T *)D.thb, *pik = (const T *)D.pik, *ipb = (const T *)D.ipb;
   auto tho = [&](int ii, int jj, int kk) { return theta_pert(D, thb, rhobp, ipb, kk + GH, ppO[widx(D, ii, jj, kk)]); };
-  T dd = d4(tho(i - 2, j, k), tho(i - 1, j, k), tho(i, j, k), tho(i + 1, j, k), tho(i + 2, j, k)) +
-         d4(tho(i, j - 2, k), tho(i, j - 1, k), tho(i, j, k), tho(i, j + 1, k), tho(i, j + 2, k)) +
-         d4(tho(i, j, k - 2), tho(i, j, k - 1), tho(i, j, k), tho(i, j, k + 1), tho(i, j, k + 2));
+  T dd = scalar_diffusion<T>(D.dcol[qidx(D, i, j)], k, tho, i, j);
   T Dth = -(T)D.kdif * dd;
   const T v0inv = (T)(1.0 / (D.dx * D.dy * D.dz));
   long long o = pidx(D, i, j, k);
@@ -1470,19 +1527,11 @@ __global__ void k_mass_active(const DomDev *__restrict__ dom, int rC, int rO, in
     double m = (double)r1[o] + (both ? (double)r0[o] : 0.0);
     acc.add(D.vf[t] * V0 * m);
   }
-  __shared__ double sh[2][DIAG_TPB];
-  sh[0][threadIdx.x] = acc.s;
-  sh[1][threadIdx.x] = acc.c;
-  __syncthreads();
+  __shared__ CSum shc[DIAG_TPB / 32];
+  const CSum ms = block_csum<DIAG_TPB>(CSum{acc.s, acc.c}, shc);
   if (threadIdx.x == 0) {
-    NSum<double> S{0, 0};
-    double cc = 0;
-    for (int a = 0; a < DIAG_TPB; a++) {
-      S.add(sh[0][a]);
-      cc += sh[1][a];
-    }
-    part[5 * blockIdx.x + 0] = S.s;
-    part[5 * blockIdx.x + 1] = S.c + cc;
+    part[5 * blockIdx.x + 0] = ms.s;
+    part[5 * blockIdx.x + 1] = ms.c;
     part[5 * blockIdx.x + 2] = 0;
     part[5 * blockIdx.x + 3] = 0;
     part[5 * blockIdx.x + 4] = 0;
@@ -1507,7 +1556,7 @@ cudaError_t full_t(const StepLaunch &L, int rO, int rC, int rN, int rF, int firs
   }
   if (L.nitems > 0)
     k_full<T, TYv><<<L.nitems, TILE_X * TYv, full_smem<T, TYv>(), st>>>(L.d_doms, L.items, rO, rC, rN, rF,
-                                                                        first, L.eos);
+                                                                        first, L.eos, L.watch);
   return cudaGetLastError();
 }
 
@@ -1590,7 +1639,7 @@ cudaError_t launch_diag_reduce(const DomDev &D, const DomDev *d_dom, int prec, i
   double *part = d_out + 8;
   if (prec == CC_FP64) k_diag_partial<double><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(d_dom, r, part);
   else k_diag_partial<float><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(d_dom, r, part);
-  k_diag_final<<<1, 32, 0, st>>>(part, DIAG_BLOCKS, d_out);
+  k_diag_final<<<1, DIAG_TPB, 0, st>>>(part, DIAG_BLOCKS, d_out);
   return cudaGetLastError();
 }
 
@@ -1617,14 +1666,14 @@ cudaError_t launch_norms(const DomDev *a, int prec_a, int ra, const DomDev *b, i
     k_norms<float, double><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(a, ra, b, rb, which, p, q, kmin, d_part);
   else
     k_norms<float, float><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(a, ra, b, rb, which, p, q, kmin, d_part);
-  k_norms_final<<<1, 32, 0, st>>>(d_part, DIAG_BLOCKS, d_out);
+  k_norms_final<<<1, DIAG_TPB, 0, st>>>(d_part, DIAG_BLOCKS, d_out);
   return cudaGetLastError();
 }
 
 cudaError_t launch_heat(const DomDev *d_dom, int prec, int r, double *d_out, double *d_part, cudaStream_t st) {
   if (prec == CC_FP64) k_heat_partial<double><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(d_dom, r, d_part);
   else k_heat_partial<float><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(d_dom, r, d_part);
-  k_heat_final<<<1, 32, 0, st>>>(d_part, DIAG_BLOCKS, d_out);
+  k_heat_final<<<1, DIAG_TPB, 0, st>>>(d_part, DIAG_BLOCKS, d_out);
   return cudaGetLastError();
 }
 
@@ -1672,7 +1721,7 @@ cudaError_t launch_mass_active(const DomDev &D, const DomDev *d_dom, int prec, i
     k_mass_active<double><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(d_dom, rC, rO, both, bx0, bx1, by0, by1, bz1, part);
   else
     k_mass_active<float><<<DIAG_BLOCKS, DIAG_TPB, 0, st>>>(d_dom, rC, rO, both, bx0, bx1, by0, by1, bz1, part);
-  k_diag_final<<<1, 32, 0, st>>>(part, DIAG_BLOCKS, d_out);
+  k_diag_final<<<1, DIAG_TPB, 0, st>>>(part, DIAG_BLOCKS, d_out);
   return cudaGetLastError();
 }
 

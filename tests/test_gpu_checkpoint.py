@@ -102,7 +102,10 @@ def test_checkpoint_mismatch_is_rejected(cc, tmp_path):
     for other in (lambda: ensemble(cc, cc.CC_FP64),            # precision
                   lambda: ensemble(cc, cc.CC_FP32, ENS[:2]),   # domain count
                   lambda: ensemble(cc, cc.CC_FP32, [ENS[1], ENS[0], ENS[2]]),  # sizes
-                  lambda: refined(cc, cc.CC_FP32)):             # refinement
+                  lambda: refined(cc, cc.CC_FP32),              # refinement
+                  # the same sizes, another hill or another flow: the fingerprint
+                  lambda: ensemble(cc, cc.CC_FP32, [ENS[0].replace(h0=ENS[0].h0 * 0.5), ENS[1], ENS[2]]),
+                  lambda: ensemble(cc, cc.CC_FP32, [ENS[0], ENS[1].replace(U=ENS[1].U + 1.0), ENS[2]])):
         m = other()
         with pytest.raises(cc.CutcellError) as e:
             m.load(path)
@@ -111,7 +114,11 @@ def test_checkpoint_mismatch_is_rejected(cc, tmp_path):
     raw = open(path, "rb").read()
     bad = tmp_path / "bad.ckpt"
     m = ensemble(cc, cc.CC_FP32)
-    for blob in (b"not a checkpoint", raw[: len(raw) // 2]):
+    # header: magic (8 bytes), 4 int32, then per domain 10 int32 (sizes, the
+    # four time-level roles at bytes 24 .. 39), int64 steps, uint64 fingerprint
+    roles = bytearray(raw)
+    roles[8 + 16 + 28:8 + 16 + 32] = roles[8 + 16 + 24:8 + 16 + 28]  # role 1 := role 0
+    for blob in (b"not a checkpoint", raw[: len(raw) // 2], bytes(roles)):
         bad.write_bytes(blob)
         with pytest.raises(cc.CutcellError) as e:
             m.load(str(bad))

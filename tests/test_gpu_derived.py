@@ -267,3 +267,25 @@ def test_error_norms_at_a_rational_ratio_match_oracle(cc, oracle_mod):
         assert abs(l1 - r1) <= 1e-9 * r1 and abs(l2 - r2) <= 1e-9 * r2, (wg, l1, r1, l2, r2)
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec_name", ["fp64", "fp32"])
+def test_diagnostics_repeat_bit_for_bit(cc, prec_name):
+    """The conservation sums (Neumaier per thread, fixed-order warp-shuffle
+    TwoSum trees over fixed blocks) do not depend on scheduling: two models
+    stepped alike report the same bits, and so does a second call on one."""
+    prec = cc.CC_FP64 if prec_name == "fp64" else cc.CC_FP32
+    cfgs = [W.SMALL_HEMI, W.C1_BELL]
+    out = []
+    for _ in range(2):
+        m = gpu_model(cc, cfgs, prec)
+        m.init_state()
+        m.step(12)
+        out.append([m.diagnostics(d) for d in range(2)])
+        out.append([m.diagnostics(d) for d in range(2)])
+        m.close()
+    for run in out[1:]:
+        for d in range(2):
+            for key in ("mass", "mass_comp", "heat", "heat_comp", "max_u", "max_w"):
+                assert run[d][key] == out[0][d][key], (d, key)
+    assert out[0][0]["max_u"] > 0.0

@@ -40,11 +40,17 @@ def test_noalloc_mass_matches_diagnostics(env, prec_name, tol):
     vol_dev = torch.tensor(vol.ravel(), dtype=torch.float64, device="cuda")
     out = torch.full((2,), float("nan"), dtype=torch.float64, device="cuda")
     scale = np.abs(rp).max() * cfg.dx * cfg.dy * cfg.dz * cfg.cells
-    for call in range(2):
-        cc.mass_sum_noalloc(rho_dev.data_ptr(), prec, vol_dev.data_ptr(), rp.size, 256, out.data_ptr())
-        torch.cuda.synchronize()
-        got = float(out[0].item())
-        assert abs(got - ref) <= tol * scale, (call, got, ref)
+    # 256 partials is cc_diagnostics' own block count and reduction: the same
+    # bits; one partial and the whole scratch array (its two edges) agree
+    # within the tolerance, each on two calls in a row
+    for nparts in (256, 1, cc.CC_NOALLOC_MAX_PARTS):
+        for call in range(2):
+            cc.mass_sum_noalloc(rho_dev.data_ptr(), prec, vol_dev.data_ptr(), rp.size, nparts, out.data_ptr())
+            torch.cuda.synchronize()
+            got = float(out[0].item())
+            if nparts == 256:
+                assert got == ref, (call, got, ref)
+            assert abs(got - ref) <= tol * scale, (nparts, call, got, ref)
     m.close()
 
 
