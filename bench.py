@@ -285,6 +285,74 @@ def cpu_baseline(cfgs, seconds):
             "sample": "; ".join(inst) + f" ({t_used:.1f} s, single-threaded FP64 oracle)"}
 
 
+def _allcore_worker(cfg, seconds, barrier, q):
+    """One core: build the oracle instance, one untimed forward-Euler step,
+    then (after every worker is ready) step it for about `seconds`."""
+    import oracle
+    m = oracle.Model(cfg)
+    nf = int((m.geometry()["cls"] != 0).sum())
+    m.init_state()
+    m.step(1)
+    barrier.wait()
+    s, t0 = 0, time.perf_counter()
+    while time.perf_counter() - t0 < seconds:
+        m.step(1)
+        s += 1
+    q.put((cfg.name, nf * s, s, time.perf_counter() - t0))
+
+
+def cpu_baseline_allcores(cfgs, seconds):
+    """The FP64 oracle as it stands on every host core at once: one spawned
+    process per core, each stepping its own instance of the workload (the
+    smallest ones, so that the memory stays bounded) from a common start; the
+    rate is the sum of the processes' rates."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    ncores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    pick = sorted(cfgs, key=lambda c: c.cells)
+    pick = [pick[w % len(pick)] for w in range(ncores)]
+    ctx = mp.get_context("spawn")
+    barrier, q = ctx.Barrier(ncores), ctx.Queue()
+    procs = [ctx.Process(target=_allcore_worker, args=(c, seconds, barrier, q)) for c in pick]
+    for p in procs:
+        p.start()
+    res = []
+    try:
+        import queue as _queue
+        for _ in procs:
+            res.append(q.get(timeout=seconds + 600.0))  # set-up and stepping; a dead worker ends the wait
+    except _queue.Empty:
+        pass
+    for p in procs:
+        p.join(timeout=5.0)
+        if p.is_alive():
+            p.terminate()
+            p.join()
+    if len(res) < ncores:
+        return {"value": None, "unit": METRIC, "cores": ncores, "kind": "oracle",
+                "error": f"{ncores - len(res)} of {ncores} oracle processes did not finish"}
+    rate = sum(r[1] / r[3] for r in res)
+    names = sorted({r[0] for r in res})
+    return {"value": rate, "unit": METRIC, "cores": ncores, "kind": "oracle",
+            "sample": f"{ncores} processes, one per host core, each stepping one instance for {seconds:.0f} s "
+                      f"({', '.join(names)}); single-threaded FP64 oracle in each"}
+
+
+def fp64_flops_per_cell():
+    """Executed FP64 flops of the FP64 full-cell stencil per interior cell
+    (2 per fused multiply-add), from the committed ncu count, or None when the
+    kernel changed since the count."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "k_full_fp64_flops.json")) as f:
+            t = json.load(f)
+    except Exception:
+        return None
+    if t.get("source_hash") != kfull_source_hash():
+        return None
+    return t.get("flops_per_interior_cell")
+
+
 def make_refined(cc, rc, prec):
     m = cc.RefinedModel(rc.base, rc.boxes, prec)
     for l, c in enumerate(m.cfgs):
@@ -726,6 +794,28 @@ def main():
                            "rel_linf": linf / scale if scale > 0 else 0.0}
         line["fp64_plain"] = {"value": v64, "unit": METRIC, "dtype": "f64", "ms_per_step": ms64 / ksteps,
                               "steps": ksteps, "how": "each domain stepped alone in FP64, looped over domains"}
+        # its roofline: the FP64 pipe, not HBM, bounds it (160 B per cell at
+        # 1e9 cells/s is a few per cent of HBM); per-launch time of its
+        # full-cell stencil from events on one profiled step of every domain
+        for s in singles:
+            s.profile(True)
+            s.profile_reset()
+        for s in singles:
+            s.step(1)
+        torch.cuda.synchronize()
+        k64_ms = sum(s.profile_read(cc.CC_K_FULL)[0] for s in singles)
+        for s in singles:
+            s.profile(False)
+        peak64 = cc.fma_peak(cc.CC_FP64)
+        fpc = fp64_flops_per_cell()
+        ach64 = None if fpc is None else fpc * ninterior / (k64_ms / 1e3)
+        line["fp64_plain"]["roofline"] = {
+            "bound": "alu", "achieved": None if ach64 is None else ach64 / 1e12, "peak": peak64 / 1e12,
+            "unit": "TFLOP/s", "frac": None if ach64 is None else ach64 / peak64, "kernel": "k_full (FP64)",
+            "kernel_ms_per_step": k64_ms, "flops_per_cell": fpc,
+            "peak_kind": "measured FP64 fused multiply-add rate (cc_fma_peak, this run)",
+            "how": "executed FP64 flops per interior cell (ncu: 2 dfma + dadd + dmul, profiles/"
+                   "k_full_fp64_flops.json) x interior cells / the stencil's event time over one step"}
         line["l2_error"] = {"vs": "plain FP64 GPU form", "after_steps": n32, "fields": errs}
         for s in singles:
             s.close()
@@ -788,6 +878,7 @@ def main():
 
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(cfgs, args.cpu_seconds)
+        line["cpu_baseline"]["all_cores"] = cpu_baseline_allcores(cfgs, args.cpu_seconds)
     model.close()
     if args.workload == "ensemble" and not args.no_refined:
         line["refined"] = bench_refined(cc, torch, args, hbm, peak_kind, barrier, world)

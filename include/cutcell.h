@@ -385,6 +385,17 @@ typedef struct {
 cc_status cc_cbcm_cubes(int nx0, int ny0, int nz0, int cube, double H, int nlev, const double *h_finest,
                         cc_cube *out, int capacity, int *count);
 
+/* Fused multiply-add peak of the current GPU (no counterpart in the paper;
+ * the denominator of the roofline of the plain FP64 form, which is bound by
+ * the FP64 pipe rather than by memory): independent chains x <- x a + b in
+ * registers on 8 blocks of 256 threads per SM, iters steps per chain, one
+ * warm-up launch and one launch timed with CUDA events on `stream`.
+ * *flops_per_s receives 2 x the fused multiply-adds per second.  precision:
+ * CC_FP64 or CC_FP32.  CC_EINVAL for a bad argument, CC_ECUDA for a CUDA
+ * error (also when an earlier call left one pending, which is not cleared).
+ * Synchronises `stream`; changes no clock or other GPU setting. */
+cc_status cc_fma_peak(int precision, int iters, void *stream, double *flops_per_s);
+
 /* Allocation-free mass sum (the paper has no counterpart; it is an entry
  * point for callers that cannot call cudaMalloc -- code running inside
  * another framework's memory pool, or a host application that reserves all

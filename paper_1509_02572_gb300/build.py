@@ -22,6 +22,7 @@ UNITS = {
     "capi.cu": [],
     "noalloc.cu": [],
     "cbcm.cu": [],
+    "peak.cu": [],
 }
 
 

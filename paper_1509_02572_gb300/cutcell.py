@@ -30,7 +30,7 @@ EXPORTS = ("cc_create", "cc_destroy", "cc_last_error", "cc_set_terrain", "cc_bui
            "cc_graphs_enable", "cc_upload_state_async", "cc_download_state_async", "cc_save", "cc_load",
            "cc_set_terrain_analytic", "cc_get_terrain", "cc_download_derived", "cc_error_norms", "cc_cbcm_cubes",
            "cc_mass_sum_noalloc", "cc_noalloc_last_error", "cc_upload_state_f32", "cc_download_state_f32",
-           "cc_upload_state_f32_async", "cc_download_state_f32_async")
+           "cc_upload_state_f32_async", "cc_download_state_f32_async", "cc_fma_peak")
 CC_NOALLOC_MAX_PARTS = 1024
 CC_HILL_BELL, CC_HILL_ELLIPSOID, CC_HILL_COSINE = range(3)
 HILL_KINDS = {"bell": CC_HILL_BELL, "ellipsoid": CC_HILL_ELLIPSOID, "hemisphere": CC_HILL_ELLIPSOID,
@@ -127,6 +127,7 @@ def load(path: str = LIB_PATH):
     L.cc_set_schedule.argtypes = [vp, i, i, i]
     L.cc_mass_sum_noalloc.argtypes = [vp, i, vp, ct.c_longlong, i, vp, vp]
     L.cc_noalloc_last_error.restype = ct.c_char_p
+    L.cc_fma_peak.argtypes = [i, i, vp, ct.POINTER(ct.c_double)]
     L.cc_noalloc_last_error.argtypes = []
     _lib = L
     return L
@@ -167,6 +168,19 @@ def mass_sum_noalloc(rho_ptr: int, precision: int, volume_ptr: int, n: int, npar
     if st != CC_OK:
         raise CutcellError(st, L.cc_noalloc_last_error().decode())
     return st
+
+
+def fma_peak(precision: int, iters: int = 1 << 16, stream=None) -> float:
+    """cc_fma_peak: the measured fused multiply-add rate of the current GPU
+    in flop/s (2 per fused multiply-add)."""
+    L = load()
+    if stream is None:
+        stream = _current_stream()
+    out = ct.c_double(0.0)
+    st = L.cc_fma_peak(int(precision), int(iters), stream, ct.byref(out))
+    if st != CC_OK:
+        raise CutcellError(st, "cc_fma_peak failed")
+    return out.value
 
 
 class Model:
