@@ -1,0 +1,604 @@
+// The full-cell stencil in FP32 with two x-adjacent cells per thread
+// (included by step.cu, after k_full, whose helpers it uses).
+//
+// The same step as k_full (Sec 2.4: aperture-weighted face fluxes and their
+// divergence, the p' and rho' tendencies, the momentum equations
+// momentum_u_d .. momentum_w_d, the artificial diffusion of Sec 2.1 with the
+// wall-aware form of Sec 2.4, sponge, leapfrog and Robert-Asselin filter),
+// each thread taking the cells (i, j, k) and (i + 1, j, k), i even, and their
+// corners.  Two adjacent cells are two adjacent values of a shared-memory row,
+// so one 8-byte load feeds both and the arithmetic runs on float2 pairs
+// (packed FP32: every lane is rounded as the scalar operation would be).  The
+// face fluxes, corner densities, corner velocities and equation of state are
+// the scalar kernels' operations in their order, so a face this kernel shares
+// with a cut cell or a refined box has the same bits on both sides.  The
+// x-face between this thread's pair and the next thread's is computed once,
+// by the next thread, and passed with a warp shuffle.
+
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+// a - b as fma(b, -1, a): one rounding, the same value as the rounded difference
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.0f, -1.0f), a); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 ld2(const float *p) { return *reinterpret_cast<const float2 *>(p); }
+__device__ __forceinline__ void st2(float *p, float2 v) { *reinterpret_cast<float2 *>(p) = v; }
+// the pair (p[-1], p[0]) from the aligned pairs at p - 2 and p
+__device__ __forceinline__ float2 odd2(float2 lo, float2 hi) { return make_float2(lo.y, hi.x); }
+
+__device__ __forceinline__ float2 face_flux2(float2 pa, float2 pb, float2 un, float2 S) {
+  return mul2(mul2(mul2(add2(pa, pb), bc2(0.5f)), un), S);
+}
+__device__ __forceinline__ float2 mean4(float2 u1, float2 u2, float2 u3, float2 u4) {
+  return mul2(add2(add2(u1, u2), add2(u3, u4)), bc2(0.25f));
+}
+__device__ __forceinline__ float2 rho8_2(float2 a, float2 b, float2 c, float2 d, float2 e, float2 f, float2 g,
+                                         float2 h) {
+  return mul2(add2(add2(add2(a, b), add2(c, d)), add2(add2(e, f), add2(g, h))), bc2(0.125f));
+}
+__device__ __forceinline__ float2 rinv2(float2 r) { return make_float2(rinv(r.x), rinv(r.y)); }
+
+// (1 + x)^a - 1 for a pair: the binomial series of pow1pm1_e on both lanes
+// when both are small, else lane by lane
+__device__ __forceinline__ float2 pow1pm1_2(float2 x, const float (&c)[8]) {
+  if (fabsf(x.x) < 0.0625f && fabsf(x.y) < 0.0625f) {
+    float2 s = bc2(c[6]);
+    s = fma2(s, x, bc2(c[5]));
+    s = fma2(s, x, bc2(c[4]));
+    s = fma2(s, x, bc2(c[3]));
+    s = fma2(s, x, bc2(c[2]));
+    s = fma2(s, x, bc2(c[1]));
+    s = fma2(s, x, bc2(c[0]));
+    return mul2(s, x);
+  }
+  return make_float2(pow1pm1_e(x.x, c), pow1pm1_e(x.y, c));
+}
+struct EosK2 {
+  float thb, ipb, pik;
+  __device__ __forceinline__ void load(const float *thb_, const float *ipb_, const float *pik_, int kp) {
+    thb = thb_[kp];
+    ipb = ipb_[kp];
+    pik = pik_[kp];
+  }
+  __device__ __forceinline__ float2 pert(const Eos &E, float2 pp) const {
+    return mul2(bc2(thb), pow1pm1_2(mul2(pp, bc2(ipb)), E.sth));
+  }
+  __device__ __forceinline__ float2 tot(const Eos &E, float2 pp) const { return add2(bc2(thb), pert(E, pp)); }
+  __device__ __forceinline__ float2 exner(const Eos &E, float2 pp) const {
+    return fma2(bc2(pik), pow1pm1_2(mul2(pp, bc2(ipb)), E.sex), bc2(pik));
+  }
+};
+
+// the diffusion sum of one axis for a pair, lane by lane (diff_axis)
+__device__ __forceinline__ float2 dax2(float2 a, float2 b, float2 c, float2 d, float2 e, bool scalar, const bool (&f0)[4],
+                                       const bool (&f1)[4]) {
+  return make_float2(diff_axis(a.x, b.x, c.x, d.x, e.x, f0[0], f0[1], f0[2], f0[3], scalar),
+                     diff_axis(a.y, b.y, c.y, d.y, e.y, f1[0], f1[1], f1[2], f1[3], scalar));
+}
+__device__ __forceinline__ float2 d4_2(float2 a, float2 b, float2 c, float2 d, float2 e) {
+  return make_float2(d4(a.x, b.x, c.x, d.x, e.x), d4(a.y, b.y, c.y, d.y, e.y));
+}
+
+template <int TYv>
+struct PairCfg {
+  static constexpr int TX = TILE_X, TY = TYv, NT = (TILE_X / 2) * TYv, HX = TX + 4, HY = TYv + 4, PL = HX * HY,
+                       NPP = PL / 2, NLPP = (NPP + NT - 1) / NT;
+};
+
+template <int TYv>
+__global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
+    k_pair(const DomDev *__restrict__ doms, const WorkItem *__restrict__ items, int rO, int rC, int rN, int rF,
+           int first, const Eos E, unsigned *__restrict__ watch) {
+  using C = PairCfg<TYv>;
+  constexpr int NT = C::NT, HX = C::HX, PL = C::PL, NPP = C::NPP, NLPP = C::NLPP;
+  static_assert(HX % 2 == 0, "pairs of points per halo row");
+  extern __shared__ __align__(16) unsigned char smraw[];
+  FullSmem<float, PL> &S = *reinterpret_cast<FullSmem<float, PL> *>(smraw);
+  const WorkItem W = items[blockIdx.x];
+  const DomDev &D = doms[W.dom];
+  const float dt2 = (float)(first ? D.dt : 2.0 * D.dt);
+  const float nu = (float)(first ? 0.0 : D.ra_nu);
+  const int tid = threadIdx.x;
+  const int nx = D.nx, ny = D.ny, nz = D.nz, px = D.px;
+  const long long plane = D.plane;
+  const float *__restrict__ rpC = (const float *)D.f[rC][0];
+  const float *__restrict__ ppC = (const float *)D.f[rC][1];
+  const float *__restrict__ mC0 = (const float *)D.f[rC][2];
+  const float *__restrict__ mC1 = (const float *)D.f[rC][3];
+  const float *__restrict__ mC2 = (const float *)D.f[rC][4];
+  const float *__restrict__ rpO = (const float *)D.f[rO][0];
+  const float *__restrict__ ppO = (const float *)D.f[rO][1];
+  const float *__restrict__ mO0 = (const float *)D.f[rO][2];
+  const float *__restrict__ mO1 = (const float *)D.f[rO][3];
+  const float *__restrict__ mO2 = (const float *)D.f[rO][4];
+  float *__restrict__ rpN = (float *)D.f[rN][0];
+  float *__restrict__ ppN = (float *)D.f[rN][1];
+  float *__restrict__ rpF = (float *)D.f[rF][0];
+  float *__restrict__ ppF = (float *)D.f[rF][1];
+  float *__restrict__ mN[3] = {(float *)D.f[rN][2], (float *)D.f[rN][3], (float *)D.f[rN][4]};
+  float *__restrict__ mF[3] = {(float *)D.f[rF][2], (float *)D.f[rF][3], (float *)D.f[rF][4]};
+  const float *__restrict__ rhob = (const float *)D.rhob;
+  const float *__restrict__ ipb = (const float *)D.ipb;
+  const float *__restrict__ thb = (const float *)D.thb;
+  const float *__restrict__ pik = (const float *)D.pik;
+  const float *__restrict__ rhobc = (const float *)D.rhobc;
+  const float *__restrict__ tau = (const float *)D.tau;
+  const int i0 = W.i0, j0 = W.j0, k0 = W.k0, k1 = W.k1;
+
+  auto col_x = [&](int gi) { return D.periodic ? wrapi(gi, nx) : min(max(gi, -GX), px - GX - 1); };
+  auto row_y = [&](int gj) { return D.periodic ? wrapi(gj, ny) : min(max(gj, -GH), D.py - GH - 1); };
+  // pairs of halo points this thread derives: points 2 pp and 2 pp + 1
+  int loff[NLPP][2], kbv[NLPP][2];
+#pragma unroll
+  for (int s = 0; s < NLPP; s++) {
+    const int pp = tid + s * NT;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const int p = 2 * pp + h;
+      const int hx = p % HX, hy = p / HX;
+      loff[s][h] = (row_y(j0 - 2 + hy) + GH) * px + (col_x(i0 - 2 + hx) + GX);
+      kbv[s][h] = pp < NPP ? D.kb[loff[s][h]] : KB_NONE;
+    }
+  }
+  // 16-byte chunks of the haloed rows, as in k_full
+  constexpr int VEC = 4, CPR = HX / VEC, NCH = CPR * C::HY, NCQ = (NCH + NT - 1) / NT;
+  static_assert(HX % VEC == 0, "halo rows are whole chunks");
+  int ch_dst[NCQ], ch_e[NCQ][VEC];
+  bool ch_whole[NCQ];
+#pragma unroll
+  for (int q = 0; q < NCQ; q++) {
+    const int t = tid + q * NT;
+    const int row = t / CPR, col = t % CPR;
+    const int x = i0 - 2 + VEC * col;
+    const int rowoff = (row_y(j0 - 2 + row) + GH) * px;
+    ch_dst[q] = t < NCH ? row * HX + VEC * col : -1;
+    ch_whole[q] = D.periodic ? (x >= 0 && x + VEC <= nx) : (x >= -GX && x + VEC <= px - GX);
+#pragma unroll
+    for (int e = 0; e < VEC; e++) ch_e[q][e] = rowoff + col_x(x + e) + GX;
+  }
+  const float *__restrict__ ubC = (const float *)D.ub[rC];
+  const int kmaxp = D.pz - GH - 1;
+  auto chunk = [&](float *dst, const float *src) {
+#pragma unroll
+    for (int q = 0; q < NCQ; q++) {
+      if (ch_dst[q] < 0) continue;
+      if (ch_whole[q]) {
+        acopy16(dst + ch_dst[q], src + ch_e[q][0]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VEC; e++) acopy(dst + ch_dst[q] + e, src + ch_e[q][e]);
+      }
+    }
+  };
+  auto issue = [&](int kk, bool with_m, bool with_o) {
+    const long long zo = (long long)(min(kk, kmaxp) + GH) * plane;
+    const int a5 = s5(kk), a4 = s4(kk);
+    chunk(S.cr[a5], rpC + zo);
+    chunk(S.cp[a5], ppC + zo);
+    if (with_m) {
+      chunk(S.cm[a4][0], mC0 + zo);
+      chunk(S.cm[a4][1], mC1 + zo);
+      chunk(S.cm[a4][2], mC2 + zo);
+    }
+    if (with_o) {
+      chunk(S.op[a4], ppO + zo);
+      chunk(S.om[a4][0], mO0 + zo);
+      chunk(S.om[a4][1], mO1 + zo);
+      chunk(S.om[a4][2], mO2 + zo);
+    }
+  };
+  // totals of plane kk (pairs of halo points)
+  auto derive_e = [&](int kk, const float rb, const EosK2 ek) {
+    const float *cr = S.cr[s5(kk)], *cp = S.cp[s5(kk)];
+    float *rh = S.rh[s4(kk)], *th = S.th[s4(kk)];
+#pragma unroll
+    for (int s = 0; s < NLPP; s++) {
+      const int pp = tid + s * NT;
+      if (pp < NPP) {
+        const int p = 2 * pp;
+        st2(rh + p, add2(bc2(rb), ld2(cr + p)));
+        st2(th + p, ek.tot(E, ld2(cp + p)));
+      }
+    }
+  };
+  auto derive = [&](int kk) {
+    EosK2 ek;
+    ek.load(thb, ipb, pik, kk + GH);
+    derive_e(kk, rhob[kk + GH], ek);
+  };
+  // corner velocities of plane K, two corners at a time; a corner at or below
+  // the terrain takes the boundary-point velocity of its column
+  auto velocity = [&](int K) {
+    const float *lo = S.rh[s4(K - 1)], *hi = S.rh[s4(K)];
+    const int su = s3(K), sm = s4(K);
+#pragma unroll
+    for (int s = 0; s < NLPP; s++) {
+      const int pp = tid + s * NT;
+      const int p = 2 * pp;
+      const int hx = p % HX, hy = p / HX;
+      if (pp < NPP && hy != 0) {
+        // corner p needs cells p-HX-1, p-HX, p-1, p; corner p+1 cells p-HX .. p+1.  On the
+        // halo's first column (hx = 0) the corner p is never used: read the pair at p instead
+        const int am = hx == 0 ? 0 : 2;
+        const float2 A0 = ld2(lo + p - HX - am), B0 = ld2(lo + p - HX), C0 = ld2(lo + p - am), D0 = ld2(lo + p);
+        const float2 A1 = ld2(hi + p - HX - am), B1 = ld2(hi + p - HX), C1 = ld2(hi + p - am), D1 = ld2(hi + p);
+        const float2 iv = rinv2(rho8_2(odd2(A0, B0), B0, odd2(C0, D0), D0, odd2(A1, B1), B1, odd2(C1, D1), D1));
+        float2 u0 = mul2(ld2(S.cm[sm][0] + p), iv), u1 = mul2(ld2(S.cm[sm][1] + p), iv),
+               u2 = mul2(ld2(S.cm[sm][2] + p), iv);
+        if (K <= kbv[s][0] || K <= kbv[s][1]) {
+          if (K <= kbv[s][0]) {
+            const float *u = ubC + 3 * loff[s][0];
+            u0.x = u[0];
+            u1.x = u[1];
+            u2.x = u[2];
+          }
+          if (K <= kbv[s][1]) {
+            const float *u = ubC + 3 * loff[s][1];
+            u0.y = u[0];
+            u1.y = u[1];
+            u2.y = u[2];
+          }
+        }
+        st2(S.uu[su][0] + p, u0);
+        st2(S.uu[su][1] + p, u1);
+        st2(S.uu[su][2] + p, u2);
+      }
+    }
+  };
+  auto derive_old_e = [&](int kk, const EosK2 ek) {
+    const float *op = S.op[s4(kk)];
+#pragma unroll
+    for (int s = 0; s < NLPP; s++) {
+      const int pp = tid + s * NT;
+      if (pp < NPP) st2(S.to + 2 * pp, ek.pert(E, ld2(op + 2 * pp)));
+    }
+  };
+
+  const int tx = tid & 15, ty = tid >> 4;
+  const int i = i0 + 2 * tx, j = j0 + ty;
+  const bool rowok = j < D.cj1;
+  const bool a0 = rowok && i >= D.ci0 && i < D.ci1, a1 = rowok && i + 1 >= D.ci0 && i + 1 < D.ci1;
+  const bool active = a0 || a1;
+  // corners of a refined box outside -1 .. n+1 are ghost values from the coarser level
+  const bool q0 = a0 && i >= D.qi0 && j >= D.qj0, q1 = a1 && i + 1 >= D.qi0 && j >= D.qj0;
+  const int c = (ty + 2) * HX + (2 * tx + 2);
+  const long long own = active ? (long long)(j + GH) * px + (i + GX) : 0;
+  const float qdx = (float)(0.25 / D.dx), qdy = (float)(0.25 / D.dy), qdz = (float)(0.25 / D.dz);
+  const float2 Sx = bc2((float)(D.dy * D.dz)), Sy = bc2((float)(D.dx * D.dz)), Sz = bc2((float)(D.dx * D.dy));
+  const float hSx = (float)(0.25 * D.dy * D.dz), hSy = (float)(0.25 * D.dx * D.dz), hSz = (float)(0.25 * D.dx * D.dy);
+  const float v0inv = (float)(1.0 / (D.dx * D.dy * D.dz));
+  const float kdif = (float)D.kdif, Cp = (float)D.Cp, g = (float)D.g, U = (float)D.U;
+  const int kug0 = a0 ? D.kug[own] : 0, kug1 = a1 ? D.kug[own + 1] : 0;
+  const int dlo = active ? max(a0 ? (int)D.dcol[own].lo : -1000, a1 ? (int)D.dcol[own + 1].lo : -1000) : 0;
+  const int dhi = active ? min(a0 ? (int)D.dcol[own].hi : 1000000, a1 ? (int)D.dcol[own + 1].hi : 1000000) : 0;
+  const bool last_tx = tx == 15;
+
+  // own columns at n-1 for the vertical diffusion stencils, levels k-2 .. k+2
+  float2 treg[5], mreg[5][3];
+  auto own_old_e = [&](int a, int kk, const EosK2 ek) {
+    const int a4 = s4(kk);
+    treg[a] = ek.pert(E, ld2(S.op[a4] + c));
+    mreg[a][0] = ld2(S.om[a4][0] + c);
+    mreg[a][1] = ld2(S.om[a4][1] + c);
+    mreg[a][2] = ld2(S.om[a4][2] + c);
+  };
+
+  for (int kk = k0 - 2; kk <= k0 + 2; kk++) issue(kk, kk != k0 - 2, kk != k0 - 2);
+  acommit();
+  {
+    const long long o2 = (long long)(k0 - 2 + GH) * plane + own;
+    EosK2 ek;
+    ek.load(thb, ipb, pik, k0 - 2 + GH);
+    treg[0] = ek.pert(E, ld2(ppO + o2));
+    mreg[0][0] = ld2(mO0 + o2);
+    mreg[0][1] = ld2(mO1 + o2);
+    mreg[0][2] = ld2(mO2 + o2);
+  }
+  await_groups<0>();
+  __syncthreads();
+  for (int kk = k0 - 2; kk <= k0 + 1; kk++) derive(kk);
+#pragma unroll
+  for (int a = 1; a < 4; a++) {
+    EosK2 ek;
+    ek.load(thb, ipb, pik, k0 - 2 + a + GH);
+    own_old_e(a, k0 - 2 + a, ek);
+  }
+  __syncthreads();
+  velocity(k0 - 1);
+  velocity(k0);
+
+  float2 fz_carry = bc2(0.0f), hz_carry = bc2(0.0f);
+  unsigned wflag = 0;
+  const float cfx = (float)(D.dt / D.dx), cfy = (float)(D.dt / D.dy), cfz = (float)(D.dt / D.dz);
+  for (int k = k0; k < k1; k++) {
+    const long long o = (long long)(k + GH) * plane + own;
+    float2 rO_ = bc2(0.0f);
+    if (active) rO_ = ld2(rpO + o);
+    EosK2 ek0, ek2;
+    ek0.load(thb, ipb, pik, k + GH);
+    ek2.load(thb, ipb, pik, k + 2 + GH);
+    const float rb2 = rhob[k + 2 + GH], tk = tau[k + GH];
+    const float rbc[5] = {rhobc[k + GH - 2] * U, rhobc[k + GH - 1] * U, rhobc[k + GH] * U, rhobc[k + GH + 1] * U,
+                          rhobc[k + GH + 2] * U};
+    await_groups<0>();
+    __syncthreads();
+    issue(k + 3, true, true);
+    acommit();
+    derive_e(k + 2, rb2, ek2);
+    velocity(k + 1);
+    derive_old_e(k, ek0);
+    own_old_e(4, k + 2, ek2);
+    __syncthreads();
+    // the x-faces: this thread's low faces (i - 1/2, i + 1/2) as a pair; its
+    // highest face (i + 3/2) is the next thread's lowest, taken by shuffle
+    const int sk = s4(k), skm = s4(k - 1), skp = s4(k + 1);
+    const int ck = s5(k), ckm = s5(k - 1);
+    const float *R0 = S.rh[sk], *Rm = S.rh[skm], *Rp = S.rh[skp];
+    const float *H0 = S.th[sk], *Hm = S.th[skm], *Hp = S.th[skp];
+    const int uk = s3(k), ukp = s3(k + 1), ukm = s3(k - 1);
+    const float *ux0 = S.uu[uk][0], *uy0 = S.uu[uk][1], *uz0 = S.uu[uk][2];
+    const float *uxp = S.uu[ukp][0], *uyp = S.uu[ukp][1], *uzp = S.uu[ukp][2];
+    const float2 Rc = ld2(R0 + c), Hc = ld2(H0 + c);
+    const float2 Rl = ld2(R0 + c - 2), Hl = ld2(H0 + c - 2);
+    const float2 unx = mean4(ld2(ux0 + c), ld2(ux0 + c + HX), ld2(uxp + c), ld2(uxp + c + HX));
+    const float2 fxl = face_flux2(odd2(Rl, Rc), Rc, unx, Sx), hxl = face_flux2(odd2(Hl, Hc), Hc, unx, Sx);
+    float fxh = __shfl_down_sync(0xffffffffu, fxl.x, 1), hxh = __shfl_down_sync(0xffffffffu, hxl.x, 1);
+    if (last_tx) {
+      // the tile's last face, from the halo
+      const float r2 = R0[c + 2], h2 = H0[c + 2];
+      const float un = Ar<float>::mul(Ar<float>::add(Ar<float>::add(ux0[c + 2], ux0[c + 2 + HX]),
+                                                     Ar<float>::add(uxp[c + 2], uxp[c + 2 + HX])),
+                                      0.25f);
+      fxh = Ar<float>::mul(Ar<float>::mul(Ar<float>::mul(Ar<float>::add(Rc.y, r2), 0.5f), un), Sx.x);
+      hxh = Ar<float>::mul(Ar<float>::mul(Ar<float>::mul(Ar<float>::add(Hc.y, h2), 0.5f), un), Sx.x);
+    }
+    if (active) {
+      const float2 fxm = fxl, fxp = make_float2(fxl.y, fxh);
+      const float2 hxm = hxl, hxp = make_float2(hxl.y, hxh);
+      // y-faces: the corners (c, c+1) of cell c and (c+1, c+2) of cell c+1
+      const float2 uy00 = ld2(uy0 + c), uy02 = ld2(uy0 + c + 2), uyp0 = ld2(uyp + c), uyp2 = ld2(uyp + c + 2);
+      const float2 uy0H = ld2(uy0 + c + HX), uy0H2 = ld2(uy0 + c + HX + 2), uypH = ld2(uyp + c + HX),
+                   uypH2 = ld2(uyp + c + HX + 2);
+      const float2 unym = mean4(uy00, odd2(uy00, uy02), uyp0, odd2(uyp0, uyp2));
+      const float2 unyp = mean4(uy0H, odd2(uy0H, uy0H2), uypH, odd2(uypH, uypH2));
+      const float2 RS = ld2(R0 + c - HX), RN = ld2(R0 + c + HX), HS = ld2(H0 + c - HX), HN = ld2(H0 + c + HX);
+      const float2 fym = face_flux2(RS, Rc, unym, Sy), fyp = face_flux2(Rc, RN, unyp, Sy);
+      const float2 hym = face_flux2(HS, Hc, unym, Sy), hyp = face_flux2(Hc, HN, unyp, Sy);
+      // z-faces: corners (c, c+1, c+HX, c+HX+1) of the upper face; the lower
+      // face is the one of the plane below
+      const float2 uzp0 = ld2(uzp + c), uzp2 = ld2(uzp + c + 2), uzpH = ld2(uzp + c + HX),
+                   uzpH2 = ld2(uzp + c + HX + 2);
+      const float2 unzp = mean4(uzp0, odd2(uzp0, uzp2), uzpH, odd2(uzpH, uzpH2));
+      float2 fzp = face_flux2(Rc, ld2(Rp + c), unzp, Sz), hzp = face_flux2(Hc, ld2(Hp + c), unzp, Sz);
+      float2 fzm = fz_carry, hzm = hz_carry;
+      if (k == k0) {
+        const float2 uz00 = ld2(uz0 + c), uz02 = ld2(uz0 + c + 2), uz0H = ld2(uz0 + c + HX),
+                     uz0H2 = ld2(uz0 + c + HX + 2);
+        const float2 unzm = mean4(uz00, odd2(uz00, uz02), uz0H, odd2(uz0H, uz0H2));
+        fzm = face_flux2(ld2(Rm + c), Rc, unzm, Sz);
+        hzm = face_flux2(ld2(Hm + c), Hc, unzm, Sz);
+      }
+      fz_carry = fzp;
+      hz_carry = hzp;
+      if (k == 0) {
+        fzm = bc2(0.0f);
+        hzm = bc2(0.0f);
+      }
+      if (D.lid && k == nz - 1) {
+        fzp = bc2(0.0f);
+        hzp = bc2(0.0f);
+      }
+      const float2 RM = add2(add2(sub2(fxp, fxm), sub2(fyp, fym)), sub2(fzp, fzm));
+      const float2 RH = add2(add2(sub2(hxp, hxm), sub2(hyp, hym)), sub2(hzp, hzm));
+
+      // ---- artificial diffusion at n-1
+      const float *Tk = S.to;
+      const int ok4 = s4(k);
+      const bool wall = k < dlo || k >= dhi;
+      const float2 Tm2 = ld2(Tk + c - 2), Tc = ld2(Tk + c), Tp2 = ld2(Tk + c + 2);
+      const float2 Tl = odd2(Tm2, Tc), Tr = odd2(Tc, Tp2);
+      const float2 TS2 = ld2(Tk + c - 2 * HX), TS = ld2(Tk + c - HX), TN = ld2(Tk + c + HX), TN2 = ld2(Tk + c + 2 * HX);
+      float2 dd, dmv[3];
+      if (!wall) {
+        // x stencil of the pair: (c-2, c-1, c, c+1, c+2) and (c-1, c, c+1, c+2, c+3)
+        dd = add2(add2(d4_2(Tm2, Tl, Tc, Tr, Tp2), d4_2(TS2, TS, Tc, TN, TN2)),
+                  d4_2(treg[0], treg[1], treg[2], treg[3], treg[4]));
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          const float *Mk = S.om[ok4][d];
+          const float2 ref0 = bc2(d == 0 ? rbc[2] : 0.0f);
+          const float2 m2 = sub2(ld2(Mk + c - 2), ref0), m0 = sub2(ld2(Mk + c), ref0), p2 = sub2(ld2(Mk + c + 2), ref0);
+          const float2 l1 = odd2(m2, m0), r1 = odd2(m0, p2);
+          float2 dm = add2(d4_2(m2, l1, m0, r1, p2),
+                           d4_2(sub2(ld2(Mk + c - 2 * HX), ref0), sub2(ld2(Mk + c - HX), ref0), m0,
+                                sub2(ld2(Mk + c + HX), ref0), sub2(ld2(Mk + c + 2 * HX), ref0)));
+          if (d == 0)
+            dm = add2(dm, d4_2(sub2(mreg[0][0], bc2(rbc[0])), sub2(mreg[1][0], bc2(rbc[1])), sub2(mreg[2][0], ref0),
+                               sub2(mreg[3][0], bc2(rbc[3])), sub2(mreg[4][0], bc2(rbc[4]))));
+          else
+            dm = add2(dm, d4_2(mreg[0][d], mreg[1][d], mreg[2][d], mreg[3][d], mreg[4][d]));
+          dmv[d] = dm;
+        }
+      } else {
+        bool fx0[4], fx1[4], fy0[4], fy1[4], fz0[4], fz1[4];
+        bool gx0[4], gx1[4], gy0[4], gy1[4], gz0[4], gz1[4];
+        const DiffCol &Q0 = D.dcol[own], &Q1 = D.dcol[own + 1];
+        const int offz[4] = {-2, -1, 1, 2};
+#pragma unroll
+        for (int a = 0; a < 4; a++) {
+          fx0[a] = fluid_at(k, Q0.cx[a], Q0.ctop);
+          fx1[a] = fluid_at(k, Q1.cx[a], Q1.ctop);
+          fy0[a] = fluid_at(k, Q0.cy[a], Q0.ctop);
+          fy1[a] = fluid_at(k, Q1.cy[a], Q1.ctop);
+          fz0[a] = fluid_at(k + offz[a], Q0.c0, Q0.ctop);
+          fz1[a] = fluid_at(k + offz[a], Q1.c0, Q1.ctop);
+          gx0[a] = fluid_at(k, Q0.vx[a], Q0.vtop);
+          gx1[a] = fluid_at(k, Q1.vx[a], Q1.vtop);
+          gy0[a] = fluid_at(k, Q0.vy[a], Q0.vtop);
+          gy1[a] = fluid_at(k, Q1.vy[a], Q1.vtop);
+          gz0[a] = fluid_at(k + offz[a], Q0.v0, Q0.vtop);
+          gz1[a] = fluid_at(k + offz[a], Q1.v0, Q1.vtop);
+        }
+        dd = add2(add2(dax2(Tm2, Tl, Tc, Tr, Tp2, true, fx0, fx1), dax2(TS2, TS, Tc, TN, TN2, true, fy0, fy1)),
+                  dax2(treg[0], treg[1], treg[2], treg[3], treg[4], true, fz0, fz1));
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          const float *Mk = S.om[ok4][d];
+          const float2 ref0 = bc2(d == 0 ? rbc[2] : 0.0f);
+          const float2 m2 = sub2(ld2(Mk + c - 2), ref0), m0 = sub2(ld2(Mk + c), ref0), p2 = sub2(ld2(Mk + c + 2), ref0);
+          const float2 l1 = odd2(m2, m0), r1 = odd2(m0, p2);
+          float2 dm = add2(dax2(m2, l1, m0, r1, p2, false, gx0, gx1),
+                           dax2(sub2(ld2(Mk + c - 2 * HX), ref0), sub2(ld2(Mk + c - HX), ref0), m0,
+                                sub2(ld2(Mk + c + HX), ref0), sub2(ld2(Mk + c + 2 * HX), ref0), false, gy0, gy1));
+          if (d == 0)
+            dm = add2(dm, dax2(sub2(mreg[0][0], bc2(rbc[0])), sub2(mreg[1][0], bc2(rbc[1])), sub2(mreg[2][0], ref0),
+                               sub2(mreg[3][0], bc2(rbc[3])), sub2(mreg[4][0], bc2(rbc[4])), false, gz0, gz1));
+          else
+            dm = add2(dm, dax2(mreg[0][d], mreg[1][d], mreg[2][d], mreg[3][d], mreg[4][d], false, gz0, gz1));
+          dmv[d] = dm;
+        }
+      }
+
+      // ---- scalar update: rho', p' (Sec 2.4), leapfrog and filter
+      const float2 Dth = mul2(bc2(-kdif), dd);
+      const float2 rC_ = ld2(S.cr[ck] + c), pC_ = ld2(S.cp[ck] + c), pO_ = ld2(S.op[ok4] + c);
+      const float2 dtv = bc2(dt2);
+      float2 rN_ = sub2(rO_, mul2(dtv, mul2(RM, bc2(v0inv))));
+      float2 pN_ = sub2(pO_, mul2(mul2(mul2(dtv, bc2(Cp)), ek0.exner(E, pC_)), sub2(mul2(RH, bc2(v0inv)), Dth)));
+      if (k < kug0) {
+        rN_.x = 0.0f;
+        pN_.x = 0.0f;
+      }
+      if (k < kug1) {
+        rN_.y = 0.0f;
+        pN_.y = 0.0f;
+      }
+      float2 rF_ = fma2(bc2(nu), add2(sub2(rN_, mul2(bc2(2.0f), rC_)), rO_), rC_);
+      float2 pF_ = fma2(bc2(nu), add2(sub2(pN_, mul2(bc2(2.0f), pC_)), pO_), pC_);
+      if (k < kug0) {
+        rF_.x = 0.0f;
+        pF_.x = 0.0f;
+      }
+      if (k < kug1) {
+        rF_.y = 0.0f;
+        pF_.y = 0.0f;
+      }
+
+      // ---- velocity cells centred on the corners (c, c+1): Eqs. momentum_u_d .. w_d
+      // vertical pair sums of the four cell columns around each corner: the
+      // south-west columns (c-HX-1, c-HX) and west (c-1, c) as odd pairs
+      const float2 Rmc = ld2(Rm + c), RmS = ld2(Rm + c - HX), RmS2 = ld2(Rm + c - HX - 2), Rm2 = ld2(Rm + c - 2);
+      const float2 RS2 = ld2(R0 + c - HX - 2);
+      const float2 cS = RS, cSW = odd2(RS2, RS), cW = odd2(Rl, Rc);
+      const float2 mS = RmS, mSW = odd2(RmS2, RmS), mW = odd2(Rm2, Rmc);
+      const float2 v00 = add2(mSW, cSW), v10 = add2(mS, cS), v01 = add2(mW, cW), v11 = add2(Rmc, Rc);
+      const float2 q = bc2(0.25f);
+      const float2 rE = mul2(add2(v10, v11), q), rW = mul2(add2(v00, v01), q);
+      const float2 rNn = mul2(add2(v01, v11), q), rS = mul2(add2(v00, v10), q);
+      const float2 rT = mul2(add2(add2(cSW, cS), add2(cW, Rc)), q);
+      const float2 rB = mul2(add2(add2(mSW, mS), add2(mW, Rmc)), q);
+      // corner velocities: this pair (c, c+1), its x-neighbours (c-1, c) and
+      // (c+1, c+2), y-neighbours and the planes above and below
+      const float *uxm = S.uu[ukm][0], *uym = S.uu[ukm][1], *uzm = S.uu[ukm][2];
+      float2 u0[3], uE[3], uW[3], uN[3], uS[3], uT[3], uB[3];
+      {
+        const float *uk3[3] = {ux0, uy0, uz0}, *up3[3] = {uxp, uyp, uzp}, *um3[3] = {uxm, uym, uzm};
+#pragma unroll
+        for (int d = 0; d < 3; d++) {
+          const float2 a = ld2(uk3[d] + c - 2), b = ld2(uk3[d] + c), e = ld2(uk3[d] + c + 2);
+          u0[d] = b;
+          uW[d] = odd2(a, b);
+          uE[d] = odd2(b, e);
+          uN[d] = ld2(uk3[d] + c + HX);
+          uS[d] = ld2(uk3[d] + c - HX);
+          uT[d] = ld2(up3[d] + c);
+          uB[d] = ld2(um3[d] + c);
+        }
+      }
+      const float2 gE = mul2(mul2(rE, add2(u0[0], uE[0])), bc2(hSx)), gW = mul2(mul2(rW, add2(uW[0], u0[0])), bc2(hSx));
+      const float2 gN = mul2(mul2(rNn, add2(u0[1], uN[1])), bc2(hSy)), gS = mul2(mul2(rS, add2(uS[1], u0[1])), bc2(hSy));
+      const float2 gT = mul2(mul2(rT, add2(u0[2], uT[2])), bc2(hSz)), gB = mul2(mul2(rB, add2(uB[2], u0[2])), bc2(hSz));
+      const float2 gsum = add2(add2(sub2(gE, gW), sub2(gN, gS)), sub2(gT, gB));
+      // pressure sums and the buoyancy mean (rho' of the eight cells)
+      const float *P0 = S.cp[ck], *Pm = S.cp[ckm];
+      const float2 P0c = ld2(P0 + c), P0S = ld2(P0 + c - HX), P0S2 = ld2(P0 + c - HX - 2), P02 = ld2(P0 + c - 2);
+      const float2 Pmc = ld2(Pm + c), PmS = ld2(Pm + c - HX), PmS2 = ld2(Pm + c - HX - 2), Pm2 = ld2(Pm + c - 2);
+      const float2 pcSW = odd2(P0S2, P0S), pcW = odd2(P02, P0c), pmSW = odd2(PmS2, PmS), pmW = odd2(Pm2, Pmc);
+      const float2 w00 = add2(pmSW, pcSW), w10 = add2(PmS, P0S), w01 = add2(pmW, pcW), w11 = add2(Pmc, P0c);
+      const float2 pE = add2(w10, w11), pW = add2(w00, w01), pNn = add2(w01, w11), pS = add2(w00, w10);
+      const float2 pT = add2(add2(pcSW, P0S), add2(pcW, P0c));
+      const float2 pB = add2(add2(pmSW, PmS), add2(pmW, Pmc));
+      const float *Q0p = S.cr[ck], *Qmp = S.cr[ckm];
+      const float2 Q0c = ld2(Q0p + c), Q0S = ld2(Q0p + c - HX), Q0S2 = ld2(Q0p + c - HX - 2), Q02 = ld2(Q0p + c - 2);
+      const float2 Qmc = ld2(Qmp + c), QmS = ld2(Qmp + c - HX), QmS2 = ld2(Qmp + c - HX - 2), Qm2 = ld2(Qmp + c - 2);
+      const float2 r8 = add2(add2(add2(odd2(Q0S2, Q0S), Q0S), add2(odd2(Q02, Q0c), Q0c)),
+                             add2(add2(odd2(QmS2, QmS), QmS), add2(odd2(Qm2, Qmc), Qmc)));
+      const float2 pg[3] = {mul2(sub2(pE, pW), bc2(qdx)), mul2(sub2(pNn, pS), bc2(qdy)), mul2(sub2(pT, pB), bc2(qdz))};
+      const float2 mcur[3] = {ld2(S.cm[sk][0] + c), ld2(S.cm[sk][1] + c), ld2(S.cm[sk][2] + c)};
+      float2 mnew[3], mflt[3];
+#pragma unroll
+      for (int d = 0; d < 3; d++) {
+        const float2 adv =
+            fma2(u0[d], gsum,
+                 add2(add2(sub2(mul2(gE, uE[d]), mul2(gW, uW[d])), sub2(mul2(gN, uN[d]), mul2(gS, uS[d]))),
+                      sub2(mul2(gT, uT[d]), mul2(gB, uB[d]))));
+        float2 tend = sub2(mul2(adv, bc2(-v0inv)), pg[d]);
+        if (d == 2) tend = sub2(tend, mul2(bc2(g * 0.125f), r8));
+        const float2 ref0 = bc2(d == 0 ? rbc[2] : 0.0f);
+        const float2 mold = mreg[2][d];
+        tend = sub2(tend, fma2(bc2(kdif), dmv[d], mul2(bc2(tk), sub2(mold, ref0))));
+        mnew[d] = fma2(bc2(dt2), tend, mold);
+        mflt[d] = fma2(bc2(nu), add2(sub2(mnew[d], mul2(bc2(2.0f), mcur[d])), mold), mcur[d]);
+      }
+      {
+        const float2 chk = add2(add2(add2(rN_, pN_), add2(mnew[0], mnew[1])), mnew[2]);
+        const float cx = a0 ? chk.x : 0.0f, cy = a1 ? chk.y : 0.0f;
+        if (!isfinite(cx) || !isfinite(cy)) wflag |= WATCH_NONFINITE;
+        const float2 cou = fma2(make_float2(fabsf(u0[0].x), fabsf(u0[0].y)), bc2(cfx),
+                                fma2(make_float2(fabsf(u0[1].x), fabsf(u0[1].y)), bc2(cfy),
+                                     mul2(make_float2(fabsf(u0[2].x), fabsf(u0[2].y)), bc2(cfz))));
+        if ((a0 && cou.x > 1.0f) || (a1 && cou.y > 1.0f)) wflag |= WATCH_COURANT;
+      }
+      // stores: both cells as one 8-byte store where both are computed
+      if (a0 && a1) {
+        st2(rpN + o, rN_);
+        st2(ppN + o, pN_);
+        st2(rpF + o, rF_);
+        st2(ppF + o, pF_);
+      } else if (a0) {
+        rpN[o] = rN_.x;
+        ppN[o] = pN_.x;
+        rpF[o] = rF_.x;
+        ppF[o] = pF_.x;
+      } else if (a1) {
+        rpN[o + 1] = rN_.y;
+        ppN[o + 1] = pN_.y;
+        rpF[o + 1] = rF_.y;
+        ppF[o + 1] = pF_.y;
+      }
+#pragma unroll
+      for (int d = 0; d < 3; d++) {
+        if (q0 && q1) {
+          st2(mN[d] + o, mnew[d]);
+          st2(mF[d] + o, mflt[d]);
+        } else if (q0) {
+          mN[d][o] = mnew[d].x;
+          mF[d][o] = mflt[d].x;
+        } else if (q1) {
+          mN[d][o + 1] = mnew[d].y;
+          mF[d][o + 1] = mflt[d].y;
+        }
+      }
+    }
+#pragma unroll
+    for (int a = 0; a < 4; a++) {
+      treg[a] = treg[a + 1];
+      mreg[a][0] = mreg[a + 1][0];
+      mreg[a][1] = mreg[a + 1][1];
+      mreg[a][2] = mreg[a + 1][2];
+    }
+  }
+  await_groups<0>();
+  wflag = __reduce_or_sync(0xffffffffu, wflag);
+  if (wflag && (tid & 31) == 0 && watch) atomicOr(watch, wflag);
+}

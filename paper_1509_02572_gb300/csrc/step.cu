@@ -748,6 +748,8 @@ __global__ void __launch_bounds__(TILE_X * TYv, FullOcc<T, TYv>::MINB) k_full(co
   if (wflag && (tid & 31) == 0 && watch) atomicOr(watch, wflag);
 }
 
+#include "pair.cuh"
+
 // ------------------------------------------------------------------ cut cells and merge groups
 template <typename T>
 __device__ __forceinline__ T cell_rho(const DomDev &D, const T *rp, const T *rhob, int i, int j, int k) {
@@ -1560,6 +1562,19 @@ cudaError_t full_t(const StepLaunch &L, int rO, int rC, int rN, int rF, int firs
   return cudaGetLastError();
 }
 
+template <int TYv>
+size_t pair_smem() {
+  return sizeof(FullSmem<float, PairCfg<TYv>::PL>);
+}
+
+template <int TYv>
+cudaError_t pair_t(const StepLaunch &L, int rO, int rC, int rN, int rF, int first, cudaStream_t st) {
+  if (L.nitems > 0)
+    k_pair<TYv><<<L.nitems, PairCfg<TYv>::NT, pair_smem<TYv>(), st>>>(L.d_doms, L.items, rO, rC, rN, rF, first,
+                                                                      L.eos, L.watch);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t groups_t(const StepLaunch &L, int rO, int rC, int rN, int rF, int first, cudaStream_t st) {
   if (L.ngroups > 0)
@@ -1580,8 +1595,8 @@ cudaError_t full_prepare(int prec) {
     if ((e = set(k_full<double, 8>, full_smem<double, 8>())) != cudaSuccess) return e;
     return set(k_full<double, 4>, full_smem<double, 4>());
   }
-  if ((e = set(k_full<float, 16>, full_smem<float, 16>())) != cudaSuccess) return e;
-  return set(k_full<float, 8>, full_smem<float, 8>());
+  if ((e = set(k_pair<16>, pair_smem<16>())) != cudaSuccess) return e;
+  return set(k_pair<8>, pair_smem<8>());
 }
 
 cudaError_t launch_base(const DomDev &D, int prec, double theta0, double N, double p_surf, double sponge_frac,
@@ -1604,8 +1619,9 @@ cudaError_t launch_full(const StepLaunch &L, int prec, int rO, int rC, int rN, i
     if (L.ty == 8) return full_t<double, 8>(L, rO, rC, rN, rF, first, st);
     if (L.ty == 4) return full_t<double, 4>(L, rO, rC, rN, rF, first, st);
   } else {
-    if (L.ty == 16) return full_t<float, 16>(L, rO, rC, rN, rF, first, st);
-    if (L.ty == 8) return full_t<float, 8>(L, rO, rC, rN, rF, first, st);
+    // FP32: two cells per thread with packed arithmetic
+    if (L.ty == 16) return pair_t<16>(L, rO, rC, rN, rF, first, st);
+    if (L.ty == 8) return pair_t<8>(L, rO, rC, rN, rF, first, st);
   }
   return cudaErrorInvalidValue;
 }
