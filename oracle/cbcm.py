@@ -9,16 +9,40 @@ completely inside the terrain are dropped.
 
 Reading of the refinement test (the paper only says that cubes close to the
 terrain surface are split; the reading is fitted to its cube counts): a cube
-of level l below the finest level is split when (i) its bottom lies below the highest terrain point and (ii) the
-horizontal distance between its footprint and the columns where the terrain
-is raised above its lowest value is at most one cube width. Lateral
-boundaries are periodic. Only tests import this module.
+of level l below the finest level is split when (i) its bottom lies below the
+highest terrain point and (ii) the horizontal distance between its footprint
+and the finest-level corners where the terrain is raised above its lowest
+value is at most one cube width.  Lateral boundaries are periodic.
+
+Brute force over the finest cube grid: an array holds, for every position of
+a finest-level cube, the level of the leaf cube that covers it.  Splitting a
+cube raises the level of all its positions by one.  The 2:1 balance is the
+plain definition iterated to its fixed point: wherever two touching positions
+differ by more than one level, the cube of the coarser one is split; the
+least balanced refinement containing the terrain refinement is unique, so the
+order of the splits does not matter.  Only tests import this module.
 """
 from __future__ import annotations
 
-import math
+import itertools
 
 import numpy as np
+
+
+def _near_terrain(c0, c1, size, hmax, raised, Lx, Ly):
+    """Refinement test of a cube with horizontal footprint [c0, c1] (metres,
+    x and y) whose bottom is at c0[2]: bottom below the highest terrain and a
+    raised corner within one cube width of the footprint (periodic)."""
+    if not c0[2] < hmax or len(raised) == 0:
+        return False
+    best = np.inf
+    for px, py in raised:
+        dx = min(max(0.0, c0[0] - x, x - c1[0]) for x in (px - Lx, px, px + Lx))
+        dy = min(max(0.0, c0[1] - y, y - c1[1]) for y in (py - Ly, py, py + Ly))
+        best = min(best, (dx * dx + dy * dy) ** 0.5)
+        if best <= size:
+            return True
+    return False
 
 
 def cube_layout(nx0: int, ny0: int, nz0: int, cube: int, H: float, nlev: int, h_finest: np.ndarray):
@@ -29,96 +53,63 @@ def cube_layout(nx0: int, ny0: int, nz0: int, cube: int, H: float, nlev: int, h_
     L = nlev - 1
     hf = np.asarray(h_finest, dtype=np.float64)
     assert hf.shape == (ny0 << L, nx0 << L)
+    df = H / (1 << L)
     Lx, Ly = nx0 * H, ny0 * H
-    df = H / (1 << L)  # finest spacing
     hmin, hmax = float(hf.min()), float(hf.max())
-    jr, ir = np.nonzero(hf > hmin)
-    rx, ry = ir * df, jr * df  # raised corner points
-    ncx = [(nx0 // cube) << l for l in range(nlev)]
-    ncy = [(ny0 // cube) << l for l in range(nlev)]
-    ncz = [(nz0 // cube) << l for l in range(nlev)]
-    size = [cube * H / (1 << l) for l in range(nlev)]
-    refined = [set() for _ in range(nlev)]
+    raised = [(I * df, J * df) for J, I in zip(*np.nonzero(hf > hmin))]
+    nf = ((nz0 // cube) << L, (ny0 // cube) << L, (nx0 // cube) << L)  # finest cube grid (k, j, i)
+    lev = np.zeros(nf, dtype=np.int64)
 
-    def exists(l, c):
-        return l == 0 or (c[0] // 2, c[1] // 2, c[2] // 2) in refined[l - 1]
+    def width(l):  # finest positions along one edge of a level-l cube
+        return 1 << (L - l)
 
-    def axis_gap(p, a0, a1, period):
-        # distance from coordinates p to the interval [a0, a1] on a circle
-        best = None
-        for sh in (-period, 0.0, period):
-            q = p + sh
-            g = np.maximum(0.0, np.maximum(a0 - q, q - a1))
-            best = g if best is None else np.minimum(best, g)
-        return best
-
-    def near_terrain(l, c):
-        s = size[l]
-        if not (c[2] * s < hmax) or rx.size == 0:
-            return False
-        gx = axis_gap(rx, c[0] * s, (c[0] + 1) * s, Lx)
-        gy = axis_gap(ry, c[1] * s, (c[1] + 1) * s, Ly)
-        return bool(np.min(np.sqrt(gx * gx + gy * gy)) <= s)
-
-    # refinement by the terrain test, level by level
+    # terrain refinement, level by level, of every level-l leaf
     for l in range(L):
-        for ck in range(ncz[l]):
-            for cj in range(ncy[l]):
-                for ci in range(ncx[l]):
-                    c = (ci, cj, ck)
-                    if exists(l, c) and near_terrain(l, c):
-                        refined[l].add(c)
-
-    def leaf_level(l, c):
-        """Level of the leaf covering the region of cube c of level l."""
-        # the centre of the region in finest cube units
-        f = 1 << (L - l)
-        p = ((2 * c[0] + 1) * f, (2 * c[1] + 1) * f, (2 * c[2] + 1) * f)  # twice the finest index
-        for m in range(nlev):
-            g = 1 << (L - m + 1)
-            cm = (p[0] // g, p[1] // g, p[2] // g)
-            if cm not in refined[m]:
-                return m, cm
-        raise AssertionError("refined at the finest level")
+        f = width(l)
+        s = cube * H / (1 << l)
+        for ck, cj, ci in itertools.product(range(nf[0] // f), range(nf[1] // f), range(nf[2] // f)):
+            blk = lev[ck * f:(ck + 1) * f, cj * f:(cj + 1) * f, ci * f:(ci + 1) * f]
+            if (blk == l).all() and _near_terrain((ci * s, cj * s, ck * s), ((ci + 1) * s, (cj + 1) * s), s, hmax,
+                                                  raised, Lx, Ly):
+                blk[...] = l + 1
 
     # 2:1 balance across faces, edges and corners (periodic in x and y)
-    changed = True
-    while changed:
-        changed = False
-        for l in range(L, 1, -1):
-            for c in sorted(refined[l - 1]):
-                for a in range(2):
-                    for b in range(2):
-                        for e in range(2):
-                            leaf = (2 * c[0] + a, 2 * c[1] + b, 2 * c[2] + e)
-                            if leaf in refined[l]:
-                                continue
-                            for dk in (-1, 0, 1):
-                                for dj in (-1, 0, 1):
-                                    for di in (-1, 0, 1):
-                                        if di == dj == dk == 0:
-                                            continue
-                                        nk = leaf[2] + dk
-                                        if nk < 0 or nk >= ncz[l]:
-                                            continue
-                                        nb = ((leaf[0] + di) % ncx[l], (leaf[1] + dj) % ncy[l], nk)
-                                        m, cm = leaf_level(l, nb)
-                                        if m < l - 1:
-                                            refined[m].add(cm)
-                                            changed = True
-    # leaves, minus the cubes completely inside the terrain
+    while True:
+        coarse = np.zeros(nf, dtype=bool)
+        for dk, dj, di in itertools.product((-1, 0, 1), repeat=3):
+            if dk == dj == di == 0:
+                continue
+            nb = np.roll(np.roll(lev, -dj, axis=1), -di, axis=2)
+            if dk:
+                nb = np.roll(nb, -dk, axis=0)
+                edge = nf[0] - 1 if dk == 1 else 0  # no neighbour across the floor or the top
+                nb[edge] = -1
+            coarse |= nb > lev + 1
+        if not coarse.any():
+            break
+        for k, j, i in zip(*np.nonzero(coarse)):
+            b = lev[k, j, i]
+            if b >= L:
+                continue
+            f = width(b)
+            ck, cj, ci = k // f, j // f, i // f
+            lev[ck * f:(ck + 1) * f, cj * f:(cj + 1) * f, ci * f:(ci + 1) * f] = b + 1
+
+    # leaves (every level-l cube whose positions all carry level l), minus the
+    # cubes completely inside the terrain
     out = []
     for l in range(nlev):
-        s, f = size[l], cube << (L - l)  # cube width in finest cells
-        for ck in range(ncz[l]):
-            for cj in range(ncy[l]):
-                for ci in range(ncx[l]):
-                    c = (ci, cj, ck)
-                    if not exists(l, c) or c in refined[l]:
-                        continue
-                    I = np.arange(ci * f, (ci + 1) * f + 1) % hf.shape[1]
-                    J = np.arange(cj * f, (cj + 1) * f + 1) % hf.shape[0]
-                    if hf[np.ix_(J, I)].min() >= (ck + 1) * s:
-                        continue
-                    out.append((l, ci, cj, ck))
+        f = width(l)
+        s = cube * H / (1 << l)
+        w = cube << (L - l)  # cube width in finest cells
+        for ck, cj, ci in itertools.product(range(nf[0] // f), range(nf[1] // f), range(nf[2] // f)):
+            blk = lev[ck * f:(ck + 1) * f, cj * f:(cj + 1) * f, ci * f:(ci + 1) * f]
+            if not (blk == l).all():
+                assert not (blk == l).any(), "a leaf must be a whole cube"
+                continue
+            I = np.arange(ci * w, (ci + 1) * w + 1) % hf.shape[1]
+            J = np.arange(cj * w, (cj + 1) * w + 1) % hf.shape[0]
+            if hf[np.ix_(J, I)].min() >= (ck + 1) * s:
+                continue
+            out.append((l, ci, cj, ck))
     return out
