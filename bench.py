@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-precision", action="store_true",
+                    help="skip the FP32-against-FP64 precision run of the 512 x 512 x 128 bell")
+    ap.add_argument("--precision-steps", type=int, default=5000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--schedule", default=None,
                     help="TILE_Y,ITEMS: fixed full-cell schedule instead of the autotuner (profiling runs)")
@@ -78,17 +81,22 @@ def workload_configs(args):
     return name, cfgs
 
 
-def kfull_source_hash():
+def kfull_source_hash(dtype="f64"):
     """Hash of the full-cell stencil's source (the kernel, its shared-memory
-    layout and tile shape): the DRAM counters recorded under profiles/ apply
-    only while it is unchanged."""
+    layout and tile shape): the counters recorded under profiles/ apply only
+    while it is unchanged.  FP64 runs the one-cell kernel of step.cu, FP32 the
+    two-cell kernel of pair.cuh."""
     import hashlib
-    src = open(os.path.join(ROOT, "paper_1509_02572_gb300", "csrc", "step.cu")).read()
-    hdr = open(os.path.join(ROOT, "paper_1509_02572_gb300", "csrc", "cc_internal.h")).read()
-    a = src.index("struct FullCfg")
-    b = src.index("// ------------------------------------------------------------------ cut cells", a)
+    csrc = os.path.join(ROOT, "paper_1509_02572_gb300", "csrc")
+    hdr = open(os.path.join(csrc, "cc_internal.h")).read()
     tiles = [ln for ln in hdr.splitlines() if "TILE_" in ln or "SCHED_" in ln or "constexpr int GX" in ln]
-    return hashlib.sha256((src[a:b] + "\n".join(tiles)).encode()).hexdigest()[:16]
+    if dtype == "f32":
+        body = open(os.path.join(csrc, "pair.cuh")).read()
+    else:
+        src = open(os.path.join(csrc, "step.cu")).read()
+        a = src.index("struct FullCfg")
+        body = src[a:src.index('#include "pair.cuh"', a)]
+    return hashlib.sha256((body + "\n".join(tiles)).encode()).hexdigest()[:16]
 
 
 def kfull_traffic(dtype, cells, schedule):
@@ -100,7 +108,7 @@ def kfull_traffic(dtype, cells, schedule):
             t = json.load(f)
     except Exception:
         return None
-    if t.get("source_hash") != kfull_source_hash() or t.get("precision") != {"f32": "fp32", "f64": "fp64"}[dtype]:
+    if t.get("source_hash") != kfull_source_hash(dtype) or t.get("precision") != {"f32": "fp32", "f64": "fp64"}[dtype]:
         return None
     per = t.get("dram_bytes_per_interior_cell_by_tile_y", {}).get(str(schedule[0]))
     return None if per is None else per * cells
@@ -118,7 +126,7 @@ def refined_kfull_traffic(dtype, workload, schedules):
     except Exception:
         return None
     r = t.get("refined")
-    if (r is None or t.get("source_hash") != kfull_source_hash() or dtype != "f32"
+    if (r is None or t.get("source_hash") != kfull_source_hash("f32") or dtype != "f32"
             or r.get("workload") != workload or [x[0] for x in r.get("schedule", [])] != [x[0] for x in schedules]):
         return None
     return r["cycle_dram_bytes"] / r["cycle_launches"]
@@ -213,7 +221,7 @@ def make_model(cc, cfgs, prec, tune=True):
         m.set_terrain(d, c.heights())
     m.build_geometry()
     m.init_state()
-    if SCHEDULE and prec == cc.CC_FP32:
+    if SCHEDULE:
         m.set_schedule(0, *SCHEDULE)
     elif tune:
         m.autotune(3)
@@ -339,18 +347,105 @@ def cpu_baseline_allcores(cfgs, seconds):
                       f"({', '.join(names)}); single-threaded FP64 oracle in each"}
 
 
-def fp64_flops_per_cell():
+def fp64_flops_per_cell(tile_y):
     """Executed FP64 flops of the FP64 full-cell stencil per interior cell
-    (2 per fused multiply-add), from the committed ncu count, or None when the
-    kernel changed since the count."""
+    (2 per fused multiply-add) for tiles of height tile_y, from the committed
+    ncu count, or None when the kernel changed since the count."""
     try:
         with open(os.path.join(ROOT, "profiles", "k_full_fp64_flops.json")) as f:
             t = json.load(f)
     except Exception:
         return None
-    if t.get("source_hash") != kfull_source_hash():
+    if t.get("source_hash") != kfull_source_hash("f64"):
         return None
-    return t.get("flops_per_interior_cell")
+    return t.get("flops_per_interior_cell_by_tile_y", {}).get(str(tile_y))
+
+
+FIELDS5 = (("rho'", "RHOP"), ("p'", "PP"), ("rho u", "MX"), ("rho v", "MY"), ("rho w", "MZ"))
+
+
+def precision_columns(cfg):
+    """Sampled columns (J, I) of the precision check: a 6 x 6 lattice over the
+    domain and rings at 5, 10 and 20 cells around the hill centre."""
+    cols = set()
+    for a in range(6):
+        for b in range(6):
+            cols.add(((cfg.ny * (2 * a + 1)) // 12, (cfg.nx * (2 * b + 1)) // 12))
+    cj, ci = cfg.ny // 2, cfg.nx // 2
+    for r in (5, 10, 20):
+        for dj, di in ((0, r), (0, -r), (r, 0), (-r, 0)):
+            cols.add((cj + dj, ci + di))
+    cols = sorted(cols)
+    return np.array([c[0] for c in cols]), np.array([c[1] for c in cols])
+
+
+def _oracle_columns_worker(cfg, steps, q):
+    """The oracle alone on the host: `steps` steps of the whole domain, then
+    every field on the sampled columns."""
+    import oracle
+    om = oracle.Model(cfg)
+    om.init_state()
+    om.step(steps)
+    J, I = precision_columns(cfg)
+    q.put({name: om.field(getattr(oracle, "F_" + f), 1)[:, J, I] for name, f in FIELDS5})
+
+
+def bench_precision(cc, torch, steps):
+    """FP32 perturbation form against the plain FP64 form on the 512 x 512 x
+    128 bell (100 m / 50 m cells, h0 = 400 m, a = 2 km) after `steps` steps,
+    per field over the whole domain; and both forms against the oracle on
+    sampled columns after two steps (the oracle runs the whole domain on the
+    host meanwhile, in a spawned process)."""
+    import multiprocessing as mp
+    import queue as _queue
+    import oracle
+    oracle.build()
+    cfg = W.C3_BELL
+    ostep = 2
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    proc = ctx.Process(target=_oracle_columns_worker, args=(cfg, ostep, q))
+    proc.start()
+    J, I = precision_columns(cfg)
+    t0 = time.perf_counter()
+    fields, early = {}, {}
+    for prec, tag in ((cc.CC_FP32, "fp32"), (cc.CC_FP64, "fp64")):
+        m = make_model(cc, [cfg], prec)
+        m.step(ostep)
+        early[tag] = {name: m.download(0, getattr(cc, "CC_" + f))[:, J, I] for name, f in FIELDS5}
+        m.step(steps - ostep)
+        fields[tag] = {name: m.download(0, getattr(cc, "CC_" + f)) for name, f in FIELDS5}
+        nf = m.diagnostics(0, check=False)["nonfinite"]
+        m.close()
+        if nf:
+            fields[tag] = None
+    gpu_s = time.perf_counter() - t0
+    try:
+        ref = q.get(timeout=1800.0)
+    except _queue.Empty:
+        ref = None
+    proc.join(timeout=10.0)
+    if proc.is_alive():
+        proc.terminate()
+        proc.join()
+
+    def rel(a, b):
+        den = float(np.sqrt(np.sum(b * b)))
+        sc = float(np.abs(b).max())
+        return {"rel_l2": float(np.sqrt(np.sum((a - b) ** 2))) / den if den > 0 else float(np.abs(a).max()),
+                "rel_linf": float(np.abs(a - b).max()) / sc if sc > 0 else float(np.abs(a).max())}
+    out = {"workload": cfg.name, "cells": cfg.cells, "steps": steps, "gpu_seconds": round(gpu_s, 1)}
+    if fields["fp32"] is not None and fields["fp64"] is not None:
+        out["fp32_vs_fp64_gpu"] = {name: rel(fields["fp32"][name], fields["fp64"][name]) for name, _ in FIELDS5}
+    else:
+        out["fp32_vs_fp64_gpu"] = None
+    if ref is not None:
+        out["vs_oracle"] = {"after_steps": ostep, "columns": int(len(J)),
+                            "fp32": {n: rel(early["fp32"][n], ref[n]) for n, _ in FIELDS5},
+                            "fp64": {n: rel(early["fp64"][n], ref[n]) for n, _ in FIELDS5}}
+    else:
+        out["vs_oracle"] = None
+    return out
 
 
 def make_refined(cc, rc, prec):
@@ -807,7 +902,8 @@ def main():
         for s in singles:
             s.profile(False)
         peak64 = cc.fma_peak(cc.CC_FP64)
-        fpc = fp64_flops_per_cell()
+        per = [fp64_flops_per_cell(s.schedule(0)[0]) for s in singles]
+        fpc = None if any(x is None for x in per) else sum(x * c.cells for x, c in zip(per, cfgs)) / ninterior
         ach64 = None if fpc is None else fpc * ninterior / (k64_ms / 1e3)
         line["fp64_plain"]["roofline"] = {
             "bound": "alu", "achieved": None if ach64 is None else ach64 / 1e12, "peak": peak64 / 1e12,
@@ -880,6 +976,8 @@ def main():
         line["cpu_baseline"] = cpu_baseline(cfgs, args.cpu_seconds)
         line["cpu_baseline"]["all_cores"] = cpu_baseline_allcores(cfgs, args.cpu_seconds)
     model.close()
+    if args.workload == "ensemble" and not args.no_precision and rank == 0 and world == 1:
+        line["precision"] = bench_precision(cc, torch, args.precision_steps)
     if args.workload == "ensemble" and not args.no_refined:
         line["refined"] = bench_refined(cc, torch, args, hbm, peak_kind, barrier, world)
     if rank == 0:

@@ -233,28 +233,86 @@ def test_refined_graph_replay_equals_direct_launches(cc):
         assert np.array_equal(x, y)
 
 
+PAPER_BASE = W.RunConfig("hemisphere-400m", 160, 80, 40, 400.0, 400.0, 400.0, 0.3, 1, "hemisphere", 1000.0, 1000.0,
+                         theta0=300.0)
+# the regions behind the fine levels' inflow faces (m): x, y ranges and z < 3.2 km
+INFLOW = {1: (16000.0, 22000.0, 8000.0, 24000.0), 2: (24000.0, 30000.0, 12000.0, 20000.0)}
+TIMES = (1200, 2400, 3600)
+
+
+def _max_w(w, dx, dz, x0, ox, oy, region):
+    """Largest |w| at the corners of a level whose corner (0, 0) lies at
+    (ox, oy) m, inside the region (x0 .. x1, y0 .. y1, z below 3.2 km)."""
+    xa, xb, ya, yb = region
+    nk, ny, nx = w.shape
+    X, Y, Z = ox + np.arange(nx) * dx, oy + np.arange(ny) * dx, np.arange(nk) * dz
+    sel = w[np.ix_(Z < 3200.0, (Y >= ya) & (Y <= yb), (X >= xa) & (X < xb))]
+    return float(np.abs(sel).max())
+
+
+@pytest.fixture(scope="module")
+def uniform200(cc):
+    """The uniform 200 m run of the same flow: largest |w| in the two regions
+    at 1,200, 2,400 and 3,600 s."""
+    u = PAPER_BASE.replace(nx=320, ny=160, nz=80, dx=200.0, dy=200.0, dz=200.0, dt=0.15)
+    m = cc.Model([u], cc.CC_FP32)
+    m.set_terrain(0, u.heights())
+    m.build_geometry()
+    m.init_state()
+    out = {}
+    for T in TIMES:
+        m.step(8000)
+        w = m.derived(0, cc.CC_W)
+        out[T] = {l: _max_w(w, 200.0, 200.0, 0.0, 0.0, 0.0, INFLOW[l]) for l in (1, 2)}
+    m.close()
+    return out
+
+
+# measured bounds on the largest |w| (m/s) behind the inflow faces, with some
+# headroom: run (levels) -> level -> time -> bound
+INFLOW_BOUND = {2: {1: {2400: 6.0, 3600: 18.0}},
+                3: {1: {2400: 0.8, 3600: 1.0}, 2: {1200: 2.0, 2400: 2.6, 3600: 11.0}}}
+
+
 @pytest.mark.timeout(900)
 @pytest.mark.parametrize("nbox", [1, 2], ids=["two-levels", "three-levels"])
-def test_refined_paper_domain_one_hour(cc, nbox):
+def test_refined_paper_domain_one_hour(cc, uniform200, nbox):
     """The 1 km hemisphere on the paper's 64 x 32 x 16 km domain at 400 m with
     a 200 m box (x 16-48 km, y 8-24 km, z 0-8 km) and, for three levels, a
     100 m box (x 24-40 km, y 12-20 km, z 0-4 km), FP32, one hour (12,000
-    coarse steps): every level stays finite with |w| bounded. With the
-    corners on the box faces computed by both levels, or with the fine
-    level's integrated ghost layers never reset to the coarse solution, these
-    runs blew up within a quarter of the hour."""
-    base = W.RunConfig("hemisphere-400m", 160, 80, 40, 400.0, 400.0, 400.0, 0.3, 1, "hemisphere", 1000.0, 1000.0,
-                       theta0=300.0)
+    coarse steps).  Every level stays finite.  The largest |w| below 3.2 km in
+    the 6 km behind each fine level's inflow face is compared with the uniform
+    200 m run at the same points.  At 1,200 s the 200 m levels match it (two
+    levels 0.12 against 0.12 m/s; three levels 0.02).  The open defect
+    (DESIGN, long refined runs) then shows: at 2,400 s the two-level run
+    reaches 4.2 m/s there against 0.014 for the uniform grid, about 300 times
+    more, and 12.5 m/s at 3,600 s; in the three-level run the 200 m level
+    reaches 0.52 m/s (about 37 times the uniform run) and the 100 m box,
+    already at 1.3 against 0.48 m/s at 1,200 s, 7.3 m/s at 3,600 s.  The test
+    asserts the 1,200 s agreement of the 200 m levels and bounds the rest at
+    the measured values (so that the defect cannot grow unnoticed); it does
+    not claim that the refined runs are right behind their inflow faces."""
     boxes = [(160, 80, 40, 80, 40)] * nbox
-    rc = W.RefinedConfig("paper-domain", base, boxes)
-    m = cc.RefinedModel(base, boxes, cc.CC_FP32)
+    rc = W.RefinedConfig("paper-domain", PAPER_BASE, boxes)
+    m = cc.RefinedModel(PAPER_BASE, boxes, cc.CC_FP32)
     for l, c in enumerate(m.cfgs):
         m.set_terrain(l, rc.finest_heights() if l == m.nlev - 1 else np.zeros((c.ny, c.nx)))
     m.build_geometry()
     m.init_state()
-    m.step(12000)
+    got = {}
+    for T in TIMES:
+        m.step(4000)
+        for l in range(1, m.nlev):
+            c = m.cfgs[l]
+            ox, oy = rc.level_origin(l)
+            got[(l, T)] = _max_w(m.derived(l, cc.CC_W), c.dx, c.dz, 0.0, ox, oy, INFLOW[l])
     ds = [m.diagnostics(l, check=False) for l in range(m.nlev)]
     m.close()
     for l, d in enumerate(ds):
         assert d["nonfinite"] == 0, l
         assert d["max_w"] < 20.0, (l, d["max_w"])
+    # the 200 m level agrees with the uniform 200 m run at 1,200 s
+    assert got[(1, 1200)] <= 1.5 * uniform200[1200][1] + 0.02, (got[(1, 1200)], uniform200[1200][1])
+    for l, per in INFLOW_BOUND[nbox + 1].items():
+        for T, bound in per.items():
+            assert got[(l, T)] <= bound, (l, T, got[(l, T)], uniform200[T][l])
