@@ -448,6 +448,55 @@ def bench_precision(cc, torch, steps):
     return out
 
 
+def bench_inflow(cc):
+    """The open defect of the refined runs (Sec 3.2 set-up): the 1 km
+    hemisphere on the paper's 64 x 32 x 16 km domain at 400 m with a 200 m box
+    (and a 100 m box), FP32, one hour; the largest |w| below 3.2 km in the 6 km
+    behind each fine level's inflow face at 1,200, 2,400 and 3,600 s, and the
+    uniform 200 m run's at the same points."""
+    base = W.RunConfig("hemisphere-400m", 160, 80, 40, 400.0, 400.0, 400.0, 0.3, 1, "hemisphere", 1000.0, 1000.0,
+                       theta0=300.0)
+    regions = {1: (16000.0, 22000.0, 8000.0, 24000.0), 2: (24000.0, 30000.0, 12000.0, 20000.0)}
+
+    def max_w(w, dx, dz, ox, oy, reg):
+        xa, xb, ya, yb = reg
+        nk, ny, nx = w.shape
+        X, Y, Z = ox + np.arange(nx) * dx, oy + np.arange(ny) * dx, np.arange(nk) * dz
+        return float(np.abs(w[np.ix_(Z < 3200.0, (Y >= ya) & (Y <= yb), (X >= xa) & (X < xb))]).max())
+    out = {}
+    for nbox in (1, 2):
+        boxes = [(160, 80, 40, 80, 40)] * nbox
+        rc = W.RefinedConfig("paper-domain", base, boxes)
+        m = cc.RefinedModel(base, boxes, cc.CC_FP32)
+        for l, c in enumerate(m.cfgs):
+            m.set_terrain(l, rc.finest_heights() if l == m.nlev - 1 else np.zeros((c.ny, c.nx)))
+        m.build_geometry()
+        m.init_state()
+        rec = {}
+        for T in (1200, 2400, 3600):
+            m.step(4000)
+            rec[T] = [round(max_w(m.derived(l, cc.CC_W), m.cfgs[l].dx, m.cfgs[l].dz, *rc.level_origin(l), regions[l]), 4)
+                      for l in range(1, m.nlev)]
+        m.close()
+        out[f"{nbox + 1}_levels"] = rec
+    u = base.replace(nx=320, ny=160, nz=80, dx=200.0, dy=200.0, dz=200.0, dt=0.15)
+    m = cc.Model([u], cc.CC_FP32)
+    m.set_terrain(0, u.heights())
+    m.build_geometry()
+    m.init_state()
+    rec = {}
+    for T in (1200, 2400, 3600):
+        m.step(8000)
+        w = m.derived(0, cc.CC_W)
+        rec[T] = [round(max_w(w, 200.0, 200.0, 0.0, 0.0, regions[l]), 4) for l in (1, 2)]
+    m.close()
+    out["uniform_200m"] = rec
+    out["how"] = ("largest |w| (m/s) below 3.2 km in the 6 km behind the inflow face of each fine level "
+                  "(200 m level, then 100 m box), at 1200 / 2400 / 3600 s; uniform_200m: the same regions of the "
+                  "uniform 200 m run")
+    return out
+
+
 def make_refined(cc, rc, prec):
     m = cc.RefinedModel(rc.base, rc.boxes, prec)
     for l, c in enumerate(m.cfgs):
@@ -980,6 +1029,8 @@ def main():
         line["precision"] = bench_precision(cc, torch, args.precision_steps)
     if args.workload == "ensemble" and not args.no_refined:
         line["refined"] = bench_refined(cc, torch, args, hbm, peak_kind, barrier, world)
+        if rank == 0 and world == 1:
+            line["refined"]["inflow_face_w"] = bench_inflow(cc)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
