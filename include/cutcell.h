@@ -42,7 +42,8 @@ typedef enum {
   CC_EGEOM = 3,     /* merge or boundary stencil cannot be formed           */
   CC_ENUMERIC = 4,  /* NaN or Inf in the state (cc_diagnostics), or the step watchdog raised */
   CC_ENOMEM = 5,    /* device allocation failed                             */
-  CC_ESTATE = 6     /* call out of order (e.g. step before geometry)        */
+  CC_ESTATE = 6,    /* call out of order (e.g. step before geometry)        */
+  CC_ETIMEOUT = 7   /* a bounded wait inside a kernel ran out (step watchdog) */
 } cc_status;
 
 enum { CC_FP64 = 0, CC_FP32 = 1 };
@@ -245,11 +246,14 @@ cc_status cc_load(cc_model *m, const char *path);
  * Step watchdog (no counterpart in the paper): every step's full-cell stencil
  * raises a flag when it writes a non-finite value or when a corner's
  * advective Courant number sum_d |u_d| dt / d_d exceeds 1 (the stability
- * limit of centred leapfrog advection).  Each call queues a copy of the
- * flags to the host after its steps; a later cc_step whose copy has arrived
- * (checked without waiting) and cc_synchronize return CC_ENUMERIC, with the
- * reason in cc_last_error, instead of stepping on.  cc_init_state and
- * cc_load clear the flags. */
+ * limit of centred leapfrog advection), and a third when one of its bounded
+ * waits for the TMA copies of a plane ran out (after two seconds; the block
+ * then stops, waits a bounded time for its copies in flight and returns, so
+ * the step is void but the context stays usable).  Each call queues a copy of
+ * the flags to the host after its steps; a later cc_step whose copy has
+ * arrived (checked without waiting) and cc_synchronize return CC_ENUMERIC
+ * (first two) or CC_ETIMEOUT (third), with the reason in cc_last_error,
+ * instead of stepping on.  cc_init_state and cc_load clear the flags. */
 cc_status cc_step(cc_model *m, int n);
 
 /* CUDA graphs (no counterpart in the paper): with graphs on (the default),
@@ -264,9 +268,9 @@ cc_status cc_graphs_enable(cc_model *m, int on);
  * Returns CC_ENUMERIC when non-finite values are present. */
 cc_status cc_diagnostics(cc_model *m, int d, cc_diag *out);
 
-/* Wait for all work queued on the model's stream; CC_ENUMERIC if the step
- * watchdog (see cc_step) was raised by a step since the last cc_init_state
- * or cc_load. */
+/* Wait for all work queued on the model's stream; CC_ENUMERIC or
+ * CC_ETIMEOUT if the step watchdog (see cc_step) was raised by a step since
+ * the last cc_init_state or cc_load. */
 cc_status cc_synchronize(cc_model *m);
 
 /* Number of kernels the last cc_step launched (for launch accounting). */

@@ -1,6 +1,7 @@
 // C ABI of the cut-cell library: model creation, device memory, geometry,
 // state transfer, time stepping and diagnostics (declarations and the paper
 // references are in include/cutcell.h).
+#include <cuda.h>  // CUtensorMap and its enumerations (the encoder is looked up at run time)
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -30,7 +31,10 @@ struct DomHost {
   int r[4] = {0, 1, 2, 3};  // roles: old (filtered n-1), current, new, filtered n
   long long nsteps = 0;
   // this domain's ranges of the model-wide work, group and column lists
-  int item0[NSCHED] = {}, nitem[NSCHED] = {}, group0 = 0, ngroup = 0, col0 = 0, ncol = 0;
+  // (FP32: the items of a refined box, staged by TMA; witem0/nwitem those of
+  // a periodic domain, gathered from the cyclic indices)
+  int item0[NSCHED] = {}, nitem[NSCHED] = {}, witem0[NSCHED] = {}, nwitem[NSCHED] = {};
+  int group0 = 0, ngroup = 0, col0 = 0, ncol = 0;
   int sched = 0;  // full-cell schedule of this level (refined models)
 };
 
@@ -54,7 +58,8 @@ struct cc_model {
   std::vector<DomHost> dom;
   DomDev *d_doms = nullptr;
   WorkItem *d_items[NSCHED] = {};  // work list of every full-cell schedule
-  int nitems[NSCHED] = {};
+  int nitems[NSCHED] = {};         // its first part (FP32: the items of refined boxes, staged by TMA)
+  int nwitems[NSCHED] = {};        // FP32: the items of periodic domains (cyclic gather), after the first part
   int sched = 0;                   // schedule of the ensemble launch
   bool tuned = false;
   // CUDA graphs of one step (one cycle of level 0 for a refined model), keyed
@@ -102,6 +107,10 @@ struct cc_model {
   unsigned *d_watch = nullptr, *h_watch = nullptr;
   cudaEvent_t ev_watch = nullptr;
   bool watch_pending = false;
+  // FP32: TMA tensor maps of the two-cell stencil, two per domain (tile
+  // heights 8 and 16), in device memory
+  unsigned char *d_tmaps = nullptr;
+
   std::string err;
   std::vector<void *> allocs;
 };
@@ -132,6 +141,8 @@ cc_status watch_verdict(cc_model *m) {
   if (w & WATCH_NONFINITE) return fail(m, CC_ENUMERIC, "step watchdog: a step wrote a non-finite value");
   if (w & WATCH_COURANT)
     return fail(m, CC_ENUMERIC, "step watchdog: an advective Courant number sum |u_d| dt / d_d exceeded 1");
+  if (w & WATCH_TIMEOUT)
+    return fail(m, CC_ETIMEOUT, "step watchdog: a bounded wait in the full-cell stencil ran out (the step is void)");
   return CC_OK;
 }
 
@@ -208,6 +219,8 @@ StepLaunch make_launch(const cc_model *m, int d = -1) {
   L.d_doms = m->d_doms;
   L.items = m->d_items[m->sched];
   L.nitems = m->nitems[m->sched];
+  L.witems = m->d_items[m->sched] + m->nitems[m->sched];
+  L.nwitems = m->nwitems[m->sched];
   L.ty = sched_tile_y(m->prec, m->sched);
   L.groups = m->d_groups;
   L.ngroups = m->ngroups;
@@ -217,10 +230,13 @@ StepLaunch make_launch(const cc_model *m, int d = -1) {
   L.ndom = m->ndom;
   L.eos = m->eos;
   L.watch = m->d_watch;
+  L.tmaps = m->d_tmaps;
   if (d >= 0) {
     const DomHost &H = m->dom[d];
     L.items = m->d_items[H.sched] + H.item0[H.sched];
     L.nitems = H.nitem[H.sched];
+    L.witems = m->d_items[H.sched] + H.witem0[H.sched];
+    L.nwitems = H.nwitem[H.sched];
     L.ty = sched_tile_y(m->prec, H.sched);
     L.groups = m->d_groups + H.group0;
     L.ngroups = H.ngroup;
@@ -274,6 +290,58 @@ struct DomKind {
   double ztop;
 };
 
+// cuTensorMapEncodeTiled, from the driver through the runtime's entry-point
+// query (no link against the driver library)
+using EncodeTiled = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                 const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_tiled() {
+  static const EncodeTiled fn = [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (EncodeTiled) nullptr;
+    return (EncodeTiled)p;
+  }();
+  return fn;
+}
+
+// Two tensor maps per domain for the FP32 two-cell stencil: a 3-D view of
+// the domain's twenty padded field arrays (x: px, y: py, z: twenty times pz)
+// with the box of one haloed tile plane, (TILE_X + 4) x (tile height + 4) x 1,
+// for the tile heights 8 and 16.  Points outside the view read as zeros.
+static_assert(sizeof(CUtensorMap) == 128, "128-byte tensor maps");
+cudaError_t make_tensor_maps(const cc_model *m, std::vector<unsigned char> &out, std::string &why) {
+  const EncodeTiled enc = encode_tiled();
+  if (!enc) {
+    why = "cuTensorMapEncodeTiled not available from the driver";
+    return cudaErrorSymbolNotFound;
+  }
+  out.assign((size_t)m->ndom * 2 * sizeof(CUtensorMap), 0);
+  for (int d = 0; d < m->ndom; d++) {
+    const DomDev &D = m->dom[d].D;
+    for (int t = 0; t < 2; t++) {
+      const int ty = t == 0 ? 8 : 16;
+      CUtensorMap tm;
+      const cuuint64_t dims[3] = {(cuuint64_t)D.px, (cuuint64_t)D.py, (cuuint64_t)D.pz * NBUF * NFIELD};
+      const cuuint64_t strides[2] = {(cuuint64_t)D.px * sizeof(float), (cuuint64_t)D.plane * sizeof(float)};
+      const cuuint32_t box[3] = {(cuuint32_t)(TILE_X + 4), (cuuint32_t)(ty + 4), 1};
+      const cuuint32_t es[3] = {1, 1, 1};
+      const CUresult r = enc(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, D.f[0][0], dims, strides, box, es,
+                             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                             CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS) {
+        why = "cuTensorMapEncodeTiled failed with " + std::to_string((int)r) + " for domain " + std::to_string(d);
+        return cudaErrorInvalidValue;
+      }
+      std::memcpy(out.data() + (2 * (size_t)d + t) * sizeof(CUtensorMap), &tm, sizeof(CUtensorMap));
+    }
+  }
+  return cudaSuccess;
+}
+
 }  // namespace
 
 namespace {
@@ -326,9 +394,13 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
       D.ci0 = -2; D.ci1 = c.nx + 2; D.cj0 = -2; D.cj1 = c.ny + 2; D.ck1 = c.nz + 2; D.qi0 = -1; D.qj0 = -1;
     }
     long long ncol = (long long)c.nx * c.ny, ncell = ncol * c.nz, npc = D.plane;
+    // the twenty field arrays back to back, level b field f at
+    // (b NFIELD + f) ncellp elements, so that one tensor map covers them
+    unsigned char *fields = nullptr;
+    if ((e = dalloc(H.allocs, &fields, (size_t)NBUF * NFIELD * D.ncellp * m->esz, m->st)) != cudaSuccess)
+      return bail(e, "field alloc");
     for (int b = 0; b < NBUF; b++) {
-      for (int f = 0; f < NFIELD; f++)
-        if ((e = dalloc(H.allocs, &D.f[b][f], D.ncellp * m->esz, m->st)) != cudaSuccess) return bail(e, "field alloc");
+      for (int f = 0; f < NFIELD; f++) D.f[b][f] = fields + ((size_t)b * NFIELD + f) * D.ncellp * m->esz;
       if ((e = dalloc(H.allocs, &D.ub[b], 3 * npc * m->esz, m->st)) != cudaSuccess) return bail(e, "ub alloc");
     }
     void *bt[7];
@@ -395,6 +467,18 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
     m->eos.cvcp = D0.cvcp;
     m->eos.kap = D0.kap;
   }
+  // TMA tensor maps of the FP32 stencil
+  if (precision == CC_FP32) {
+    std::vector<unsigned char> maps;
+    std::string why;
+    if ((e = make_tensor_maps(m, maps, why)) != cudaSuccess) {
+      cc_destroy(m);
+      return fail(nullptr, CC_ECUDA, "tensor maps: " + why);
+    }
+    if ((e = dalloc(m->allocs, &m->d_tmaps, maps.size(), m->st)) != cudaSuccess) return bail(e, "tensor maps");
+    if ((e = cudaMemcpyAsync(m->d_tmaps, maps.data(), maps.size(), cudaMemcpyHostToDevice, m->st)) != cudaSuccess)
+      return bail(e, "tensor map copy");
+  }
   // device domain table
   if ((e = dalloc(m->allocs, &m->d_doms, sizeof(DomDev) * n, m->st)) != cudaSuccess) return bail(e, "domain table");
   {
@@ -420,25 +504,35 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
       for (auto &H : m->dom) all_tiles += tiles_of(H.D);
       const long long want = SCHED_ITEMS[sc];
       std::vector<WorkItem> items;
-      for (int d = 0; d < n; d++) {
-        DomHost &H = m->dom[d];
-        const DomDev &D = H.D;
-        long long tiles = m->refined ? tiles_of(D) : all_tiles;
-        long long splits = std::max(1LL, (want + tiles - 1) / tiles);
-        int chunk = (int)std::max(8LL, (D.ck1 + splits - 1) / splits);
-        H.item0[sc] = (int)items.size();
-        // tiles start at multiples of 4 in x (16-byte halo rows)
-        const int ib = D.ci0 - ((D.ci0 % 4) + 4) % 4;
-        for (int k0 = 0; k0 < D.ck1; k0 += chunk)
-          for (int j0 = D.cj0; j0 < D.cj1; j0 += TY)
-            for (int i0 = ib; i0 < D.ci1; i0 += TILE_X) {
-              WorkItem w{};
-              w.dom = d; w.i0 = i0; w.j0 = j0; w.k0 = k0; w.k1 = std::min(D.ck1, k0 + chunk);
-              items.push_back(w);
-            }
-        H.nitem[sc] = (int)items.size() - H.item0[sc];
+      // FP32: the tiles of a periodic domain go to the second part, gathered
+      // from cyclic indices; those of a refined box, whose halos never wrap,
+      // to the first, staged with TMA boxes (a domain's tiles stay together,
+      // so that neighbouring tiles, which share halo rows in L2, run together)
+      const bool split = precision == CC_FP32;
+      auto wraps = [&](const DomDev &D, int, int) { return split && D.periodic; };
+      for (int part = 0; part < 2; part++) {
+        for (int d = 0; d < n; d++) {
+          DomHost &H = m->dom[d];
+          const DomDev &D = H.D;
+          long long tiles = m->refined ? tiles_of(D) : all_tiles;
+          long long splits = std::max(1LL, (want + tiles - 1) / tiles);
+          int chunk = (int)std::max(8LL, (D.ck1 + splits - 1) / splits);
+          (part == 0 ? H.item0 : H.witem0)[sc] = (int)items.size();
+          // tiles start at multiples of 4 in x (16-byte halo rows, 16-byte
+          // aligned TMA boxes)
+          const int ib = D.ci0 - ((D.ci0 % 4) + 4) % 4;
+          for (int k0 = 0; k0 < D.ck1; k0 += chunk)
+            for (int j0 = D.cj0; j0 < D.cj1; j0 += TY)
+              for (int i0 = ib; i0 < D.ci1; i0 += TILE_X) {
+                if (wraps(D, i0, j0) != (part == 1)) continue;
+                WorkItem w{};
+                w.dom = d; w.i0 = i0; w.j0 = j0; w.k0 = k0; w.k1 = std::min(D.ck1, k0 + chunk);
+                items.push_back(w);
+              }
+          (part == 0 ? H.nitem : H.nwitem)[sc] = (int)items.size() - (part == 0 ? H.item0 : H.witem0)[sc];
+        }
+        (part == 0 ? m->nitems : m->nwitems)[sc] = (int)items.size() - (part == 0 ? 0 : m->nitems[sc]);
       }
-      m->nitems[sc] = (int)items.size();
       if ((e = dalloc(m->allocs, &m->d_items[sc], sizeof(WorkItem) * items.size(), m->st)) != cudaSuccess)
         return bail(e, "work list");
       if ((e = cudaMemcpyAsync(m->d_items[sc], items.data(), sizeof(WorkItem) * items.size(),
@@ -1189,9 +1283,9 @@ static cc_status step_domains(cc_model *m, int d, long long &nl) {
   const int rC = H0.r[1], rN = H0.r[2], rF = H0.r[3], pr = m->prec;
   cudaStream_t st = m->st;
   StepLaunch L = make_launch(m, d);
-  if (L.nitems > 0) {
+  if (L.nitems > 0 || L.nwitems > 0) {
     CK(m, timed(m, CC_K_FULL, [&] { return launch_full(L, pr, rO, rC, rN, rF, first, st); }), "full-cell stencil");
-    nl++;
+    nl += (L.nitems > 0) + (L.nwitems > 0);
   }
   if (L.ngroups > 0) {
     CK(m, timed(m, CC_K_GROUPS, [&] { return launch_groups(L, pr, rO, rC, rN, rF, first, st); }), "cut cells");

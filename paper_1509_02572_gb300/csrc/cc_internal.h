@@ -250,8 +250,10 @@ struct Eos {
 // step kernels (step.cu)
 struct StepLaunch {
   const DomDev *d_doms;
-  const WorkItem *items;
+  const WorkItem *items;   // the full-cell work items (FP32: those of refined boxes, staged by TMA)
   int nitems;
+  const WorkItem *witems;  // FP32: the items of periodic domains (cyclic gather)
+  int nwitems;
   const GroupRec *groups;
   int ngroups;
   const int32_t *members;
@@ -261,10 +263,12 @@ struct StepLaunch {
   Eos eos;
   int ty;                  // tile height of the work items
   unsigned *watch;         // step watchdog flags (CC_WATCH_*), or null
+  const unsigned char *tmaps;  // FP32: two 128-byte TMA tensor maps per domain (tile heights 8, 16)
 };
 // step watchdog flags, set by the full-cell stencil
 constexpr unsigned WATCH_NONFINITE = 1u;  // a non-finite value was written
 constexpr unsigned WATCH_COURANT = 2u;    // advective Courant number sum_d |u_d| dt / d_d above 1
+constexpr unsigned WATCH_TIMEOUT = 4u;    // a bounded wait inside a kernel ran out (the step is void)
 cudaError_t launch_base(const DomDev &D, int prec, double theta0, double N, double p_surf,
                         double sponge_frac, double tau_max, cudaStream_t st);
 cudaError_t launch_full(const StepLaunch &L, int prec, int rO, int rC, int rN, int rF, int first,

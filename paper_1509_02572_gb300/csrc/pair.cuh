@@ -14,6 +14,62 @@
 // with a cut cell or a refined box has the same bits on both sides.  The
 // x-face between this thread's pair and the next thread's is computed once,
 // by the next thread, and passed with a warp shuffle.
+//
+// Staging, by domain: two instantiations, each launched over its part of the
+// work list.  k_pair<TY, true> takes the tiles of refined boxes, whose haloed
+// planes lie inside the padded arrays: one thread moves each plane with TMA
+// box copies (cp.async.bulk.tensor; one tensor map per domain over its twenty
+// padded field arrays, which lie back to back), completing on an mbarrier per
+// plane in flight, on whose phase the other threads wait.  The box starts two
+// columns left of the tile, on a 16-byte boundary (tiles start at multiples
+// of 4 and the padding is 6 columns); points past the padding arrive as
+// zeros, which no computed point reads.  k_pair<TY, false> takes the tiles of
+// periodic domains, whose halos wrap at the lateral edges (a box cannot), and
+// gathers each plane with per-thread 16-byte cp.async copies from the cyclic
+// indices.  Measured alternatives for the periodic tiles, all slower than the
+// gather: a ghost frame kept current by the writers or by a copy kernel, the
+// two paths mixed in one launch, and the seam tiles in a launch of their own.
+
+__device__ __forceinline__ unsigned smem_u32(const void *p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+// the one arrival of a plane's barrier, with the bytes its copies will bring
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long *bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long *bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
+  return t;
+}
+// waits for the phase of the given parity to complete; false after about two
+// seconds without completion (the caller reports it and stops)
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > 2000000000ull) return false;
+  return true;
+}
+// box copy of the tensor map's box at (x, y, z) into dst, completing on bar
+__device__ __forceinline__ void tma_load3(void *dst, const void *tmap, unsigned long long *bar, int x, int y, int z) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
 
 __device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
 __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
@@ -83,19 +139,47 @@ template <int TYv>
 struct PairCfg {
   static constexpr int TX = TILE_X, TY = TYv, NT = (TILE_X / 2) * TYv, HX = TX + 4, HY = TYv + 4, PL = HX * HY,
                        NPP = PL / 2, NLPP = (NPP + NT - 1) / NT;
+  // pitch of a raw plane slot: whole 128-byte lines, so that every TMA
+  // destination is 128-byte aligned
+  static constexpr int PLP = (PL + 31) / 32 * 32;
 };
 
-template <int TYv>
+// planes in flight at most: five at the start of a column, one per plane after
+constexpr int PAIR_NBAR = 8;
+
+// shared memory of k_pair: the rings of FullSmem, raw slots padded to whole
+// 128-byte lines, and the plane barriers
+template <int PL, int PLP>
+struct PairSmem {
+  float cr[5][PLP], cp[5][PLP];  // raw rho', p' (current level), planes k-1 .. k+3
+  float cm[4][3][PLP];           // raw momentum (current level), planes k-1 .. k+2 (+ in flight)
+  float op[4][PLP];              // raw p' at n-1, planes k .. k+3
+  float om[4][3][PLP];           // raw momentum at n-1, planes k .. k+3
+  float rh[4][PL], th[4][PL];    // total density and total rho theta, planes k-1 .. k+2
+  float uu[3][3][PL];            // corner velocity, planes k-1 .. k+1
+  float to[PL];                  // (rho theta)' at n-1, plane k
+  unsigned long long bar[PAIR_NBAR];
+  int abort;
+};
+
+// TMA: the tiles of the work list are staged with TMA box copies; otherwise
+// (periodic tiles whose halo crosses a lateral edge) by the cyclic gather
+template <int TYv, bool TMA>
 __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
-    k_pair(const DomDev *__restrict__ doms, const WorkItem *__restrict__ items, int rO, int rC, int rN, int rF,
-           int first, const Eos E, unsigned *__restrict__ watch) {
+    k_pair(const DomDev *__restrict__ doms, const WorkItem *__restrict__ items, const unsigned char *__restrict__ tmaps,
+           int rO, int rC, int rN, int rF, int first, const Eos E, unsigned *__restrict__ watch) {
   using C = PairCfg<TYv>;
-  constexpr int NT = C::NT, HX = C::HX, PL = C::PL, NPP = C::NPP, NLPP = C::NLPP;
-  static_assert(HX % 2 == 0, "pairs of points per halo row");
-  extern __shared__ __align__(16) unsigned char smraw[];
-  FullSmem<float, PL> &S = *reinterpret_cast<FullSmem<float, PL> *>(smraw);
+  constexpr int NT = C::NT, HX = C::HX, PL = C::PL, PLP = C::PLP, NPP = C::NPP, NLPP = C::NLPP;
+  static_assert(HX % 4 == 0, "halo rows of whole 16-byte chunks");
+  extern __shared__ __align__(128) unsigned char smraw[];
+  // TMA: the rings start on a 128-byte line (the launch adds 128 bytes for
+  // this) and their raw slots are whole lines
+  using Smem = PairSmem<PL, TMA ? PLP : PL>;
+  Smem &S = *reinterpret_cast<Smem *>(smraw + (TMA ? ((128u - (smem_u32(smraw) & 127u)) & 127u) : 0u));
   const WorkItem W = items[blockIdx.x];
   const DomDev &D = doms[W.dom];
+  // this domain's tensor map for this tile height (two 128-byte maps per domain)
+  const void *tmap = tmaps + (2 * W.dom + (TYv == 16 ? 1 : 0)) * 128;
   const float dt2 = (float)(first ? D.dt : 2.0 * D.dt);
   const float nu = (float)(first ? 0.0 : D.ra_nu);
   const int tid = threadIdx.x;
@@ -140,9 +224,41 @@ __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
       kbv[s][h] = pp < NPP ? D.kb[loff[s][h]] : KB_NONE;
     }
   }
-  // 16-byte chunks of the haloed rows, as in k_full
+  const float *__restrict__ ubC = (const float *)D.ub[rC];
+  const int kmaxp = D.pz - GH - 1;  // highest plane inside the padding
+  // TMA coordinates: box origin (padded x and y of the halo's first point);
+  // z runs over the twenty arrays, level b field f at (b NFIELD + f) pz
+  const int bx = i0 - 2 + GX, by = j0 - 2 + GH, pz = D.pz;
+  const int zC = rC * NFIELD * pz, zO = rO * NFIELD * pz;
+  // the copies of plane kk (thread 0): the current-level momentum when with_m,
+  // the n-1 fields when with_o; planes past the top are never used
+  auto issue = [&](int kk, bool with_m, bool with_o) {
+    const int zc = min(kk, kmaxp) + GH;
+    unsigned long long *bar = &S.bar[(kk - (k0 - 2)) & (PAIR_NBAR - 1)];
+    mbar_expect_tx(bar, (unsigned)((2 + (with_m ? 3 : 0) + (with_o ? 4 : 0)) * PL * sizeof(float)));
+    const int a5 = s5(kk), a4 = s4(kk);
+    tma_load3(S.cr[a5], tmap, bar, bx, by, zC + zc);
+    tma_load3(S.cp[a5], tmap, bar, bx, by, zC + pz + zc);
+    if (with_m) {
+#pragma unroll
+      for (int d = 0; d < 3; d++) tma_load3(S.cm[a4][d], tmap, bar, bx, by, zC + (2 + d) * pz + zc);
+    }
+    if (with_o) {
+      tma_load3(S.op[a4], tmap, bar, bx, by, zO + pz + zc);
+#pragma unroll
+      for (int d = 0; d < 3; d++) tma_load3(S.om[a4][d], tmap, bar, bx, by, zO + (2 + d) * pz + zc);
+    }
+  };
+  // every thread waits for the copies of plane kk; a wait that runs out
+  // marks the block for abort
+  auto wait_plane = [&](int kk) {
+    const int u = kk - (k0 - 2);
+    if (!mbar_wait(&S.bar[u & (PAIR_NBAR - 1)], (unsigned)(u / PAIR_NBAR) & 1u)) S.abort = 1;
+  };
+  // a periodic tile whose halo crosses a lateral edge: 16-byte chunks of the
+  // haloed rows from the cyclic indices, element by element where a chunk
+  // crosses the edge
   constexpr int VEC = 4, CPR = HX / VEC, NCH = CPR * C::HY, NCQ = (NCH + NT - 1) / NT;
-  static_assert(HX % VEC == 0, "halo rows are whole chunks");
   int ch_dst[NCQ], ch_e[NCQ][VEC];
   bool ch_whole[NCQ];
 #pragma unroll
@@ -151,13 +267,11 @@ __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
     const int row = t / CPR, col = t % CPR;
     const int x = i0 - 2 + VEC * col;
     const int rowoff = (row_y(j0 - 2 + row) + GH) * px;
-    ch_dst[q] = t < NCH ? row * HX + VEC * col : -1;
-    ch_whole[q] = D.periodic ? (x >= 0 && x + VEC <= nx) : (x >= -GX && x + VEC <= px - GX);
+    ch_dst[q] = !TMA && t < NCH ? row * HX + VEC * col : -1;
+    ch_whole[q] = x >= 0 && x + VEC <= nx;
 #pragma unroll
     for (int e = 0; e < VEC; e++) ch_e[q][e] = rowoff + col_x(x + e) + GX;
   }
-  const float *__restrict__ ubC = (const float *)D.ub[rC];
-  const int kmaxp = D.pz - GH - 1;
   auto chunk = [&](float *dst, const float *src) {
 #pragma unroll
     for (int q = 0; q < NCQ; q++) {
@@ -170,7 +284,7 @@ __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
       }
     }
   };
-  auto issue = [&](int kk, bool with_m, bool with_o) {
+  auto gather = [&](int kk, bool with_m, bool with_o) {
     const long long zo = (long long)(min(kk, kmaxp) + GH) * plane;
     const int a5 = s5(kk), a4 = s4(kk);
     chunk(S.cr[a5], rpC + zo);
@@ -186,6 +300,21 @@ __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
       chunk(S.om[a4][1], mO1 + zo);
       chunk(S.om[a4][2], mO2 + zo);
     }
+    acommit();
+  };
+  // the copies of plane kk by the path of this kernel, and the wait for them
+  auto stage = [&](int kk, bool with_m, bool with_o) {
+    if constexpr (TMA) {
+      if (tid == 0) issue(kk, with_m, with_o);
+    } else {
+      gather(kk, with_m, with_o);
+    }
+  };
+  auto arrive = [&](int kk) {
+    if constexpr (TMA)
+      wait_plane(kk);
+    else
+      await_groups<0>();
   };
   // totals of plane kk (pairs of halo points)
   auto derive_e = [&](int kk, const float rb, const EosK2 ek) {
@@ -283,8 +412,24 @@ __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
     mreg[a][2] = ld2(S.om[a4][2] + c);
   };
 
-  for (int kk = k0 - 2; kk <= k0 + 2; kk++) issue(kk, kk != k0 - 2, kk != k0 - 2);
-  acommit();
+  // a TMA wait that ran out (the same answer in every thread after a barrier)
+  auto aborted = [&] {
+    if constexpr (TMA)
+      return S.abort != 0;
+    else
+      return false;
+  };
+  if constexpr (TMA) {
+    if (tid == 0) {
+      for (int b = 0; b < PAIR_NBAR; b++) mbar_init(&S.bar[b], 1);
+      S.abort = 0;
+      asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    }
+    __syncthreads();
+  }
+  for (int kk = k0 - 2; kk <= k0 + 2; kk++) stage(kk, kk != k0 - 2, kk != k0 - 2);
+  int issued = k0 + 2;  // last plane whose copies were issued
   {
     const long long o2 = (long long)(k0 - 2 + GH) * plane + own;
     EosK2 ek;
@@ -294,8 +439,11 @@ __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
     mreg[0][1] = ld2(mO1 + o2);
     mreg[0][2] = ld2(mO2 + o2);
   }
-  await_groups<0>();
+  for (int kk = k0 - 2; kk <= k0 + 2; kk++) arrive(kk);
   __syncthreads();
+  // after an abort the set-up below runs on whatever the rings hold (shared
+  // memory only) and the z-march, the one writer of global memory, is skipped
+  const bool started = !aborted();
   for (int kk = k0 - 2; kk <= k0 + 1; kk++) derive(kk);
 #pragma unroll
   for (int a = 1; a < 4; a++) {
@@ -310,7 +458,7 @@ __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
   float2 fz_carry = bc2(0.0f), hz_carry = bc2(0.0f);
   unsigned wflag = 0;
   const float cfx = (float)(D.dt / D.dx), cfy = (float)(D.dt / D.dy), cfz = (float)(D.dt / D.dz);
-  for (int k = k0; k < k1; k++) {
+  for (int k = k0; started && k < k1; k++) {
     const long long o = (long long)(k + GH) * plane + own;
     float2 rO_ = bc2(0.0f);
     if (active) rO_ = ld2(rpO + o);
@@ -320,10 +468,14 @@ __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
     const float rb2 = rhob[k + 2 + GH], tk = tau[k + GH];
     const float rbc[5] = {rhobc[k + GH - 2] * U, rhobc[k + GH - 1] * U, rhobc[k + GH] * U, rhobc[k + GH + 1] * U,
                           rhobc[k + GH + 2] * U};
-    await_groups<0>();
+    arrive(k + 2);
     __syncthreads();
-    issue(k + 3, true, true);
-    acommit();
+    if (aborted()) break;
+    // plane k + 3 is read from the next plane on; the last plane needs k1 + 1
+    if (k + 3 <= k1 + 1) {
+      stage(k + 3, true, true);
+      issued = k + 3;
+    }
     derive_e(k + 2, rb2, ek2);
     velocity(k + 1);
     derive_old_e(k, ek0);
@@ -599,6 +751,16 @@ __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
     }
   }
   await_groups<0>();
+  if (aborted()) {
+    // a plane's copies did not arrive: wait (bounded) for every copy in
+    // flight before the block's shared memory is given up
+    if (tid == 0)
+      for (int kk = max(k0 - 2, issued - (PAIR_NBAR - 1)); kk <= issued; kk++) {
+        const int u = kk - (k0 - 2);
+        mbar_wait(&S.bar[u & (PAIR_NBAR - 1)], (unsigned)(u / PAIR_NBAR) & 1u);
+      }
+    wflag |= WATCH_TIMEOUT;
+  }
   wflag = __reduce_or_sync(0xffffffffu, wflag);
   if (wflag && (tid & 31) == 0 && watch) atomicOr(watch, wflag);
 }

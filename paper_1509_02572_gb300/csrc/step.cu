@@ -20,6 +20,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <algorithm>
+
 #include "cc_internal.h"
 
 namespace cc {
@@ -1559,19 +1561,31 @@ cudaError_t full_t(const StepLaunch &L, int rO, int rC, int rN, int rF, int firs
   if (L.nitems > 0)
     k_full<T, TYv><<<L.nitems, TILE_X * TYv, full_smem<T, TYv>(), st>>>(L.d_doms, L.items, rO, rC, rN, rF,
                                                                         first, L.eos, L.watch);
+  // (FP64 lists are not split; this kernel reads cyclic neighbours itself)
+  if (L.nwitems > 0)
+    k_full<T, TYv><<<L.nwitems, TILE_X * TYv, full_smem<T, TYv>(), st>>>(L.d_doms, L.witems, rO, rC, rN, rF,
+                                                                         first, L.eos, L.watch);
   return cudaGetLastError();
 }
 
-template <int TYv>
+// the shared memory of k_pair; TMA: raw slots of whole 128-byte lines, plus
+// 128 bytes to start the rings on a line
+template <int TYv, bool TMA>
 size_t pair_smem() {
-  return sizeof(FullSmem<float, PairCfg<TYv>::PL>);
+  using C = PairCfg<TYv>;
+  return TMA ? sizeof(PairSmem<C::PL, C::PLP>) + 128 : sizeof(PairSmem<C::PL, C::PL>);
 }
 
+// the items of refined boxes (TMA), then those of periodic domains (gather)
 template <int TYv>
 cudaError_t pair_t(const StepLaunch &L, int rO, int rC, int rN, int rF, int first, cudaStream_t st) {
+  if (!L.tmaps) return cudaErrorInvalidValue;
   if (L.nitems > 0)
-    k_pair<TYv><<<L.nitems, PairCfg<TYv>::NT, pair_smem<TYv>(), st>>>(L.d_doms, L.items, rO, rC, rN, rF, first,
-                                                                      L.eos, L.watch);
+    k_pair<TYv, true><<<L.nitems, PairCfg<TYv>::NT, pair_smem<TYv, true>(), st>>>(L.d_doms, L.items, L.tmaps, rO, rC, rN,
+                                                                            rF, first, L.eos, L.watch);
+  if (L.nwitems > 0)
+    k_pair<TYv, false><<<L.nwitems, PairCfg<TYv>::NT, pair_smem<TYv, false>(), st>>>(L.d_doms, L.witems, L.tmaps, rO, rC,
+                                                                              rN, rF, first, L.eos, L.watch);
   return cudaGetLastError();
 }
 
@@ -1595,8 +1609,10 @@ cudaError_t full_prepare(int prec) {
     if ((e = set(k_full<double, 8>, full_smem<double, 8>())) != cudaSuccess) return e;
     return set(k_full<double, 4>, full_smem<double, 4>());
   }
-  if ((e = set(k_pair<16>, pair_smem<16>())) != cudaSuccess) return e;
-  return set(k_pair<8>, pair_smem<8>());
+  if ((e = set(k_pair<16, true>, pair_smem<16, true>())) != cudaSuccess) return e;
+  if ((e = set(k_pair<16, false>, pair_smem<16, false>())) != cudaSuccess) return e;
+  if ((e = set(k_pair<8, true>, pair_smem<8, true>())) != cudaSuccess) return e;
+  return set(k_pair<8, false>, pair_smem<8, false>());
 }
 
 cudaError_t launch_base(const DomDev &D, int prec, double theta0, double N, double p_surf, double sponge_frac,

@@ -14,11 +14,11 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcutcell.so")
 
-CC_OK, CC_EINVAL, CC_ECUDA, CC_EGEOM, CC_ENUMERIC, CC_ENOMEM, CC_ESTATE = range(7)
+CC_OK, CC_EINVAL, CC_ECUDA, CC_EGEOM, CC_ENUMERIC, CC_ENOMEM, CC_ESTATE, CC_ETIMEOUT = range(8)
 CC_FP64, CC_FP32 = 0, 1
 CC_RHOP, CC_PP, CC_MX, CC_MY, CC_MZ, CC_UB = range(6)
 STATUS = {0: "CC_OK", 1: "CC_EINVAL", 2: "CC_ECUDA", 3: "CC_EGEOM", 4: "CC_ENUMERIC", 5: "CC_ENOMEM",
-          6: "CC_ESTATE"}
+          6: "CC_ESTATE", 7: "CC_ETIMEOUT"}
 HOST_GZ = 2
 
 # every entry point of include/cutcell.h
