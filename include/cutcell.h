@@ -256,6 +256,14 @@ cc_status cc_load(cc_model *m, const char *path);
  * instead of stepping on.  cc_init_state and cc_load clear the flags. */
 cc_status cc_step(cc_model *m, int n);
 
+/* Failure detection test (no counterpart in the paper): with on != 0, every
+ * TMA plane barrier of the FP32 stencil's refined-box kernel expects 16 bytes
+ * more than its copies bring, so each of its bounded waits runs out and the
+ * step watchdog reports CC_ETIMEOUT; nothing faults and the context stays
+ * usable.  Periodic domains (cyclic gather, no barriers) are not affected.
+ * Off by default; drops the captured graphs. */
+cc_status cc_inject_wait_timeout(cc_model *m, int on);
+
 /* CUDA graphs (no counterpart in the paper): with graphs on (the default),
  * cc_step captures the launches of one step (one cycle of level 0 of a
  * refined model) once per arrangement of time levels and schedules, on a

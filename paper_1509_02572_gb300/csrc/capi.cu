@@ -110,6 +110,7 @@ struct cc_model {
   // FP32: TMA tensor maps of the two-cell stencil, two per domain (tile
   // heights 8 and 16), in device memory
   unsigned char *d_tmaps = nullptr;
+  unsigned stall_tx = 0;  // cc_inject_wait_timeout
 
   std::string err;
   std::vector<void *> allocs;
@@ -231,6 +232,7 @@ StepLaunch make_launch(const cc_model *m, int d = -1) {
   L.eos = m->eos;
   L.watch = m->d_watch;
   L.tmaps = m->d_tmaps;
+  L.stall_tx = m->stall_tx;
   if (d >= 0) {
     const DomHost &H = m->dom[d];
     L.items = m->d_items[H.sched] + H.item0[H.sched];
@@ -1439,6 +1441,17 @@ cc_status cc_step(cc_model *m, int n) {
     m->watch_pending = true;
   }
   return r;
+}
+
+cc_status cc_inject_wait_timeout(cc_model *m, int on) {
+  if (!m) return fail(m, CC_EINVAL, "null model");
+  m->stall_tx = on ? 16u : 0u;
+  // captured graphs hold the old launch parameters
+  CK(m, cudaStreamSynchronize(m->st), "inject sync");
+  for (auto &g : m->graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+  m->graphs.clear();
+  return CC_OK;
 }
 
 cc_status cc_graphs_enable(cc_model *m, int on) {

@@ -264,6 +264,7 @@ struct StepLaunch {
   int ty;                  // tile height of the work items
   unsigned *watch;         // step watchdog flags (CC_WATCH_*), or null
   const unsigned char *tmaps;  // FP32: two 128-byte TMA tensor maps per domain (tile heights 8, 16)
+  unsigned stall_tx;           // extra bytes every TMA plane barrier expects (0; the watchdog's test only)
 };
 // step watchdog flags, set by the full-cell stencil
 constexpr unsigned WATCH_NONFINITE = 1u;  // a non-finite value was written

@@ -53,15 +53,17 @@ __device__ __forceinline__ unsigned long long global_ns() {
   asm volatile("mov.u64 %0, %globaltimer;\n" : "=l"(t));
   return t;
 }
-// waits for the phase of the given parity to complete; false after about two
-// seconds without completion (the caller reports it and stops)
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+// waits for the phase of the given parity to complete; false after limit_ns
+// without completion (the caller reports it and stops)
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity, unsigned long long limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   while (!mbar_try_wait(bar, parity))
-    if (global_ns() - t0 > 2000000000ull) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   return true;
 }
+constexpr unsigned long long PAIR_WAIT_NS = 1000000000ull;  // a plane's copies: one second
+constexpr unsigned long long PAIR_DRAIN_NS = 250000000ull;  // after an abort, per plane in flight
 // box copy of the tensor map's box at (x, y, z) into dst, completing on bar
 __device__ __forceinline__ void tma_load3(void *dst, const void *tmap, unsigned long long *bar, int x, int y, int z) {
   asm volatile(
@@ -167,7 +169,8 @@ struct PairSmem {
 template <int TYv, bool TMA>
 __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
     k_pair(const DomDev *__restrict__ doms, const WorkItem *__restrict__ items, const unsigned char *__restrict__ tmaps,
-           int rO, int rC, int rN, int rF, int first, const Eos E, unsigned *__restrict__ watch) {
+           int rO, int rC, int rN, int rF, int first, const Eos E, unsigned *__restrict__ watch,
+           unsigned stall_tx) {
   using C = PairCfg<TYv>;
   constexpr int NT = C::NT, HX = C::HX, PL = C::PL, PLP = C::PLP, NPP = C::NPP, NLPP = C::NLPP;
   static_assert(HX % 4 == 0, "halo rows of whole 16-byte chunks");
@@ -235,7 +238,9 @@ __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
   auto issue = [&](int kk, bool with_m, bool with_o) {
     const int zc = min(kk, kmaxp) + GH;
     unsigned long long *bar = &S.bar[(kk - (k0 - 2)) & (PAIR_NBAR - 1)];
-    mbar_expect_tx(bar, (unsigned)((2 + (with_m ? 3 : 0) + (with_o ? 4 : 0)) * PL * sizeof(float)));
+    // (stall_tx, zero but in the watchdog's test, makes the phase wait for
+    // bytes that never come)
+    mbar_expect_tx(bar, (unsigned)((2 + (with_m ? 3 : 0) + (with_o ? 4 : 0)) * PL * sizeof(float)) + stall_tx);
     const int a5 = s5(kk), a4 = s4(kk);
     tma_load3(S.cr[a5], tmap, bar, bx, by, zC + zc);
     tma_load3(S.cp[a5], tmap, bar, bx, by, zC + pz + zc);
@@ -250,10 +255,15 @@ __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
     }
   };
   // every thread waits for the copies of plane kk; a wait that runs out
-  // marks the block for abort
+  // marks the block for abort, and the thread waits no more
+  bool late = false;
   auto wait_plane = [&](int kk) {
     const int u = kk - (k0 - 2);
-    if (!mbar_wait(&S.bar[u & (PAIR_NBAR - 1)], (unsigned)(u / PAIR_NBAR) & 1u)) S.abort = 1;
+    if (late) return;
+    if (!mbar_wait(&S.bar[u & (PAIR_NBAR - 1)], (unsigned)(u / PAIR_NBAR) & 1u, PAIR_WAIT_NS)) {
+      late = true;
+      S.abort = 1;
+    }
   };
   // a periodic tile whose halo crosses a lateral edge: 16-byte chunks of the
   // haloed rows from the cyclic indices, element by element where a chunk
@@ -757,7 +767,7 @@ __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
     if (tid == 0)
       for (int kk = max(k0 - 2, issued - (PAIR_NBAR - 1)); kk <= issued; kk++) {
         const int u = kk - (k0 - 2);
-        mbar_wait(&S.bar[u & (PAIR_NBAR - 1)], (unsigned)(u / PAIR_NBAR) & 1u);
+        mbar_wait(&S.bar[u & (PAIR_NBAR - 1)], (unsigned)(u / PAIR_NBAR) & 1u, PAIR_DRAIN_NS);
       }
     wflag |= WATCH_TIMEOUT;
   }

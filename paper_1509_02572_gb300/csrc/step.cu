@@ -1581,11 +1581,11 @@ template <int TYv>
 cudaError_t pair_t(const StepLaunch &L, int rO, int rC, int rN, int rF, int first, cudaStream_t st) {
   if (!L.tmaps) return cudaErrorInvalidValue;
   if (L.nitems > 0)
-    k_pair<TYv, true><<<L.nitems, PairCfg<TYv>::NT, pair_smem<TYv, true>(), st>>>(L.d_doms, L.items, L.tmaps, rO, rC, rN,
-                                                                            rF, first, L.eos, L.watch);
+    k_pair<TYv, true><<<L.nitems, PairCfg<TYv>::NT, pair_smem<TYv, true>(), st>>>(
+        L.d_doms, L.items, L.tmaps, rO, rC, rN, rF, first, L.eos, L.watch, L.stall_tx);
   if (L.nwitems > 0)
-    k_pair<TYv, false><<<L.nwitems, PairCfg<TYv>::NT, pair_smem<TYv, false>(), st>>>(L.d_doms, L.witems, L.tmaps, rO, rC,
-                                                                              rN, rF, first, L.eos, L.watch);
+    k_pair<TYv, false><<<L.nwitems, PairCfg<TYv>::NT, pair_smem<TYv, false>(), st>>>(
+        L.d_doms, L.witems, L.tmaps, rO, rC, rN, rF, first, L.eos, L.watch, 0u);
   return cudaGetLastError();
 }
 

@@ -27,7 +27,8 @@ EXPORTS = ("cc_create", "cc_destroy", "cc_last_error", "cc_set_terrain", "cc_bui
            "cc_download_state", "cc_step", "cc_diagnostics", "cc_synchronize", "cc_last_launch_count",
            "cc_profile_enable", "cc_profile_read", "cc_profile_reset", "cc_create_refined",
            "cc_refine_mass", "cc_domain_count", "cc_autotune", "cc_get_schedule", "cc_set_schedule",
-           "cc_graphs_enable", "cc_upload_state_async", "cc_download_state_async", "cc_save", "cc_load",
+           "cc_graphs_enable", "cc_inject_wait_timeout", "cc_upload_state_async", "cc_download_state_async",
+           "cc_save", "cc_load",
            "cc_set_terrain_analytic", "cc_get_terrain", "cc_download_derived", "cc_error_norms", "cc_cbcm_cubes",
            "cc_mass_sum_noalloc", "cc_noalloc_last_error", "cc_upload_state_f32", "cc_download_state_f32",
            "cc_upload_state_f32_async", "cc_download_state_f32_async", "cc_fma_peak")
@@ -121,6 +122,7 @@ def load(path: str = LIB_PATH):
     L.cc_domain_count.argtypes = [vp]
     L.cc_autotune.argtypes = [vp, i]
     L.cc_graphs_enable.argtypes = [vp, i]
+    L.cc_inject_wait_timeout.argtypes = [vp, i]
     L.cc_save.argtypes = [vp, ct.c_char_p]
     L.cc_load.argtypes = [vp, ct.c_char_p]
     L.cc_get_schedule.argtypes = [vp, i, ct.POINTER(i), ct.POINTER(i)]
@@ -371,6 +373,11 @@ class Model:
 
     def graphs(self, on: bool = True):
         self._check(self.L.cc_graphs_enable(self.h, 1 if on else 0))
+
+    def inject_wait_timeout(self, on: bool = True):
+        """Make every bounded TMA wait of the refined-box stencil run out (the
+        step watchdog's test)."""
+        self._check(self.L.cc_inject_wait_timeout(self.h, 1 if on else 0))
 
     def schedule(self, d: int = 0) -> tuple:
         ty, items = ct.c_int(), ct.c_int()

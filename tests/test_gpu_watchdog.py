@@ -1,9 +1,10 @@
 """Step watchdog (no counterpart in the paper).  A non-finite value or a corner
 whose advective Courant number sum_d |u_d| dt / d_d exceeds 1 raises a flag in
 the full-cell stencil; cc_synchronize, and a later cc_step, report it as
-CC_ENUMERIC instead of stepping on silently, and cc_init_state clears it.  The
-faults are planted on the host, in the uploaded state: nothing faults on the
-GPU."""
+CC_ENUMERIC instead of stepping on silently, and cc_init_state clears it.  A
+bounded wait for TMA copies that runs out raises a third flag, reported as
+CC_ETIMEOUT.  The faults are planted on the host, in the uploaded state, or
+by a barrier that expects bytes which never come: nothing faults on the GPU."""
 import numpy as np
 import pytest
 
@@ -71,4 +72,46 @@ def test_watchdog_reports_an_excessive_courant_number(cc):
     with pytest.raises(cc.CutcellError) as e:
         m.synchronize()
     assert e.value.status == cc.CC_ENUMERIC and "Courant" in str(e.value)
+    m.close()
+
+
+def _refined(cc, prec):
+    rc = W.SMALL_REFINED
+    m = cc.RefinedModel(rc.base, rc.boxes, prec)
+    for lev, c in enumerate(m.cfgs):
+        m.set_terrain(lev, rc.finest_heights() if lev == m.nlev - 1 else np.zeros((c.ny, c.nx)))
+    m.build_geometry()
+    return m
+
+
+def test_watchdog_reports_a_tma_wait_that_runs_out(cc):
+    """The refined boxes' FP32 stencil stages its planes with TMA copies and
+    waits for each plane's barrier at most a second.  With every barrier made
+    to expect 16 bytes more than its copies bring, each block's wait runs out:
+    the block stops, drains its copies (bounded) and returns, and the host
+    reads CC_ETIMEOUT.  The context stays usable: the same model, restarted,
+    matches a fresh one bit for bit."""
+    m = _refined(cc, cc.CC_FP32)
+    m.init_state()
+    m.step(1)
+    m.synchronize()
+    m.inject_wait_timeout(True)
+    m.step(1)
+    with pytest.raises(cc.CutcellError) as e:
+        m.synchronize()
+    assert e.value.status == cc.CC_ETIMEOUT and "bounded wait" in str(e.value)
+    with pytest.raises(cc.CutcellError) as e:
+        m.step(1)
+    assert e.value.status == cc.CC_ETIMEOUT
+    m.inject_wait_timeout(False)
+    m.init_state()
+    m.step(3)
+    m.synchronize()
+    fresh = _refined(cc, cc.CC_FP32)
+    fresh.init_state()
+    fresh.step(3)
+    for lev in range(m.nlev):
+        for f in (cc.CC_RHOP, cc.CC_PP, cc.CC_MX, cc.CC_MY, cc.CC_MZ):
+            assert np.array_equal(m.download(lev, f), fresh.download(lev, f)), (lev, f)
+    fresh.close()
     m.close()
