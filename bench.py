@@ -49,7 +49,8 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="ensemble",
-                    choices=["ensemble", "hemisphere", "bell512", "refined", "convergence", "refined-vs-uniform"])
+                    choices=["ensemble", "hemisphere", "bell512", "refined", "refined-blocks", "convergence",
+                             "refined-vs-uniform"])
     ap.add_argument("--seconds", type=float, default=3600.0,
                     help="simulated time of each run of the convergence workload")
     ap.add_argument("--error-steps", type=int, default=0,
@@ -498,9 +499,13 @@ def bench_inflow(cc):
 
 
 def make_refined(cc, rc, prec):
-    m = cc.RefinedModel(rc.base, rc.boxes, prec)
-    for l, c in enumerate(m.cfgs):
-        m.set_terrain(l, rc.finest_heights() if l == m.nlev - 1 else np.zeros((c.ny, c.nx)))
+    m = cc.RefinedModel(rc.base, rc.boxes, prec, xcuts=rc.xcuts, ycuts=rc.ycuts)
+    for l in range(m.nlev):
+        if l == m.nlev - 1:
+            m.set_level_terrain(l, rc.finest_heights())
+        else:
+            c = m.cfgs[l]
+            m.set_terrain(l, np.zeros((c.ny, c.nx)))
     m.build_geometry()
     m.init_state()
     m.autotune(3)
@@ -512,8 +517,9 @@ def refined_cell_updates(model):
     the next finer level does not cover, times its 2^l substeps (the covered
     cells are computed too, but the finer level's values stand for them)."""
     n = 0
-    for l in range(model.nlev):
-        fluid = model.geometry(l)["cls"] != 0
+    for d in range(model.ndom):
+        l = model.blocks[d][0]
+        fluid = model.geometry(d)["cls"] != 0
         if l + 1 < model.nlev:
             nx, ny, nz, ox, oy = model.boxes[l]
             fluid[:nz // 2, oy // 2:(oy + ny) // 2, ox // 2:(ox + nx) // 2] = False
@@ -524,13 +530,14 @@ def refined_cell_updates(model):
 def refined_kfull_bytes(model, dtype):
     """Algorithmic bytes of the full-cell stencil over one cycle (interior
     cells of every level times its substeps)."""
-    return sum(BYTES_PER_CELL[dtype] * c.nx * c.ny * c.nz * 2 ** l for l, c in enumerate(model.cfgs))
+    return sum(BYTES_PER_CELL[dtype] * c.nx * c.ny * c.nz * 2 ** model.blocks[d][0] for d, c in enumerate(model.cfgs))
 
 
-def bench_refined(cc, torch, args, hbm, peak_kind, barrier, world):
+def bench_refined(cc, torch, args, hbm, peak_kind, barrier, world, rc=None, fp64=True):
     """The refined workload: FP32 cycles timed on the device, k_full roofline
-    over all levels, the plain FP64 form and the FP32 error against it."""
-    rc = W.C4_REFINED
+    over all levels, the plain FP64 form and the FP32 error against it (the
+    finest level cut into sibling blocks when rc has cuts)."""
+    rc = W.C4_REFINED if rc is None else rc
     m = make_refined(cc, rc, cc.CC_FP32)
     upd = refined_cell_updates(m)
     clocks = Clocks(int(os.environ.get("LOCAL_RANK", "0")))
@@ -554,9 +561,9 @@ def bench_refined(cc, torch, args, hbm, peak_kind, barrier, world):
     # covered and underground cells of its boxes (frac_computed)
     achieved = BYTES_PER_CELL["f32"] * upd / per_cycle / (kavg / 1e3) / 1e9
     computed = refined_kfull_bytes(m, "f32") / per_cycle / (kavg / 1e3) / 1e9
-    schedules = [list(m.schedule(l)) for l in range(m.nlev)]
+    schedules = [list(m.schedule(m.level_domains(l)[0])) for l in range(m.nlev)]
     out = {"workload": rc.name, "levels": [list(b) for b in rc.boxes], "value": upd * args.steps * world / (ms / 1e3),
-           "schedule": [list(m.schedule(l)) for l in range(m.nlev)],
+           "schedule": schedules,
            "unit": METRIC, "ms_per_step": ms / args.steps, "cell_updates_per_step": upd, "dtype": "f32",
            "gpu_launches": launches, "clocks": clk, "stages": stages,
            "graphs": {"ms_per_step": gms, "value": upd * world / (gms / 1e3), "unit": METRIC,
@@ -569,7 +576,11 @@ def bench_refined(cc, torch, args, hbm, peak_kind, barrier, world):
                         "bytes_per_cell": BYTES_PER_CELL["f32"], "frac_computed": computed / hbm,
                         "how": "80 B per cell update of a cycle (uncovered fluid cells of every level times its "
                                "substeps), per launch averaged over the cycle's launches"}}
-    if not args.no_fp64:
+    if rc.xcuts or rc.ycuts:
+        out["blocks"] = {"xcuts": list(rc.xcuts), "ycuts": list(rc.ycuts), "finest_level_blocks": len(m.level_domains(m.nlev - 1)),
+                         "how": "the 50 m level as sibling blocks of uneven sizes, each with its own ghost shell filled "
+                                "by same-level copies after every step; all blocks in one launch per stage"}
+    if fp64 and not args.no_fp64:
         m64 = make_refined(cc, rc, cc.CC_FP64)
         ks = max(2, min(args.steps, 5))
         m64.step(args.warmup)
@@ -587,7 +598,7 @@ def bench_refined(cc, torch, args, hbm, peak_kind, barrier, world):
         for fname, f in (("rho'", cc.CC_RHOP), ("p'", cc.CC_PP), ("rho u", cc.CC_MX), ("rho v", cc.CC_MY),
                          ("rho w", cc.CC_MZ)):
             num = den = linf = scale = 0.0
-            for l in range(m.nlev):
+            for l in range(m.ndom):
                 a, b = m.download(l, f), m64.download(l, f)
                 num += float(((a - b) ** 2).sum())
                 den += float((b ** 2).sum())
@@ -837,14 +848,16 @@ def main():
         if world > 1:
             dist.destroy_process_group()
         return
-    if args.workload == "refined":
-        r = bench_refined(cc, torch, args, hbm, peak_kind, barrier, world)
+    if args.workload in ("refined", "refined-blocks"):
+        r = bench_refined(cc, torch, args, hbm, peak_kind, barrier, world,
+                          rc=W.C4_BLOCKED if args.workload == "refined-blocks" else W.C4_REFINED)
         msps, rate = job_time_and_rate(r["ms_per_step"], r["cell_updates_per_step"], world, dist)
         line = {"metric": METRIC, "value": rate, "unit": METRIC,
                 "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": msps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
                 "data": "synthetic",
                 "config": {"workload": r["workload"], "levels": r["levels"], "schedule": r["schedule"],
+                           **({"blocks": r["blocks"]} if "blocks" in r else {}),
                            "cell_updates_per_step": r["cell_updates_per_step"],
                            "precision": "fp32 perturbations, fp64 geometry and base state",
                            "l2": "inputs larger than L2 (state of all levels)"},
@@ -1041,6 +1054,8 @@ def main():
         line["refined"] = bench_refined(cc, torch, args, hbm, peak_kind, barrier, world)
         if rank == 0 and world == 1:
             line["refined"]["inflow_face_w"] = bench_inflow(cc)
+        line["refined_blocks"] = bench_refined(cc, torch, args, hbm, peak_kind, barrier, world, rc=W.C4_BLOCKED,
+                                               fp64=False)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:

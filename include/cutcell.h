@@ -357,6 +357,33 @@ typedef struct {
 cc_status cc_create_refined(const cc_config *base, int nlev, const cc_box *boxes, int precision,
                             void *stream, cc_model **out);
 
+/* Sibling blocks (Sec 2.2: a level is made of blocks, each with its own ghost
+ * shell, filled by copies from the blocks next to it on the same level and by
+ * injection from the coarser level elsewhere).  As cc_create_refined, with
+ * the box of the finest level cut at the nxcut x positions xcut[] and the
+ * nycut y positions ycut[] (its cells; even, strictly increasing, every block
+ * at least 18 cells wide) into (nxcut + 1)(nycut + 1) blocks of uneven sizes,
+ * each spanning the level's height.  The blocks are domains nlev - 1 ..
+ * nlev - 2 + (nxcut + 1)(nycut + 1), by y block, then x block; each has its own
+ * padded arrays, cc_set_terrain heights (its corners, zero within 8 corners
+ * of its edges, so the terrain stays clear of the cuts) and host layouts of
+ * its nx, ny.  After every step of the level each block's ghost shell
+ * (4 deep) where it lies in a sibling takes the sibling's cells, corners and
+ * boundary-point velocities (the two time levels the next step reads); the
+ * coarse-fine injection, restriction and flux register run per block over the
+ * faces and cells of the level's outer boundary only.  All blocks of the
+ * level advance in the same launches (one work list over the blocks).  The
+ * arithmetic of every cell is that of the undivided box, so the results equal
+ * its results bit for bit.  nxcut = nycut = 0 is cc_create_refined. */
+cc_status cc_create_refined_blocks(const cc_config *base, int nlev, const cc_box *boxes, int nxcut,
+                                   const int *xcut, int nycut, const int *ycut, int precision, void *stream,
+                                   cc_model **out);
+
+/* Level of domain d (0 for every domain of a model made by cc_create) and the
+ * origin of its block in the level's box (fine cells; 0, 0 for an undivided
+ * level).  Null outputs are skipped. */
+cc_status cc_domain_block(const cc_model *m, int d, int *level, int *ox, int *oy);
+
 /* Two-time-level perturbation mass of a refined model (Sec 2.2, reading of
  * the conservation check): sum over the levels of V rho' over the merged cells
  * of each level outside the box covered by the next finer level, at the
@@ -364,7 +391,8 @@ cc_status cc_create_refined(const cc_config *base, int nlev, const cc_box *boxes
  * out[0] receives the sum (kg).  Synchronises the stream. */
 cc_status cc_refine_mass(cc_model *m, int both, double *out);
 
-/* Number of domains (ensemble members, or levels of a refined model). */
+/* Number of domains (ensemble members, or levels and blocks of a refined
+ * model). */
 int cc_domain_count(const cc_model *m);
 
 /* A cube of the block-structured layout: its refinement level and its index

@@ -38,12 +38,24 @@ struct DomHost {
   int sched = 0;  // full-cell schedule of this level (refined models)
 };
 
-// Coarse-fine link of refined level l >= 1 with level l-1 (host side; the
-// LevelLink holds the device lists)
+// Coarse-fine link of a domain of refined level l >= 1 (a level's box or one
+// of its blocks) with the domain of level l-1 (host side; the LevelLink holds
+// the device lists)
 struct LinkHost {
-  cc_box box{};
+  cc_box box{};                                // this domain's box, in the coarser level's frame
+  int dc = 0;                                  // the coarser level's domain
   int x0 = 0, x1 = 0, y0 = 0, y1 = 0, z1 = 0;  // covered box in coarse cells
   LevelLink L{};
+};
+
+// Domains of a refined model: the level of each domain, its box relative to
+// the coarser level (level >= 1), the whole box of each level, and the origin
+// of each domain's block in its level's box (sibling blocks of the finest level)
+struct Layout {
+  std::vector<int> level;
+  std::vector<cc_box> box;
+  std::vector<cc_box> lev_box;
+  std::vector<std::array<int, 2>> off;
 };
 
 thread_local std::string g_create_error;
@@ -80,7 +92,16 @@ struct cc_model {
   ColItem *d_cols = nullptr;
   int ncols = 0;
   bool refined = false;
-  std::vector<LinkHost> link;  // link[l] for level l >= 1 of a refined model
+  std::vector<LinkHost> link;  // link[d] for every domain d of level >= 1 of a refined model
+  // refined models: the domains of each level (consecutive), the level and
+  // block origin of each domain, each level's whole box; the same-level
+  // copies of each level with sibling blocks
+  int nlev = 0;
+  std::vector<int> lev_first, lev_count, dom_level;
+  std::vector<std::array<int, 2>> blk_off;
+  std::vector<cc_box> lev_box;
+  std::vector<XchItem *> d_xch;
+  std::vector<long long> nxch;
   Eos eos{};                   // equation-of-state coefficients of every domain
   long long last_launches = 0;
   bool geom = false, state = false;
@@ -215,7 +236,9 @@ __global__ void k_gather_raw(const P *src, P *dst, DomDev D, int nlev, int k_fir
 inline unsigned nb256(long long n) { return (unsigned)((n + 255) / 256); }
 
 // launch description of every domain (d < 0) or of domain d alone
-StepLaunch make_launch(const cc_model *m, int d = -1) {
+// The launches of every domain (lev < 0), or of level lev of a refined model
+// (all its blocks: their items, groups and columns are consecutive).
+StepLaunch make_launch(const cc_model *m, int lev = -1) {
   StepLaunch L{};
   L.d_doms = m->d_doms;
   L.items = m->d_items[m->sched];
@@ -233,17 +256,22 @@ StepLaunch make_launch(const cc_model *m, int d = -1) {
   L.watch = m->d_watch;
   L.tmaps = m->d_tmaps;
   L.stall_tx = m->stall_tx;
-  if (d >= 0) {
-    const DomHost &H = m->dom[d];
-    L.items = m->d_items[H.sched] + H.item0[H.sched];
-    L.nitems = H.nitem[H.sched];
-    L.witems = m->d_items[H.sched] + H.witem0[H.sched];
-    L.nwitems = H.nwitem[H.sched];
-    L.ty = sched_tile_y(m->prec, H.sched);
+  if (lev >= 0) {
+    const int d0 = m->lev_first[lev], d1 = d0 + m->lev_count[lev];
+    const DomHost &H = m->dom[d0];
+    const int sc = H.sched;  // the blocks of a level share one schedule
+    L.items = m->d_items[sc] + H.item0[sc];
+    L.witems = m->d_items[sc] + H.witem0[sc];
+    L.ty = sched_tile_y(m->prec, sc);
     L.groups = m->d_groups + H.group0;
-    L.ngroups = H.ngroup;
     L.cols = m->d_cols + H.col0;
-    L.ncols = H.ncol;
+    L.nitems = L.nwitems = L.ngroups = L.ncols = 0;
+    for (int q = d0; q < d1; q++) {
+      L.nitems += m->dom[q].nitem[sc];
+      L.nwitems += m->dom[q].nwitem[sc];
+      L.ngroups += m->dom[q].ngroup;
+      L.ncols += m->dom[q].ncol;
+    }
   }
   return L;
 }
@@ -348,10 +376,10 @@ cudaError_t make_tensor_maps(const cc_model *m, std::vector<unsigned char> &out,
 
 namespace {
 
-// Creates the model of the given domains (shared by cc_create and
-// cc_create_refined); boxes non-empty makes it a refined model.
-cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomKind> &kinds,
-                      const std::vector<cc_box> &boxes, int precision, void *stream, cc_model **out) {
+// Creates the model of the given domains (shared by cc_create and the
+// refined constructors); a non-empty layout makes it a refined model.
+cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomKind> &kinds, const Layout &lay,
+                      int precision, void *stream, cc_model **out) {
   const int n = (int)cfgs.size();
   cc_model *m = new cc_model();
   m->ndom = n;
@@ -359,7 +387,21 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
   m->esz = precision == CC_FP64 ? 8 : 4;
   m->st = (cudaStream_t)stream;
   m->dom.resize(n);
-  m->refined = !boxes.empty();
+  m->refined = !lay.level.empty();
+  m->dom_level.assign(n, 0);
+  m->blk_off.assign(n, {0, 0});
+  if (m->refined) {
+    m->dom_level = lay.level;
+    m->blk_off = lay.off;
+    m->lev_box = lay.lev_box;
+    m->nlev = lay.level.back() + 1;
+    m->lev_first.assign(m->nlev, 0);
+    m->lev_count.assign(m->nlev, 0);
+    for (int d = n - 1; d >= 0; d--) m->lev_first[lay.level[d]] = d;
+    for (int d = 0; d < n; d++) m->lev_count[lay.level[d]]++;
+    m->d_xch.assign(m->nlev, nullptr);
+    m->nxch.assign(m->nlev, 0);
+  }
   cudaError_t e = cudaSuccess;
   auto bail = [&](cudaError_t ee, const char *where) {
     std::string msg = std::string(where) + ": " + cudaGetErrorString(ee);
@@ -386,6 +428,8 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
     D.ra_nu = c.ra_nu;
     D.bc_slip = c.bc_slip;
     D.periodic = kinds[d].periodic;
+    D.gox = m->blk_off[d][0];
+    D.goy = m->blk_off[d][1];
     D.lid = kinds[d].lid;
     D.ztop = kinds[d].ztop;
     if (D.periodic) {
@@ -494,7 +538,7 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
   // domain's computed region, one per schedule (tile height, items per
   // launch): z is split so that every SM gets several work items per launch
   // (all domains of an ensemble share one launch, each level of a refined
-  // model has its own)
+  // model, all its blocks, has its own)
   {
     std::vector<ColItem> cols;
     for (int sc = 0; sc < NSCHED; sc++) {
@@ -504,6 +548,14 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
       };
       long long all_tiles = 0;
       for (auto &H : m->dom) all_tiles += tiles_of(H.D);
+      // the tiles that share a launch with domain d
+      auto launch_tiles = [&](int d) {
+        if (!m->refined) return all_tiles;
+        long long t = 0;
+        const int l = m->dom_level[d];
+        for (int q = m->lev_first[l]; q < m->lev_first[l] + m->lev_count[l]; q++) t += tiles_of(m->dom[q].D);
+        return t;
+      };
       const long long want = SCHED_ITEMS[sc];
       std::vector<WorkItem> items;
       // FP32: the tiles of a periodic domain go to the second part, gathered
@@ -516,7 +568,7 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
         for (int d = 0; d < n; d++) {
           DomHost &H = m->dom[d];
           const DomDev &D = H.D;
-          long long tiles = m->refined ? tiles_of(D) : all_tiles;
+          long long tiles = launch_tiles(d);
           long long splits = std::max(1LL, (want + tiles - 1) / tiles);
           int chunk = (int)std::max(8LL, (D.ck1 + splits - 1) / splits);
           (part == 0 ? H.item0 : H.witem0)[sc] = (int)items.size();
@@ -558,43 +610,103 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
       return bail(e, "column list copy");
     if ((e = cudaStreamSynchronize(m->st)) != cudaSuccess) return bail(e, "sync");
   }
-  // coarse-fine links of a refined model
+  // coarse-fine links of a refined model, one per domain of level >= 1, and
+  // the same-level copies of every level made of sibling blocks
   if (m->refined) {
     m->link.resize(n);
-    for (int l = 1; l < n; l++) {
-      LinkHost &K = m->link[l];
-      K.box = boxes[l - 1];
-      const DomDev &C = m->dom[l - 1].D, &F = m->dom[l].D;
-      const cc_box &b = K.box;
+    std::vector<std::vector<XchItem>> xch(m->nlev);
+    for (int d = 0; d < n; d++) {
+      const int lev = m->dom_level[d];
+      if (lev == 0) continue;
+      LinkHost &K = m->link[d];
+      K.box = lay.box[d];
+      K.dc = m->lev_first[lev - 1];
+      const DomDev &C = m->dom[K.dc].D, &F = m->dom[d].D;
+      const cc_box &b = K.box, &U = m->lev_box[lev];
+      const int bx = m->blk_off[d][0], by = m->blk_off[d][1];
       K.x0 = b.ox / 2; K.x1 = (b.ox + b.nx) / 2;
       K.y0 = b.oy / 2; K.y1 = (b.oy + b.ny) / 2;
       K.z1 = b.nz / 2;
+      // the level's whole box in coarse cells: its outer boundary is the
+      // coarse-fine interface (the faces between siblings are not)
+      const int ux0 = U.ox / 2, ux1 = (U.ox + U.nx) / 2, uy0 = U.oy / 2, uy1 = (U.oy + U.ny) / 2;
+      const bool xlo = bx == 0, xhi = bx + F.nx == U.nx, ylo = by == 0, yhi = by + F.ny == U.ny;
+      // The undivided level integrates its cells -2 .. N+1 and corners
+      // -1 .. N+1 in x and y below level nz + 2 (the ghost layers included),
+      // and every block integrates its own share of them: the point's owner is
+      // the block that holds it once clamped into the level's box.  A point
+      // of this block's ghost shell that the level integrates and another
+      // block owns is copied from the owner after every step; a point outside
+      // the level's box is injected from the coarser level at every coarse
+      // step, as for the undivided level (the ghost layers are both).
+      const int NX = U.nx, NY = U.ny;
+      auto owner = [&](int gx, int gy) {
+        const int cx = std::min(std::max(gx, 0), NX - 1), cy = std::min(std::max(gy, 0), NY - 1);
+        for (int q = m->lev_first[lev]; q < m->lev_first[lev] + m->lev_count[lev]; q++) {
+          const int ox = m->blk_off[q][0], oy = m->blk_off[q][1];
+          const DomDev &Q = m->dom[q].D;
+          if (cx >= ox && cx < ox + Q.nx && cy >= oy && cy < oy + Q.ny) return q;
+        }
+        return d;
+      };
+      auto copy_from = [&](int q, int i, int j, int k, int kind) {
+        const DomDev &Q = m->dom[q].D;
+        const int qi = bx + i - m->blk_off[q][0], qj = by + j - m->blk_off[q][1];
+        XchItem x{};
+        x.ddom = d; x.sdom = q; x.kind = kind;
+        x.dst = kind == XCH_COLUMN ? qidx(F, i, j) : pidx(F, i, j, k);
+        x.src = kind == XCH_COLUMN ? qidx(Q, qi, qj) : pidx(Q, qi, qj, k);
+        xch[lev].push_back(x);
+      };
       std::vector<long long> pcell, pcorn, rcell, rcorn;
-      for (int k = 0; k < F.nz + GH; k++)
+      for (int k = -GH; k < F.nz + GH; k++)
         for (int j = -GH; j < F.ny + GH; j++)
-          for (int i = -GH; i < F.nx + GH; i++)
-            if (!(i >= 0 && i < F.nx && j >= 0 && j < F.ny && k < F.nz)) pcell.push_back(pidx(F, i, j, k));
+          for (int i = -GH; i < F.nx + GH; i++) {
+            if (i >= 0 && i < F.nx && j >= 0 && j < F.ny && k < F.nz) continue;
+            const int gx = bx + i, gy = by + j;
+            const bool inside = gx >= 0 && gx < NX && gy >= 0 && gy < NY && k < F.nz;
+            if (!inside && k >= 0) pcell.push_back(pidx(F, i, j, k));
+            if (gx >= -2 && gx < NX + 2 && gy >= -2 && gy < NY + 2 && k >= 0 && k < F.nz + 2) {
+              const int q = owner(gx, gy);
+              if (q != d) copy_from(q, i, j, k, XCH_CELL);
+            }
+          }
       for (int Kk = -GH + 1; Kk < F.nz + GH; Kk++)
         for (int J = -GH; J < F.ny + GH; J++)
-          for (int I = -GH; I < F.nx + GH; I++)
-            if (!(I >= 0 && I <= F.nx && J >= 0 && J <= F.ny && Kk <= F.nz))
-              pcorn.push_back(pidx(F, I, J, Kk));
+          for (int I = -GH; I < F.nx + GH; I++) {
+            if (I >= 0 && I <= F.nx && J >= 0 && J <= F.ny && Kk <= F.nz) continue;
+            const int gx = bx + I, gy = by + J;
+            const bool inside = gx >= 0 && gx <= NX && gy >= 0 && gy <= NY && Kk <= F.nz;
+            if (!inside) pcorn.push_back(pidx(F, I, J, Kk));
+            if (gx >= -1 && gx < NX + 2 && gy >= -1 && gy < NY + 2 && Kk < F.nz + 2) {
+              const int q = owner(gx, gy);
+              if (q != d) copy_from(q, I, J, Kk, XCH_CORNER);
+            }
+          }
+      for (int J = -GH; J < F.ny + GH; J++)
+        for (int I = -GH; I < F.nx + GH; I++) {
+          if (I >= 0 && I <= F.nx && J >= 0 && J <= F.ny) continue;
+          const int gx = bx + I, gy = by + J;
+          if (gx >= -1 && gx < NX + 2 && gy >= -1 && gy < NY + 2) {
+            const int q = owner(gx, gy);
+            if (q != d) copy_from(q, I, J, 0, XCH_COLUMN);
+          }
+        }
+      // restriction: the coarse cells and corners of this domain within GH
+      // of the level's outer boundary (a corner on a cut between siblings
+      // belongs to the block on its high side)
       for (int kc = 0; kc < K.z1; kc++)
         for (int jc = K.y0; jc < K.y1; jc++)
           for (int ic = K.x0; ic < K.x1; ic++) {
-            int dd = std::min({ic - K.x0, K.x1 - 1 - ic, jc - K.y0, K.y1 - 1 - jc, K.z1 - 1 - kc});
+            int dd = std::min({ic - ux0, ux1 - 1 - ic, jc - uy0, uy1 - 1 - jc, K.z1 - 1 - kc});
             if (dd < GH) rcell.push_back(pidx(C, ic, jc, kc));
           }
       for (int Kc = 1; Kc <= K.z1; Kc++)
-        for (int Jc = K.y0; Jc <= K.y1; Jc++)
-          for (int Ic = K.x0; Ic <= K.x1; Ic++) {
-            int dd = std::min({Ic - K.x0, K.x1 - Ic, Jc - K.y0, K.y1 - Jc, K.z1 - Kc});
+        for (int Jc = K.y0; Jc <= K.y1 - (yhi ? 0 : 1); Jc++)
+          for (int Ic = K.x0; Ic <= K.x1 - (xhi ? 0 : 1); Ic++) {
+            int dd = std::min({Ic - ux0, ux1 - Ic, Jc - uy0, uy1 - Jc, K.z1 - Kc});
             if (dd <= GH) rcorn.push_back(pidx(C, Ic, Jc, Kc));
           }
-      // interface faces (x low, x high, y low, y high, top); the coarse cells
-      // on both sides of each one take the register flux through it (the
-      // covered side is restricted afterwards, but the velocity diagnosis of
-      // the corners on the box boundary reads its new density first)
       std::vector<IfaceFace> faces;
       std::vector<IfaceCell> icells;
       std::map<long long, int> where;
@@ -618,17 +730,22 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
         touch(lo_i, lo_j, lo_k, ax * 2 + 1, q);
         touch(hi_i, hi_j, hi_k, ax * 2 + 0, q);
       };
+      // (only the faces on the level's outer boundary)
       for (int sd = 0; sd < 2; sd++)
-        for (int kc = 0; kc < K.z1; kc++)
-          for (int jc = K.y0; jc < K.y1; jc++) add(0, sd ? b.nx : 0, 2 * jc - b.oy, 2 * kc, sd ? K.x1 : K.x0, jc, kc);
+        if (sd ? xhi : xlo)
+          for (int kc = 0; kc < K.z1; kc++)
+            for (int jc = K.y0; jc < K.y1; jc++)
+              add(0, sd ? b.nx : 0, 2 * jc - b.oy, 2 * kc, sd ? K.x1 : K.x0, jc, kc);
       for (int sd = 0; sd < 2; sd++)
-        for (int kc = 0; kc < K.z1; kc++)
-          for (int ic = K.x0; ic < K.x1; ic++) add(1, 2 * ic - b.ox, sd ? b.ny : 0, 2 * kc, ic, sd ? K.y1 : K.y0, kc);
+        if (sd ? yhi : ylo)
+          for (int kc = 0; kc < K.z1; kc++)
+            for (int ic = K.x0; ic < K.x1; ic++)
+              add(1, 2 * ic - b.ox, sd ? b.ny : 0, 2 * kc, ic, sd ? K.y1 : K.y0, kc);
       for (int jc = K.y0; jc < K.y1; jc++)
         for (int ic = K.x0; ic < K.x1; ic++) add(2, 2 * ic - b.ox, 2 * jc - b.oy, b.nz, ic, jc, K.z1);
       LevelLink &L = K.L;
-      L.dc = m->d_doms + (l - 1);
-      L.df = m->d_doms + l;
+      L.dc = m->d_doms + K.dc;
+      L.df = m->d_doms + d;
       L.ox = b.ox;
       L.oy = b.oy;
       auto up = [&](auto &vec, auto **dst) -> cudaError_t {
@@ -657,6 +774,15 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
           (e = dalloc(m->allocs, &L.regh, faces.size() * m->esz, m->st)))
         return bail(e, "flux register");
       if ((e = cudaStreamSynchronize(m->st)) != cudaSuccess) return bail(e, "sync");
+    }
+    for (int l = 0; l < m->nlev; l++) {
+      if (xch[l].empty()) continue;
+      if ((e = dalloc(m->allocs, &m->d_xch[l], sizeof(XchItem) * xch[l].size(), m->st)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(m->d_xch[l], xch[l].data(), sizeof(XchItem) * xch[l].size(), cudaMemcpyHostToDevice,
+                               m->st)) != cudaSuccess ||
+          (e = cudaStreamSynchronize(m->st)) != cudaSuccess)
+        return bail(e, "same-level copies");
+      m->nxch[l] = (long long)xch[l].size();
     }
   }
   if ((e = dalloc(m->allocs, &m->d_diag, sizeof(double) * (8 + 7 * 256), m->st)) != cudaSuccess) return bail(e, "diag");
@@ -692,14 +818,22 @@ cc_status cc_create(const cc_config *cfgs, int n, int precision, void *stream, c
       return fail(nullptr, CC_EINVAL, "all domains of a model share R, cp and p0");
     kinds[d] = DomKind{1, 1, cfgs[d].nz * cfgs[d].dz};
   }
-  return create_impl(cv, kinds, {}, precision, stream, out);
+  return create_impl(cv, kinds, Layout{}, precision, stream, out);
 }
 
 cc_status cc_create_refined(const cc_config *base, int nlev, const cc_box *boxes, int precision, void *stream,
                             cc_model **out) {
+  return cc_create_refined_blocks(base, nlev, boxes, 0, nullptr, 0, nullptr, precision, stream, out);
+}
+
+cc_status cc_create_refined_blocks(const cc_config *base, int nlev, const cc_box *boxes, int nxcut,
+                                   const int *xcut, int nycut, const int *ycut, int precision, void *stream,
+                                   cc_model **out) {
   if (!out) return fail(nullptr, CC_EINVAL, "out is NULL");
   *out = nullptr;
   if (!base || !boxes) return fail(nullptr, CC_EINVAL, "null argument");
+  if (nxcut < 0 || nycut < 0 || (nxcut > 0 && !xcut) || (nycut > 0 && !ycut))
+    return fail(nullptr, CC_EINVAL, "bad cut lists");
   if (nlev < 2 || nlev > 8) return fail(nullptr, CC_EINVAL, "nlev must be 2 .. 8");
   if (precision != CC_FP64 && precision != CC_FP32) return fail(nullptr, CC_EINVAL, "precision must be CC_FP64 or CC_FP32");
   std::string why;
@@ -729,7 +863,56 @@ cc_status cc_create_refined(const cc_config *base, int nlev, const cc_box *boxes
     cv[l] = f;
     kinds[l] = DomKind{0, 0, ztop};
   }
-  return create_impl(cv, kinds, bx, precision, stream, out);
+  // the finest level's blocks: cut positions (even, increasing, every block
+  // wider than twice the flat margin), blocks by y, then x
+  const cc_box &fb = bx[nlev - 2];
+  std::vector<int> xs{0}, ys{0};
+  for (int a = 0; a < nxcut; a++) xs.push_back(xcut[a]);
+  for (int a = 0; a < nycut; a++) ys.push_back(ycut[a]);
+  xs.push_back(fb.nx);
+  ys.push_back(fb.ny);
+  for (size_t a = 1; a < xs.size(); a++)
+    if ((xs[a] & 1) || xs[a] - xs[a - 1] <= 2 * FLAT_MARGIN + 1)
+      return fail(nullptr, CC_EINVAL, "x cuts must be even, increasing and leave blocks of at least 18 cells");
+  for (size_t a = 1; a < ys.size(); a++)
+    if ((ys[a] & 1) || ys[a] - ys[a - 1] <= 2 * FLAT_MARGIN + 1)
+      return fail(nullptr, CC_EINVAL, "y cuts must be even, increasing and leave blocks of at least 18 cells");
+  Layout lay;
+  lay.lev_box.assign(nlev, cc_box{});
+  for (int l = 1; l < nlev; l++) lay.lev_box[l] = bx[l - 1];
+  std::vector<cc_config> cvb(cv.begin(), cv.end() - 1);
+  std::vector<DomKind> kb(kinds.begin(), kinds.end() - 1);
+  for (int l = 0; l < nlev - 1; l++) {
+    lay.level.push_back(l);
+    lay.box.push_back(l ? bx[l - 1] : cc_box{});
+    lay.off.push_back({0, 0});
+  }
+  for (size_t by = 0; by + 1 < ys.size(); by++)
+    for (size_t bxi = 0; bxi + 1 < xs.size(); bxi++) {
+      cc_config f = cv[nlev - 1];
+      f.nx = xs[bxi + 1] - xs[bxi];
+      f.ny = ys[by + 1] - ys[by];
+      cc_box b = fb;
+      b.ox = fb.ox + xs[bxi];
+      b.oy = fb.oy + ys[by];
+      b.nx = f.nx;
+      b.ny = f.ny;
+      cvb.push_back(f);
+      kb.push_back(kinds[nlev - 1]);
+      lay.level.push_back(nlev - 1);
+      lay.box.push_back(b);
+      lay.off.push_back({xs[bxi], ys[by]});
+    }
+  return create_impl(cvb, kb, lay, precision, stream, out);
+}
+
+cc_status cc_domain_block(const cc_model *m, int d, int *level, int *ox, int *oy) {
+  if (!m) return fail(nullptr, CC_EINVAL, "null model");
+  if (d < 0 || d >= m->ndom) return fail(const_cast<cc_model *>(m), CC_EINVAL, "domain index out of range");
+  if (level) *level = m->dom_level[d];
+  if (ox) *ox = m->blk_off[d][0];
+  if (oy) *oy = m->blk_off[d][1];
+  return CC_OK;
 }
 
 int cc_domain_count(const cc_model *m) { return m ? m->ndom : 0; }
@@ -847,11 +1030,11 @@ cc_status cc_build_geometry(cc_model *m) {
     if (!H.terrain) return fail(m, CC_ESTATE, "terrain not set for every domain");
   // a coarser level is flat around every covered box: the coarse cells that
   // exchange fluxes with the box are full cells
-  for (int l = 1; l < (int)m->link.size(); l++) {
-    const LinkHost &K = m->link[l];
-    const DomHost &C = m->dom[l - 1];
-    for (int J = K.y0 - 4; J <= K.y1 + 4; J++)
-      for (int I = K.x0 - 4; I <= K.x1 + 4; I++)
+  for (int l = 1; l < m->nlev; l++) {
+    const cc_box &U = m->lev_box[l];
+    const DomHost &C = m->dom[m->lev_first[l - 1]];
+    for (int J = U.oy / 2 - 4; J <= (U.oy + U.ny) / 2 + 4; J++)
+      for (int I = U.ox / 2 - 4; I <= (U.ox + U.nx) / 2 + 4; I++)
         if (C.hh[(long long)wrapi(J, C.cfg.ny) * C.cfg.nx + wrapi(I, C.cfg.nx)] != 0.0)
           return fail(m, CC_EGEOM, "level " + std::to_string(l - 1) +
                                        ": terrain must be flat within 4 cells of the refined box");
@@ -1020,13 +1203,20 @@ cc_status cc_init_state(cc_model *m) {
        "init momentum");
   StepLaunch L = make_launch(m);
   CK(m, launch_diagnose(L, m->prec, 1, 1, 1, 1, 1, 0, m->st), "init diagnose");
-  // refined model: fine -> coarse, then coarse -> fine, down the hierarchy
-  for (int l = 1; l < (int)m->link.size(); l++) {
-    const LevelLink &K = m->link[l].L;
-    CK(m, cudaMemsetAsync(K.regm, 0, K.nfaces * m->esz, m->st), "register reset");
-    CK(m, cudaMemsetAsync(K.regh, 0, K.nfaces * m->esz, m->st), "register reset");
-    CK(m, launch_restrict(K, m->prec, m->dom[l].r[1], m->st), "init restrict");
-    CK(m, launch_prolong(K, m->prec, m->dom[l - 1].r[1], m->st), "init prolong");
+  // refined model: fine -> coarse, then coarse -> fine, down the hierarchy,
+  // then the same-level copies between the blocks of a level
+  for (int l = 1; l < m->nlev; l++) {
+    const int d0 = m->lev_first[l], d1 = d0 + m->lev_count[l];
+    for (int d = d0; d < d1; d++) {
+      const LevelLink &K = m->link[d].L;
+      CK(m, cudaMemsetAsync(K.regm, 0, K.nfaces * m->esz, m->st), "register reset");
+      CK(m, cudaMemsetAsync(K.regh, 0, K.nfaces * m->esz, m->st), "register reset");
+      CK(m, launch_restrict(K, m->prec, m->dom[d].r[1], m->st), "init restrict");
+    }
+    for (int d = d0; d < d1; d++)
+      CK(m, launch_prolong(m->link[d].L, m->prec, m->dom[m->link[d].dc].r[1], m->st), "init prolong");
+    CK(m, launch_exchange(m->d_doms, m->d_xch[l], m->nxch[l], m->prec, m->dom[d0].r[0], m->dom[d0].r[1], m->st),
+       "init same-level copies");
   }
   cc_status w = watch_reset(m);
   if (w != CC_OK) return w;
@@ -1278,13 +1468,16 @@ static cudaError_t timed(cc_model *m, int kid, F &&launch) {
 // One step of domain d (every domain of an ensemble when d < 0): the
 // full-cell stencil, the cut cells, the coarse cells next to a refined box
 // (flux register), then the velocity diagnosis; rotates the roles.
-static cc_status step_domains(cc_model *m, int d, long long &nl) {
-  DomHost &H0 = m->dom[d < 0 ? 0 : d];
+// One step of every domain (lev < 0) or of level lev of a refined model (all
+// its blocks), with the flux-register corrections of the next finer level's
+// interface cells, then the same-level copies between the level's blocks.
+static cc_status step_domains(cc_model *m, int lev, long long &nl) {
+  DomHost &H0 = m->dom[lev < 0 ? 0 : m->lev_first[lev]];
   const int first = H0.nsteps == 0;
   const int rO = first ? H0.r[1] : H0.r[0];
   const int rC = H0.r[1], rN = H0.r[2], rF = H0.r[3], pr = m->prec;
   cudaStream_t st = m->st;
-  StepLaunch L = make_launch(m, d);
+  StepLaunch L = make_launch(m, lev);
   if (L.nitems > 0 || L.nwitems > 0) {
     CK(m, timed(m, CC_K_FULL, [&] { return launch_full(L, pr, rO, rC, rN, rF, first, st); }), "full-cell stencil");
     nl += (L.nitems > 0) + (L.nwitems > 0);
@@ -1293,17 +1486,21 @@ static cc_status step_domains(cc_model *m, int d, long long &nl) {
     CK(m, timed(m, CC_K_GROUPS, [&] { return launch_groups(L, pr, rO, rC, rN, rF, first, st); }), "cut cells");
     nl++;
   }
-  if (d >= 0 && d + 1 < (int)m->link.size()) {
-    const LevelLink &K = m->link[d + 1].L;
-    CK(m, timed(m, CC_K_REFINE, [&] { return launch_iface(K, pr, rO, rC, rN, rF, first, st); }), "flux register");
-    nl++;
+  if (lev >= 0 && lev + 1 < m->nlev) {
+    const int f0 = m->lev_first[lev + 1], f1 = f0 + m->lev_count[lev + 1];
+    for (int q = f0; q < f1; q++) {
+      const LevelLink &K = m->link[q].L;
+      CK(m, timed(m, CC_K_REFINE, [&] { return launch_iface(K, pr, rO, rC, rN, rF, first, st); }),
+         "flux register");
+      nl++;
+    }
   }
   if (L.ncols > 0) {
     CK(m, timed(m, CC_K_DIAGNOSE, [&] { return launch_diagnose(L, pr, rN, rC, rO, rF, first, 1, st); }),
        "velocity diagnosis");
     nl++;
   }
-  int lo = d < 0 ? 0 : d, hi = d < 0 ? m->ndom : d + 1;
+  int lo = lev < 0 ? 0 : m->lev_first[lev], hi = lev < 0 ? m->ndom : lo + m->lev_count[lev];
   for (int q = lo; q < hi; q++) {
     DomHost &H = m->dom[q];
     int o = H.r[0], c = H.r[1];
@@ -1312,6 +1509,15 @@ static cc_status step_domains(cc_model *m, int d, long long &nl) {
     H.r[2] = o;
     H.r[3] = c;
     H.nsteps++;
+  }
+  // the blocks' ghost shells where they lie in siblings: the new current and
+  // the filtered old level, the two the next step reads
+  if (lev >= 0 && m->nxch[lev] > 0) {
+    CK(m, timed(m, CC_K_REFINE, [&] {
+         return launch_exchange(m->d_doms, m->d_xch[lev], m->nxch[lev], pr, H0.r[0], H0.r[1], st);
+       }),
+       "same-level copies");
+    nl++;
   }
   return CC_OK;
 }
@@ -1324,13 +1530,16 @@ static cc_status step_domains(cc_model *m, int d, long long &nl) {
 static cc_status cycle(cc_model *m, int l, long long &nl) {
   const int pr = m->prec;
   cudaStream_t st = m->st;
-  const bool fine = l + 1 < m->ndom;
+  const bool fine = l + 1 < m->nlev;
+  const int f0 = fine ? m->lev_first[l + 1] : 0, f1 = fine ? f0 + m->lev_count[l + 1] : 0;
   if (fine) {
-    const LevelLink &K = m->link[l + 1].L;
     for (int s = 0; s < 2; s++) {
-      CK(m, timed(m, CC_K_REFINE, [&] { return launch_register_add(K, pr, m->dom[l + 1].r[1], st); }),
-         "register add");
-      nl++;
+      for (int q = f0; q < f1; q++) {
+        const LevelLink &K = m->link[q].L;
+        CK(m, timed(m, CC_K_REFINE, [&] { return launch_register_add(K, pr, m->dom[q].r[1], st); }),
+           "register add");
+        nl++;
+      }
       cc_status r = cycle(m, l + 1, nl);
       if (r != CC_OK) return r;
     }
@@ -1338,11 +1547,20 @@ static cc_status cycle(cc_model *m, int l, long long &nl) {
   cc_status r = step_domains(m, l, nl);
   if (r != CC_OK) return r;
   if (fine) {
-    const LevelLink &K = m->link[l + 1].L;
-    CK(m, timed(m, CC_K_REFINE, [&] { return launch_register_clear(K, pr, st); }), "register clear");
-    CK(m, timed(m, CC_K_REFINE, [&] { return launch_restrict(K, pr, m->dom[l + 1].r[1], st); }), "restrict");
-    CK(m, timed(m, CC_K_REFINE, [&] { return launch_prolong(K, pr, m->dom[l].r[1], st); }), "prolong");
-    nl += 3;
+    // every block restricted before any is prolonged: the injection into a
+    // block's shell reads coarse corners that a neighbouring block restricts
+    const int dc = m->lev_first[l];
+    for (int q = f0; q < f1; q++) {
+      const LevelLink &K = m->link[q].L;
+      CK(m, timed(m, CC_K_REFINE, [&] { return launch_register_clear(K, pr, st); }), "register clear");
+      CK(m, timed(m, CC_K_REFINE, [&] { return launch_restrict(K, pr, m->dom[q].r[1], st); }), "restrict");
+      nl += 2;
+    }
+    for (int q = f0; q < f1; q++) {
+      const LevelLink &K = m->link[q].L;
+      CK(m, timed(m, CC_K_REFINE, [&] { return launch_prolong(K, pr, m->dom[dc].r[1], st); }), "prolong");
+      nl++;
+    }
   }
   return CC_OK;
 }
@@ -1598,8 +1816,9 @@ cc_status cc_load(cc_model *m, const char *path) {
     m->dom[d].nsteps = cd[d].nsteps;
   }
   // the flux registers are empty between steps
-  for (int l = 1; l < (int)m->link.size(); l++) {
-    const LevelLink &K = m->link[l].L;
+  for (int d = 0; d < (int)m->link.size(); d++) {
+    if (m->dom_level[d] == 0) continue;
+    const LevelLink &K = m->link[d].L;
     CK(m, cudaMemsetAsync(K.regm, 0, K.nfaces * m->esz, m->st), "register reset");
     CK(m, cudaMemsetAsync(K.regh, 0, K.nfaces * m->esz, m->st), "register reset");
   }
@@ -1637,14 +1856,16 @@ cc_status cc_refine_mass(cc_model *m, int both, double *out) {
   if (!m->refined) return fail(m, CC_EINVAL, "not a refined model");
   if (!m->state) return fail(m, CC_ESTATE, "state not initialised");
   double tot = 0.0;
-  for (int l = 0; l < m->ndom; l++) {
-    const DomHost &H = m->dom[l];
+  for (int d = 0; d < m->ndom; d++) {
+    const DomHost &H = m->dom[d];
+    const int l = m->dom_level[d];
     int x0 = 0, x1 = 0, y0 = 0, y1 = 0, z1 = 0;
-    if (l + 1 < m->ndom) {
-      const LinkHost &K = m->link[l + 1];
-      x0 = K.x0; x1 = K.x1; y0 = K.y0; y1 = K.y1; z1 = K.z1;
+    if (l + 1 < m->nlev) {
+      // the whole box of the next finer level (all its blocks)
+      const cc_box &U = m->lev_box[l + 1];
+      x0 = U.ox / 2; x1 = (U.ox + U.nx) / 2; y0 = U.oy / 2; y1 = (U.oy + U.ny) / 2; z1 = U.nz / 2;
     }
-    CK(m, launch_mass_active(H.D, m->d_doms + l, m->prec, H.r[1], H.r[0], both, x0, x1, y0, y1, z1, m->d_diag,
+    CK(m, launch_mass_active(H.D, m->d_doms + d, m->prec, H.r[1], H.r[0], both, x0, x1, y0, y1, z1, m->d_diag,
                              m->st),
        "mass");
     double h = 0.0;
@@ -1667,18 +1888,25 @@ cc_status cc_autotune(cc_model *m, int reps) {
     return fail(m, CC_ECUDA, "event");
   }
   cc_status res = CC_OK;
-  // launch groups: the whole ensemble, or each level of a refined model
-  const int ngroup = m->refined ? m->ndom : 1;
+  // launch groups: the whole ensemble, or each level of a refined model (all
+  // its blocks, which share the schedule)
+  const int ngroup = m->refined ? m->nlev : 1;
   for (int g = 0; g < ngroup && res == CC_OK; g++) {
     const int d = m->refined ? g : -1;
-    DomHost &H = m->dom[m->refined ? g : 0];
+    DomHost &H = m->dom[m->refined ? m->lev_first[g] : 0];
+    auto set_sched = [&](int sc) {
+      if (!m->refined) {
+        m->sched = sc;
+        return;
+      }
+      for (int q = m->lev_first[g]; q < m->lev_first[g] + m->lev_count[g]; q++) m->dom[q].sched = sc;
+    };
     const int first = H.nsteps == 0;
     const int rO = first ? H.r[1] : H.r[0], rC = H.r[1], rN = H.r[2], rF = H.r[3];
     int best = 0;
     float best_ms = 0;
     for (int sc = 0; sc < NSCHED && res == CC_OK; sc++) {
-      if (m->refined) H.sched = sc;
-      else m->sched = sc;
+      set_sched(sc);
       StepLaunch L = make_launch(m, d);
       // the stencil writes only the new and filtered levels, which the next
       // step overwrites with the same values: timing it leaves the state alone
@@ -1698,8 +1926,7 @@ cc_status cc_autotune(cc_model *m, int reps) {
         best_ms = ms;
       }
     }
-    if (m->refined) H.sched = best;
-    else m->sched = best;
+    set_sched(best);
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
@@ -1722,8 +1949,13 @@ cc_status cc_set_schedule(cc_model *m, int d, int tile_y, int items_per_launch) 
   if (d < 0 || d >= m->ndom) return fail(m, CC_EINVAL, "domain index out of range");
   for (int sc = 0; sc < NSCHED; sc++)
     if (sched_tile_y(m->prec, sc) == tile_y && SCHED_ITEMS[sc] == items_per_launch) {
-      if (m->refined) m->dom[d].sched = sc;
-      else m->sched = sc;
+      if (m->refined) {
+        // every block of the domain's level (one launch)
+        const int l = m->dom_level[d];
+        for (int q = m->lev_first[l]; q < m->lev_first[l] + m->lev_count[l]; q++) m->dom[q].sched = sc;
+      } else {
+        m->sched = sc;
+      }
       return CC_OK;
     }
   return fail(m, CC_EINVAL, "no such schedule");

@@ -61,6 +61,8 @@ struct DomDev {
   double ra_nu;              // Robert-Asselin coefficient
   int bc_slip;
   int periodic;              // lateral indices wrap (cyclic boundaries)
+  int gox, goy;              // origin of this block in its level's box (cells; 0 for a whole level):
+                             // the geometry forms positions from the level's indices
   int lid;                   // the top is the rigid lid (else a refinement face)
   // computed region: cells ci0 <= i < ci1, cj0 <= j < cj1, 0 <= k < ck1;
   // corner columns qi0 <= I < ci1, qj0 <= J < cj1
@@ -222,6 +224,20 @@ struct LevelLink {
   int nicells;
   void *regm, *regh;         // register sums per face (model precision)
 };
+// Same-level copy between sibling blocks of a level (Sec 2.2): a point of a
+// block's ghost shell that lies in a sibling takes the sibling's value.
+// kind: XCH_CELL (rho', p' at a cell), XCH_CORNER (the three momenta at a
+// corner), XCH_COLUMN (the boundary-point velocity of a corner column; the
+// offsets are padded column indices).  Offsets are padded indices of the
+// destination and the source domain.
+enum { XCH_CELL = 0, XCH_CORNER = 1, XCH_COLUMN = 2 };
+struct XchItem {
+  long long dst, src;
+  int ddom, sdom, kind, pad;
+};
+// copies the listed points of the two time levels r0 and r1 (ub: r1 only)
+cudaError_t launch_exchange(const DomDev *d_doms, const XchItem *items, long long n, int prec, int r0, int r1,
+                            cudaStream_t st);
 cudaError_t launch_prolong(const LevelLink &L, int prec, int rC, cudaStream_t st);
 cudaError_t launch_restrict(const LevelLink &L, int prec, int rF, cudaStream_t st);
 cudaError_t launch_register_add(const LevelLink &L, int prec, int rF, cudaStream_t st);

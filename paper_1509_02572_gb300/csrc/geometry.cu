@@ -425,9 +425,11 @@ __global__ void k_bstencil(DomDev D, const double *hc, const int8_t *vcls, int32
   while (K0 * D.dz <= hh) K0++;
   for (int K = K0; K < K0 + 8 && K <= ktopsearch; K++) {
     double tt = (K * D.dz - hh) / nzv;
-    double xN = I * D.dx + tt * nxv, yN = J * D.dy + tt * nyv;
+    // position from the level's indices (a block's origin offsets them), so
+    // that a block and the whole level round alike
+    double xN = (I + D.gox) * D.dx + tt * nxv, yN = (J + D.goy) * D.dy + tt * nyv;
     double fi = floor(xN / D.dx), fj = floor(yN / D.dy);
-    int i0 = (int)fi, j0 = (int)fj;
+    int i0 = (int)fi - D.gox, j0 = (int)fj - D.goy;
     double a = xN / D.dx - fi, b = yN / D.dy - fj;
     bool ok = vcls_at(D, vcls, i0, j0, K) == V_PRED &&
               (a == 0.0 || vcls_at(D, vcls, i0 + 1, j0, K) == V_PRED) &&

@@ -1277,6 +1277,32 @@ __global__ void k_prolong(LevelLink L, int rC) {
   }
 }
 
+// Sibling blocks of one level: one thread per listed ghost-shell point copies
+// the sibling's value at the two time levels the next step reads (Sec 2.2,
+// the same-level copy of the cube-based mesh).  Sources are interior points
+// of the siblings and destinations ghost points, so no thread reads what
+// another writes.
+template <typename T>
+__global__ void k_exchange(const DomDev *__restrict__ doms, const XchItem *__restrict__ x, long long n, int r0,
+                           int r1) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= n) return;
+  const XchItem it = x[t];
+  const DomDev &D = doms[it.ddom], &S = doms[it.sdom];
+  if (it.kind == XCH_COLUMN) {
+    const T *su = (const T *)S.ub[r1];
+    T *du = (T *)D.ub[r1];
+#pragma unroll
+    for (int c = 0; c < 3; c++) du[3 * it.dst + c] = su[3 * it.src + c];
+    return;
+  }
+  const int f0 = it.kind == XCH_CELL ? 0 : 2, f1 = it.kind == XCH_CELL ? 2 : NFIELD;
+  for (int f = f0; f < f1; f++) {
+    ((T *)D.f[r0][f])[it.dst] = ((const T *)S.f[r0][f])[it.src];
+    ((T *)D.f[r1][f])[it.dst] = ((const T *)S.f[r1][f])[it.src];
+  }
+}
+
 // Fine -> coarse: coarse cells near the covered box boundary take the mean of
 // the 8 fine cells they contain; coarse corners inside it or on its lateral
 // and top faces take the coincident fine corner.  All four time-level
@@ -1599,6 +1625,17 @@ cudaError_t groups_t(const StepLaunch &L, int rO, int rC, int rN, int rF, int fi
 }  // namespace
 
 int sched_tile_y(int prec, int s) { return prec == CC_FP64 ? SCHED_TY_F64[s] : SCHED_TY_F32[s]; }
+
+cudaError_t launch_exchange(const DomDev *d_doms, const XchItem *items, long long n, int prec, int r0, int r1,
+                            cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const unsigned blocks = (unsigned)((n + 255) / 256);
+  if (prec == CC_FP64)
+    k_exchange<double><<<blocks, 256, 0, st>>>(d_doms, items, n, r0, r1);
+  else
+    k_exchange<float><<<blocks, 256, 0, st>>>(d_doms, items, n, r0, r1);
+  return cudaGetLastError();
+}
 
 cudaError_t full_prepare(int prec) {
   auto set = [](auto kern, size_t bytes) {

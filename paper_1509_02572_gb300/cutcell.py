@@ -26,7 +26,7 @@ EXPORTS = ("cc_create", "cc_destroy", "cc_last_error", "cc_set_terrain", "cc_bui
            "cc_get_geometry", "cc_get_stencils", "cc_get_groups", "cc_init_state", "cc_upload_state",
            "cc_download_state", "cc_step", "cc_diagnostics", "cc_synchronize", "cc_last_launch_count",
            "cc_profile_enable", "cc_profile_read", "cc_profile_reset", "cc_create_refined",
-           "cc_refine_mass", "cc_domain_count", "cc_autotune", "cc_get_schedule", "cc_set_schedule",
+           "cc_refine_mass", "cc_domain_count", "cc_create_refined_blocks", "cc_domain_block", "cc_autotune", "cc_get_schedule", "cc_set_schedule",
            "cc_graphs_enable", "cc_inject_wait_timeout", "cc_upload_state_async", "cc_download_state_async",
            "cc_save", "cc_load",
            "cc_set_terrain_analytic", "cc_get_terrain", "cc_download_derived", "cc_error_norms", "cc_cbcm_cubes",
@@ -117,6 +117,9 @@ def load(path: str = LIB_PATH):
     L.cc_profile_read.argtypes = [vp, i, ct.POINTER(d), ct.POINTER(ct.c_longlong)]
     L.cc_profile_reset.argtypes = [vp]
     L.cc_create_refined.argtypes = [ct.POINTER(CCConfig), i, ct.POINTER(CCBox), i, vp, ct.POINTER(vp)]
+    L.cc_create_refined_blocks.argtypes = [ct.POINTER(CCConfig), i, ct.POINTER(CCBox), i, ct.POINTER(i), i,
+                                           ct.POINTER(i), i, vp, ct.POINTER(vp)]
+    L.cc_domain_block.argtypes = [vp, i, ct.POINTER(i), ct.POINTER(i), ct.POINTER(i)]
     L.cc_refine_mass.argtypes = [vp, i, ct.POINTER(d)]
     L.cc_domain_count.restype = i
     L.cc_domain_count.argtypes = [vp]
@@ -428,11 +431,12 @@ class _Level:
 
 
 class RefinedModel(Model):
-    """Block-structured refinement (levels as domains 0 .. nlev-1) advanced on
-    the GPU through the C ABI: cc_create_refined, cc_step (one cycle of level
-    0 per step), cc_refine_mass."""
+    """Block-structured refinement advanced on the GPU through the C ABI:
+    cc_create_refined_blocks (levels as domains 0 .. nlev-1; with cuts the
+    finest level as sibling blocks, domains nlev-1 ..), cc_step (one cycle of
+    level 0 per step), cc_refine_mass."""
 
-    def __init__(self, base, boxes, precision: int = CC_FP64, stream=None):
+    def __init__(self, base, boxes, precision: int = CC_FP64, stream=None, xcuts=(), ycuts=()):
         self.L = load()
         self.base = base
         self.boxes = [tuple(b) for b in boxes]
@@ -444,15 +448,62 @@ class RefinedModel(Model):
             stream = _current_stream()
         self.stream = stream
         h = ct.c_void_p()
-        st = self.L.cc_create_refined(ct.byref(cb), len(self.boxes) + 1, arr, precision, stream, ct.byref(h))
+        xc = (ct.c_int * max(1, len(xcuts)))(*xcuts)
+        yc = (ct.c_int * max(1, len(ycuts)))(*ycuts)
+        st = self.L.cc_create_refined_blocks(ct.byref(cb), len(self.boxes) + 1, arr, len(xcuts), xc, len(ycuts), yc,
+                                             precision, stream, ct.byref(h))
         if st != CC_OK:
             raise CutcellError(st, self.L.cc_last_error(None).decode())
         self.h = h
         self.precision = precision
+        # per domain: (level, block origin x, y); the finest level's blocks
+        # replace its single entry in cfgs
+        self.blocks = []
+        for d in range(self.L.cc_domain_count(self.h)):
+            lv, ox, oy = ct.c_int(), ct.c_int(), ct.c_int()
+            self._check(self.L.cc_domain_block(self.h, d, ct.byref(lv), ct.byref(ox), ct.byref(oy)))
+            self.blocks.append((lv.value, ox.value, oy.value))
+        self._nlev = len(self.boxes) + 1
+        fine = self.boxes[-1]
+        xs, ys = [0, *xcuts, fine[0]], [0, *ycuts, fine[1]]
+        self.cfgs = self.cfgs[:-1] + [_Level(base, self._nlev - 1, (xs[a + 1] - xs[a], ys[b + 1] - ys[b], fine[2]))
+                                      for b in range(len(ys) - 1) for a in range(len(xs) - 1)]
 
     @property
     def nlev(self) -> int:
+        return self._nlev
+
+    @property
+    def ndom(self) -> int:
         return len(self.cfgs)
+
+    def level_domains(self, lev: int) -> list:
+        return [d for d, b in enumerate(self.blocks) if b[0] == lev]
+
+    def set_level_terrain(self, lev: int, h: np.ndarray):
+        """Corner heights of a whole level (its box's corners), cut into its blocks."""
+        for d in self.level_domains(lev):
+            _, ox, oy = self.blocks[d]
+            c = self.cfgs[d]
+            self.set_terrain(d, np.ascontiguousarray(h[oy:oy + c.ny, ox:ox + c.nx]))
+
+    def download_level(self, lev: int, field: int, level: int = 1) -> np.ndarray:
+        """One field of a whole level in the host layout of its box, stitched
+        from its blocks."""
+        ds = self.level_domains(lev)
+        parts = [(self.blocks[d], self.download(d, field, level)) for d in ds]
+        ny = max(b[2] + a.shape[-2 if field != CC_UB else 0] for b, a in parts)
+        nx = max(b[1] + a.shape[-1 if field != CC_UB else 1] for b, a in parts)
+        first = parts[0][1]
+        if field == CC_UB:
+            out = np.zeros((ny, nx, 3), first.dtype)
+            for (_, ox, oy), a in parts:
+                out[oy:oy + a.shape[0], ox:ox + a.shape[1]] = a
+        else:
+            out = np.zeros(first.shape[:-2] + (ny, nx), first.dtype)
+            for (_, ox, oy), a in parts:
+                out[..., oy:oy + a.shape[-2], ox:ox + a.shape[-1]] = a
+        return out
 
     def mass(self, both: bool = True) -> float:
         out = ct.c_double()

@@ -159,6 +159,9 @@ class RefinedConfig:
     name: str
     base: RunConfig
     boxes: list
+    # cuts of the finest level's box into sibling blocks (its cells)
+    xcuts: tuple = ()
+    ycuts: tuple = ()
 
     @property
     def nlev(self) -> int:
@@ -212,6 +215,15 @@ SMALL_REFINED = RefinedConfig(
     RunConfig("refined-base", 32, 32, 16, 400.0, 400.0, 400.0, 0.3, 20, "hemisphere", 600.0, 600.0),
     [(32, 32, 16, 16, 16), (32, 32, 16, 16, 16)])
 
+# Three levels around a hemisphere of radius 500 m, 400 m / 200 m / 100 m,
+# the finest 64 x 64 x 16 box cut into six sibling blocks of uneven sizes
+# (x cuts 18 and 46, y cut 46; the hill, corners 28 .. 36, stays 8 corners
+# clear of every cut) (oracle-sized).
+SMALL_BLOCKED = RefinedConfig(
+    "refined-blocks-48x48x16-hemisphere",
+    RunConfig("blocked-base", 48, 48, 16, 400.0, 400.0, 400.0, 0.3, 20, "hemisphere", 500.0, 500.0),
+    [(64, 64, 16, 16, 16), (64, 64, 16, 32, 32)], xcuts=(18, 46), ycuts=(46,))
+
 # Hemisphere of radius 1 km with three levels: 200 m over the 64 x 32 x 16 km
 # domain, 100 m over x in [6.4, 57.6] km, y in [1.6, 30.4] km, z < 8 km, and
 # 50 m over x in [12.8, 51.2] km, y in [4.8, 27.2] km, z < 4.8 km.
@@ -220,3 +232,11 @@ C4_REFINED = RefinedConfig(
     RunConfig("refined-base-320x160x80-200m", 320, 160, 80, 200.0, 200.0, 200.0, 0.15, 200,
               "hemisphere", 1000.0, 1000.0),
     [(512, 288, 80, 64, 16), (768, 448, 96, 128, 64)])
+
+# The same three levels with the 50 m level cut into 15 sibling blocks of
+# uneven sizes (x cuts 96, 250, 480, 640; y cuts 120, 300 of its 768 x 448
+# cells); the hemisphere, corners 364 .. 404 in x and 204 .. 244 in y, lies in
+# one block, at least 56 cells clear of every cut.
+C4_BLOCKED = RefinedConfig(
+    "refined-hemisphere-200-100-50m-15-blocks",
+    C4_REFINED.base, C4_REFINED.boxes, xcuts=(96, 250, 480, 640), ycuts=(120, 300))
