@@ -102,6 +102,7 @@ struct cc_model {
   std::vector<cc_box> lev_box;
   std::vector<XchItem *> d_xch;
   std::vector<long long> nxch;
+  std::vector<LinkSet> lset;  // the links of each level >= 1 (one launch per operation)
   Eos eos{};                   // equation-of-state coefficients of every domain
   long long last_launches = 0;
   bool geom = false, state = false;
@@ -401,6 +402,7 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
     for (int d = 0; d < n; d++) m->lev_count[lay.level[d]]++;
     m->d_xch.assign(m->nlev, nullptr);
     m->nxch.assign(m->nlev, 0);
+    m->lset.assign(m->nlev, LinkSet{});
   }
   cudaError_t e = cudaSuccess;
   auto bail = [&](cudaError_t ee, const char *where) {
@@ -635,11 +637,19 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
       // -1 .. N+1 in x and y below level nz + 2 (the ghost layers included),
       // and every block integrates its own share of them: the point's owner is
       // the block that holds it once clamped into the level's box.  A point
-      // of this block's ghost shell that the level integrates and another
+      // of this block's ghost shell within two of its interior (the reach of
+      // the stencils of its own points) that the level integrates and another
       // block owns is copied from the owner after every step; a point outside
       // the level's box is injected from the coarser level at every coarse
-      // step, as for the undivided level (the ghost layers are both).
+      // step, as for the undivided level (the ghost layers are both).  The
+      // block also integrates the ghost points that siblings own, from shell
+      // values it does not keep current; the copies replace those results.
       const int NX = U.nx, NY = U.ny;
+      // the copy records hold 32-bit offsets and 16-bit domain indices
+      if (m->lev_count[lev] > 1 && (F.ncellp >= (1LL << 31) || n >= 65535)) {
+        cc_destroy(m);
+        return fail(nullptr, CC_EINVAL, "a block of a cut level is too large for 32-bit offsets");
+      }
       auto owner = [&](int gx, int gy) {
         const int cx = std::min(std::max(gx, 0), NX - 1), cy = std::min(std::max(gy, 0), NY - 1);
         for (int q = m->lev_first[lev]; q < m->lev_first[lev] + m->lev_count[lev]; q++) {
@@ -653,9 +663,9 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
         const DomDev &Q = m->dom[q].D;
         const int qi = bx + i - m->blk_off[q][0], qj = by + j - m->blk_off[q][1];
         XchItem x{};
-        x.ddom = d; x.sdom = q; x.kind = kind;
-        x.dst = kind == XCH_COLUMN ? qidx(F, i, j) : pidx(F, i, j, k);
-        x.src = kind == XCH_COLUMN ? qidx(Q, qi, qj) : pidx(Q, qi, qj, k);
+        x.ddom = (uint16_t)d; x.sdom = (uint16_t)q; x.kind = kind;
+        x.dst = (int32_t)(kind == XCH_COLUMN ? qidx(F, i, j) : pidx(F, i, j, k));
+        x.src = (int32_t)(kind == XCH_COLUMN ? qidx(Q, qi, qj) : pidx(Q, qi, qj, k));
         xch[lev].push_back(x);
       };
       std::vector<long long> pcell, pcorn, rcell, rcorn;
@@ -666,7 +676,8 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
             const int gx = bx + i, gy = by + j;
             const bool inside = gx >= 0 && gx < NX && gy >= 0 && gy < NY && k < F.nz;
             if (!inside && k >= 0) pcell.push_back(pidx(F, i, j, k));
-            if (gx >= -2 && gx < NX + 2 && gy >= -2 && gy < NY + 2 && k >= 0 && k < F.nz + 2) {
+            const bool reach = i >= -2 && i < F.nx + 2 && j >= -2 && j < F.ny + 2;
+            if (reach && gx >= -2 && gx < NX + 2 && gy >= -2 && gy < NY + 2 && k >= 0 && k < F.nz + 2) {
               const int q = owner(gx, gy);
               if (q != d) copy_from(q, i, j, k, XCH_CELL);
             }
@@ -678,7 +689,8 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
             const int gx = bx + I, gy = by + J;
             const bool inside = gx >= 0 && gx <= NX && gy >= 0 && gy <= NY && Kk <= F.nz;
             if (!inside) pcorn.push_back(pidx(F, I, J, Kk));
-            if (gx >= -1 && gx < NX + 2 && gy >= -1 && gy < NY + 2 && Kk < F.nz + 2) {
+            const bool reach = I >= -2 && I <= F.nx + 2 && J >= -2 && J <= F.ny + 2;
+            if (reach && gx >= -1 && gx < NX + 2 && gy >= -1 && gy < NY + 2 && Kk < F.nz + 2) {
               const int q = owner(gx, gy);
               if (q != d) copy_from(q, I, J, Kk, XCH_CORNER);
             }
@@ -687,7 +699,8 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
         for (int I = -GH; I < F.nx + GH; I++) {
           if (I >= 0 && I <= F.nx && J >= 0 && J <= F.ny) continue;
           const int gx = bx + I, gy = by + J;
-          if (gx >= -1 && gx < NX + 2 && gy >= -1 && gy < NY + 2) {
+          const bool reach = I >= -2 && I <= F.nx + 2 && J >= -2 && J <= F.ny + 2;
+          if (reach && gx >= -1 && gx < NX + 2 && gy >= -1 && gy < NY + 2) {
             const int q = owner(gx, gy);
             if (q != d) copy_from(q, I, J, 0, XCH_COLUMN);
           }
@@ -783,6 +796,26 @@ cc_status create_impl(const std::vector<cc_config> &cfgs, const std::vector<DomK
           (e = cudaStreamSynchronize(m->st)) != cudaSuccess)
         return bail(e, "same-level copies");
       m->nxch[l] = (long long)xch[l].size();
+    }
+    for (int l = 1; l < m->nlev; l++) {
+      std::vector<LevelLink> ls;
+      LinkSet &S = m->lset[l];
+      for (int d = m->lev_first[l]; d < m->lev_first[l] + m->lev_count[l]; d++) {
+        const LevelLink &L = m->link[d].L;
+        ls.push_back(L);
+        S.maxp = std::max(S.maxp, L.npcell + L.npcorn);
+        S.maxr = std::max(S.maxr, L.nrcell + L.nrcorn);
+        S.maxf = std::max(S.maxf, (long long)L.nfaces);
+        S.maxi = std::max(S.maxi, (long long)L.nicells);
+      }
+      LevelLink *dl = nullptr;
+      if ((e = dalloc(m->allocs, &dl, sizeof(LevelLink) * ls.size(), m->st)) != cudaSuccess ||
+          (e = cudaMemcpyAsync(dl, ls.data(), sizeof(LevelLink) * ls.size(), cudaMemcpyHostToDevice, m->st)) !=
+              cudaSuccess ||
+          (e = cudaStreamSynchronize(m->st)) != cudaSuccess)
+        return bail(e, "link sets");
+      S.links = dl;
+      S.n = (int)ls.size();
     }
   }
   if ((e = dalloc(m->allocs, &m->d_diag, sizeof(double) * (8 + 7 * 256), m->st)) != cudaSuccess) return bail(e, "diag");
@@ -1211,10 +1244,9 @@ cc_status cc_init_state(cc_model *m) {
       const LevelLink &K = m->link[d].L;
       CK(m, cudaMemsetAsync(K.regm, 0, K.nfaces * m->esz, m->st), "register reset");
       CK(m, cudaMemsetAsync(K.regh, 0, K.nfaces * m->esz, m->st), "register reset");
-      CK(m, launch_restrict(K, m->prec, m->dom[d].r[1], m->st), "init restrict");
     }
-    for (int d = d0; d < d1; d++)
-      CK(m, launch_prolong(m->link[d].L, m->prec, m->dom[m->link[d].dc].r[1], m->st), "init prolong");
+    CK(m, launch_restrict(m->lset[l], m->prec, m->dom[d0].r[1], m->st), "init restrict");
+    CK(m, launch_prolong(m->lset[l], m->prec, m->dom[m->lev_first[l - 1]].r[1], m->st), "init prolong");
     CK(m, launch_exchange(m->d_doms, m->d_xch[l], m->nxch[l], m->prec, m->dom[d0].r[0], m->dom[d0].r[1], m->st),
        "init same-level copies");
   }
@@ -1487,13 +1519,9 @@ static cc_status step_domains(cc_model *m, int lev, long long &nl) {
     nl++;
   }
   if (lev >= 0 && lev + 1 < m->nlev) {
-    const int f0 = m->lev_first[lev + 1], f1 = f0 + m->lev_count[lev + 1];
-    for (int q = f0; q < f1; q++) {
-      const LevelLink &K = m->link[q].L;
-      CK(m, timed(m, CC_K_REFINE, [&] { return launch_iface(K, pr, rO, rC, rN, rF, first, st); }),
-         "flux register");
-      nl++;
-    }
+    const LinkSet &S = m->lset[lev + 1];
+    CK(m, timed(m, CC_K_REFINE, [&] { return launch_iface(S, pr, rO, rC, rN, rF, first, st); }), "flux register");
+    nl++;
   }
   if (L.ncols > 0) {
     CK(m, timed(m, CC_K_DIAGNOSE, [&] { return launch_diagnose(L, pr, rN, rC, rO, rF, first, 1, st); }),
@@ -1531,15 +1559,13 @@ static cc_status cycle(cc_model *m, int l, long long &nl) {
   const int pr = m->prec;
   cudaStream_t st = m->st;
   const bool fine = l + 1 < m->nlev;
-  const int f0 = fine ? m->lev_first[l + 1] : 0, f1 = fine ? f0 + m->lev_count[l + 1] : 0;
   if (fine) {
+    const LinkSet &S = m->lset[l + 1];
+    const int f0 = m->lev_first[l + 1];
     for (int s = 0; s < 2; s++) {
-      for (int q = f0; q < f1; q++) {
-        const LevelLink &K = m->link[q].L;
-        CK(m, timed(m, CC_K_REFINE, [&] { return launch_register_add(K, pr, m->dom[q].r[1], st); }),
-           "register add");
-        nl++;
-      }
+      CK(m, timed(m, CC_K_REFINE, [&] { return launch_register_add(S, pr, m->dom[f0].r[1], st); }),
+         "register add");
+      nl++;
       cc_status r = cycle(m, l + 1, nl);
       if (r != CC_OK) return r;
     }
@@ -1549,18 +1575,12 @@ static cc_status cycle(cc_model *m, int l, long long &nl) {
   if (fine) {
     // every block restricted before any is prolonged: the injection into a
     // block's shell reads coarse corners that a neighbouring block restricts
-    const int dc = m->lev_first[l];
-    for (int q = f0; q < f1; q++) {
-      const LevelLink &K = m->link[q].L;
-      CK(m, timed(m, CC_K_REFINE, [&] { return launch_register_clear(K, pr, st); }), "register clear");
-      CK(m, timed(m, CC_K_REFINE, [&] { return launch_restrict(K, pr, m->dom[q].r[1], st); }), "restrict");
-      nl += 2;
-    }
-    for (int q = f0; q < f1; q++) {
-      const LevelLink &K = m->link[q].L;
-      CK(m, timed(m, CC_K_REFINE, [&] { return launch_prolong(K, pr, m->dom[dc].r[1], st); }), "prolong");
-      nl++;
-    }
+    const LinkSet &S = m->lset[l + 1];
+    const int f0 = m->lev_first[l + 1], dc = m->lev_first[l];
+    CK(m, timed(m, CC_K_REFINE, [&] { return launch_register_clear(S, pr, st); }), "register clear");
+    CK(m, timed(m, CC_K_REFINE, [&] { return launch_restrict(S, pr, m->dom[f0].r[1], st); }), "restrict");
+    CK(m, timed(m, CC_K_REFINE, [&] { return launch_prolong(S, pr, m->dom[dc].r[1], st); }), "prolong");
+    nl += 3;
   }
   return CC_OK;
 }

@@ -232,17 +232,26 @@ struct LevelLink {
 // destination and the source domain.
 enum { XCH_CELL = 0, XCH_CORNER = 1, XCH_COLUMN = 2 };
 struct XchItem {
-  long long dst, src;
-  int ddom, sdom, kind, pad;
+  int32_t dst, src;
+  uint16_t ddom, sdom;
+  int32_t kind;
 };
 // copies the listed points of the two time levels r0 and r1 (ub: r1 only)
 cudaError_t launch_exchange(const DomDev *d_doms, const XchItem *items, long long n, int prec, int r0, int r1,
                             cudaStream_t st);
-cudaError_t launch_prolong(const LevelLink &L, int prec, int rC, cudaStream_t st);
-cudaError_t launch_restrict(const LevelLink &L, int prec, int rF, cudaStream_t st);
-cudaError_t launch_register_add(const LevelLink &L, int prec, int rF, cudaStream_t st);
-cudaError_t launch_register_clear(const LevelLink &L, int prec, cudaStream_t st);
-cudaError_t launch_iface(const LevelLink &L, int prec, int rO, int rC, int rN, int rF, int first,
+// the links of one level's domains (a box, or its blocks) in device memory,
+// with the longest list of each kind; the operations below run all of them
+// in one launch
+struct LinkSet {
+  const LevelLink *links;
+  int n;
+  long long maxp, maxr, maxf, maxi;  // prolonged points, restricted points, faces, interface cells
+};
+cudaError_t launch_prolong(const LinkSet &S, int prec, int rC, cudaStream_t st);
+cudaError_t launch_restrict(const LinkSet &S, int prec, int rF, cudaStream_t st);
+cudaError_t launch_register_add(const LinkSet &S, int prec, int rF, cudaStream_t st);
+cudaError_t launch_register_clear(const LinkSet &S, int prec, cudaStream_t st);
+cudaError_t launch_iface(const LinkSet &S, int prec, int rO, int rC, int rN, int rF, int first,
                          cudaStream_t st);
 cudaError_t launch_mass_active(const DomDev &D, const DomDev *d_dom, int prec, int rC, int rO, int both,
                                int bx0, int bx1, int by0, int by1, int bz1, double *d_out, cudaStream_t st);

@@ -1238,7 +1238,8 @@ __device__ __forceinline__ void decode(const DomDev &D, long long off, int &i, i
 // axis (coincident points copy).  All four time-level buffers of the fine
 // level receive the current coarse values.
 template <typename T>
-__global__ void k_prolong(LevelLink L, int rC) {
+__global__ void k_prolong(const LevelLink *__restrict__ links, int rC) {
+  const LevelLink &L = links[blockIdx.y];
   const DomDev &C = *L.dc, &F = *L.df;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < L.npcell) {
@@ -1308,7 +1309,8 @@ __global__ void k_exchange(const DomDev *__restrict__ doms, const XchItem *__res
 // and top faces take the coincident fine corner.  All four time-level
 // buffers of the coarse level.
 template <typename T>
-__global__ void k_restrict(LevelLink L, int rF) {
+__global__ void k_restrict(const LevelLink *__restrict__ links, int rF) {
+  const LevelLink &L = links[blockIdx.y];
   const DomDev &C = *L.dc, &F = *L.df;
   long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t < L.nrcell) {
@@ -1395,7 +1397,8 @@ __device__ __forceinline__ void face_fluxes(const DomDev &D, int rC, int ax, int
 // interface face, from the fine level's current state (the state its next
 // step uses).
 template <typename T>
-__global__ void k_reg_add(LevelLink L, int rF) {
+__global__ void k_reg_add(const LevelLink *__restrict__ links, int rF) {
+  const LevelLink &L = links[blockIdx.y];
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= L.nfaces) return;
   const IfaceFace f = L.faces[q];
@@ -1444,7 +1447,8 @@ __global__ void k_reg_add(LevelLink L, int rF) {
 }
 
 template <typename T>
-__global__ void k_reg_clear(LevelLink L) {
+__global__ void k_reg_clear(const LevelLink *__restrict__ links) {
+  const LevelLink &L = links[blockIdx.y];
   int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= L.nfaces) return;
   ((T *)L.regm)[q] = 0;
@@ -1455,7 +1459,8 @@ __global__ void k_reg_clear(LevelLink L) {
 // stencil with the interface faces' fluxes taken from the register (the mean
 // over the two fine substeps; cube-boundary flux of Sec 2.2).
 template <typename T>
-__global__ void k_iface(LevelLink L, int rO, int rC, int rN, int rF, int first) {
+__global__ void k_iface(const LevelLink *__restrict__ links, int rO, int rC, int rN, int rF, int first) {
+  const LevelLink &L = links[blockIdx.y];
   using A = Ar<T>;
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= L.nicells) return;
@@ -1746,40 +1751,44 @@ cudaError_t launch_heat(const DomDev *d_dom, int prec, int r, double *d_out, dou
   return cudaGetLastError();
 }
 
-cudaError_t launch_prolong(const LevelLink &L, int prec, int rC, cudaStream_t st) {
-  long long n = L.npcell + L.npcorn;
-  if (n <= 0) return cudaSuccess;
-  if (prec == CC_FP64) k_prolong<double><<<nb256(n), 256, 0, st>>>(L, rC);
-  else k_prolong<float><<<nb256(n), 256, 0, st>>>(L, rC);
+// One launch per operation for all the links of a level (its blocks): grid
+// rows (blockIdx.y) select the link, columns cover the longest list.
+namespace {
+dim3 link_grid(const LinkSet &S, long long n) { return dim3(nb256(n), (unsigned)S.n); }
+}  // namespace
+
+cudaError_t launch_prolong(const LinkSet &S, int prec, int rC, cudaStream_t st) {
+  if (S.n <= 0 || S.maxp <= 0) return cudaSuccess;
+  if (prec == CC_FP64) k_prolong<double><<<link_grid(S, S.maxp), 256, 0, st>>>(S.links, rC);
+  else k_prolong<float><<<link_grid(S, S.maxp), 256, 0, st>>>(S.links, rC);
   return cudaGetLastError();
 }
 
-cudaError_t launch_restrict(const LevelLink &L, int prec, int rF, cudaStream_t st) {
-  long long n = L.nrcell + L.nrcorn;
-  if (n <= 0) return cudaSuccess;
-  if (prec == CC_FP64) k_restrict<double><<<nb256(n), 256, 0, st>>>(L, rF);
-  else k_restrict<float><<<nb256(n), 256, 0, st>>>(L, rF);
+cudaError_t launch_restrict(const LinkSet &S, int prec, int rF, cudaStream_t st) {
+  if (S.n <= 0 || S.maxr <= 0) return cudaSuccess;
+  if (prec == CC_FP64) k_restrict<double><<<link_grid(S, S.maxr), 256, 0, st>>>(S.links, rF);
+  else k_restrict<float><<<link_grid(S, S.maxr), 256, 0, st>>>(S.links, rF);
   return cudaGetLastError();
 }
 
-cudaError_t launch_register_add(const LevelLink &L, int prec, int rF, cudaStream_t st) {
-  if (L.nfaces <= 0) return cudaSuccess;
-  if (prec == CC_FP64) k_reg_add<double><<<nb256(L.nfaces), 256, 0, st>>>(L, rF);
-  else k_reg_add<float><<<nb256(L.nfaces), 256, 0, st>>>(L, rF);
+cudaError_t launch_register_add(const LinkSet &S, int prec, int rF, cudaStream_t st) {
+  if (S.n <= 0 || S.maxf <= 0) return cudaSuccess;
+  if (prec == CC_FP64) k_reg_add<double><<<link_grid(S, S.maxf), 256, 0, st>>>(S.links, rF);
+  else k_reg_add<float><<<link_grid(S, S.maxf), 256, 0, st>>>(S.links, rF);
   return cudaGetLastError();
 }
 
-cudaError_t launch_register_clear(const LevelLink &L, int prec, cudaStream_t st) {
-  if (L.nfaces <= 0) return cudaSuccess;
-  if (prec == CC_FP64) k_reg_clear<double><<<nb256(L.nfaces), 256, 0, st>>>(L);
-  else k_reg_clear<float><<<nb256(L.nfaces), 256, 0, st>>>(L);
+cudaError_t launch_register_clear(const LinkSet &S, int prec, cudaStream_t st) {
+  if (S.n <= 0 || S.maxf <= 0) return cudaSuccess;
+  if (prec == CC_FP64) k_reg_clear<double><<<link_grid(S, S.maxf), 256, 0, st>>>(S.links);
+  else k_reg_clear<float><<<link_grid(S, S.maxf), 256, 0, st>>>(S.links);
   return cudaGetLastError();
 }
 
-cudaError_t launch_iface(const LevelLink &L, int prec, int rO, int rC, int rN, int rF, int first, cudaStream_t st) {
-  if (L.nicells <= 0) return cudaSuccess;
-  if (prec == CC_FP64) k_iface<double><<<nb256(L.nicells), 256, 0, st>>>(L, rO, rC, rN, rF, first);
-  else k_iface<float><<<nb256(L.nicells), 256, 0, st>>>(L, rO, rC, rN, rF, first);
+cudaError_t launch_iface(const LinkSet &S, int prec, int rO, int rC, int rN, int rF, int first, cudaStream_t st) {
+  if (S.n <= 0 || S.maxi <= 0) return cudaSuccess;
+  if (prec == CC_FP64) k_iface<double><<<link_grid(S, S.maxi), 256, 0, st>>>(S.links, rO, rC, rN, rF, first);
+  else k_iface<float><<<link_grid(S, S.maxi), 256, 0, st>>>(S.links, rO, rC, rN, rF, first);
   return cudaGetLastError();
 }
 
