@@ -86,13 +86,15 @@ def kfull_source_hash(dtype="f64"):
     """Hash of the full-cell stencil's source (the kernel, its shared-memory
     layout and tile shape): the counters recorded under profiles/ apply only
     while it is unchanged.  FP64 runs the one-cell kernel of step.cu, FP32 the
-    two-cell kernel of pair.cuh."""
+    two-cell kernel of pair.cuh with the helpers of step.cu it calls (the
+    copies and the equation of state)."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_1509_02572_gb300", "csrc")
     hdr = open(os.path.join(csrc, "cc_internal.h")).read()
     tiles = [ln for ln in hdr.splitlines() if "TILE_" in ln or "SCHED_" in ln or "constexpr int GX" in ln]
     if dtype == "f32":
-        body = open(os.path.join(csrc, "pair.cuh")).read()
+        src = open(os.path.join(csrc, "step.cu")).read()
+        body = src[:src.index("struct FullCfg")] + open(os.path.join(csrc, "pair.cuh")).read()
     else:
         src = open(os.path.join(csrc, "step.cu")).read()
         a = src.index("struct FullCfg")

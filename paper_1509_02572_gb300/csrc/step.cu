@@ -130,6 +130,9 @@ __device__ __forceinline__ float exner_fac(const DomDev &D, const float *pik, co
   return fmaf(pik[kp], pow1pm1(__fmul_rn(pp, ipb[kp]), D.sex), pik[kp]);
 }
 
+// (1 + x)^a - 1 away from zero: rare, kept out of line so that the stencils'
+// loops stay small
+__device__ __noinline__ float pow1pm1_far(float x, float a) { return expm1f(__fmul_rn(a, log1pf(x))); }
 // The same equation-of-state operations on per-level base values already in
 // registers and on coefficients passed as kernel parameters (constant bank):
 // bit-identical to the functions above.
@@ -144,7 +147,7 @@ __device__ __forceinline__ float pow1pm1_e(float x, const float (&c)[8]) {
     s = fmaf(s, x, c[0]);
     return __fmul_rn(s, x);
   }
-  return expm1f(__fmul_rn(c[7], log1pf(x)));
+  return pow1pm1_far(x, c[7]);
 }
 __device__ __forceinline__ float theta_pert_e(const Eos &E, float thb, float ipb, float pp) {
   return __fmul_rn(thb, pow1pm1_e(__fmul_rn(pp, ipb), E.sth));
@@ -314,11 +317,13 @@ __device__ __forceinline__ void acopy(T *dst, const T *src) {
   else
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(src) : "memory");
 }
-// asynchronous global -> shared copy of 16 bytes (both addresses 16-byte aligned)
+// asynchronous global -> shared copy of 16 bytes (both addresses 16-byte
+// aligned), cached in L2 only: the staged planes are not read again through
+// L1, which is left to the per-level and per-column values
 template <typename T>
 __device__ __forceinline__ void acopy16(T *dst, const T *src) {
   unsigned d = (unsigned)__cvta_generic_to_shared(dst);
-  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(src) : "memory");
 }
 __device__ __forceinline__ void acommit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
