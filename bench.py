@@ -1006,7 +1006,10 @@ def main():
             outs = [torch.empty(tuple(model._shape(d, cc.CC_PP)), dtype=t_dt).pin_memory() for d in range(len(cfgs))]
             h2d = sum(a.numel() * es for a in host.values())
             d2h = sum(o.numel() * es for o in outs)
-            ke = max(3, min(args.steps, 8))
+            # as many steps as the device-timed loop (up to 24): the host link
+            # shows rare one-off stalls of 50-120 ms, which a short window
+            # would over- or under-weight
+            ke = max(3, min(args.steps, 24))
 
             def e2e_step():
                 for (d, f, lev), a in host.items():
