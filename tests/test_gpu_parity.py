@@ -193,6 +193,29 @@ def test_fp32_error_against_oracle(cc, oracle_mod):
     m.close()
 
 
+def test_long_run_against_oracle(cc, oracle_mod):
+    """5,000 steps (the step count of the 512 x 512 x 128 precision case) on
+    the 32 x 32 x 24 bell, against the oracle run for as long: the FP64 form
+    stays at rounding level, and the FP32 perturbation form's error stays at
+    the level that FP32 rounding accumulated over 5,000 steps gives (relative
+    L2 1e-3 at most on the large domain against the FP64 GPU form)."""
+    cfg = W.C1_BELL
+    om = oracle_mod.Model(cfg)
+    om.init_state()
+    om.step(5000)
+    for prec, l2tol, litol in ((cc.CC_FP64, 1e-9, 1e-7), (cc.CC_FP32, 5e-3, 5e-2)):
+        m = gpu_model(cc, cfg, prec)
+        m.init_state()
+        m.step(5000)
+        errs = _compare(cc, oracle_mod, m, om, report=True)
+        print("5000 steps", "FP64" if prec == cc.CC_FP64 else "FP32",
+              {f"{k[0]}/{k[1]}": (float(f"{l2:.2e}"), float(f"{li:.2e}")) for k, (l2, li) in errs.items()})
+        for key, (l2, li) in errs.items():
+            assert l2 <= l2tol and li <= litol, (prec, key, l2, li)
+        assert m.diagnostics(0)["steps"] == 5000
+        m.close()
+
+
 def test_ensemble_equals_single_domain_runs(cc):
     """Domains of uneven sizes advanced in one launch give the same bits as
     each domain advanced alone."""
