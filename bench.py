@@ -998,13 +998,13 @@ def main():
             """Pinned host buffers in FP32 (the model's own precision, copied
             unchanged) or FP64; per step: upload, one step, download p'."""
             np_dt, t_dt, es = (np.float32, torch.float32, 4) if f32 else (np.float64, torch.float64, 8)
-            host = {}
-            for d in range(len(cfgs)):
-                for f in fields:
-                    for lev in (0, 1):
-                        host[(d, f, lev)] = torch.from_numpy(model.download(d, f, lev, dtype=np_dt)).pin_memory()
+            # the whole state in one pinned buffer, in the order of cc_upload_all_*
+            host = torch.from_numpy(np.concatenate([model.download(d, f, lev, dtype=np_dt).ravel()
+                                                    for d in range(len(cfgs)) for f in fields
+                                                    for lev in (0, 1)])).pin_memory()
+            assert host.numel() == model.state_elems()
             outs = [torch.empty(tuple(model._shape(d, cc.CC_PP)), dtype=t_dt).pin_memory() for d in range(len(cfgs))]
-            h2d = sum(a.numel() * es for a in host.values())
+            h2d = host.numel() * es
             d2h = sum(o.numel() * es for o in outs)
             # as many steps as the device-timed loop (up to 24): the host link
             # shows rare one-off stalls of 50-120 ms, which a short window
@@ -1012,8 +1012,7 @@ def main():
             ke = max(3, min(args.steps, 24))
 
             def e2e_step():
-                for (d, f, lev), a in host.items():
-                    model.upload_ptr(d, f, lev, a.data_ptr(), wait=False, f32=f32)
+                model.upload_all_ptr(host.data_ptr(), f32=f32)
                 model.step(1)
                 for d in range(len(cfgs)):
                     model.download_ptr(d, cc.CC_PP, 1, outs[d].data_ptr(), wait=False, f32=f32)
@@ -1040,8 +1039,9 @@ def main():
 
         f32 = prec_main == cc.CC_FP32
         line["e2e"] = e2e_run(f32)
-        line["e2e"]["how"] = ("per step: upload both time levels of every prognostic field from pinned host "
-                              + ("FP32 arrays (the model's precision, copied unchanged)" if f32 else "FP64 arrays")
+        line["e2e"]["how"] = ("per step: upload both time levels of every prognostic field of every domain from "
+                              "one pinned host buffer (cc_upload_all_*, one copy per domain) in "
+                              + ("FP32 (the model's precision, copied unchanged)" if f32 else "FP64")
                               + ", one step, download p' of every domain, then wait for it (transfers queued on "
                                 "the model's stream, one host wait per step); untimed warm-up steps first")
         if f32:

@@ -226,6 +226,23 @@ cc_status cc_download_state_f32(const cc_model *m, int d, int field, int level, 
 cc_status cc_upload_state_f32_async(cc_model *m, int d, int field, int level, const float *host);
 cc_status cc_download_state_f32_async(const cc_model *m, int d, int field, int level, float *host);
 
+/* The two-time-level state of every domain in one host buffer (no
+ * counterpart in the paper; for callers that move whole states every step):
+ * for each domain d = 0 .. ndom-1 in turn, the fields CC_RHOP, CC_PP, CC_MX,
+ * CC_MY, CC_MZ in that order, each at level 0 then level 1, every array in
+ * the host layout of cc_upload_state, back to back.  cc_state_elems sets *n
+ * to the buffer's element count.  cc_upload_all_async and
+ * cc_upload_all_f32_async (FP32 models only, FP32 host values copied
+ * unchanged) queue the upload on the model's stream as the _async transfers
+ * do, with one host-to-device copy per domain instead of one per array, into
+ * a device staging buffer of the whole state made on first use (CC_ENOMEM
+ * when it cannot be made); the host buffer must stay valid and unchanged
+ * until cc_synchronize.  CC_EINVAL for a null argument or an FP64 model with
+ * FP32 values, CC_ESTATE before a state. */
+cc_status cc_state_elems(const cc_model *m, long long *n);
+cc_status cc_upload_all_async(cc_model *m, const double *host);
+cc_status cc_upload_all_f32_async(cc_model *m, const float *host);
+
 /* Checkpoint and resume (no counterpart in the paper; long runs are split
  * over several jobs).  cc_save writes the whole state of every domain -- all
  * four time levels of the five fields and of the boundary-point velocity in

@@ -122,6 +122,13 @@ struct cc_model {
   bool used_valid[2] = {false, false};
   int xslot = 0;
   size_t stage_elems = 0;
+  // whole-state uploads (cc_upload_all_*): a staging buffer of the whole
+  // state, one copy event per domain, and the event after the conversions
+  void *d_bulk = nullptr;
+  size_t bulk_bytes = 0;
+  std::vector<cudaEvent_t> ev_bulk;
+  cudaEvent_t ev_bulk_done = nullptr;
+  bool bulk_used = false;
   int *d_err = nullptr;
   // step watchdog (flags of the full-cell stencil): the device word, its copy
   // in pinned host memory, made after each cc_step call, and the event that
@@ -974,6 +981,9 @@ cc_status cc_destroy(cc_model *m) {
     if (m->ev_staged[a]) cudaEventDestroy(m->ev_staged[a]);
   }
   cudaFree(m->d_stage2);
+  for (auto e : m->ev_bulk) cudaEventDestroy(e);
+  if (m->ev_bulk_done) cudaEventDestroy(m->ev_bulk_done);
+  cudaFree(m->d_bulk);
   if (m->h_watch) cudaFreeHost(m->h_watch);
   if (m->ev_watch) cudaEventDestroy(m->ev_watch);
   delete m;
@@ -1338,6 +1348,82 @@ static cc_status upload(cc_model *m, int d, int field, int level, const void *ho
   return CC_OK;
 }
 
+// elements of the whole two-time-level state in the host layout (five fields,
+// levels 0 and 1, every domain)
+static long long state_elems(const cc_model *m) {
+  long long n = 0;
+  int nlev, kfirst;
+  for (const auto &H : m->dom)
+    for (int f = 0; f < NFIELD; f++) n += 2 * field_elems(H.D, f, &nlev, &kfirst);
+  return n;
+}
+
+// the whole state from one host buffer: one copy per domain on the transfer
+// stream, each domain's conversions on the model's stream once its copy is in
+static cc_status upload_all(cc_model *m, const void *host, bool f32) {
+  if (!m || !host) return fail(m, CC_EINVAL, "null argument");
+  if (f32 && m->prec != CC_FP32) return fail(m, CC_EINVAL, "FP32 host buffers need an FP32 model");
+  if (!m->state) return fail(m, CC_ESTATE, "state not initialised");
+  cc_status r = transfer_setup(m);
+  if (r != CC_OK) return r;
+  const size_t es = f32 ? sizeof(float) : sizeof(double);
+  const size_t bytes = (size_t)state_elems(m) * es;
+  if (m->bulk_bytes < bytes) {
+    if (m->d_bulk) {
+      // the stream may still read the smaller buffer
+      CK(m, cudaStreamSynchronize(m->st), "bulk staging sync");
+      cudaFree(m->d_bulk);
+      m->d_bulk = nullptr;
+      m->bulk_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&m->d_bulk, bytes);
+    if (e != cudaSuccess) {
+      m->d_bulk = nullptr;
+      cudaGetLastError();
+      return fail(m, e == cudaErrorMemoryAllocation ? CC_ENOMEM : CC_ECUDA, "whole-state staging buffer");
+    }
+    m->bulk_bytes = bytes;
+  }
+  while (m->ev_bulk.size() < m->dom.size()) {
+    cudaEvent_t e = nullptr;
+    CK(m, cudaEventCreateWithFlags(&e, cudaEventDisableTiming), "transfer event");
+    m->ev_bulk.push_back(e);
+  }
+  if (!m->ev_bulk_done) CK(m, cudaEventCreateWithFlags(&m->ev_bulk_done, cudaEventDisableTiming), "transfer event");
+  // the copies overwrite the staging buffer once the previous whole-state
+  // upload's conversions have read it
+  if (m->bulk_used) CK(m, cudaStreamWaitEvent(m->xs, m->ev_bulk_done, 0), "upload order");
+  char *stage = (char *)m->d_bulk;
+  const char *src = (const char *)host;
+  size_t off = 0;
+  for (int d = 0; d < m->ndom; d++) {
+    const DomDev &D = m->dom[d].D;
+    int nlev, kfirst;
+    size_t bd = 0;
+    for (int f = 0; f < NFIELD; f++) bd += 2 * (size_t)field_elems(D, f, &nlev, &kfirst) * es;
+    CK(m, cudaMemcpyAsync(stage + off, src + off, bd, cudaMemcpyHostToDevice, m->xs), "upload");
+    CK(m, cudaEventRecord(m->ev_bulk[d], m->xs), "upload event");
+    CK(m, cudaStreamWaitEvent(m->st, m->ev_bulk[d], 0), "upload order");
+    for (int f = 0; f < NFIELD; f++)
+      for (int level = 0; level < 2; level++) {
+        const long long n = field_elems(D, f, &nlev, &kfirst);
+        void *dst = D.f[level == 0 ? m->dom[d].r[0] : m->dom[d].r[1]][f];
+        const void *a = stage + off;
+        if (m->prec == CC_FP64)
+          k_scatter<double><<<nb256(n), 256, 0, m->st>>>((const double *)a, (double *)dst, D, nlev, kfirst);
+        else if (f32)
+          k_scatter<float><<<nb256(n), 256, 0, m->st>>>((const float *)a, (float *)dst, D, nlev, kfirst);
+        else
+          k_scatter<float><<<nb256(n), 256, 0, m->st>>>((const double *)a, (float *)dst, D, nlev, kfirst);
+        off += (size_t)n * es;
+      }
+  }
+  CK(m, cudaGetLastError(), "upload scatter");
+  CK(m, cudaEventRecord(m->ev_bulk_done, m->st), "upload event");
+  m->bulk_used = true;
+  return CC_OK;
+}
+
 static cc_status download(cc_model *m, int d, int field, int level, void *host, bool sync, bool f32 = false) {
   if (!m || !host) return fail(m, CC_EINVAL, "null argument");
   if (f32 && m->prec != CC_FP32) return fail(m, CC_EINVAL, "FP32 host buffers need an FP32 model");
@@ -1467,6 +1553,16 @@ cc_status cc_upload_state_f32_async(cc_model *m, int d, int field, int level, co
 cc_status cc_download_state_f32_async(const cc_model *m, int d, int field, int level, float *host) {
   return download(const_cast<cc_model *>(m), d, field, level, host, false, true);
 }
+
+cc_status cc_state_elems(const cc_model *m, long long *n) {
+  if (!m || !n) return fail(const_cast<cc_model *>(m), CC_EINVAL, "null argument");
+  *n = state_elems(m);
+  return CC_OK;
+}
+
+cc_status cc_upload_all_async(cc_model *m, const double *host) { return upload_all(m, host, false); }
+
+cc_status cc_upload_all_f32_async(cc_model *m, const float *host) { return upload_all(m, host, true); }
 
 }  // extern "C"
 

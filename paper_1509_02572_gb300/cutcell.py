@@ -31,7 +31,8 @@ EXPORTS = ("cc_create", "cc_destroy", "cc_last_error", "cc_set_terrain", "cc_bui
            "cc_save", "cc_load",
            "cc_set_terrain_analytic", "cc_get_terrain", "cc_download_derived", "cc_error_norms", "cc_cbcm_cubes",
            "cc_mass_sum_noalloc", "cc_noalloc_last_error", "cc_upload_state_f32", "cc_download_state_f32",
-           "cc_upload_state_f32_async", "cc_download_state_f32_async", "cc_fma_peak")
+           "cc_upload_state_f32_async", "cc_download_state_f32_async", "cc_fma_peak",
+           "cc_state_elems", "cc_upload_all_async", "cc_upload_all_f32_async")
 CC_NOALLOC_MAX_PARTS = 1024
 CC_HILL_BELL, CC_HILL_ELLIPSOID, CC_HILL_COSINE = range(3)
 HILL_KINDS = {"bell": CC_HILL_BELL, "ellipsoid": CC_HILL_ELLIPSOID, "hemisphere": CC_HILL_ELLIPSOID,
@@ -108,6 +109,9 @@ def load(path: str = LIB_PATH):
     for fn in ("cc_upload_state_f32", "cc_download_state_f32", "cc_upload_state_f32_async",
                "cc_download_state_f32_async"):
         getattr(L, fn).argtypes = [vp, i, i, i, vp]
+    L.cc_state_elems.argtypes = [vp, ct.POINTER(ct.c_longlong)]
+    L.cc_upload_all_async.argtypes = [vp, vp]
+    L.cc_upload_all_f32_async.argtypes = [vp, vp]
     L.cc_step.argtypes = [vp, i]
     L.cc_diagnostics.argtypes = [vp, i, ct.POINTER(CCDiag)]
     L.cc_synchronize.argtypes = [vp]
@@ -335,6 +339,21 @@ class Model:
         else:
             fn = self.L.cc_upload_state if wait else self.L.cc_upload_state_async
         self._check(fn(self.h, d, field, level, ct.c_void_p(ptr)))
+
+    def state_elems(self) -> int:
+        """Elements of the whole two-time-level state in one host buffer
+        (cc_state_elems: every domain, fields rho', p', rho u, rho v, rho w,
+        levels 0 then 1, host layouts back to back)."""
+        n = ct.c_longlong(0)
+        self._check(self.L.cc_state_elems(self.h, ct.byref(n)))
+        return int(n.value)
+
+    def upload_all_ptr(self, ptr: int, f32: bool = False):
+        """cc_upload_all_async / cc_upload_all_f32_async: the whole state from
+        the host buffer at ptr, queued on the model's stream (the buffer stays
+        valid until synchronize)."""
+        fn = self.L.cc_upload_all_f32_async if f32 else self.L.cc_upload_all_async
+        self._check(fn(self.h, ct.c_void_p(ptr)))
 
     def step(self, n: int = 1):
         self._check(self.L.cc_step(self.h, int(n)))

@@ -103,3 +103,52 @@ def test_fp64_model_refuses_f32_buffers(cc):
     m.step(1)
     assert np.isfinite(m.download(0, 1)).all()
     m.close()
+
+
+@pytest.mark.parametrize("prec_name,f32", [("fp32", True), ("fp32", False), ("fp64", False)])
+def test_whole_state_upload_equals_per_array_uploads(cc, prec_name, f32):
+    """cc_upload_all_*: one host buffer with every domain's five fields at
+    both levels lands where the per-array uploads put them, and the next
+    steps are the same bit for bit."""
+    torch = pytest.importorskip("torch")
+    prec = cc.CC_FP32 if prec_name == "fp32" else cc.CC_FP64
+    np_dt, t_dt = (np.float32, torch.float32) if f32 else (np.float64, torch.float64)
+    src = model(cc, prec)
+    src.step(4)
+    parts = [src.download(d, f, lev, dtype=np_dt).ravel()
+             for d in range(len(CFGS)) for f in range(5) for lev in (0, 1)]
+    flat = np.concatenate(parts)
+    src.step(1)  # the source moves on: the uploads must not read it
+    a = model(cc, prec)
+    b = model(cc, prec)
+    assert a.state_elems() == flat.size == b.state_elems()
+    host = torch.from_numpy(flat).pin_memory()
+    a.upload_all_ptr(host.data_ptr(), f32=f32)
+    a.synchronize()
+    k = 0
+    for d in range(len(CFGS)):
+        for f in range(5):
+            for lev in (0, 1):
+                arr = np.ascontiguousarray(parts[k].reshape(src._shape(d, f)))
+                b.upload(d, f, lev, arr.astype(np.float64))
+                k += 1
+    for m in (a, b):
+        m.step(3)
+    for d in range(len(CFGS)):
+        for f in FIELDS:
+            for lev in (0, 1):
+                assert np.array_equal(a.download(d, f, lev), b.download(d, f, lev)), (d, f, lev)
+    for m in (src, a, b):
+        m.close()
+
+
+def test_whole_state_upload_refusals(cc):
+    m = model(cc, cc.CC_FP64)
+    buf = (ct.c_float * 4)()
+    with pytest.raises(cc.CutcellError) as e:
+        m.upload_all_ptr(ct.addressof(buf), f32=True)
+    assert e.value.status == cc.CC_EINVAL
+    with pytest.raises(cc.CutcellError) as e:
+        m.upload_all_ptr(0)
+    assert e.value.status == cc.CC_EINVAL
+    m.close()
