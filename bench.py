@@ -65,7 +65,8 @@ def parse():
     ap.add_argument("--precision-steps", type=int, default=5000)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--schedule", default=None,
-                    help="TILE_Y,ITEMS: fixed full-cell schedule instead of the autotuner (profiling runs)")
+                    help="TILE_Y,ITEMS[,ROLES]: fixed full-cell schedule (and FP32 warp roles, 1 or 2) instead "
+                         "of the autotuner (profiling runs)")
     return ap.parse_args()
 
 
@@ -102,10 +103,11 @@ def kfull_source_hash(dtype="f64"):
     return hashlib.sha256((body + "\n".join(tiles)).encode()).hexdigest()[:16]
 
 
-def kfull_traffic(dtype, cells, schedule):
+def kfull_traffic(dtype, cells, schedule, roles=1):
     """DRAM bytes of one k_full launch over `cells` interior cells, scaled
-    from the committed ncu capture (per interior cell), or None when the
-    kernel changed since the capture or the precision differs."""
+    from the committed ncu capture (per interior cell) of the same tile height
+    and warp roles, or None when the kernel changed since the capture or the
+    precision differs."""
     try:
         with open(os.path.join(ROOT, "profiles", "k_full_traffic.json")) as f:
             t = json.load(f)
@@ -113,7 +115,9 @@ def kfull_traffic(dtype, cells, schedule):
         return None
     if t.get("source_hash") != kfull_source_hash(dtype) or t.get("precision") != {"f32": "fp32", "f64": "fp64"}[dtype]:
         return None
-    per = t.get("dram_bytes_per_interior_cell_by_tile_y", {}).get(str(schedule[0]))
+    per = t.get("dram_bytes_per_interior_cell_by_schedule", {}).get(f"{schedule[0]}x{roles}")
+    if per is None and roles == 1:
+        per = t.get("dram_bytes_per_interior_cell_by_tile_y", {}).get(str(schedule[0]))
     return None if per is None else per * cells
 
 
@@ -130,7 +134,8 @@ def refined_kfull_traffic(dtype, workload, schedules):
         return None
     r = t.get("refined")
     if (r is None or t.get("source_hash") != kfull_source_hash("f32") or dtype != "f32"
-            or r.get("workload") != workload or [x[0] for x in r.get("schedule", [])] != [x[0] for x in schedules]):
+            or r.get("workload") != workload or [(x[0], (x + [1, 1])[2]) for x in r.get("schedule", [])]
+            != [(x[0], (x + [1, 1])[2]) for x in schedules]):
         return None
     return r["cycle_dram_bytes"] / r["cycle_launches"]
 
@@ -215,7 +220,7 @@ def fluid_cells(model, cfgs):
     return n
 
 
-SCHEDULE = None  # fixed (tile_y, items) from --schedule
+SCHEDULE = None  # fixed (tile_y, items[, warp roles]) from --schedule
 
 
 def make_model(cc, cfgs, prec, tune=True):
@@ -225,7 +230,9 @@ def make_model(cc, cfgs, prec, tune=True):
     m.build_geometry()
     m.init_state()
     if SCHEDULE:
-        m.set_schedule(0, *SCHEDULE)
+        m.set_schedule(0, *SCHEDULE[:2])
+        if len(SCHEDULE) > 2 and prec == cc.CC_FP32:
+            m.set_warp_roles(0, SCHEDULE[2])
     elif tune:
         m.autotune(3)
     return m
@@ -563,7 +570,9 @@ def bench_refined(cc, torch, args, hbm, peak_kind, barrier, world, rc=None, fp64
     # covered and underground cells of its boxes (frac_computed)
     achieved = BYTES_PER_CELL["f32"] * upd / per_cycle / (kavg / 1e3) / 1e9
     computed = refined_kfull_bytes(m, "f32") / per_cycle / (kavg / 1e3) / 1e9
-    schedules = [list(m.schedule(m.level_domains(l)[0])) for l in range(m.nlev)]
+    # per level: tile height, items per launch, warp roles
+    schedules = [list(m.schedule(m.level_domains(l)[0])) + [m.warp_roles(m.level_domains(l)[0])]
+                 for l in range(m.nlev)]
     out = {"workload": rc.name, "levels": [list(b) for b in rc.boxes], "value": upd * args.steps * world / (ms / 1e3),
            "schedule": schedules,
            "unit": METRIC, "ms_per_step": ms / args.steps, "cell_updates_per_step": upd, "dtype": "f32",
@@ -903,7 +912,8 @@ def main():
     # runs over the underground cells of its tiles: frac_computed)
     achieved = BYTES_PER_CELL[dtype] * nfluid / (kavg / 1e3) / 1e9
     roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s", "frac": achieved / hbm,
-            "traffic": kfull_traffic(dtype, ninterior, model.schedule(0)), "traffic_unit": "bytes per launch",
+            "traffic": kfull_traffic(dtype, ninterior, model.schedule(0), model.warp_roles(0)),
+            "traffic_unit": "bytes per launch",
             "kernel": "k_full", "kernel_ms": kavg, "peak_kind": f"{peak_kind} hbm_gbs",
             "bytes_per_cell": BYTES_PER_CELL[dtype], "cells_per_launch": nfluid,
             "frac_computed": BYTES_PER_CELL[dtype] * ninterior / (kavg / 1e3) / 1e9 / hbm,
@@ -913,7 +923,7 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": name, "instances": len(cfgs), "interior_cells": ninterior,
-                       "schedule": list(model.schedule(0)),
+                       "schedule": list(model.schedule(0)), "warp_roles": model.warp_roles(0),
                        "fluid_cells": nfluid, "precision": ("fp32 perturbations, fp64 geometry and base state"
                                                             if dtype == "f32" else "fp64"),
                        "l2": "inputs larger than L2 (state of all domains)" if ninterior * 80 > 129e6 else

@@ -306,7 +306,8 @@ long long cc_last_launch_count(const cc_model *m);
  * number of work items one launch aims for (304 or 912; the z-columns are cut
  * into chunks to reach it).  The schedule changes only how the work is
  * distributed over thread blocks, never the result (bit for bit).
- * cc_autotune times every schedule reps times on the model's current state
+ * cc_autotune times every schedule (FP32: with each warp-role form, below)
+ * reps times on the model's current state
  * and keeps the fastest, for the whole ensemble or for each level of a
  * refined model; the state is left unchanged (the stencil writes only the
  * levels the next step overwrites).  Needs cc_init_state; synchronises.
@@ -316,6 +317,22 @@ long long cc_last_launch_count(const cc_model *m);
 cc_status cc_autotune(cc_model *m, int reps);
 cc_status cc_get_schedule(const cc_model *m, int d, int *tile_y, int *items_per_launch);
 cc_status cc_set_schedule(cc_model *m, int d, int tile_y, int items_per_launch);
+
+/* Warp roles of the FP32 full-cell stencil (no counterpart in the paper; the
+ * paper's OpenMP code updates all variables of a cell in one thread).
+ * roles = 1: every thread updates rho', p' and the three momenta of its two
+ * cells.  roles = 2: each thread block holds two warpgroups over the same
+ * tile, one updating rho' and p' (Sec 2.4, the scalar fluxes and their
+ * divergence), the other the momenta (Eqs. momentum_u_d .. momentum_w_d);
+ * the two read the same staged planes, and each thread keeps the live values
+ * of one update only, so that twice as many warps fit per SM.  The result is
+ * the same either way.  cc_autotune times both with every schedule and keeps
+ * the fastest pair.  cc_get_warp_roles / cc_set_warp_roles read or set the
+ * roles of domain d's launch (of an ensemble: the one shared by all domains;
+ * of a refined model: every block of d's level).  CC_EINVAL for roles other
+ * than 1 or 2, or 2 on an FP64 model (its stencil has one form). */
+cc_status cc_get_warp_roles(const cc_model *m, int d, int *roles);
+cc_status cc_set_warp_roles(cc_model *m, int d, int roles);
 
 /* Kernel timing for measurement (no counterpart in the paper).  When enabled,
  * cc_step brackets each stage with CUDA events on the model's stream;

@@ -36,6 +36,7 @@ struct DomHost {
   int item0[NSCHED] = {}, nitem[NSCHED] = {}, witem0[NSCHED] = {}, nwitem[NSCHED] = {};
   int group0 = 0, ngroup = 0, col0 = 0, ncol = 0;
   int sched = 0;  // full-cell schedule of this level (refined models)
+  int roles = 1;  // FP32: warp roles per block of this level's stencil (refined models)
 };
 
 // Coarse-fine link of a domain of refined level l >= 1 (a level's box or one
@@ -73,6 +74,7 @@ struct cc_model {
   int nitems[NSCHED] = {};         // its first part (FP32: the items of refined boxes, staged by TMA)
   int nwitems[NSCHED] = {};        // FP32: the items of periodic domains (cyclic gather), after the first part
   int sched = 0;                   // schedule of the ensemble launch
+  int roles = 1;                   // FP32: warp roles per block of the ensemble launch
   bool tuned = false;
   // CUDA graphs of one step (one cycle of level 0 for a refined model), keyed
   // by the time-level roles and schedules of every domain; captured on a
@@ -254,6 +256,7 @@ StepLaunch make_launch(const cc_model *m, int lev = -1) {
   L.witems = m->d_items[m->sched] + m->nitems[m->sched];
   L.nwitems = m->nwitems[m->sched];
   L.ty = sched_tile_y(m->prec, m->sched);
+  L.roles = m->roles;
   L.groups = m->d_groups;
   L.ngroups = m->ngroups;
   L.members = m->d_members;
@@ -271,6 +274,7 @@ StepLaunch make_launch(const cc_model *m, int lev = -1) {
     L.items = m->d_items[sc] + H.item0[sc];
     L.witems = m->d_items[sc] + H.witem0[sc];
     L.ty = sched_tile_y(m->prec, sc);
+    L.roles = H.roles;
     L.groups = m->d_groups + H.group0;
     L.cols = m->d_cols + H.col0;
     L.nitems = L.nwitems = L.ngroups = L.ncols = 0;
@@ -1688,9 +1692,11 @@ static cc_status one_step(cc_model *m, long long &nl) { return m->refined ? cycl
 static std::vector<int> graph_key(const cc_model *m) {
   std::vector<int> k;
   k.push_back(m->sched);
+  k.push_back(m->roles);
   for (const auto &H : m->dom) {
     for (int a = 0; a < 4; a++) k.push_back(H.r[a]);
     k.push_back(H.sched);
+    k.push_back(H.roles);
   }
   return k;
 }
@@ -2010,19 +2016,26 @@ cc_status cc_autotune(cc_model *m, int reps) {
   for (int g = 0; g < ngroup && res == CC_OK; g++) {
     const int d = m->refined ? g : -1;
     DomHost &H = m->dom[m->refined ? m->lev_first[g] : 0];
-    auto set_sched = [&](int sc) {
+    auto set_sched = [&](int sc, int nr) {
       if (!m->refined) {
         m->sched = sc;
+        m->roles = nr;
         return;
       }
-      for (int q = m->lev_first[g]; q < m->lev_first[g] + m->lev_count[g]; q++) m->dom[q].sched = sc;
+      for (int q = m->lev_first[g]; q < m->lev_first[g] + m->lev_count[g]; q++) {
+        m->dom[q].sched = sc;
+        m->dom[q].roles = nr;
+      }
     };
     const int first = H.nsteps == 0;
     const int rO = first ? H.r[1] : H.r[0], rC = H.r[1], rN = H.r[2], rF = H.r[3];
     int best = 0;
     float best_ms = 0;
-    for (int sc = 0; sc < NSCHED && res == CC_OK; sc++) {
-      set_sched(sc);
+    // every schedule, and in FP32 with one and with two warp roles
+    const int nrmax = m->prec == CC_FP32 ? 2 : 1;
+    for (int sr = 0; sr < NSCHED * nrmax && res == CC_OK; sr++) {
+      const int sc = sr % NSCHED, nr = 1 + sr / NSCHED;
+      set_sched(sc, nr);
       StepLaunch L = make_launch(m, d);
       // the stencil writes only the new and filtered levels, which the next
       // step overwrites with the same values: timing it leaves the state alone
@@ -2037,12 +2050,12 @@ cc_status cc_autotune(cc_model *m, int reps) {
         res = cuda_fail(m, e, "autotune");
         break;
       }
-      if (sc == 0 || ms < best_ms) {
-        best = sc;
+      if (sr == 0 || ms < best_ms) {
+        best = sr;
         best_ms = ms;
       }
     }
-    set_sched(best);
+    set_sched(best % NSCHED, 1 + best / NSCHED);
   }
   cudaEventDestroy(a);
   cudaEventDestroy(b);
@@ -2075,6 +2088,28 @@ cc_status cc_set_schedule(cc_model *m, int d, int tile_y, int items_per_launch) 
       return CC_OK;
     }
   return fail(m, CC_EINVAL, "no such schedule");
+}
+
+cc_status cc_get_warp_roles(const cc_model *mc, int d, int *roles) {
+  cc_model *m = const_cast<cc_model *>(mc);
+  if (!m || !roles) return fail(m, CC_EINVAL, "null argument");
+  if (d < 0 || d >= m->ndom) return fail(m, CC_EINVAL, "domain index out of range");
+  *roles = m->refined ? m->dom[d].roles : m->roles;
+  return CC_OK;
+}
+
+cc_status cc_set_warp_roles(cc_model *m, int d, int roles) {
+  if (!m) return fail(m, CC_EINVAL, "null model");
+  if (d < 0 || d >= m->ndom) return fail(m, CC_EINVAL, "domain index out of range");
+  if (roles != 1 && (roles != 2 || m->prec != CC_FP32))
+    return fail(m, CC_EINVAL, "warp roles must be 1, or 2 in FP32");
+  if (m->refined) {
+    const int l = m->dom_level[d];
+    for (int q = m->lev_first[l]; q < m->lev_first[l] + m->lev_count[l]; q++) m->dom[q].roles = roles;
+  } else {
+    m->roles = roles;
+  }
+  return CC_OK;
 }
 
 cc_status cc_synchronize(cc_model *m) {

@@ -287,6 +287,7 @@ struct StepLaunch {
   int ndom;
   Eos eos;
   int ty;                  // tile height of the work items
+  int roles;               // FP32: warp roles per block of the full-cell stencil (1, or 2: scalars and momenta apart)
   unsigned *watch;         // step watchdog flags (CC_WATCH_*), or null
   const unsigned char *tmaps;  // FP32: two 128-byte TMA tensor maps per domain (tile heights 8, 16)
   unsigned stall_tx;           // extra bytes every TMA plane barrier expects (0; the watchdog's test only)

@@ -137,10 +137,22 @@ __device__ __forceinline__ float2 d4_2(float2 a, float2 b, float2 c, float2 d, f
   return make_float2(d4(a.x, b.x, c.x, d.x, e.x), d4(a.y, b.y, c.y, d.y, e.y));
 }
 
-template <int TYv>
+// NR warp roles: 1, every thread updates the scalars and the momenta of its
+// pair; 2, the block holds two warpgroups of NT threads over the same tile,
+// the first updating rho' and p', the second the three momenta (the two
+// updates read the same staged planes and nothing of each other), so that
+// each thread holds the live values of one update only and twice as many
+// warps fit per SM.  The staging and the derived planes are shared out over
+// all NR NT threads.
+template <bool B>
+struct RoleTag {
+  static constexpr bool value = B;
+};
+
+template <int TYv, int NR = 1>
 struct PairCfg {
-  static constexpr int TX = TILE_X, TY = TYv, NT = (TILE_X / 2) * TYv, HX = TX + 4, HY = TYv + 4, PL = HX * HY,
-                       NPP = PL / 2, NLPP = (NPP + NT - 1) / NT;
+  static constexpr int TX = TILE_X, TY = TYv, NT = (TILE_X / 2) * TYv, NTH = NR * NT, HX = TX + 4, HY = TYv + 4,
+                       PL = HX * HY, NPP = PL / 2, NLPP = (NPP + NTH - 1) / NTH;
   // pitch of a raw plane slot: whole 128-byte lines, so that every TMA
   // destination is 128-byte aligned
   static constexpr int PLP = (PL + 31) / 32 * 32;
@@ -166,13 +178,15 @@ struct PairSmem {
 
 // TMA: the tiles of the work list are staged with TMA box copies; otherwise
 // (periodic tiles whose halo crosses a lateral edge) by the cyclic gather
-template <int TYv, bool TMA>
-__global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
+// NR = 2 takes 128 registers per thread at most: two blocks of 8 warps per SM
+// for 32x8 tiles, one of 16 warps for 32x16 tiles
+template <int TYv, bool TMA, int NR>
+__global__ void __launch_bounds__(NR *(TILE_X / 2) * TYv, NR == 2 && TYv == 8 ? 2 : 1)
     k_pair(const DomDev *__restrict__ doms, const WorkItem *__restrict__ items, const unsigned char *__restrict__ tmaps,
            int rO, int rC, int rN, int rF, int first, const Eos E, unsigned *__restrict__ watch,
            unsigned stall_tx) {
-  using C = PairCfg<TYv>;
-  constexpr int NT = C::NT, HX = C::HX, PL = C::PL, PLP = C::PLP, NPP = C::NPP, NLPP = C::NLPP;
+  using C = PairCfg<TYv, NR>;
+  constexpr int NT = C::NT, NTH = C::NTH, HX = C::HX, PL = C::PL, PLP = C::PLP, NPP = C::NPP, NLPP = C::NLPP;
   static_assert(HX % 4 == 0, "halo rows of whole 16-byte chunks");
   extern __shared__ __align__(128) unsigned char smraw[];
   // TMA: the rings start on a 128-byte line (the launch adds 128 bytes for
@@ -218,7 +232,7 @@ __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
   int loff[NLPP][2], kbv[NLPP][2];
 #pragma unroll
   for (int s = 0; s < NLPP; s++) {
-    const int pp = tid + s * NT;
+    const int pp = tid + s * NTH;
 #pragma unroll
     for (int h = 0; h < 2; h++) {
       const int p = 2 * pp + h;
@@ -268,6 +282,8 @@ __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
   // a periodic tile whose halo crosses a lateral edge: 16-byte chunks of the
   // haloed rows from the cyclic indices, element by element where a chunk
   // crosses the edge
+  // (the first NT threads: with two roles the scalar warpgroup, so that the
+  // momentum warpgroup holds no copy state)
   constexpr int VEC = 4, CPR = HX / VEC, NCH = CPR * C::HY, NCQ = (NCH + NT - 1) / NT;
   int ch_dst[NCQ], ch_e[NCQ][VEC];
   bool ch_whole[NCQ];
@@ -277,7 +293,7 @@ __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
     const int row = t / CPR, col = t % CPR;
     const int x = i0 - 2 + VEC * col;
     const int rowoff = (row_y(j0 - 2 + row) + GH) * px;
-    ch_dst[q] = !TMA && t < NCH ? row * HX + VEC * col : -1;
+    ch_dst[q] = !TMA && tid < NT && t < NCH ? row * HX + VEC * col : -1;
     ch_whole[q] = x >= 0 && x + VEC <= nx;
 #pragma unroll
     for (int e = 0; e < VEC; e++) ch_e[q][e] = rowoff + col_x(x + e) + GX;
@@ -332,7 +348,7 @@ __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
     float *rh = S.rh[s4(kk)], *th = S.th[s4(kk)];
 #pragma unroll
     for (int s = 0; s < NLPP; s++) {
-      const int pp = tid + s * NT;
+      const int pp = tid + s * NTH;
       if (pp < NPP) {
         const int p = 2 * pp;
         st2(rh + p, add2(bc2(rb), ld2(cr + p)));
@@ -352,7 +368,7 @@ __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
     const int su = s3(K), sm = s4(K);
 #pragma unroll
     for (int s = 0; s < NLPP; s++) {
-      const int pp = tid + s * NT;
+      const int pp = tid + s * NTH;
       const int p = 2 * pp;
       const int hx = p % HX, hy = p / HX;
       if (pp < NPP && hy != 0) {
@@ -388,12 +404,16 @@ __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
     const float *op = S.op[s4(kk)];
 #pragma unroll
     for (int s = 0; s < NLPP; s++) {
-      const int pp = tid + s * NT;
+      const int pp = tid + s * NTH;
       if (pp < NPP) st2(S.to + 2 * pp, ek.pert(E, ld2(op + 2 * pp)));
     }
   };
 
-  const int tx = tid & 15, ty = tid >> 4;
+  // the pair of this thread (both warpgroups of NR = 2 map onto the tile's NT
+  // pairs alike) and its role
+  const int lt = NR == 1 ? tid : tid % NT;
+  const int role = NR == 1 ? 0 : tid / NT;  // NR = 2: 0 the scalars, 1 the momenta
+  const int tx = lt & 15, ty = lt >> 4;
   const int i = i0 + 2 * tx, j = j0 + ty;
   const bool rowok = j < D.cj1;
   const bool a0 = rowok && i >= D.ci0 && i < D.ci1, a1 = rowok && i + 1 >= D.ci0 && i + 1 < D.ci1;
@@ -422,6 +442,15 @@ __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
     mreg[a][2] = ld2(S.om[a4][2] + c);
   };
 
+  // the barrier of the z-march: with two roles the warpgroups run separate
+  // code, so a named barrier over all NTH threads (warps may reach it from
+  // different places)
+  auto sync_all = [] {
+    if constexpr (NR == 1)
+      __syncthreads();
+    else
+      asm volatile("bar.sync 1, %0;\n" ::"r"(NTH) : "memory");
+  };
   // a TMA wait that ran out (the same answer in every thread after a barrier)
   auto aborted = [&] {
     if constexpr (TMA)
@@ -465,301 +494,375 @@ __global__ void __launch_bounds__((TILE_X / 2) * TYv, 1)
   velocity(k0 - 1);
   velocity(k0);
 
-  float2 fz_carry = bc2(0.0f), hz_carry = bc2(0.0f);
-  unsigned wflag = 0;
   const float cfx = (float)(D.dt / D.dx), cfy = (float)(D.dt / D.dy), cfz = (float)(D.dt / D.dz);
-  for (int k = k0; started && k < k1; k++) {
-    const long long o = (long long)(k + GH) * plane + own;
-    float2 rO_ = bc2(0.0f);
-    if (active) rO_ = ld2(rpO + o);
-    EosK2 ek0, ek2;
-    ek0.load(thb, ipb, pik, k + GH);
-    ek2.load(thb, ipb, pik, k + 2 + GH);
-    const float rb2 = rhob[k + 2 + GH], tk = tau[k + GH];
-    const float rbc[5] = {rhobc[k + GH - 2] * U, rhobc[k + GH - 1] * U, rhobc[k + GH] * U, rhobc[k + GH + 1] * U,
-                          rhobc[k + GH + 2] * U};
-    arrive(k + 2);
-    __syncthreads();
-    if (aborted()) break;
-    // plane k + 3 is read from the next plane on; the last plane needs k1 + 1
-    if (k + 3 <= k1 + 1) {
-      stage(k + 3, true, true);
-      issued = k + 3;
-    }
-    derive_e(k + 2, rb2, ek2);
-    velocity(k + 1);
-    derive_old_e(k, ek0);
-    own_old_e(4, k + 2, ek2);
-    __syncthreads();
-    // the x-faces: this thread's low faces (i - 1/2, i + 1/2) as a pair; its
-    // highest face (i + 3/2) is the next thread's lowest, taken by shuffle
-    const int sk = s4(k), skm = s4(k - 1), skp = s4(k + 1);
-    const int ck = s5(k), ckm = s5(k - 1);
-    const float *R0 = S.rh[sk], *Rm = S.rh[skm], *Rp = S.rh[skp];
-    const float *H0 = S.th[sk], *Hm = S.th[skm], *Hp = S.th[skp];
-    const int uk = s3(k), ukp = s3(k + 1), ukm = s3(k - 1);
-    const float *ux0 = S.uu[uk][0], *uy0 = S.uu[uk][1], *uz0 = S.uu[uk][2];
-    const float *uxp = S.uu[ukp][0], *uyp = S.uu[ukp][1], *uzp = S.uu[ukp][2];
-    const float2 Rc = ld2(R0 + c), Hc = ld2(H0 + c);
-    const float2 Rl = ld2(R0 + c - 2), Hl = ld2(H0 + c - 2);
-    const float2 unx = mean4(ld2(ux0 + c), ld2(ux0 + c + HX), ld2(uxp + c), ld2(uxp + c + HX));
-    const float2 fxl = face_flux2(odd2(Rl, Rc), Rc, unx, Sx), hxl = face_flux2(odd2(Hl, Hc), Hc, unx, Sx);
-    float fxh = __shfl_down_sync(0xffffffffu, fxl.x, 1), hxh = __shfl_down_sync(0xffffffffu, hxl.x, 1);
-    if (last_tx) {
-      // the tile's last face, from the halo
-      const float r2 = R0[c + 2], h2 = H0[c + 2];
-      const float un = Ar<float>::mul(Ar<float>::add(Ar<float>::add(ux0[c + 2], ux0[c + 2 + HX]),
-                                                     Ar<float>::add(uxp[c + 2], uxp[c + 2 + HX])),
-                                      0.25f);
-      fxh = Ar<float>::mul(Ar<float>::mul(Ar<float>::mul(Ar<float>::add(Rc.y, r2), 0.5f), un), Sx.x);
-      hxh = Ar<float>::mul(Ar<float>::mul(Ar<float>::mul(Ar<float>::add(Hc.y, h2), 0.5f), un), Sx.x);
-    }
-    if (active) {
-      const float2 fxm = fxl, fxp = make_float2(fxl.y, fxh);
-      const float2 hxm = hxl, hxp = make_float2(hxl.y, hxh);
-      // y-faces: the corners (c, c+1) of cell c and (c+1, c+2) of cell c+1
-      const float2 uy00 = ld2(uy0 + c), uy02 = ld2(uy0 + c + 2), uyp0 = ld2(uyp + c), uyp2 = ld2(uyp + c + 2);
-      const float2 uy0H = ld2(uy0 + c + HX), uy0H2 = ld2(uy0 + c + HX + 2), uypH = ld2(uyp + c + HX),
-                   uypH2 = ld2(uyp + c + HX + 2);
-      const float2 unym = mean4(uy00, odd2(uy00, uy02), uyp0, odd2(uyp0, uyp2));
-      const float2 unyp = mean4(uy0H, odd2(uy0H, uy0H2), uypH, odd2(uypH, uypH2));
-      const float2 RS = ld2(R0 + c - HX), RN = ld2(R0 + c + HX), HS = ld2(H0 + c - HX), HN = ld2(H0 + c + HX);
-      const float2 fym = face_flux2(RS, Rc, unym, Sy), fyp = face_flux2(Rc, RN, unyp, Sy);
-      const float2 hym = face_flux2(HS, Hc, unym, Sy), hyp = face_flux2(Hc, HN, unyp, Sy);
-      // z-faces: corners (c, c+1, c+HX, c+HX+1) of the upper face; the lower
-      // face is the one of the plane below
-      const float2 uzp0 = ld2(uzp + c), uzp2 = ld2(uzp + c + 2), uzpH = ld2(uzp + c + HX),
-                   uzpH2 = ld2(uzp + c + HX + 2);
-      const float2 unzp = mean4(uzp0, odd2(uzp0, uzp2), uzpH, odd2(uzpH, uzpH2));
-      float2 fzp = face_flux2(Rc, ld2(Rp + c), unzp, Sz), hzp = face_flux2(Hc, ld2(Hp + c), unzp, Sz);
-      float2 fzm = fz_carry, hzm = hz_carry;
-      if (k == k0) {
-        const float2 uz00 = ld2(uz0 + c), uz02 = ld2(uz0 + c + 2), uz0H = ld2(uz0 + c + HX),
-                     uz0H2 = ld2(uz0 + c + HX + 2);
-        const float2 unzm = mean4(uz00, odd2(uz00, uz02), uz0H, odd2(uz0H, uz0H2));
-        fzm = face_flux2(ld2(Rm + c), Rc, unzm, Sz);
-        hzm = face_flux2(ld2(Hm + c), Hc, unzm, Sz);
-      }
-      fz_carry = fzp;
-      hz_carry = hzp;
-      if (k == 0) {
-        fzm = bc2(0.0f);
-        hzm = bc2(0.0f);
-      }
-      if (D.lid && k == nz - 1) {
-        fzp = bc2(0.0f);
-        hzp = bc2(0.0f);
-      }
-      const float2 RM = add2(add2(sub2(fxp, fxm), sub2(fyp, fym)), sub2(fzp, fzm));
-      const float2 RH = add2(add2(sub2(hxp, hxm), sub2(hyp, hym)), sub2(hzp, hzm));
-
-      // ---- artificial diffusion at n-1
-      const float *Tk = S.to;
-      const int ok4 = s4(k);
-      const bool wall = k < dlo || k >= dhi;
-      const float2 Tm2 = ld2(Tk + c - 2), Tc = ld2(Tk + c), Tp2 = ld2(Tk + c + 2);
-      const float2 Tl = odd2(Tm2, Tc), Tr = odd2(Tc, Tp2);
-      const float2 TS2 = ld2(Tk + c - 2 * HX), TS = ld2(Tk + c - HX), TN = ld2(Tk + c + HX), TN2 = ld2(Tk + c + 2 * HX);
-      float2 dd, dmv[3];
-      if (!wall) {
-        // x stencil of the pair: (c-2, c-1, c, c+1, c+2) and (c-1, c, c+1, c+2, c+3)
-        dd = add2(add2(d4_2(Tm2, Tl, Tc, Tr, Tp2), d4_2(TS2, TS, Tc, TN, TN2)),
-                  d4_2(treg[0], treg[1], treg[2], treg[3], treg[4]));
+  // the z-march of this thread's role: DS the scalar update, DM the momentum
+  // update (both when NR = 1); returns the watchdog flags
+  auto march = [&](auto ds_, auto dm_) -> unsigned {
+    constexpr bool DS = decltype(ds_)::value, DM = decltype(dm_)::value;
+    float2 fz_carry = bc2(0.0f), hz_carry = bc2(0.0f);
+    unsigned wflag = 0;
+    for (int k = k0; started && k < k1; k++) {
+      const long long o = (long long)(k + GH) * plane + own;
+      float2 rO_ = bc2(0.0f);
+      if (DS && active) rO_ = ld2(rpO + o);
+      EosK2 ek0, ek2;
+      ek0.load(thb, ipb, pik, k + GH);
+      ek2.load(thb, ipb, pik, k + 2 + GH);
+      const float rb2 = rhob[k + 2 + GH];
+      float tk = 0.0f, rbc[5] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+      if constexpr (DM) {
+        tk = tau[k + GH];
 #pragma unroll
-        for (int d = 0; d < 3; d++) {
+        for (int a = 0; a < 5; a++) rbc[a] = rhobc[k + GH - 2 + a] * U;
+      }
+      arrive(k + 2);
+      sync_all();
+      if (aborted()) break;
+      // plane k + 3 is read from the next plane on; the last plane needs k1 + 1
+      // (its copies are issued by the scalar role: thread 0 or the gather's threads)
+      if (DS && k + 3 <= k1 + 1) {
+        stage(k + 3, true, true);
+        issued = k + 3;
+      }
+      derive_e(k + 2, rb2, ek2);
+      velocity(k + 1);
+      derive_old_e(k, ek0);
+      if constexpr (DS) treg[4] = ek2.pert(E, ld2(S.op[s4(k + 2)] + c));
+      if constexpr (DM && NR == 1) {
+        const int a4 = s4(k + 2);
+        mreg[4][0] = ld2(S.om[a4][0] + c);
+        mreg[4][1] = ld2(S.om[a4][1] + c);
+        mreg[4][2] = ld2(S.om[a4][2] + c);
+      }
+      // the own column's momentum at n-1, level k - 2 + a: one role keeps all
+      // five levels in registers; the momentum role of two keeps levels k-2
+      // and k-1 and reads k .. k+2 from the ring, which still holds them
+      auto mo = [&](int a, int d) -> float2 {
+        if constexpr (NR == 2)
+          if (a >= 2) return ld2(S.om[s4(k - 2 + a)][d] + c);
+        return mreg[a][d];
+      };
+      sync_all();
+      // the x-faces: this thread's low faces (i - 1/2, i + 1/2) as a pair; its
+      // highest face (i + 3/2) is the next thread's lowest, taken by shuffle
+      const int sk = s4(k), skm = s4(k - 1), skp = s4(k + 1);
+      const int ck = s5(k), ckm = s5(k - 1);
+      const float *R0 = S.rh[sk], *Rm = S.rh[skm], *Rp = S.rh[skp];
+      const float *H0 = S.th[sk], *Hm = S.th[skm], *Hp = S.th[skp];
+      const int uk = s3(k), ukp = s3(k + 1), ukm = s3(k - 1);
+      const float *ux0 = S.uu[uk][0], *uy0 = S.uu[uk][1], *uz0 = S.uu[uk][2];
+      const float *uxp = S.uu[ukp][0], *uyp = S.uu[ukp][1], *uzp = S.uu[ukp][2];
+      const float2 Rc = ld2(R0 + c), Rl = ld2(R0 + c - 2);
+      float2 Hc = bc2(0.0f), fxl = bc2(0.0f), hxl = bc2(0.0f);
+      float fxh = 0.0f, hxh = 0.0f;
+      if constexpr (DS) {
+        Hc = ld2(H0 + c);
+        const float2 Hl = ld2(H0 + c - 2);
+        const float2 unx = mean4(ld2(ux0 + c), ld2(ux0 + c + HX), ld2(uxp + c), ld2(uxp + c + HX));
+        fxl = face_flux2(odd2(Rl, Rc), Rc, unx, Sx);
+        hxl = face_flux2(odd2(Hl, Hc), Hc, unx, Sx);
+        fxh = __shfl_down_sync(0xffffffffu, fxl.x, 1);
+        hxh = __shfl_down_sync(0xffffffffu, hxl.x, 1);
+        if (last_tx) {
+          // the tile's last face, from the halo
+          const float r2 = R0[c + 2], h2 = H0[c + 2];
+          const float un = Ar<float>::mul(Ar<float>::add(Ar<float>::add(ux0[c + 2], ux0[c + 2 + HX]),
+                                                         Ar<float>::add(uxp[c + 2], uxp[c + 2 + HX])),
+                                          0.25f);
+          fxh = Ar<float>::mul(Ar<float>::mul(Ar<float>::mul(Ar<float>::add(Rc.y, r2), 0.5f), un), Sx.x);
+          hxh = Ar<float>::mul(Ar<float>::mul(Ar<float>::mul(Ar<float>::add(Hc.y, h2), 0.5f), un), Sx.x);
+        }
+      }
+      if (active) {
+        const float2 RS = ld2(R0 + c - HX);
+        float2 RM = bc2(0.0f), RH = bc2(0.0f);
+        if constexpr (DS) {
+        const float2 fxm = fxl, fxp = make_float2(fxl.y, fxh);
+        const float2 hxm = hxl, hxp = make_float2(hxl.y, hxh);
+        // y-faces: the corners (c, c+1) of cell c and (c+1, c+2) of cell c+1
+        const float2 uy00 = ld2(uy0 + c), uy02 = ld2(uy0 + c + 2), uyp0 = ld2(uyp + c), uyp2 = ld2(uyp + c + 2);
+        const float2 uy0H = ld2(uy0 + c + HX), uy0H2 = ld2(uy0 + c + HX + 2), uypH = ld2(uyp + c + HX),
+                     uypH2 = ld2(uyp + c + HX + 2);
+        const float2 unym = mean4(uy00, odd2(uy00, uy02), uyp0, odd2(uyp0, uyp2));
+        const float2 unyp = mean4(uy0H, odd2(uy0H, uy0H2), uypH, odd2(uypH, uypH2));
+        const float2 RN = ld2(R0 + c + HX), HS = ld2(H0 + c - HX), HN = ld2(H0 + c + HX);
+        const float2 fym = face_flux2(RS, Rc, unym, Sy), fyp = face_flux2(Rc, RN, unyp, Sy);
+        const float2 hym = face_flux2(HS, Hc, unym, Sy), hyp = face_flux2(Hc, HN, unyp, Sy);
+        // z-faces: corners (c, c+1, c+HX, c+HX+1) of the upper face; the lower
+        // face is the one of the plane below
+        const float2 uzp0 = ld2(uzp + c), uzp2 = ld2(uzp + c + 2), uzpH = ld2(uzp + c + HX),
+                     uzpH2 = ld2(uzp + c + HX + 2);
+        const float2 unzp = mean4(uzp0, odd2(uzp0, uzp2), uzpH, odd2(uzpH, uzpH2));
+        float2 fzp = face_flux2(Rc, ld2(Rp + c), unzp, Sz), hzp = face_flux2(Hc, ld2(Hp + c), unzp, Sz);
+        float2 fzm = fz_carry, hzm = hz_carry;
+        if (k == k0) {
+          const float2 uz00 = ld2(uz0 + c), uz02 = ld2(uz0 + c + 2), uz0H = ld2(uz0 + c + HX),
+                       uz0H2 = ld2(uz0 + c + HX + 2);
+          const float2 unzm = mean4(uz00, odd2(uz00, uz02), uz0H, odd2(uz0H, uz0H2));
+          fzm = face_flux2(ld2(Rm + c), Rc, unzm, Sz);
+          hzm = face_flux2(ld2(Hm + c), Hc, unzm, Sz);
+        }
+        fz_carry = fzp;
+        hz_carry = hzp;
+        if (k == 0) {
+          fzm = bc2(0.0f);
+          hzm = bc2(0.0f);
+        }
+        if (D.lid && k == nz - 1) {
+          fzp = bc2(0.0f);
+          hzp = bc2(0.0f);
+        }
+        RM = add2(add2(sub2(fxp, fxm), sub2(fyp, fym)), sub2(fzp, fzm));
+        RH = add2(add2(sub2(hxp, hxm), sub2(hyp, hym)), sub2(hzp, hzm));
+        }
+
+        // ---- artificial diffusion at n-1
+        const int ok4 = s4(k);
+        const bool wall = k < dlo || k >= dhi;
+        float2 dd = bc2(0.0f), dmv[3] = {bc2(0.0f), bc2(0.0f), bc2(0.0f)};
+        // the momentum sums of one component d, with the axis sum f (fourth
+        // difference or wall-aware form) and the vertical flags gz
+        auto dmom = [&](int d, auto f) {
           const float *Mk = S.om[ok4][d];
           const float2 ref0 = bc2(d == 0 ? rbc[2] : 0.0f);
           const float2 m2 = sub2(ld2(Mk + c - 2), ref0), m0 = sub2(ld2(Mk + c), ref0), p2 = sub2(ld2(Mk + c + 2), ref0);
           const float2 l1 = odd2(m2, m0), r1 = odd2(m0, p2);
-          float2 dm = add2(d4_2(m2, l1, m0, r1, p2),
-                           d4_2(sub2(ld2(Mk + c - 2 * HX), ref0), sub2(ld2(Mk + c - HX), ref0), m0,
-                                sub2(ld2(Mk + c + HX), ref0), sub2(ld2(Mk + c + 2 * HX), ref0)));
+          float2 dm = add2(f(0, m2, l1, m0, r1, p2),
+                           f(1, sub2(ld2(Mk + c - 2 * HX), ref0), sub2(ld2(Mk + c - HX), ref0), m0,
+                             sub2(ld2(Mk + c + HX), ref0), sub2(ld2(Mk + c + 2 * HX), ref0)));
           if (d == 0)
-            dm = add2(dm, d4_2(sub2(mreg[0][0], bc2(rbc[0])), sub2(mreg[1][0], bc2(rbc[1])), sub2(mreg[2][0], ref0),
-                               sub2(mreg[3][0], bc2(rbc[3])), sub2(mreg[4][0], bc2(rbc[4]))));
+            dm = add2(dm, f(2, sub2(mo(0, 0), bc2(rbc[0])), sub2(mo(1, 0), bc2(rbc[1])), sub2(mo(2, 0), ref0),
+                            sub2(mo(3, 0), bc2(rbc[3])), sub2(mo(4, 0), bc2(rbc[4]))));
           else
-            dm = add2(dm, d4_2(mreg[0][d], mreg[1][d], mreg[2][d], mreg[3][d], mreg[4][d]));
-          dmv[d] = dm;
-        }
-      } else {
-        bool fx0[4], fx1[4], fy0[4], fy1[4], fz0[4], fz1[4];
-        bool gx0[4], gx1[4], gy0[4], gy1[4], gz0[4], gz1[4];
-        const DiffCol &Q0 = D.dcol[own], &Q1 = D.dcol[own + 1];
-        const int offz[4] = {-2, -1, 1, 2};
+            dm = add2(dm, f(2, mo(0, d), mo(1, d), mo(2, d), mo(3, d), mo(4, d)));
+          return dm;
+        };
+        if (!wall) {
+          auto f4 = [](int, float2 a, float2 b, float2 c_, float2 d, float2 e) { return d4_2(a, b, c_, d, e); };
+          if constexpr (DS) {
+            const float *Tk = S.to;
+            const float2 Tm2 = ld2(Tk + c - 2), Tc = ld2(Tk + c), Tp2 = ld2(Tk + c + 2);
+            const float2 Tl = odd2(Tm2, Tc), Tr = odd2(Tc, Tp2);
+            const float2 TS2 = ld2(Tk + c - 2 * HX), TS = ld2(Tk + c - HX), TN = ld2(Tk + c + HX),
+                         TN2 = ld2(Tk + c + 2 * HX);
+            // x stencil of the pair: (c-2, c-1, c, c+1, c+2) and (c-1, c, c+1, c+2, c+3)
+            dd = add2(add2(d4_2(Tm2, Tl, Tc, Tr, Tp2), d4_2(TS2, TS, Tc, TN, TN2)),
+                      d4_2(treg[0], treg[1], treg[2], treg[3], treg[4]));
+          }
+          if constexpr (DM) {
 #pragma unroll
-        for (int a = 0; a < 4; a++) {
-          fx0[a] = fluid_at(k, Q0.cx[a], Q0.ctop);
-          fx1[a] = fluid_at(k, Q1.cx[a], Q1.ctop);
-          fy0[a] = fluid_at(k, Q0.cy[a], Q0.ctop);
-          fy1[a] = fluid_at(k, Q1.cy[a], Q1.ctop);
-          fz0[a] = fluid_at(k + offz[a], Q0.c0, Q0.ctop);
-          fz1[a] = fluid_at(k + offz[a], Q1.c0, Q1.ctop);
-          gx0[a] = fluid_at(k, Q0.vx[a], Q0.vtop);
-          gx1[a] = fluid_at(k, Q1.vx[a], Q1.vtop);
-          gy0[a] = fluid_at(k, Q0.vy[a], Q0.vtop);
-          gy1[a] = fluid_at(k, Q1.vy[a], Q1.vtop);
-          gz0[a] = fluid_at(k + offz[a], Q0.v0, Q0.vtop);
-          gz1[a] = fluid_at(k + offz[a], Q1.v0, Q1.vtop);
-        }
-        dd = add2(add2(dax2(Tm2, Tl, Tc, Tr, Tp2, true, fx0, fx1), dax2(TS2, TS, Tc, TN, TN2, true, fy0, fy1)),
-                  dax2(treg[0], treg[1], treg[2], treg[3], treg[4], true, fz0, fz1));
+            for (int d = 0; d < 3; d++) dmv[d] = dmom(d, f4);
+          }
+        } else {
+          const DiffCol &Q0 = D.dcol[own], &Q1 = D.dcol[own + 1];
+          const int offz[4] = {-2, -1, 1, 2};
+          if constexpr (DS) {
+            bool fx0[4], fx1[4], fy0[4], fy1[4], fz0[4], fz1[4];
 #pragma unroll
-        for (int d = 0; d < 3; d++) {
-          const float *Mk = S.om[ok4][d];
-          const float2 ref0 = bc2(d == 0 ? rbc[2] : 0.0f);
-          const float2 m2 = sub2(ld2(Mk + c - 2), ref0), m0 = sub2(ld2(Mk + c), ref0), p2 = sub2(ld2(Mk + c + 2), ref0);
-          const float2 l1 = odd2(m2, m0), r1 = odd2(m0, p2);
-          float2 dm = add2(dax2(m2, l1, m0, r1, p2, false, gx0, gx1),
-                           dax2(sub2(ld2(Mk + c - 2 * HX), ref0), sub2(ld2(Mk + c - HX), ref0), m0,
-                                sub2(ld2(Mk + c + HX), ref0), sub2(ld2(Mk + c + 2 * HX), ref0), false, gy0, gy1));
-          if (d == 0)
-            dm = add2(dm, dax2(sub2(mreg[0][0], bc2(rbc[0])), sub2(mreg[1][0], bc2(rbc[1])), sub2(mreg[2][0], ref0),
-                               sub2(mreg[3][0], bc2(rbc[3])), sub2(mreg[4][0], bc2(rbc[4])), false, gz0, gz1));
-          else
-            dm = add2(dm, dax2(mreg[0][d], mreg[1][d], mreg[2][d], mreg[3][d], mreg[4][d], false, gz0, gz1));
-          dmv[d] = dm;
+            for (int a = 0; a < 4; a++) {
+              fx0[a] = fluid_at(k, Q0.cx[a], Q0.ctop);
+              fx1[a] = fluid_at(k, Q1.cx[a], Q1.ctop);
+              fy0[a] = fluid_at(k, Q0.cy[a], Q0.ctop);
+              fy1[a] = fluid_at(k, Q1.cy[a], Q1.ctop);
+              fz0[a] = fluid_at(k + offz[a], Q0.c0, Q0.ctop);
+              fz1[a] = fluid_at(k + offz[a], Q1.c0, Q1.ctop);
+            }
+            const float *Tk = S.to;
+            const float2 Tm2 = ld2(Tk + c - 2), Tc = ld2(Tk + c), Tp2 = ld2(Tk + c + 2);
+            const float2 Tl = odd2(Tm2, Tc), Tr = odd2(Tc, Tp2);
+            const float2 TS2 = ld2(Tk + c - 2 * HX), TS = ld2(Tk + c - HX), TN = ld2(Tk + c + HX),
+                         TN2 = ld2(Tk + c + 2 * HX);
+            dd = add2(add2(dax2(Tm2, Tl, Tc, Tr, Tp2, true, fx0, fx1), dax2(TS2, TS, Tc, TN, TN2, true, fy0, fy1)),
+                      dax2(treg[0], treg[1], treg[2], treg[3], treg[4], true, fz0, fz1));
+          }
+          if constexpr (DM) {
+            bool gx0[4], gx1[4], gy0[4], gy1[4], gz0[4], gz1[4];
+#pragma unroll
+            for (int a = 0; a < 4; a++) {
+              gx0[a] = fluid_at(k, Q0.vx[a], Q0.vtop);
+              gx1[a] = fluid_at(k, Q1.vx[a], Q1.vtop);
+              gy0[a] = fluid_at(k, Q0.vy[a], Q0.vtop);
+              gy1[a] = fluid_at(k, Q1.vy[a], Q1.vtop);
+              gz0[a] = fluid_at(k + offz[a], Q0.v0, Q0.vtop);
+              gz1[a] = fluid_at(k + offz[a], Q1.v0, Q1.vtop);
+            }
+            auto fw = [&](int axis, float2 a, float2 b, float2 c_, float2 d, float2 e) {
+              return axis == 0 ? dax2(a, b, c_, d, e, false, gx0, gx1)
+                               : axis == 1 ? dax2(a, b, c_, d, e, false, gy0, gy1) : dax2(a, b, c_, d, e, false, gz0, gz1);
+            };
+#pragma unroll
+            for (int d = 0; d < 3; d++) dmv[d] = dmom(d, fw);
+          }
         }
-      }
 
-      // ---- scalar update: rho', p' (Sec 2.4), leapfrog and filter
-      const float2 Dth = mul2(bc2(-kdif), dd);
-      const float2 rC_ = ld2(S.cr[ck] + c), pC_ = ld2(S.cp[ck] + c), pO_ = ld2(S.op[ok4] + c);
-      const float2 dtv = bc2(dt2);
-      float2 rN_ = sub2(rO_, mul2(dtv, mul2(RM, bc2(v0inv))));
-      float2 pN_ = sub2(pO_, mul2(mul2(mul2(dtv, bc2(Cp)), ek0.exner(E, pC_)), sub2(mul2(RH, bc2(v0inv)), Dth)));
-      if (k < kug0) {
-        rN_.x = 0.0f;
-        pN_.x = 0.0f;
-      }
-      if (k < kug1) {
-        rN_.y = 0.0f;
-        pN_.y = 0.0f;
-      }
-      float2 rF_ = fma2(bc2(nu), add2(sub2(rN_, mul2(bc2(2.0f), rC_)), rO_), rC_);
-      float2 pF_ = fma2(bc2(nu), add2(sub2(pN_, mul2(bc2(2.0f), pC_)), pO_), pC_);
-      if (k < kug0) {
-        rF_.x = 0.0f;
-        pF_.x = 0.0f;
-      }
-      if (k < kug1) {
-        rF_.y = 0.0f;
-        pF_.y = 0.0f;
-      }
+        float2 rN_ = bc2(0.0f), pN_ = bc2(0.0f), rF_ = bc2(0.0f), pF_ = bc2(0.0f);
+        if constexpr (DS) {
+          // ---- scalar update: rho', p' (Sec 2.4), leapfrog and filter
+          const float2 Dth = mul2(bc2(-kdif), dd);
+          const float2 rC_ = ld2(S.cr[ck] + c), pC_ = ld2(S.cp[ck] + c), pO_ = ld2(S.op[ok4] + c);
+          const float2 dtv = bc2(dt2);
+          rN_ = sub2(rO_, mul2(dtv, mul2(RM, bc2(v0inv))));
+          pN_ = sub2(pO_, mul2(mul2(mul2(dtv, bc2(Cp)), ek0.exner(E, pC_)), sub2(mul2(RH, bc2(v0inv)), Dth)));
+          if (k < kug0) {
+            rN_.x = 0.0f;
+            pN_.x = 0.0f;
+          }
+          if (k < kug1) {
+            rN_.y = 0.0f;
+            pN_.y = 0.0f;
+          }
+          rF_ = fma2(bc2(nu), add2(sub2(rN_, mul2(bc2(2.0f), rC_)), rO_), rC_);
+          pF_ = fma2(bc2(nu), add2(sub2(pN_, mul2(bc2(2.0f), pC_)), pO_), pC_);
+          if (k < kug0) {
+            rF_.x = 0.0f;
+            pF_.x = 0.0f;
+          }
+          if (k < kug1) {
+            rF_.y = 0.0f;
+            pF_.y = 0.0f;
+          }
+        }
 
-      // ---- velocity cells centred on the corners (c, c+1): Eqs. momentum_u_d .. w_d
-      // vertical pair sums of the four cell columns around each corner: the
-      // south-west columns (c-HX-1, c-HX) and west (c-1, c) as odd pairs
-      const float2 Rmc = ld2(Rm + c), RmS = ld2(Rm + c - HX), RmS2 = ld2(Rm + c - HX - 2), Rm2 = ld2(Rm + c - 2);
-      const float2 RS2 = ld2(R0 + c - HX - 2);
-      const float2 cS = RS, cSW = odd2(RS2, RS), cW = odd2(Rl, Rc);
-      const float2 mS = RmS, mSW = odd2(RmS2, RmS), mW = odd2(Rm2, Rmc);
-      const float2 v00 = add2(mSW, cSW), v10 = add2(mS, cS), v01 = add2(mW, cW), v11 = add2(Rmc, Rc);
-      const float2 q = bc2(0.25f);
-      const float2 rE = mul2(add2(v10, v11), q), rW = mul2(add2(v00, v01), q);
-      const float2 rNn = mul2(add2(v01, v11), q), rS = mul2(add2(v00, v10), q);
-      const float2 rT = mul2(add2(add2(cSW, cS), add2(cW, Rc)), q);
-      const float2 rB = mul2(add2(add2(mSW, mS), add2(mW, Rmc)), q);
-      // corner velocities: this pair (c, c+1), its x-neighbours (c-1, c) and
-      // (c+1, c+2), y-neighbours and the planes above and below
-      const float *uxm = S.uu[ukm][0], *uym = S.uu[ukm][1], *uzm = S.uu[ukm][2];
-      float2 u0[3], uE[3], uW[3], uN[3], uS[3], uT[3], uB[3];
-      {
-        const float *uk3[3] = {ux0, uy0, uz0}, *up3[3] = {uxp, uyp, uzp}, *um3[3] = {uxm, uym, uzm};
+        if constexpr (DM) {
+          // ---- velocity cells centred on the corners (c, c+1): Eqs. momentum_u_d .. w_d
+          // vertical pair sums of the four cell columns around each corner: the
+          // south-west columns (c-HX-1, c-HX) and west (c-1, c) as odd pairs
+          const float2 Rmc = ld2(Rm + c), RmS = ld2(Rm + c - HX), RmS2 = ld2(Rm + c - HX - 2), Rm2 = ld2(Rm + c - 2);
+          const float2 RS2 = ld2(R0 + c - HX - 2);
+          const float2 cS = RS, cSW = odd2(RS2, RS), cW = odd2(Rl, Rc);
+          const float2 mS = RmS, mSW = odd2(RmS2, RmS), mW = odd2(Rm2, Rmc);
+          const float2 v00 = add2(mSW, cSW), v10 = add2(mS, cS), v01 = add2(mW, cW), v11 = add2(Rmc, Rc);
+          const float2 q = bc2(0.25f);
+          const float2 rE = mul2(add2(v10, v11), q), rW = mul2(add2(v00, v01), q);
+          const float2 rNn = mul2(add2(v01, v11), q), rS = mul2(add2(v00, v10), q);
+          const float2 rT = mul2(add2(add2(cSW, cS), add2(cW, Rc)), q);
+          const float2 rB = mul2(add2(add2(mSW, mS), add2(mW, Rmc)), q);
+          // corner velocities: this pair (c, c+1), its x-neighbours (c-1, c) and
+          // (c+1, c+2), y-neighbours and the planes above and below
+          const float *uxm = S.uu[ukm][0], *uym = S.uu[ukm][1], *uzm = S.uu[ukm][2];
+          float2 u0[3], uE[3], uW[3], uN[3], uS[3], uT[3], uB[3];
+          {
+            const float *uk3[3] = {ux0, uy0, uz0}, *up3[3] = {uxp, uyp, uzp}, *um3[3] = {uxm, uym, uzm};
+    #pragma unroll
+            for (int d = 0; d < 3; d++) {
+              const float2 a = ld2(uk3[d] + c - 2), b = ld2(uk3[d] + c), e = ld2(uk3[d] + c + 2);
+              u0[d] = b;
+              uW[d] = odd2(a, b);
+              uE[d] = odd2(b, e);
+              uN[d] = ld2(uk3[d] + c + HX);
+              uS[d] = ld2(uk3[d] + c - HX);
+              uT[d] = ld2(up3[d] + c);
+              uB[d] = ld2(um3[d] + c);
+            }
+          }
+          const float2 gE = mul2(mul2(rE, add2(u0[0], uE[0])), bc2(hSx)), gW = mul2(mul2(rW, add2(uW[0], u0[0])), bc2(hSx));
+          const float2 gN = mul2(mul2(rNn, add2(u0[1], uN[1])), bc2(hSy)), gS = mul2(mul2(rS, add2(uS[1], u0[1])), bc2(hSy));
+          const float2 gT = mul2(mul2(rT, add2(u0[2], uT[2])), bc2(hSz)), gB = mul2(mul2(rB, add2(uB[2], u0[2])), bc2(hSz));
+          const float2 gsum = add2(add2(sub2(gE, gW), sub2(gN, gS)), sub2(gT, gB));
+          // pressure sums and the buoyancy mean (rho' of the eight cells)
+          const float *P0 = S.cp[ck], *Pm = S.cp[ckm];
+          const float2 P0c = ld2(P0 + c), P0S = ld2(P0 + c - HX), P0S2 = ld2(P0 + c - HX - 2), P02 = ld2(P0 + c - 2);
+          const float2 Pmc = ld2(Pm + c), PmS = ld2(Pm + c - HX), PmS2 = ld2(Pm + c - HX - 2), Pm2 = ld2(Pm + c - 2);
+          const float2 pcSW = odd2(P0S2, P0S), pcW = odd2(P02, P0c), pmSW = odd2(PmS2, PmS), pmW = odd2(Pm2, Pmc);
+          const float2 w00 = add2(pmSW, pcSW), w10 = add2(PmS, P0S), w01 = add2(pmW, pcW), w11 = add2(Pmc, P0c);
+          const float2 pE = add2(w10, w11), pW = add2(w00, w01), pNn = add2(w01, w11), pS = add2(w00, w10);
+          const float2 pT = add2(add2(pcSW, P0S), add2(pcW, P0c));
+          const float2 pB = add2(add2(pmSW, PmS), add2(pmW, Pmc));
+          const float *Q0p = S.cr[ck], *Qmp = S.cr[ckm];
+          const float2 Q0c = ld2(Q0p + c), Q0S = ld2(Q0p + c - HX), Q0S2 = ld2(Q0p + c - HX - 2), Q02 = ld2(Q0p + c - 2);
+          const float2 Qmc = ld2(Qmp + c), QmS = ld2(Qmp + c - HX), QmS2 = ld2(Qmp + c - HX - 2), Qm2 = ld2(Qmp + c - 2);
+          const float2 r8 = add2(add2(add2(odd2(Q0S2, Q0S), Q0S), add2(odd2(Q02, Q0c), Q0c)),
+                                 add2(add2(odd2(QmS2, QmS), QmS), add2(odd2(Qm2, Qmc), Qmc)));
+          const float2 pg[3] = {mul2(sub2(pE, pW), bc2(qdx)), mul2(sub2(pNn, pS), bc2(qdy)), mul2(sub2(pT, pB), bc2(qdz))};
+          const float2 mcur[3] = {ld2(S.cm[sk][0] + c), ld2(S.cm[sk][1] + c), ld2(S.cm[sk][2] + c)};
+          float2 mnew[3], mflt[3];
+    #pragma unroll
+          for (int d = 0; d < 3; d++) {
+            const float2 adv =
+                fma2(u0[d], gsum,
+                     add2(add2(sub2(mul2(gE, uE[d]), mul2(gW, uW[d])), sub2(mul2(gN, uN[d]), mul2(gS, uS[d]))),
+                          sub2(mul2(gT, uT[d]), mul2(gB, uB[d]))));
+            float2 tend = sub2(mul2(adv, bc2(-v0inv)), pg[d]);
+            if (d == 2) tend = sub2(tend, mul2(bc2(g * 0.125f), r8));
+            const float2 ref0 = bc2(d == 0 ? rbc[2] : 0.0f);
+            const float2 mold = mo(2, d);
+            tend = sub2(tend, fma2(bc2(kdif), dmv[d], mul2(bc2(tk), sub2(mold, ref0))));
+            mnew[d] = fma2(bc2(dt2), tend, mold);
+            mflt[d] = fma2(bc2(nu), add2(sub2(mnew[d], mul2(bc2(2.0f), mcur[d])), mold), mcur[d]);
+          }
+          {
+            const float2 chk = add2(add2(mnew[0], mnew[1]), mnew[2]);
+            const float cx = q0 ? chk.x : 0.0f, cy = q1 ? chk.y : 0.0f;
+            if (!isfinite(cx) || !isfinite(cy)) wflag |= WATCH_NONFINITE;
+            const float2 cou = fma2(make_float2(fabsf(u0[0].x), fabsf(u0[0].y)), bc2(cfx),
+                                    fma2(make_float2(fabsf(u0[1].x), fabsf(u0[1].y)), bc2(cfy),
+                                         mul2(make_float2(fabsf(u0[2].x), fabsf(u0[2].y)), bc2(cfz))));
+            if ((a0 && cou.x > 1.0f) || (a1 && cou.y > 1.0f)) wflag |= WATCH_COURANT;
+          }
+          // stores after every shared-memory read of the plane: both corners as
+          // one 8-byte store where both are computed
 #pragma unroll
-        for (int d = 0; d < 3; d++) {
-          const float2 a = ld2(uk3[d] + c - 2), b = ld2(uk3[d] + c), e = ld2(uk3[d] + c + 2);
-          u0[d] = b;
-          uW[d] = odd2(a, b);
-          uE[d] = odd2(b, e);
-          uN[d] = ld2(uk3[d] + c + HX);
-          uS[d] = ld2(uk3[d] + c - HX);
-          uT[d] = ld2(up3[d] + c);
-          uB[d] = ld2(um3[d] + c);
+          for (int d = 0; d < 3; d++) {
+            if (q0 && q1) {
+              st2(mN[d] + o, mnew[d]);
+              st2(mF[d] + o, mflt[d]);
+            } else if (q0) {
+              mN[d][o] = mnew[d].x;
+              mF[d][o] = mflt[d].x;
+            } else if (q1) {
+              mN[d][o + 1] = mnew[d].y;
+              mF[d][o + 1] = mflt[d].y;
+            }
+          }
+        }
+        if constexpr (DS) {
+          const float2 chk = add2(rN_, pN_);
+          const float cx = a0 ? chk.x : 0.0f, cy = a1 ? chk.y : 0.0f;
+          if (!isfinite(cx) || !isfinite(cy)) wflag |= WATCH_NONFINITE;
+          if (a0 && a1) {
+            st2(rpN + o, rN_);
+            st2(ppN + o, pN_);
+            st2(rpF + o, rF_);
+            st2(ppF + o, pF_);
+          } else if (a0) {
+            rpN[o] = rN_.x;
+            ppN[o] = pN_.x;
+            rpF[o] = rF_.x;
+            ppF[o] = pF_.x;
+          } else if (a1) {
+            rpN[o + 1] = rN_.y;
+            ppN[o + 1] = pN_.y;
+            rpF[o + 1] = rF_.y;
+            ppF[o + 1] = pF_.y;
+          }
         }
       }
-      const float2 gE = mul2(mul2(rE, add2(u0[0], uE[0])), bc2(hSx)), gW = mul2(mul2(rW, add2(uW[0], u0[0])), bc2(hSx));
-      const float2 gN = mul2(mul2(rNn, add2(u0[1], uN[1])), bc2(hSy)), gS = mul2(mul2(rS, add2(uS[1], u0[1])), bc2(hSy));
-      const float2 gT = mul2(mul2(rT, add2(u0[2], uT[2])), bc2(hSz)), gB = mul2(mul2(rB, add2(uB[2], u0[2])), bc2(hSz));
-      const float2 gsum = add2(add2(sub2(gE, gW), sub2(gN, gS)), sub2(gT, gB));
-      // pressure sums and the buoyancy mean (rho' of the eight cells)
-      const float *P0 = S.cp[ck], *Pm = S.cp[ckm];
-      const float2 P0c = ld2(P0 + c), P0S = ld2(P0 + c - HX), P0S2 = ld2(P0 + c - HX - 2), P02 = ld2(P0 + c - 2);
-      const float2 Pmc = ld2(Pm + c), PmS = ld2(Pm + c - HX), PmS2 = ld2(Pm + c - HX - 2), Pm2 = ld2(Pm + c - 2);
-      const float2 pcSW = odd2(P0S2, P0S), pcW = odd2(P02, P0c), pmSW = odd2(PmS2, PmS), pmW = odd2(Pm2, Pmc);
-      const float2 w00 = add2(pmSW, pcSW), w10 = add2(PmS, P0S), w01 = add2(pmW, pcW), w11 = add2(Pmc, P0c);
-      const float2 pE = add2(w10, w11), pW = add2(w00, w01), pNn = add2(w01, w11), pS = add2(w00, w10);
-      const float2 pT = add2(add2(pcSW, P0S), add2(pcW, P0c));
-      const float2 pB = add2(add2(pmSW, PmS), add2(pmW, Pmc));
-      const float *Q0p = S.cr[ck], *Qmp = S.cr[ckm];
-      const float2 Q0c = ld2(Q0p + c), Q0S = ld2(Q0p + c - HX), Q0S2 = ld2(Q0p + c - HX - 2), Q02 = ld2(Q0p + c - 2);
-      const float2 Qmc = ld2(Qmp + c), QmS = ld2(Qmp + c - HX), QmS2 = ld2(Qmp + c - HX - 2), Qm2 = ld2(Qmp + c - 2);
-      const float2 r8 = add2(add2(add2(odd2(Q0S2, Q0S), Q0S), add2(odd2(Q02, Q0c), Q0c)),
-                             add2(add2(odd2(QmS2, QmS), QmS), add2(odd2(Qm2, Qmc), Qmc)));
-      const float2 pg[3] = {mul2(sub2(pE, pW), bc2(qdx)), mul2(sub2(pNn, pS), bc2(qdy)), mul2(sub2(pT, pB), bc2(qdz))};
-      const float2 mcur[3] = {ld2(S.cm[sk][0] + c), ld2(S.cm[sk][1] + c), ld2(S.cm[sk][2] + c)};
-      float2 mnew[3], mflt[3];
 #pragma unroll
-      for (int d = 0; d < 3; d++) {
-        const float2 adv =
-            fma2(u0[d], gsum,
-                 add2(add2(sub2(mul2(gE, uE[d]), mul2(gW, uW[d])), sub2(mul2(gN, uN[d]), mul2(gS, uS[d]))),
-                      sub2(mul2(gT, uT[d]), mul2(gB, uB[d]))));
-        float2 tend = sub2(mul2(adv, bc2(-v0inv)), pg[d]);
-        if (d == 2) tend = sub2(tend, mul2(bc2(g * 0.125f), r8));
-        const float2 ref0 = bc2(d == 0 ? rbc[2] : 0.0f);
-        const float2 mold = mreg[2][d];
-        tend = sub2(tend, fma2(bc2(kdif), dmv[d], mul2(bc2(tk), sub2(mold, ref0))));
-        mnew[d] = fma2(bc2(dt2), tend, mold);
-        mflt[d] = fma2(bc2(nu), add2(sub2(mnew[d], mul2(bc2(2.0f), mcur[d])), mold), mcur[d]);
-      }
-      {
-        const float2 chk = add2(add2(add2(rN_, pN_), add2(mnew[0], mnew[1])), mnew[2]);
-        const float cx = a0 ? chk.x : 0.0f, cy = a1 ? chk.y : 0.0f;
-        if (!isfinite(cx) || !isfinite(cy)) wflag |= WATCH_NONFINITE;
-        const float2 cou = fma2(make_float2(fabsf(u0[0].x), fabsf(u0[0].y)), bc2(cfx),
-                                fma2(make_float2(fabsf(u0[1].x), fabsf(u0[1].y)), bc2(cfy),
-                                     mul2(make_float2(fabsf(u0[2].x), fabsf(u0[2].y)), bc2(cfz))));
-        if ((a0 && cou.x > 1.0f) || (a1 && cou.y > 1.0f)) wflag |= WATCH_COURANT;
-      }
-      // stores: both cells as one 8-byte store where both are computed
-      if (a0 && a1) {
-        st2(rpN + o, rN_);
-        st2(ppN + o, pN_);
-        st2(rpF + o, rF_);
-        st2(ppF + o, pF_);
-      } else if (a0) {
-        rpN[o] = rN_.x;
-        ppN[o] = pN_.x;
-        rpF[o] = rF_.x;
-        ppF[o] = pF_.x;
-      } else if (a1) {
-        rpN[o + 1] = rN_.y;
-        ppN[o + 1] = pN_.y;
-        rpF[o + 1] = rF_.y;
-        ppF[o + 1] = pF_.y;
-      }
-#pragma unroll
-      for (int d = 0; d < 3; d++) {
-        if (q0 && q1) {
-          st2(mN[d] + o, mnew[d]);
-          st2(mF[d] + o, mflt[d]);
-        } else if (q0) {
-          mN[d][o] = mnew[d].x;
-          mF[d][o] = mflt[d].x;
-        } else if (q1) {
-          mN[d][o + 1] = mnew[d].y;
-          mF[d][o + 1] = mflt[d].y;
+      for (int a = 0; a < 4; a++) {
+        if constexpr (DS) treg[a] = treg[a + 1];
+        if constexpr (DM) {
+          if (NR == 1 || a == 0) {
+            mreg[a][0] = mreg[a + 1][0];
+            mreg[a][1] = mreg[a + 1][1];
+            mreg[a][2] = mreg[a + 1][2];
+          } else if (a == 1) {
+            const int a4 = s4(k);
+            mreg[1][0] = ld2(S.om[a4][0] + c);
+            mreg[1][1] = ld2(S.om[a4][1] + c);
+            mreg[1][2] = ld2(S.om[a4][2] + c);
+          }
         }
       }
     }
-#pragma unroll
-    for (int a = 0; a < 4; a++) {
-      treg[a] = treg[a + 1];
-      mreg[a][0] = mreg[a + 1][0];
-      mreg[a][1] = mreg[a + 1][1];
-      mreg[a][2] = mreg[a + 1][2];
-    }
-  }
+    return wflag;
+  };
+  unsigned wflag;
+  if constexpr (NR == 1)
+    wflag = march(RoleTag<true>{}, RoleTag<true>{});
+  else if (role == 0)
+    wflag = march(RoleTag<true>{}, RoleTag<false>{});
+  else
+    wflag = march(RoleTag<false>{}, RoleTag<true>{});
   await_groups<0>();
   if (aborted()) {
     // a plane's copies did not arrive: wait (bounded) for every copy in

@@ -1612,17 +1612,24 @@ size_t pair_smem() {
   return TMA ? sizeof(PairSmem<C::PL, C::PLP>) + 128 : sizeof(PairSmem<C::PL, C::PL>);
 }
 
-// the items of refined boxes (TMA), then those of periodic domains (gather)
+// the items of refined boxes (TMA), then those of periodic domains (gather),
+// with NR warp roles per block
+template <int TYv, int NR>
+cudaError_t pair_r(const StepLaunch &L, int rO, int rC, int rN, int rF, int first, cudaStream_t st) {
+  if (L.nitems > 0)
+    k_pair<TYv, true, NR><<<L.nitems, PairCfg<TYv, NR>::NTH, pair_smem<TYv, true>(), st>>>(
+        L.d_doms, L.items, L.tmaps, rO, rC, rN, rF, first, L.eos, L.watch, L.stall_tx);
+  if (L.nwitems > 0)
+    k_pair<TYv, false, NR><<<L.nwitems, PairCfg<TYv, NR>::NTH, pair_smem<TYv, false>(), st>>>(
+        L.d_doms, L.witems, L.tmaps, rO, rC, rN, rF, first, L.eos, L.watch, 0u);
+  return cudaGetLastError();
+}
 template <int TYv>
 cudaError_t pair_t(const StepLaunch &L, int rO, int rC, int rN, int rF, int first, cudaStream_t st) {
   if (!L.tmaps) return cudaErrorInvalidValue;
-  if (L.nitems > 0)
-    k_pair<TYv, true><<<L.nitems, PairCfg<TYv>::NT, pair_smem<TYv, true>(), st>>>(
-        L.d_doms, L.items, L.tmaps, rO, rC, rN, rF, first, L.eos, L.watch, L.stall_tx);
-  if (L.nwitems > 0)
-    k_pair<TYv, false><<<L.nwitems, PairCfg<TYv>::NT, pair_smem<TYv, false>(), st>>>(
-        L.d_doms, L.witems, L.tmaps, rO, rC, rN, rF, first, L.eos, L.watch, 0u);
-  return cudaGetLastError();
+  if (L.roles == 2) return pair_r<TYv, 2>(L, rO, rC, rN, rF, first, st);
+  if (L.roles != 1) return cudaErrorInvalidValue;
+  return pair_r<TYv, 1>(L, rO, rC, rN, rF, first, st);
 }
 
 template <typename T>
@@ -1656,10 +1663,14 @@ cudaError_t full_prepare(int prec) {
     if ((e = set(k_full<double, 8>, full_smem<double, 8>())) != cudaSuccess) return e;
     return set(k_full<double, 4>, full_smem<double, 4>());
   }
-  if ((e = set(k_pair<16, true>, pair_smem<16, true>())) != cudaSuccess) return e;
-  if ((e = set(k_pair<16, false>, pair_smem<16, false>())) != cudaSuccess) return e;
-  if ((e = set(k_pair<8, true>, pair_smem<8, true>())) != cudaSuccess) return e;
-  return set(k_pair<8, false>, pair_smem<8, false>());
+  if ((e = set(k_pair<16, true, 1>, pair_smem<16, true>())) != cudaSuccess) return e;
+  if ((e = set(k_pair<16, false, 1>, pair_smem<16, false>())) != cudaSuccess) return e;
+  if ((e = set(k_pair<8, true, 1>, pair_smem<8, true>())) != cudaSuccess) return e;
+  if ((e = set(k_pair<8, false, 1>, pair_smem<8, false>())) != cudaSuccess) return e;
+  if ((e = set(k_pair<16, true, 2>, pair_smem<16, true>())) != cudaSuccess) return e;
+  if ((e = set(k_pair<16, false, 2>, pair_smem<16, false>())) != cudaSuccess) return e;
+  if ((e = set(k_pair<8, true, 2>, pair_smem<8, true>())) != cudaSuccess) return e;
+  return set(k_pair<8, false, 2>, pair_smem<8, false>());
 }
 
 cudaError_t launch_base(const DomDev &D, int prec, double theta0, double N, double p_surf, double sponge_frac,

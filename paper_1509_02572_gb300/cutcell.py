@@ -27,6 +27,7 @@ EXPORTS = ("cc_create", "cc_destroy", "cc_last_error", "cc_set_terrain", "cc_bui
            "cc_download_state", "cc_step", "cc_diagnostics", "cc_synchronize", "cc_last_launch_count",
            "cc_profile_enable", "cc_profile_read", "cc_profile_reset", "cc_create_refined",
            "cc_refine_mass", "cc_domain_count", "cc_create_refined_blocks", "cc_domain_block", "cc_autotune", "cc_get_schedule", "cc_set_schedule",
+           "cc_get_warp_roles", "cc_set_warp_roles",
            "cc_graphs_enable", "cc_inject_wait_timeout", "cc_upload_state_async", "cc_download_state_async",
            "cc_save", "cc_load",
            "cc_set_terrain_analytic", "cc_get_terrain", "cc_download_derived", "cc_error_norms", "cc_cbcm_cubes",
@@ -134,6 +135,8 @@ def load(path: str = LIB_PATH):
     L.cc_load.argtypes = [vp, ct.c_char_p]
     L.cc_get_schedule.argtypes = [vp, i, ct.POINTER(i), ct.POINTER(i)]
     L.cc_set_schedule.argtypes = [vp, i, i, i]
+    L.cc_get_warp_roles.argtypes = [vp, i, ct.POINTER(i)]
+    L.cc_set_warp_roles.argtypes = [vp, i, i]
     L.cc_mass_sum_noalloc.argtypes = [vp, i, vp, ct.c_longlong, i, vp, vp]
     L.cc_noalloc_last_error.restype = ct.c_char_p
     L.cc_fma_peak.argtypes = [i, i, vp, ct.POINTER(ct.c_double)]
@@ -408,6 +411,14 @@ class Model:
 
     def set_schedule(self, d: int, tile_y: int, items_per_launch: int):
         self._check(self.L.cc_set_schedule(self.h, d, int(tile_y), int(items_per_launch)))
+
+    def warp_roles(self, d: int = 0) -> int:
+        nr = ct.c_int()
+        self._check(self.L.cc_get_warp_roles(self.h, d, ct.byref(nr)))
+        return nr.value
+
+    def set_warp_roles(self, d: int, roles: int):
+        self._check(self.L.cc_set_warp_roles(self.h, d, int(roles)))
 
     def profile_read(self, kernel: int):
         ms, n = ct.c_double(), ct.c_longlong()

@@ -80,6 +80,26 @@ def test_blocks_equal_the_undivided_box_bit_for_bit(cc, prec_name):
         assert np.array_equal(a, b), (key, np.abs(a - b).max())
 
 
+def test_warp_roles_give_the_same_bits_on_every_level(cc):
+    """FP32: the stencil with the scalar and momentum updates on separate
+    warpgroups gives the same bits as one thread per pair updating both, on
+    the periodic level 0 (cyclic gather) and the refined levels (TMA-staged
+    boxes and blocks) alike, after the start and four cycles."""
+    runs = []
+    for nr in (1, 2):
+        m = _model(cc, cc.CC_FP32, True)
+        for lev in range(m.nlev):
+            m.set_warp_roles(m.level_domains(lev)[0], nr)
+        assert all(m.warp_roles(d) == nr for d in range(m.ndom))
+        m.init_state()
+        m.step(1)
+        m.step(4)
+        runs.append(_state(cc, m))
+        m.close()
+    for key, a in runs[0].items():
+        assert np.array_equal(a, runs[1][key]), (key, np.abs(a - runs[1][key]).max())
+
+
 def test_blocks_against_the_oracle(cc, oracle_mod):
     """FP64: every level, field and time level against the oracle of the
     undivided levels, after the start and after five cycles."""

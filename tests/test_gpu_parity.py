@@ -178,13 +178,16 @@ def test_mass_conservation_on_gpu(cc, prec, tol):
     m.close()
 
 
-def test_fp32_error_against_oracle(cc, oracle_mod):
-    """FP32 perturbation form: per-field relative L2 / Linf against the oracle."""
+@pytest.mark.parametrize("roles", [1, 2])
+def test_fp32_error_against_oracle(cc, oracle_mod, roles):
+    """FP32 perturbation form, with either warp-role form of the stencil:
+    per-field relative L2 / Linf against the oracle."""
     cfg = W.C1_BELL
     om = oracle_mod.Model(cfg)
     om.init_state()
     om.step(100)
     m = gpu_model(cc, cfg, cc.CC_FP32)
+    m.set_warp_roles(0, roles)
     m.init_state()
     m.step(100)
     errs = _compare(cc, oracle_mod, m, om, report=True)
@@ -268,38 +271,46 @@ def test_v_shaped_valley_is_a_geometry_error(cc, oracle_mod):
 
 
 def test_schedules_give_identical_bits_and_autotune_keeps_state(cc):
-    """Every full-cell schedule (tile height, items per launch) distributes
-    the same arithmetic: the states agree bit for bit; timing the schedules
-    leaves the state unchanged."""
+    """Every full-cell schedule (tile height, items per launch) and, in FP32,
+    both warp-role forms (one thread updating scalars and momenta, or the two
+    updates on separate warpgroups) distribute the same arithmetic: the states
+    agree bit for bit; timing the schedules leaves the state unchanged."""
     a = W.SMALL_HEMI
     b = W.C1_BELL.replace(nx=48, ny=40, nz=20, U=7.0, N=0.012, dt=0.12)
-    for prec, tys in ((cc.CC_FP32, (16, 8)), (cc.CC_FP64, (8, 4))):
+    for prec, tys, roles in ((cc.CC_FP32, (16, 8), (1, 2)), (cc.CC_FP64, (8, 4), (1,))):
         ref = None
         for ty in tys:
             for items in (304, 912):
-                m = gpu_model(cc, [a, b], prec)
-                m.init_state()
-                m.set_schedule(0, ty, items)
-                assert m.schedule(0) == (ty, items)
-                m.step(7)
-                out = [m.download(d, f) for d in range(2) for f in (cc.CC_RHOP, cc.CC_PP, cc.CC_MX, cc.CC_MZ)]
-                if ref is None:
-                    ref = out
-                else:
-                    for x, y in zip(out, ref):
-                        assert np.array_equal(x, y), (prec, ty, items)
-                m.close()
+                for nr in roles:
+                    m = gpu_model(cc, [a, b], prec)
+                    m.init_state()
+                    m.set_schedule(0, ty, items)
+                    m.set_warp_roles(0, nr)
+                    assert m.schedule(0) == (ty, items) and m.warp_roles(0) == nr
+                    m.step(7)
+                    out = [m.download(d, f) for d in range(2)
+                           for f in (cc.CC_RHOP, cc.CC_PP, cc.CC_MX, cc.CC_MY, cc.CC_MZ)]
+                    if ref is None:
+                        ref = out
+                    else:
+                        for x, y in zip(out, ref):
+                            assert np.array_equal(x, y), (prec, ty, items, nr)
+                    m.close()
         m = gpu_model(cc, [a, b], prec)
         m.init_state()
         m.step(3)
         m.autotune(2)
         assert m.schedule(0)[0] in tys
+        assert m.warp_roles(0) in roles
         m.step(4)
-        out = [m.download(d, f) for d in range(2) for f in (cc.CC_RHOP, cc.CC_PP, cc.CC_MX, cc.CC_MZ)]
+        out = [m.download(d, f) for d in range(2) for f in (cc.CC_RHOP, cc.CC_PP, cc.CC_MX, cc.CC_MY, cc.CC_MZ)]
         for x, y in zip(out, ref):
             assert np.array_equal(x, y), (prec, "autotuned")
         with pytest.raises(cc.CutcellError):
             m.set_schedule(0, 5, 304)
+        for bad in (0, 3) if prec == cc.CC_FP32 else (0, 2):
+            with pytest.raises(cc.CutcellError):
+                m.set_warp_roles(0, bad)
         m.close()
 
 
