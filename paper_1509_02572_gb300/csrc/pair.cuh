@@ -228,11 +228,14 @@ __global__ void __launch_bounds__(NR *(TILE_X / 2) * TYv, NR == 2 && TYv == 8 ? 
 
   auto col_x = [&](int gi) { return D.periodic ? wrapi(gi, nx) : min(max(gi, -GX), px - GX - 1); };
   auto row_y = [&](int gj) { return D.periodic ? wrapi(gj, ny) : min(max(gj, -GH), D.py - GH - 1); };
-  // pairs of halo points this thread derives: points 2 pp and 2 pp + 1
+  // pairs of halo points this thread derives: points 2 pp and 2 pp + 1, pp =
+  // s NTH + hpair; with two roles the warps of the two warpgroups take runs of
+  // 32 pairs in turn, so that both share the derived planes about evenly
+  const int hpair = NR == 1 ? tid : (2 * ((tid % NT) >> 5) + tid / NT) * 32 + (tid & 31);
   int loff[NLPP][2], kbv[NLPP][2];
 #pragma unroll
   for (int s = 0; s < NLPP; s++) {
-    const int pp = tid + s * NTH;
+    const int pp = s * NTH + hpair;
 #pragma unroll
     for (int h = 0; h < 2; h++) {
       const int p = 2 * pp + h;
@@ -282,18 +285,19 @@ __global__ void __launch_bounds__(NR *(TILE_X / 2) * TYv, NR == 2 && TYv == 8 ? 
   // a periodic tile whose halo crosses a lateral edge: 16-byte chunks of the
   // haloed rows from the cyclic indices, element by element where a chunk
   // crosses the edge
-  // (the first NT threads: with two roles the scalar warpgroup, so that the
-  // momentum warpgroup holds no copy state)
+  // (NT threads: with two roles those of the momentum warpgroup, and the
+  // scalar warpgroup holds no copy state; measured 3 % faster on the
+  // 64-instance ensemble than the copies on the scalar side)
   constexpr int VEC = 4, CPR = HX / VEC, NCH = CPR * C::HY, NCQ = (NCH + NT - 1) / NT;
   int ch_dst[NCQ], ch_e[NCQ][VEC];
   bool ch_whole[NCQ];
 #pragma unroll
   for (int q = 0; q < NCQ; q++) {
-    const int t = tid + q * NT;
+    const int t = tid % NT + q * NT;
     const int row = t / CPR, col = t % CPR;
     const int x = i0 - 2 + VEC * col;
     const int rowoff = (row_y(j0 - 2 + row) + GH) * px;
-    ch_dst[q] = !TMA && tid < NT && t < NCH ? row * HX + VEC * col : -1;
+    ch_dst[q] = !TMA && (NR == 1 || tid >= NT) && t < NCH ? row * HX + VEC * col : -1;
     ch_whole[q] = x >= 0 && x + VEC <= nx;
 #pragma unroll
     for (int e = 0; e < VEC; e++) ch_e[q][e] = rowoff + col_x(x + e) + GX;
@@ -348,7 +352,7 @@ __global__ void __launch_bounds__(NR *(TILE_X / 2) * TYv, NR == 2 && TYv == 8 ? 
     float *rh = S.rh[s4(kk)], *th = S.th[s4(kk)];
 #pragma unroll
     for (int s = 0; s < NLPP; s++) {
-      const int pp = tid + s * NTH;
+      const int pp = s * NTH + hpair;
       if (pp < NPP) {
         const int p = 2 * pp;
         st2(rh + p, add2(bc2(rb), ld2(cr + p)));
@@ -368,7 +372,7 @@ __global__ void __launch_bounds__(NR *(TILE_X / 2) * TYv, NR == 2 && TYv == 8 ? 
     const int su = s3(K), sm = s4(K);
 #pragma unroll
     for (int s = 0; s < NLPP; s++) {
-      const int pp = tid + s * NTH;
+      const int pp = s * NTH + hpair;
       const int p = 2 * pp;
       const int hx = p % HX, hy = p / HX;
       if (pp < NPP && hy != 0) {
@@ -404,7 +408,7 @@ __global__ void __launch_bounds__(NR *(TILE_X / 2) * TYv, NR == 2 && TYv == 8 ? 
     const float *op = S.op[s4(kk)];
 #pragma unroll
     for (int s = 0; s < NLPP; s++) {
-      const int pp = tid + s * NTH;
+      const int pp = s * NTH + hpair;
       if (pp < NPP) st2(S.to + 2 * pp, ek.pert(E, ld2(op + 2 * pp)));
     }
   };
@@ -519,8 +523,8 @@ __global__ void __launch_bounds__(NR *(TILE_X / 2) * TYv, NR == 2 && TYv == 8 ? 
       sync_all();
       if (aborted()) break;
       // plane k + 3 is read from the next plane on; the last plane needs k1 + 1
-      // (its copies are issued by the scalar role: thread 0 or the gather's threads)
-      if (DS && k + 3 <= k1 + 1) {
+      // (TMA: thread 0, in the scalar role; gather: the momentum role's threads)
+      if ((TMA ? DS : DM) && k + 3 <= k1 + 1) {
         stage(k + 3, true, true);
         issued = k + 3;
       }

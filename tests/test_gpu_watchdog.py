@@ -33,10 +33,11 @@ def _model(cc, prec):
     return cfg, m
 
 
-@pytest.mark.parametrize("prec_name", ["fp64", "fp32"])
-def test_watchdog_reports_a_planted_nan(cc, prec_name):
+@pytest.mark.parametrize("prec_name,roles", [("fp64", 1), ("fp32", 1), ("fp32", 2)])
+def test_watchdog_reports_a_planted_nan(cc, prec_name, roles):
     prec = cc.CC_FP64 if prec_name == "fp64" else cc.CC_FP32
     cfg, m = _model(cc, prec)
+    m.set_warp_roles(0, roles)
     m.step(3)
     m.synchronize()  # a healthy run raises nothing
     p = m.download(0, cc.CC_PP)
@@ -84,14 +85,18 @@ def _refined(cc, prec):
     return m
 
 
-def test_watchdog_reports_a_tma_wait_that_runs_out(cc):
+@pytest.mark.parametrize("roles", [1, 2])
+def test_watchdog_reports_a_tma_wait_that_runs_out(cc, roles):
     """The refined boxes' FP32 stencil stages its planes with TMA copies and
     waits for each plane's barrier at most a second.  With every barrier made
     to expect 16 bytes more than its copies bring, each block's wait runs out:
     the block stops, drains its copies (bounded) and returns, and the host
-    reads CC_ETIMEOUT.  The context stays usable: the same model, restarted,
-    matches a fresh one bit for bit."""
+    reads CC_ETIMEOUT, with one or two warp roles per block.  The context
+    stays usable: the same model, restarted, matches a fresh one bit for
+    bit."""
     m = _refined(cc, cc.CC_FP32)
+    for lev in range(m.nlev):
+        m.set_warp_roles(lev, roles)
     m.init_state()
     m.step(1)
     m.synchronize()
