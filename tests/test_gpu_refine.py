@@ -283,9 +283,9 @@ def test_refined_paper_domain_one_hour(cc, uniform200, nbox):
     coarse steps).  Every level stays finite.  The largest |w| below 3.2 km in
     the 6 km behind each fine level's inflow face is compared with the uniform
     200 m run at the same points.  At 1,200 s the 200 m levels match it (two
-    levels 0.12 against 0.12 m/s; three levels 0.02).  The open defect
-    (DESIGN, long refined runs) then shows: at 2,400 s the two-level run
-    reaches 4.2 m/s there against 0.014 for the uniform grid, about 300 times
+    levels 0.12 against 0.12 m/s; three levels 0.02).  The open defect (a
+    disturbance behind the fine inflow faces, still unexplained) then shows:
+    at 2,400 s the two-level run reaches 4.2 m/s there against 0.014 for the uniform grid, about 300 times
     more, and 12.5 m/s at 3,600 s; in the three-level run the 200 m level
     reaches 0.52 m/s (about 37 times the uniform run) and the 100 m box,
     already at 1.3 against 0.48 m/s at 1,200 s, 7.3 m/s at 3,600 s.  The test
